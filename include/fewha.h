@@ -1,0 +1,219 @@
+/*
+ * fewha.h -- C ABI of the GB300 (sm_103a) FEWHA reconstructor.
+ *
+ * FEWHA (Finite Element Wavelet Hybrid Algorithm, Stadler & Ramlau, "Performance of
+ * an iterative wavelet reconstructor for MAORY") solves, once per frame, the MAP
+ * tomography system of Eq. (5),
+ *
+ *     M c = b,   M = W (sum_g P_g^T Gamma_g^T C_hat_g^-1 Gamma_g P_g) W^T + alpha D,
+ *                b = W sum_g P_g^T Gamma_g^T C_hat_g^-1 s_g,
+ *
+ * with a fixed number of Jacobi-preconditioned CG iterations (Eq. 7, Sec. 3.3),
+ * warm-started from the previous frame, then fits the DMs, a~ = F W^T c, and applies
+ * the open-loop gain (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - All functions return FEWHA_OK (0) or a negative FEWHA_ERR_* code; the text of
+ *     the last error of a handle is fewha_last_error(handle).
+ *   - "d_" pointers are CUDA device pointers owned by the caller; "h_" pointers are
+ *     host pointers owned by the caller.  The library owns its handle and all of the
+ *     handle's internal device state.  No entry point keeps a caller pointer after
+ *     it returns, except that a captured frame graph is re-captured when the caller
+ *     passes different device pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Device work is enqueued on it in order; entry points taking only device
+ *     pointers return before the work finishes (no host synchronisation), entry
+ *     points taking host pointers synchronise on `stream` before returning.
+ *   - Element type: a handle created with params.precision == 32 computes every
+ *     operator in float (inner products and the CG scalars alpha, beta in double);
+ *     precision == 64 computes everything in double.  Entry points with typed
+ *     pointers exist in float and _f64 twins; the void* operator entry points take
+ *     the handle's element type.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *
+ * Layouts
+ *   - coefficient vector c, b (n_coeffs): layers concatenated in creation order;
+ *     layer l is an n_l x n_l row-major array in Mallat layout (after `levels`
+ *     analysis steps on rows then columns: [LL LH; HL HH], recursion on LL).
+ *   - layer (finite-element) vector phi: same sizes, row-major node values; node
+ *     (i, j) of layer l sits at x = (j - n_l/2) delta_l, y = (i - n_l/2) delta_l.
+ *   - node vector (n_nodes): sensors concatenated; sensor g holds (N_g+1)^2 aperture
+ *     nodes, N_g = n_sub * nb, node (a, b) at x = -D/2 + b d_g, y = -D/2 + a d_g.
+ *   - slope vector s (n_slopes): sensors concatenated; sensor g holds the x-slopes of
+ *     its active subapertures in row-major order, then the y-slopes in the same
+ *     order.  A subaperture is active iff its centre radius r satisfies
+ *     obs*D/2 <= r <= D/2.  A slope is the phase difference across the subaperture
+ *     (radians).  For a coarse sensor (nb > 1) the active units are coarse
+ *     subapertures.
+ *   - DM vector (n_act): DMs concatenated, each n_act_m x n_act_m row-major,
+ *     actuator (p, q) at x = (q - (n_act_m-1)/2) spacing_m, y likewise with p.
+ */
+#ifndef FEWHA_H
+#define FEWHA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FEWHA_OK 0
+#define FEWHA_ERR_INVALID_ARG (-1) /* null pointer, bad count, precision mismatch   */
+#define FEWHA_ERR_GEOMETRY (-2)    /* footprint outside a layer grid, n not 2^k ... */
+#define FEWHA_ERR_OOM (-3)         /* device allocation failed                      */
+#define FEWHA_ERR_CUDA (-4)        /* a CUDA runtime call failed                    */
+#define FEWHA_ERR_NONFINITE (-5)   /* a NaN/Inf was found in the input slopes       */
+#define FEWHA_ERR_LIMIT (-6)       /* a size exceeds a compiled-in maximum          */
+
+#define FEWHA_MAX_LAYERS 16
+#define FEWHA_MAX_WFS 16
+#define FEWHA_MAX_DMS 4
+#define FEWHA_MAX_GRID 128   /* largest layer grid side n                           */
+#define FEWHA_MAX_NFINE 80   /* largest fine subaperture count per side, n_sub*nb   */
+#define FEWHA_MAX_COARSE 4   /* largest coarse subaperture count per side (nb > 1)  */
+#define FEWHA_MAX_ITERS 64
+
+#define FEWHA_FLAG_GRAPH 1u         /* replay each frame as a captured CUDA graph    */
+#define FEWHA_FLAG_WARM_RESIDUAL 2u /* r0 = (b - b_prev) + r_prev (Algorithm 1)     */
+
+/* Telescope aperture: diameter D [m], central obstruction as a diameter ratio. */
+typedef struct fewha_telescope {
+    double D;
+    double obs;
+} fewha_telescope;
+
+/* One Shack-Hartmann sensor (Sec. 2; Table 4).  n_sub subapertures per side; nb > 1
+ * makes a coarse sensor whose slope is (1/nb) x the sum of the fine slopes of the
+ * active fine subapertures in its nb x nb block.  An LGS (is_lgs = 1) sits at height
+ * H [m] (cone effect, s_l = 1 - h_l/H) and has its tip/tilt removed by the projector
+ * of Sec. 3.2; an NGS sits at infinity.  theta: direction [rad]; sigma: noise standard
+ * deviation per slope [rad], C_g = sigma^2 I (Eq. 2). */
+typedef struct fewha_wfs {
+    int n_sub;
+    int nb;
+    int is_lgs;
+    double theta_x, theta_y;
+    double H;
+    double sigma;
+} fewha_wfs;
+
+/* One reconstruction layer (Sec. 3.1; Table 2): altitude h [m], Cn2 weight, grid
+ * spacing [m], periodic grid side n = 2^J, number of wavelet levels (1..J). */
+typedef struct fewha_layer {
+    double h;
+    double cn2_weight;
+    double spacing;
+    int n;
+    int levels;
+} fewha_layer;
+
+/* One deformable mirror (Sec. 4.1; Table 3): altitude [m], actuator spacing [m],
+ * actuators per side. */
+typedef struct fewha_dm {
+    double h;
+    double spacing;
+    int n_act;
+} fewha_dm;
+
+/* Method parameters (Table 5): regularisation alpha, preconditioner threshold tau
+ * (Eq. 7), loop gain (Algorithm 1), von Karman r0 [m at 500 nm] and L0 [m] of the
+ * prior D, PCG iterations, precision (32 or 64) and FEWHA_FLAG_* bits. */
+typedef struct fewha_params {
+    double alpha;
+    double tau;
+    double gain;
+    double r0;
+    double L0;
+    int iters;
+    int precision;
+    unsigned flags;
+} fewha_params;
+
+typedef struct fewha_handle fewha_handle;
+
+/* Build an instance: validates the geometry (FEWHA_ERR_GEOMETRY if a projected
+ * aperture or DM footprint leaves a layer grid, n is not a power of two, or levels
+ * is out of range; FEWHA_ERR_LIMIT above the FEWHA_MAX_* sizes), computes the
+ * interpolation tables, the prior D (Sec. 3.1) and the exact Jacobi diagonal of
+ * Eq. (7) on the GPU, allocates the state (warm start c = 0, a_prev = 0) on the
+ * current CUDA device.  Synchronous.  *out receives the handle; on failure *out is
+ * NULL and the return code says why. */
+int fewha_create(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs,
+                 const fewha_layer* layers, int n_layers, const fewha_dm* dms, int n_dms,
+                 const fewha_params* params, fewha_handle** out);
+void fewha_destroy(fewha_handle* h);
+const char* fewha_last_error(const fewha_handle* h);
+/* Text of the last error of a failed fewha_create (thread-local). */
+const char* fewha_create_error(void);
+
+/* Vector sizes of an instance (any pointer may be NULL). */
+int fewha_sizes(const fewha_handle* h, int64_t* n_slopes, int64_t* n_coeffs, int64_t* n_act,
+                int64_t* n_nodes);
+
+/* On-the-fly system update (Sec. 1, Sec. 4.3): new alpha, tau, gain, r0, L0, iters
+ * and optionally new layer Cn2 weights (n_layers values) and sensor noise sigmas
+ * (n_wfs values); recomputes D and the Jacobi diagonal, discards the warm residual.
+ * precision and the geometry cannot change.  Synchronous. */
+int fewha_update_params(fewha_handle* h, const fewha_params* params, const double* cn2_weights,
+                        const double* sigmas);
+
+/* Zero the warm-start state (c, a_prev, residual history). Stream-ordered. */
+int fewha_reset(fewha_handle* h, void* stream);
+
+/* One frame of Algorithm 1 (open loop): b from d_slopes, r0 = b - M c0 (or the warm
+ * residual form with FEWHA_FLAG_WARM_RESIDUAL), `iters` PCG iterations, DM fit and
+ * gain.  d_x_warm (n_coeffs) is the warm start, read and overwritten with the new c;
+ * NULL uses the handle's internal state.  d_dm_out (n_act) receives the commands
+ * a = (1 - gain) a_prev + gain a~.  Asynchronous on `stream`. */
+int fewha_reconstruct(fewha_handle* h, const float* d_slopes, float* d_x_warm, float* d_dm_out,
+                      void* stream);
+int fewha_reconstruct_f64(fewha_handle* h, const double* d_slopes, double* d_x_warm,
+                          double* d_dm_out, void* stream);
+
+/* The same frame from and to HOST memory (pinned or pageable): copies the slopes in,
+ * runs the frame on the internal warm state, copies the commands out and synchronises
+ * on `stream`.  Returns FEWHA_ERR_NONFINITE (commands still written) if the slopes
+ * held a NaN or Inf. */
+int fewha_reconstruct_host(fewha_handle* h, const float* h_slopes, float* h_dm_out, void* stream);
+int fewha_reconstruct_host_f64(fewha_handle* h, const double* h_slopes, double* h_dm_out,
+                               void* stream);
+
+/* Non-finite flag of the slopes read by frames since the last call (1 if any NaN or
+ * Inf was seen), then cleared.  Synchronises on `stream`. */
+int fewha_check_input(fewha_handle* h, int* nonfinite, void* stream);
+
+/* ---- operator entry points (the handle's element type; asynchronous) ----------- */
+
+/* q = M c (Eq. 6). */
+int fewha_apply_M(fewha_handle* h, const void* d_c, void* d_q, void* stream);
+/* b = W sum_g P_g^T Gamma_g^T C_hat_g^-1 s_g (Sec. 3.1, Algorithm 1). */
+int fewha_rhs(fewha_handle* h, const void* d_slopes, void* d_b, void* stream);
+/* c = W phi and phi = W^T c, every layer with its own level count (Sec. 3.1). */
+int fewha_dwt(fewha_handle* h, const void* d_phi, void* d_c, void* stream);
+int fewha_idwt(fewha_handle* h, const void* d_c, void* d_phi, void* stream);
+/* nodes = P phi (all sensors, Sec. 2) and its transpose phi = sum_g P_g^T nodes_g. */
+int fewha_project(fewha_handle* h, const void* d_phi, void* d_nodes, void* stream);
+int fewha_project_adj(fewha_handle* h, const void* d_nodes, void* d_phi, void* stream);
+/* s = Gamma nodes (Sec. 2) and nodes = Gamma^T s. */
+int fewha_slopes(fewha_handle* h, const void* d_nodes, void* d_s, void* stream);
+int fewha_slopes_adj(fewha_handle* h, const void* d_s, void* d_nodes, void* stream);
+/* out = C_hat^-1 s: (I - T) sigma^-2 (I - T) s for an LGS, sigma^-2 s for an NGS
+ * (Eq. 2, Sec. 3.2). */
+int fewha_noise_weight(fewha_handle* h, const void* d_s, void* d_out, void* stream);
+/* s = A phi = Gamma P phi (Eq. 1) and phi = A^T s. */
+int fewha_forward(fewha_handle* h, const void* d_phi, void* d_s, void* stream);
+int fewha_forward_adj(fewha_handle* h, const void* d_s, void* d_phi, void* stream);
+/* a~ = F W^T c (Algorithm 1, fitting step) and c = (F W^T)^T a. */
+int fewha_fit(fewha_handle* h, const void* d_c, void* d_dm, void* stream);
+int fewha_fit_adj(fewha_handle* h, const void* d_dm, void* d_c, void* stream);
+/* `iters` Jacobi-PCG iterations on M c = b from c (in/out) with r0 = b - M c. */
+int fewha_pcg(fewha_handle* h, const void* d_b, void* d_c, int iters, void* stream);
+/* Copies of the handle's diagonals (n_coeffs each, handle element type, NULL skips):
+ * D of Sec. 3.1 and J of Eq. (7). */
+int fewha_get_diagonals(fewha_handle* h, void* d_D, void* d_J, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEWHA_H */

@@ -1,0 +1,7 @@
+"""GB300-native FEWHA: the per-frame hot path of the Finite Element Wavelet Hybrid
+Algorithm for MCAO tomography as sm_103a CUDA kernels behind a C ABI
+(include/fewha.h), with a thin Python binding."""
+
+from .fewha import (  # noqa: F401
+    FLAG_GRAPH, FLAG_WARM_RESIDUAL, FewhaError, Reconstructor, lib, structs_from_workload,
+)

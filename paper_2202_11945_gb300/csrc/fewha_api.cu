@@ -1,0 +1,744 @@
+// C ABI of the FEWHA reconstructor (declared in include/fewha.h): instance set-up,
+// the per-frame sequence of Algorithm 1 (optionally replayed as a CUDA graph) and
+// the operator entry points used by the tests and the autograd layer.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fewha_kernels.cuh"
+
+using namespace fewha;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int NPART_MAX = 512;
+constexpr int PQ_SCRATCH_SLOT = FEWHA_MAX_ITERS;   // p.q slot of the explicit r0 apply
+
+}  // namespace
+
+struct fewha_handle {
+    int device = 0;
+    int precision = 32;
+    size_t esz = 4;
+    fewha_params params{};
+    HostSetup setup;
+    std::vector<double> weights;   // current layer Cn2 weights
+    std::vector<void*> allocs;
+    // device tables (precision independent)
+    int *pi0y = nullptr, *pi0x = nullptr, *ry_lo = nullptr, *ry_hi = nullptr, *rx_lo = nullptr,
+        *rx_hi = nullptr, *sidx = nullptr, *cidx = nullptr, *di0 = nullptr, *dr_lo = nullptr,
+        *dr_hi = nullptr, *basis_off = nullptr;
+    double *pfy64 = nullptr, *pfx64 = nullptr, *basis = nullptr, *D64 = nullptr, *Jdata = nullptr,
+           *J64 = nullptr, *rzpart = nullptr, *pqpart = nullptr;
+    unsigned* status = nullptr;
+    int npart = 1;
+    // typed device arrays (float or double per precision)
+    void *pfy = nullptr, *pfx = nullptr, *dfw = nullptr, *D = nullptr, *Jinv = nullptr;
+    void *c = nullptr, *b = nullptr, *b_prev = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
+         *q = nullptr, *phi = nullptr, *u = nullptr, *a_prev = nullptr, *dm_tmp = nullptr,
+         *s_tmp = nullptr, *c_tmp = nullptr;
+    bool have_prev = false;
+    // frame-graph cache
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_s = nullptr;
+    void* g_x = nullptr;
+    void* g_dm = nullptr;
+    bool g_warm = false;
+    std::string err;
+    size_t smem_layer = 0, smem_sensor = 0;
+};
+
+namespace {
+
+int fail(fewha_handle* H, int code, const std::string& msg) {
+    if (H) H->err = msg;
+    return code;
+}
+
+int cuda_fail(fewha_handle* H, cudaError_t e, const char* where) {
+    return fail(H, FEWHA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(H, e_, where); \
+    } while (0)
+
+template <class X>
+int dalloc(fewha_handle* H, X** ptr, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = count * sizeof(X) > 0 ? count * sizeof(X) : 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(H, FEWHA_ERR_OOM, "device allocation failed");
+    }
+    cudaMemset(p, 0, bytes);
+    H->allocs.push_back(p);
+    *ptr = static_cast<X*>(p);
+    return FEWHA_OK;
+}
+
+int talloc(fewha_handle* H, void** ptr, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = count * H->esz > 0 ? count * H->esz : 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(H, FEWHA_ERR_OOM, "device allocation failed");
+    }
+    cudaMemset(p, 0, bytes);
+    H->allocs.push_back(p);
+    *ptr = p;
+    return FEWHA_OK;
+}
+
+template <class X>
+int upload(fewha_handle* H, X* dst, const std::vector<X>& src) {
+    if (src.empty()) return FEWHA_OK;
+    CK(cudaMemcpy(dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice), "upload");
+    return FEWHA_OK;
+}
+
+template <class T>
+Desc<T> make_desc(const fewha_handle* H) {
+    const HostSetup& s = H->setup;
+    Desc<T> d;
+    std::memset(&d, 0, sizeof(d));
+    d.n_layers = static_cast<int>(s.L.size());
+    d.n_wfs = static_cast<int>(s.G.size());
+    d.n_dms = static_cast<int>(s.Mi.size());
+    d.n_c = s.n_c;
+    d.n_s = s.n_s;
+    d.n_nodes = s.n_nodes;
+    d.n_act = s.n_act;
+    d.max_n = s.max_n;
+    d.max_N = s.max_N;
+    for (int l = 0; l < d.n_layers; ++l) d.L[l] = s.L[l];
+    for (int g = 0; g < d.n_wfs; ++g) d.G[g] = s.G[g];
+    for (int m = 0; m < d.n_dms; ++m) {
+        d.Mi[m] = s.Mi[m];
+        for (int l = 0; l < d.n_layers; ++l) d.fitw[m][l] = T(s.fitw[m][l]);
+    }
+    d.alpha = T(H->params.alpha);
+    d.gain = T(H->params.gain);
+    d.pi0y = H->pi0y;
+    d.pi0x = H->pi0x;
+    d.pfy = static_cast<const T*>(H->pfy);
+    d.pfx = static_cast<const T*>(H->pfx);
+    d.ry_lo = H->ry_lo;
+    d.ry_hi = H->ry_hi;
+    d.rx_lo = H->rx_lo;
+    d.rx_hi = H->rx_hi;
+    d.sidx = H->sidx;
+    d.cidx = H->cidx;
+    d.di0 = H->di0;
+    d.dfw = static_cast<const T*>(H->dfw);
+    d.dr_lo = H->dr_lo;
+    d.dr_hi = H->dr_hi;
+    d.D = static_cast<const T*>(H->D);
+    d.Jinv = static_cast<const T*>(H->Jinv);
+    return d;
+}
+
+// ---------------------------------------------------------------- launchers
+template <class T, int SRC, int DST, bool PUPD>
+int launch_layer(fewha_handle* H, const Desc<T>& d, const LayerArgs<T>& a, cudaStream_t st) {
+    k_layer<T, SRC, DST, PUPD><<<d.n_layers, BLK, H->smem_layer, st>>>(d, a);
+    CK(cudaGetLastError(), "k_layer launch");
+    return FEWHA_OK;
+}
+
+template <class T, int SRC, bool WEIGHT, int DST>
+int launch_sensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaStream_t st) {
+    SensorArgs<T> a{in, out, H->status};
+    k_sensor<T, SRC, WEIGHT, DST><<<d.n_wfs, BLK, H->smem_sensor, st>>>(d, a);
+    CK(cudaGetLastError(), "k_sensor launch");
+    return FEWHA_OK;
+}
+
+template <class T>
+VecArgs<T> vec_args(fewha_handle* H, T* c, int iter) {
+    VecArgs<T> v;
+    v.c = c;
+    v.r = static_cast<T*>(H->r);
+    v.z = static_cast<T*>(H->z);
+    v.p = static_cast<T*>(H->p);
+    v.q = static_cast<const T*>(H->q);
+    v.b = static_cast<const T*>(H->b);
+    v.b_prev = static_cast<T*>(H->b_prev);
+    v.Jinv = static_cast<const T*>(H->Jinv);
+    v.pcg = PcgSlots{H->rzpart, H->pqpart, H->npart};
+    v.iter = iter;
+    return v;
+}
+
+template <class T>
+LayerArgs<T> layer_args(fewha_handle* H, const T* in, T* out) {
+    LayerArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.pcg = PcgSlots{H->rzpart, H->pqpart, H->npart};
+    return a;
+}
+
+// q = M x (Eq. 6) into H->q; the p.q partials go to slot `slot`.
+template <class T>
+int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int slot, bool pupdate,
+                  cudaStream_t st) {
+    T* phi = static_cast<T*>(H->phi);
+    T* u = static_cast<T*>(H->u);
+    int rc;
+    LayerArgs<T> a = layer_args<T>(H, x, phi);
+    if (pupdate) {
+        a.pupd = static_cast<T*>(H->p);
+        a.zupd = static_cast<const T*>(H->z);
+        a.iter = slot;
+        rc = launch_layer<T, LSRC_COEF, LDST_PHI, true>(H, d, a, st);
+    } else {
+        rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, a, st);
+    }
+    if (rc) return rc;
+    if ((rc = launch_sensor<T, SSRC_PHI, true, SDST_ADJ>(H, d, phi, u, st))) return rc;
+    LayerArgs<T> b = layer_args<T>(H, u, qout);
+    b.pin = x;
+    b.iter = slot;
+    b.zero_piston = 1;
+    return launch_layer<T, LSRC_NODES, LDST_APPLY, false>(H, d, b, st);
+}
+
+template <class T>
+int enqueue_rhs(fewha_handle* H, const Desc<T>& d, const T* s, T* bout, cudaStream_t st) {
+    T* u = static_cast<T*>(H->u);
+    int rc;
+    if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_ADJ>(H, d, s, u, st))) return rc;
+    LayerArgs<T> a = layer_args<T>(H, u, bout);
+    a.zero_piston = 1;
+    return launch_layer<T, LSRC_NODES, LDST_COEF, false>(H, d, a, st);
+}
+
+int vec_grid(const fewha_handle* H) { return H->npart; }
+
+// `iters` PCG iterations on M c = b (b in H->b), r0 explicit or warm.
+template <class T>
+int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, cudaStream_t st) {
+    int rc;
+    if (warm) {
+        k_vec<T, V_INIT_WARM><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, c, 0));
+        CK(cudaGetLastError(), "k_vec init");
+    } else {
+        if ((rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
+        k_vec<T, V_INIT><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, c, 0));
+        CK(cudaGetLastError(), "k_vec init");
+    }
+    T* p = static_cast<T*>(H->p);
+    for (int k = 0; k < iters; ++k) {
+        if ((rc = enqueue_apply<T>(H, d, p, static_cast<T*>(H->q), k, k > 0, st))) return rc;
+        k_vec<T, V_UPDATE><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, c, k));
+        CK(cudaGetLastError(), "k_vec update");
+    }
+    return FEWHA_OK;
+}
+
+template <class T>
+int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain, cudaStream_t st) {
+    T* phi = static_cast<T*>(H->phi);
+    int rc;
+    if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, c, phi), st))) return rc;
+    k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, static_cast<T*>(H->a_prev), dm,
+                                                           gain ? 1 : 0);
+    CK(cudaGetLastError(), "k_fit launch");
+    return FEWHA_OK;
+}
+
+// One frame of Algorithm 1 (open loop).
+template <class T>
+int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStream_t st) {
+    const Desc<T> d = make_desc<T>(H);
+    int rc;
+    if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
+    if ((rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st))) return rc;
+    return enqueue_fit<T>(H, d, c, dm, true, st);
+}
+
+template <class T>
+int run_frame(fewha_handle* H, const T* s, T* c, T* dm, cudaStream_t st) {
+    const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) && H->have_prev;
+    int rc;
+    if (H->params.flags & FEWHA_FLAG_GRAPH) {
+        if (!H->gexec || H->g_s != s || H->g_x != c || H->g_dm != dm || H->g_warm != warm) {
+            if (H->gexec) {
+                cudaGraphExecDestroy(H->gexec);
+                H->gexec = nullptr;
+            }
+            CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            rc = enqueue_frame<T>(H, s, c, dm, warm, H->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(H->cap_stream, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(H, e, "end capture");
+            e = cudaGraphInstantiate(&H->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                H->gexec = nullptr;
+                return cuda_fail(H, e, "graph instantiate");
+            }
+            H->g_s = s;
+            H->g_x = c;
+            H->g_dm = dm;
+            H->g_warm = warm;
+        }
+        CK(cudaGraphLaunch(H->gexec, st), "graph launch");
+    } else {
+        if ((rc = enqueue_frame<T>(H, s, c, dm, warm, st))) return rc;
+    }
+    H->have_prev = true;
+    return FEWHA_OK;
+}
+
+void drop_graph(fewha_handle* H) {
+    if (H->gexec) cudaGraphExecDestroy(H->gexec);
+    H->gexec = nullptr;
+    H->g_s = nullptr;
+    H->g_x = nullptr;
+    H->g_dm = nullptr;
+}
+
+// D, the exact data diagonal (GPU) and J^-1 for the current parameters.
+template <class T>
+int compute_diagonals(fewha_handle* H) {
+    std::vector<double> D;
+    prior_diag(H->setup, H->weights, H->params.r0, H->params.L0, D);
+    if (upload(H, H->D64, D)) return FEWHA_ERR_CUDA;
+    const Desc<T> d = make_desc<T>(H);
+    DiagArgs a{H->basis, H->basis_off, H->pfy64, H->pfx64, H->Jdata};
+    k_jdiag<T><<<(d.n_c + 3) / 4, 128>>>(d, a);
+    CK(cudaGetLastError(), "k_jdiag launch");
+    k_jfinish<T><<<(d.n_c + 255) / 256, 256>>>(d.n_c, H->Jdata, H->D64, H->params.alpha,
+                                                H->params.tau, static_cast<T*>(H->Jinv),
+                                                static_cast<T*>(H->D), H->J64);
+    CK(cudaGetLastError(), "k_jfinish launch");
+    CK(cudaDeviceSynchronize(), "diagonal set-up");
+    return FEWHA_OK;
+}
+
+template <class T>
+int setup_tables(fewha_handle* H) {
+    const HostSetup& s = H->setup;
+    int rc = 0;
+    auto conv = [&](void* dst, const std::vector<double>& src) -> int {
+        if (src.empty()) return FEWHA_OK;
+        std::vector<T> tmp(src.begin(), src.end());
+        CK(cudaMemcpy(dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice), "table upload");
+        return FEWHA_OK;
+    };
+    if ((rc = conv(H->pfy, s.pfy)) || (rc = conv(H->pfx, s.pfx)) || (rc = conv(H->dfw, s.dfw))) return rc;
+    // wavelet taps
+    float h32[6], g32[6];
+    for (int t = 0; t < 6; ++t) {
+        h32[t] = static_cast<float>(s.taps_h[t]);
+        g32[t] = static_cast<float>(s.taps_g[t]);
+    }
+    CK(cudaMemcpyToSymbol(c_h32, h32, sizeof(h32)), "taps");
+    CK(cudaMemcpyToSymbol(c_g32, g32, sizeof(g32)), "taps");
+    CK(cudaMemcpyToSymbol(c_h64, s.taps_h, sizeof(s.taps_h)), "taps");
+    CK(cudaMemcpyToSymbol(c_g64, s.taps_g, sizeof(s.taps_g)), "taps");
+    return compute_diagonals<T>(H);
+}
+
+template <class T>
+int set_smem_limits(fewha_handle* H) {
+    const int maxsm = 227 * 1024;
+    if (H->smem_layer > static_cast<size_t>(maxsm) || H->smem_sensor > static_cast<size_t>(maxsm))
+        return fail(H, FEWHA_ERR_LIMIT, "shared-memory tile above 227 KB");
+#define SETL(S, D, P) \
+    CK(cudaFuncSetAttribute(k_layer<T, S, D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm), "smem attr")
+    SETL(LSRC_COEF, LDST_PHI, false);
+    SETL(LSRC_COEF, LDST_PHI, true);
+    SETL(LSRC_NODES, LDST_APPLY, false);
+    SETL(LSRC_NODES, LDST_COEF, false);
+    SETL(LSRC_NODES, LDST_PHI, false);
+    SETL(LSRC_PHI, LDST_COEF, false);
+    SETL(LSRC_DM, LDST_COEF, false);
+#undef SETL
+#define SETS(S, W, D) \
+    CK(cudaFuncSetAttribute(k_sensor<T, S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm), "smem attr")
+    SETS(SSRC_PHI, true, SDST_ADJ);
+    SETS(SSRC_SLOPES, true, SDST_ADJ);
+    SETS(SSRC_PHI, false, SDST_NODES);
+    SETS(SSRC_NODES, false, SDST_SLOPES);
+    SETS(SSRC_SLOPES, false, SDST_ADJ);
+    SETS(SSRC_SLOPES, true, SDST_SLOPES);
+    SETS(SSRC_PHI, false, SDST_SLOPES);
+#undef SETS
+    return FEWHA_OK;
+}
+
+void free_handle(fewha_handle* H) {
+    if (!H) return;
+    drop_graph(H);
+    if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    for (void* p : H->allocs) cudaFree(p);
+    delete H;
+}
+
+int check_params(const fewha_params* p, std::string& err) {
+    if (!p) {
+        err = "params is NULL";
+        return FEWHA_ERR_INVALID_ARG;
+    }
+    if (p->precision != 32 && p->precision != 64) {
+        err = "precision must be 32 or 64";
+        return FEWHA_ERR_INVALID_ARG;
+    }
+    if (p->iters < 0 || p->iters > FEWHA_MAX_ITERS) {
+        err = "iters out of range";
+        return FEWHA_ERR_LIMIT;
+    }
+    if (!(p->alpha >= 0) || !(p->tau >= 0) || !(p->r0 > 0) || !(p->L0 > 0) || !(p->gain >= 0) ||
+        !(p->gain <= 1)) {
+        err = "alpha, tau >= 0, r0, L0 > 0 and gain in [0, 1] required";
+        return FEWHA_ERR_INVALID_ARG;
+    }
+    return FEWHA_OK;
+}
+
+template <class T>
+int typed_create(fewha_handle* H) {
+    const HostSetup& s = H->setup;
+    int rc = 0;
+    const size_t tab = static_cast<size_t>(MAXG) * MAXL * TAB;
+    const size_t rng = static_cast<size_t>(MAXG) * MAXL * MAXN;
+    const size_t dtab = static_cast<size_t>(MAXM) * MAXL * MAXNACT;
+    const size_t drng = static_cast<size_t>(MAXM) * MAXL * MAXN;
+    if ((rc = dalloc(H, &H->pi0y, tab)) || (rc = dalloc(H, &H->pi0x, tab)) ||
+        (rc = dalloc(H, &H->pfy64, tab)) || (rc = dalloc(H, &H->pfx64, tab)) ||
+        (rc = dalloc(H, &H->ry_lo, rng)) || (rc = dalloc(H, &H->ry_hi, rng)) ||
+        (rc = dalloc(H, &H->rx_lo, rng)) || (rc = dalloc(H, &H->rx_hi, rng)) ||
+        (rc = dalloc(H, &H->sidx, s.sidx.size())) || (rc = dalloc(H, &H->cidx, s.cidx.size() + 1)) ||
+        (rc = dalloc(H, &H->di0, dtab)) || (rc = dalloc(H, &H->dr_lo, drng)) ||
+        (rc = dalloc(H, &H->dr_hi, drng)) || (rc = dalloc(H, &H->basis_off, s.basis_off.size())) ||
+        (rc = dalloc(H, &H->basis, s.basis.size())) || (rc = dalloc(H, &H->D64, s.n_c)) ||
+        (rc = dalloc(H, &H->Jdata, s.n_c)) || (rc = dalloc(H, &H->J64, s.n_c)) ||
+        (rc = dalloc(H, &H->rzpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * NPART_MAX)) ||
+        (rc = dalloc(H, &H->pqpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * MAXL)) ||
+        (rc = dalloc(H, &H->status, 1)))
+        return rc;
+    if ((rc = talloc(H, &H->pfy, tab)) || (rc = talloc(H, &H->pfx, tab)) ||
+        (rc = talloc(H, &H->dfw, dtab)) || (rc = talloc(H, &H->D, s.n_c)) ||
+        (rc = talloc(H, &H->Jinv, s.n_c)) || (rc = talloc(H, &H->c, s.n_c)) ||
+        (rc = talloc(H, &H->b, s.n_c)) || (rc = talloc(H, &H->b_prev, s.n_c)) ||
+        (rc = talloc(H, &H->r, s.n_c)) || (rc = talloc(H, &H->z, s.n_c)) ||
+        (rc = talloc(H, &H->p, s.n_c)) || (rc = talloc(H, &H->q, s.n_c)) ||
+        (rc = talloc(H, &H->phi, s.n_c)) || (rc = talloc(H, &H->c_tmp, s.n_c)) ||
+        (rc = talloc(H, &H->u, s.n_nodes)) || (rc = talloc(H, &H->a_prev, s.n_act)) ||
+        (rc = talloc(H, &H->dm_tmp, s.n_act)) || (rc = talloc(H, &H->s_tmp, s.n_s)))
+        return rc;
+    if ((rc = upload(H, H->pi0y, s.pi0y)) || (rc = upload(H, H->pi0x, s.pi0x)) ||
+        (rc = upload(H, H->pfy64, s.pfy)) || (rc = upload(H, H->pfx64, s.pfx)) ||
+        (rc = upload(H, H->ry_lo, s.ry_lo)) || (rc = upload(H, H->ry_hi, s.ry_hi)) ||
+        (rc = upload(H, H->rx_lo, s.rx_lo)) || (rc = upload(H, H->rx_hi, s.rx_hi)) ||
+        (rc = upload(H, H->sidx, s.sidx)) || (rc = upload(H, H->cidx, s.cidx)) ||
+        (rc = upload(H, H->di0, s.di0)) || (rc = upload(H, H->dr_lo, s.dr_lo)) ||
+        (rc = upload(H, H->dr_hi, s.dr_hi)) || (rc = upload(H, H->basis_off, s.basis_off)) ||
+        (rc = upload(H, H->basis, s.basis)))
+        return rc;
+    H->smem_layer = (2 * NWARP + 4) * sizeof(double) + static_cast<size_t>(s.max_n) * s.max_n * sizeof(T);
+    H->smem_sensor = (2 * NWARP + 4 + 2 * MAXCOARSE) * sizeof(double) +
+                     (static_cast<size_t>(s.max_N + 1) * (s.max_N + 1) + 2 * static_cast<size_t>(s.max_N) * s.max_N) * sizeof(T);
+    if ((rc = set_smem_limits<T>(H))) return rc;
+    return setup_tables<T>(H);
+}
+
+template <class T>
+int check_type(fewha_handle* H) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (static_cast<int>(sizeof(T) * 8) != H->precision)
+        return fail(H, FEWHA_ERR_INVALID_ARG, "element type does not match the handle's precision");
+    return FEWHA_OK;
+}
+
+template <class T>
+int reconstruct_dev(fewha_handle* H, const T* s, T* x, T* dm, void* stream) {
+    int rc;
+    if ((rc = check_type<T>(H))) return rc;
+    if (!s || !dm) return fail(H, FEWHA_ERR_INVALID_ARG, "null slope or DM pointer");
+    DeviceGuard g(H->device);
+    return run_frame<T>(H, s, x ? x : static_cast<T*>(H->c), dm, static_cast<cudaStream_t>(stream));
+}
+
+template <class T>
+int reconstruct_host(fewha_handle* H, const T* hs, T* hdm, void* stream) {
+    int rc;
+    if ((rc = check_type<T>(H))) return rc;
+    if (!hs || !hdm) return fail(H, FEWHA_ERR_INVALID_ARG, "null host pointer");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const HostSetup& s = H->setup;
+    CK(cudaMemcpyAsync(H->s_tmp, hs, s.n_s * sizeof(T), cudaMemcpyHostToDevice, st), "slopes H2D");
+    if ((rc = run_frame<T>(H, static_cast<const T*>(H->s_tmp), static_cast<T*>(H->c),
+                           static_cast<T*>(H->dm_tmp), st)))
+        return rc;
+    CK(cudaMemcpyAsync(hdm, H->dm_tmp, s.n_act * sizeof(T), cudaMemcpyDeviceToHost, st), "DM D2H");
+    unsigned flag = 0;
+    CK(cudaMemcpyAsync(&flag, H->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "status");
+    CK(cudaStreamSynchronize(st), "host frame");
+    if (flag) {
+        cudaMemsetAsync(H->status, 0, sizeof(unsigned), st);
+        cudaStreamSynchronize(st);
+        return fail(H, FEWHA_ERR_NONFINITE, "non-finite value in the input slopes");
+    }
+    return FEWHA_OK;
+}
+
+// ---------------------------------------------------------------- operators
+template <class T>
+int op_dispatch(fewha_handle* H, int op, const void* in, void* out, int iters, cudaStream_t st) {
+    const Desc<T> d = make_desc<T>(H);
+    const T* x = static_cast<const T*>(in);
+    T* y = static_cast<T*>(out);
+    T* u = static_cast<T*>(H->u);
+    T* phi = static_cast<T*>(H->phi);
+    int rc = 0;
+    switch (op) {
+        case 0:  // M
+            return enqueue_apply<T>(H, d, x, y, PQ_SCRATCH_SLOT, false, st);
+        case 1:  // rhs
+            return enqueue_rhs<T>(H, d, x, y, st);
+        case 2:  // dwt
+            return launch_layer<T, LSRC_PHI, LDST_COEF, false>(H, d, layer_args<T>(H, x, y), st);
+        case 3:  // idwt
+            return launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, x, y), st);
+        case 4:  // project
+            return launch_sensor<T, SSRC_PHI, false, SDST_NODES>(H, d, x, y, st);
+        case 5:  // project adjoint
+            return launch_layer<T, LSRC_NODES, LDST_PHI, false>(H, d, layer_args<T>(H, x, y), st);
+        case 6:  // slopes
+            return launch_sensor<T, SSRC_NODES, false, SDST_SLOPES>(H, d, x, y, st);
+        case 7:  // slopes adjoint
+            return launch_sensor<T, SSRC_SLOPES, false, SDST_ADJ>(H, d, x, y, st);
+        case 8:  // noise weight
+            return launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, x, y, st);
+        case 9:  // forward model
+            return launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, x, y, st);
+        case 10:  // forward adjoint
+            if ((rc = launch_sensor<T, SSRC_SLOPES, false, SDST_ADJ>(H, d, x, u, st))) return rc;
+            return launch_layer<T, LSRC_NODES, LDST_PHI, false>(H, d, layer_args<T>(H, u, y), st);
+        case 11:  // fit
+            return enqueue_fit<T>(H, d, x, y, false, st);
+        case 12:  // fit adjoint
+            return launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, x, y), st);
+        case 13: {  // pcg on b = in, c = out (in/out)
+            CK(cudaMemcpyAsync(H->b, x, d.n_c * sizeof(T), cudaMemcpyDeviceToDevice, st), "b copy");
+            return enqueue_pcg<T>(H, d, y, iters, false, st);
+        }
+        default:
+            (void)phi;
+            return fail(H, FEWHA_ERR_INVALID_ARG, "unknown operator");
+    }
+}
+
+int op_entry(fewha_handle* H, int op, const void* in, void* out, int iters, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!in || !out) return fail(H, FEWHA_ERR_INVALID_ARG, "null pointer");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32 ? op_dispatch<float>(H, op, in, out, iters, st)
+                              : op_dispatch<double>(H, op, in, out, iters, st);
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* fewha_create_error(void) { return g_create_error.c_str(); }
+
+const char* fewha_last_error(const fewha_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int fewha_create(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, const fewha_layer* layers,
+                 int n_layers, const fewha_dm* dms, int n_dms, const fewha_params* params,
+                 fewha_handle** out) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return FEWHA_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!tel) {
+        g_create_error = "telescope is NULL";
+        return FEWHA_ERR_INVALID_ARG;
+    }
+    int rc = check_params(params, g_create_error);
+    if (rc) return rc;
+    fewha_handle* H = new fewha_handle();
+    H->params = *params;
+    H->precision = params->precision;
+    H->esz = params->precision == 32 ? sizeof(float) : sizeof(double);
+    rc = build_setup(*tel, wfs, n_wfs, layers, n_layers, dms, n_dms, H->setup, g_create_error);
+    if (rc) {
+        delete H;
+        return rc;
+    }
+    for (int l = 0; l < n_layers; ++l) H->weights.push_back(layers[l].cn2_weight);
+    H->npart = (H->setup.n_c + PBLK * 4 - 1) / (PBLK * 4);
+    if (H->npart > NPART_MAX) H->npart = NPART_MAX;
+    if (H->npart < 1) H->npart = 1;
+    if (cudaGetDevice(&H->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "no usable CUDA device";
+        free_handle(H);
+        return FEWHA_ERR_CUDA;
+    }
+    rc = H->precision == 32 ? typed_create<float>(H) : typed_create<double>(H);
+    if (rc) {
+        g_create_error = H->err;
+        free_handle(H);
+        return rc;
+    }
+    *out = H;
+    return FEWHA_OK;
+}
+
+void fewha_destroy(fewha_handle* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    free_handle(h);
+}
+
+int fewha_sizes(const fewha_handle* h, int64_t* n_slopes, int64_t* n_coeffs, int64_t* n_act,
+                int64_t* n_nodes) {
+    if (!h) return FEWHA_ERR_INVALID_ARG;
+    if (n_slopes) *n_slopes = h->setup.n_s;
+    if (n_coeffs) *n_coeffs = h->setup.n_c;
+    if (n_act) *n_act = h->setup.n_act;
+    if (n_nodes) *n_nodes = h->setup.n_nodes;
+    return FEWHA_OK;
+}
+
+int fewha_update_params(fewha_handle* H, const fewha_params* params, const double* cn2_weights,
+                        const double* sigmas) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    std::string e;
+    int rc = check_params(params, e);
+    if (rc) return fail(H, rc, e);
+    if (params->precision != H->precision) return fail(H, FEWHA_ERR_INVALID_ARG, "precision cannot change");
+    DeviceGuard g(H->device);
+    CK(cudaDeviceSynchronize(), "update sync");
+    if (cn2_weights) {
+        for (size_t l = 0; l < H->weights.size(); ++l) {
+            if (!(cn2_weights[l] > 0)) return fail(H, FEWHA_ERR_INVALID_ARG, "Cn2 weights must be > 0");
+            H->weights[l] = cn2_weights[l];
+        }
+    }
+    if (sigmas) {
+        for (size_t g2 = 0; g2 < H->setup.G.size(); ++g2) {
+            if (!(sigmas[g2] > 0)) return fail(H, FEWHA_ERR_INVALID_ARG, "sigmas must be > 0");
+            H->setup.G[g2].sig2inv = 1.0 / (sigmas[g2] * sigmas[g2]);
+            H->setup.wfs_sigma[g2] = sigmas[g2];
+        }
+    }
+    H->params = *params;
+    drop_graph(H);
+    H->have_prev = false;
+    return H->precision == 32 ? compute_diagonals<float>(H) : compute_diagonals<double>(H);
+}
+
+int fewha_reset(fewha_handle* H, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(H->c, 0, H->setup.n_c * H->esz, st), "reset");
+    CK(cudaMemsetAsync(H->a_prev, 0, H->setup.n_act * H->esz, st), "reset");
+    CK(cudaMemsetAsync(H->r, 0, H->setup.n_c * H->esz, st), "reset");
+    CK(cudaMemsetAsync(H->b_prev, 0, H->setup.n_c * H->esz, st), "reset");
+    H->have_prev = false;
+    return FEWHA_OK;
+}
+
+int fewha_reconstruct(fewha_handle* h, const float* s, float* x, float* dm, void* stream) {
+    return reconstruct_dev<float>(h, s, x, dm, stream);
+}
+int fewha_reconstruct_f64(fewha_handle* h, const double* s, double* x, double* dm, void* stream) {
+    return reconstruct_dev<double>(h, s, x, dm, stream);
+}
+int fewha_reconstruct_host(fewha_handle* h, const float* s, float* dm, void* stream) {
+    return reconstruct_host<float>(h, s, dm, stream);
+}
+int fewha_reconstruct_host_f64(fewha_handle* h, const double* s, double* dm, void* stream) {
+    return reconstruct_host<double>(h, s, dm, stream);
+}
+
+int fewha_check_input(fewha_handle* H, int* nonfinite, void* stream) {
+    if (!H || !nonfinite) return FEWHA_ERR_INVALID_ARG;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned flag = 0;
+    CK(cudaMemcpyAsync(&flag, H->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "status");
+    CK(cudaMemsetAsync(H->status, 0, sizeof(unsigned), st), "status");
+    CK(cudaStreamSynchronize(st), "status");
+    *nonfinite = flag ? 1 : 0;
+    return FEWHA_OK;
+}
+
+int fewha_apply_M(fewha_handle* h, const void* c, void* q, void* st) { return op_entry(h, 0, c, q, 0, st); }
+int fewha_rhs(fewha_handle* h, const void* s, void* b, void* st) { return op_entry(h, 1, s, b, 0, st); }
+int fewha_dwt(fewha_handle* h, const void* phi, void* c, void* st) { return op_entry(h, 2, phi, c, 0, st); }
+int fewha_idwt(fewha_handle* h, const void* c, void* phi, void* st) { return op_entry(h, 3, c, phi, 0, st); }
+int fewha_project(fewha_handle* h, const void* phi, void* v, void* st) { return op_entry(h, 4, phi, v, 0, st); }
+int fewha_project_adj(fewha_handle* h, const void* v, void* phi, void* st) { return op_entry(h, 5, v, phi, 0, st); }
+int fewha_slopes(fewha_handle* h, const void* v, void* s, void* st) { return op_entry(h, 6, v, s, 0, st); }
+int fewha_slopes_adj(fewha_handle* h, const void* s, void* v, void* st) { return op_entry(h, 7, s, v, 0, st); }
+int fewha_noise_weight(fewha_handle* h, const void* s, void* o, void* st) { return op_entry(h, 8, s, o, 0, st); }
+int fewha_forward(fewha_handle* h, const void* phi, void* s, void* st) { return op_entry(h, 9, phi, s, 0, st); }
+int fewha_forward_adj(fewha_handle* h, const void* s, void* phi, void* st) { return op_entry(h, 10, s, phi, 0, st); }
+int fewha_fit(fewha_handle* h, const void* c, void* dm, void* st) { return op_entry(h, 11, c, dm, 0, st); }
+int fewha_fit_adj(fewha_handle* h, const void* dm, void* c, void* st) { return op_entry(h, 12, dm, c, 0, st); }
+int fewha_pcg(fewha_handle* h, const void* b, void* c, int iters, void* st) {
+    if (h && (iters < 0 || iters > FEWHA_MAX_ITERS)) return fail(h, FEWHA_ERR_LIMIT, "iters out of range");
+    return op_entry(h, 13, b, c, iters, st);
+}
+
+int fewha_get_diagonals(fewha_handle* H, void* d_D, void* d_J, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = H->setup.n_c;
+    if (d_D) CK(cudaMemcpyAsync(d_D, H->D, n * H->esz, cudaMemcpyDeviceToDevice, st), "D copy");
+    if (d_J) {
+        if (H->precision == 64) {
+            CK(cudaMemcpyAsync(d_J, H->J64, n * sizeof(double), cudaMemcpyDeviceToDevice, st), "J copy");
+        } else {
+            k_convert<float, double><<<(n + 255) / 256, 256, 0, st>>>(n, H->J64, static_cast<float*>(d_J));
+            CK(cudaGetLastError(), "J convert");
+        }
+    }
+    return FEWHA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal descriptors shared by the host set-up code and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fewha.h"
+
+namespace fewha {
+
+constexpr int MAXL = FEWHA_MAX_LAYERS;
+constexpr int MAXG = FEWHA_MAX_WFS;
+constexpr int MAXM = FEWHA_MAX_DMS;
+constexpr int MAXN = FEWHA_MAX_GRID;
+constexpr int MAXNF = FEWHA_MAX_NFINE;
+constexpr int MAXNACT = 2 * MAXN;       // actuators per DM side
+constexpr int TAB = MAXNF + 1;          // projection table stride per (sensor, layer)
+constexpr int MAXCOARSE = FEWHA_MAX_COARSE * FEWHA_MAX_COARSE;
+
+struct LayerInfo {
+    int n;        // grid side (power of two)
+    int log2n;
+    int levels;   // wavelet levels
+    int off;      // offset in coefficient / layer vectors
+    int full;     // levels == log2n: the LL band is the single piston coefficient
+};
+
+struct WfsInfo {
+    int N;          // fine subapertures per side (n_sub * nb)
+    int nb;         // fine per coarse (1: ordinary sensor)
+    int n_sub;      // subapertures per side as measured
+    int lgs;        // tip/tilt removed (Sec. 3.2)
+    int n_active;   // active measured subapertures
+    int soff;       // offset of its slopes
+    int node_off;   // offset of its (N+1)^2 aperture nodes
+    int mask_off;   // offset of its N*N slope-index table
+    int cmask_off;  // offset of its n_sub^2 coarse-index table (nb > 1)
+    double sig2inv; // 1 / sigma^2
+};
+
+struct DmInfo {
+    int n_act;
+    int off;
+};
+
+// Everything a kernel needs about one instance, passed by value.
+template <class T>
+struct Desc {
+    int n_layers, n_wfs, n_dms;
+    int n_c, n_s, n_nodes, n_act;
+    int max_n, max_N;
+    LayerInfo L[MAXL];
+    WfsInfo G[MAXG];
+    DmInfo Mi[MAXM];
+    T fitw[MAXM][MAXL];   // share of layer l given to DM m
+    T alpha, gain;
+    // P_g tables, pair (g, l) at (g * MAXL + l) * TAB: grid row/col of node a and weight
+    const int* pi0y;
+    const int* pi0x;
+    const T* pfy;
+    const T* pfx;
+    // P_g^T gather ranges, pair (g, l) at (g * MAXL + l) * MAXN: aperture rows/cols
+    // touching layer row/col i are [lo, hi)
+    const int* ry_lo;
+    const int* ry_hi;
+    const int* rx_lo;
+    const int* rx_hi;
+    // slope index tables (see WfsInfo)
+    const int* sidx;
+    const int* cidx;
+    // DM fit tables, pair (m, l) at (m * MAXL + l) * MAXNACT
+    const int* di0;
+    const T* dfw;
+    // F^T gather ranges, pair (m, l) at (m * MAXL + l) * MAXN
+    const int* dr_lo;
+    const int* dr_hi;
+    // per-coefficient diagonals
+    const T* D;
+    const T* Jinv;
+};
+
+// Host-side result of geometry set-up (all in double).
+struct HostSetup {
+    std::vector<LayerInfo> L;
+    std::vector<WfsInfo> G;
+    std::vector<DmInfo> Mi;
+    std::vector<double> layer_h, layer_w, layer_delta;
+    std::vector<double> wfs_sigma;
+    double fitw[MAXM][MAXL];
+    int n_c = 0, n_s = 0, n_nodes = 0, n_act = 0, max_n = 0, max_N = 0;
+    std::vector<int> pi0y, pi0x;        // MAXG*MAXL*TAB
+    std::vector<double> pfy, pfx;
+    std::vector<int> ry_lo, ry_hi, rx_lo, rx_hi;   // MAXG*MAXL*MAXN
+    std::vector<int> sidx, cidx;
+    std::vector<int> di0;               // MAXM*MAXL*MAXNACT
+    std::vector<double> dfw;
+    std::vector<int> dr_lo, dr_hi;      // MAXM*MAXL*MAXN
+    // 1-D wavelet basis functions at shift 0: layer l, level j (1..levels), kind 0/1
+    std::vector<double> basis;
+    std::vector<int> basis_off;         // MAXL * (MAXN_LEVELS + 1) * 2
+    double taps_h[6], taps_g[6];
+};
+
+constexpr int MAXLEV = 8;   // log2(MAXN) + 1
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int basis_index(int l, int j, int kind) { return (l * (MAXLEV + 1) + j) * 2 + kind; }
+
+// Host set-up (fewha_setup.cpp).  Return FEWHA_OK or an error code with a message.
+int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
+                const fewha_layer* layers, int n_layers, const fewha_dm* dms, int n_dms,
+                HostSetup& out, std::string& err);
+void db3_taps(double h[6], double g[6]);
+// Prior D (Sec. 3.1), one value per coefficient.
+void prior_diag(const HostSetup& s, const std::vector<double>& weights, double r0, double L0,
+                std::vector<double>& D);
+
+}  // namespace fewha

@@ -1,0 +1,883 @@
+// sm_103a kernels of the FEWHA hot path.  No tensor cores: nothing here is a dense
+// contraction; every kernel is a stencil, a gather or a reduction over data that
+// stays in L2.  All reductions use a fixed thread-to-data map and fixed shuffle
+// trees, and the adjoint operators are gathers (no atomics), so results are
+// bitwise reproducible run to run.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fewha_internal.h"
+
+namespace fewha {
+
+constexpr int BLK = 1024;   // threads of the per-layer and per-sensor kernels
+constexpr int PBLK = 256;   // threads of the vector (PCG) kernels
+constexpr int NWARP = BLK / 32;
+
+__constant__ float c_h32[6];
+__constant__ float c_g32[6];
+__constant__ double c_h64[6];
+__constant__ double c_g64[6];
+
+template <class T> __device__ __forceinline__ T tap_h(int t);
+template <class T> __device__ __forceinline__ T tap_g(int t);
+template <> __device__ __forceinline__ float tap_h<float>(int t) { return c_h32[t]; }
+template <> __device__ __forceinline__ float tap_g<float>(int t) { return c_g32[t]; }
+template <> __device__ __forceinline__ double tap_h<double>(int t) { return c_h64[t]; }
+template <> __device__ __forceinline__ double tap_g<double>(int t) { return c_g64[t]; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of two doubles (fixed tree); red holds >= 2*(NWARP+1).
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[w] = a;
+        red[NWARP + w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < nw ? red[lane] : 0.0;
+        double y = lane < nw ? red[NWARP + lane] : 0.0;
+        x = warp_sum(x);
+        y = warp_sum(y);
+        if (lane == 0) {
+            red[2 * NWARP] = x;
+            red[2 * NWARP + 1] = y;
+        }
+    }
+    __syncthreads();
+    a = red[2 * NWARP];
+    b = red[2 * NWARP + 1];
+    __syncthreads();
+}
+
+// Sum of cnt doubles in a fixed order, computed by warp 0 and broadcast via *out.
+__device__ __forceinline__ double sum_partials(const double* p, int cnt, double* slot) {
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < cnt; i += 32) v += p[i];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) *slot = v;
+    }
+    __syncthreads();
+    const double r = *slot;
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Periodic Daubechies-3 steps on the m x m top-left block of an n x n shared tile.
+// Analysis: a_k = sum_t h_t x_(2k+t mod m), d_k = sum_t g_t x_(2k+t mod m) (Sec. 3.1).
+// Each thread owns (a_k, d_k) pairs; results go through registers so the step is
+// in place.  m*m/2 <= 8192 pairs = 8 per thread at n = 128.
+// ---------------------------------------------------------------------------
+constexpr int PAIRS = (MAXN * MAXN / 2 + BLK - 1) / BLK;
+
+template <class T>
+__device__ __forceinline__ void fwd_rows(T* S, int n, int m, int lm) {
+    const int h = m >> 1, lh = lm - 1, pairs = m * h;
+    T ra[PAIRS], rd[PAIRS];
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int r = idx >> lh, k = idx & (h - 1);
+            const T* row = S + r * n;
+            T a = T(0), d = T(0);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const T x = row[(2 * k + t) & (m - 1)];
+                a += tap_h<T>(t) * x;
+                d += tap_g<T>(t) * x;
+            }
+            ra[it] = a;
+            rd[it] = d;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int r = idx >> lh, k = idx & (h - 1);
+            S[r * n + k] = ra[it];
+            S[r * n + h + k] = rd[it];
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ void fwd_cols(T* S, int n, int m, int lm) {
+    const int h = m >> 1, pairs = m * h;
+    T ra[PAIRS], rd[PAIRS];
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int c = idx & (m - 1), k = idx >> lm;
+            T a = T(0), d = T(0);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const T x = S[((2 * k + t) & (m - 1)) * n + c];
+                a += tap_h<T>(t) * x;
+                d += tap_g<T>(t) * x;
+            }
+            ra[it] = a;
+            rd[it] = d;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int c = idx & (m - 1), k = idx >> lm;
+            S[k * n + c] = ra[it];
+            S[(h + k) * n + c] = rd[it];
+        }
+    }
+    __syncthreads();
+}
+
+// Synthesis (transpose of the analysis): outputs 2k and 2k+1 take a_k, a_(k-1),
+// a_(k-2) and the same d's (indices mod m/2):
+//   x_2k   = h0 a_k + h2 a_(k-1) + h4 a_(k-2) + g0 d_k + g2 d_(k-1) + g4 d_(k-2)
+//   x_2k+1 = h1 a_k + h3 a_(k-1) + h5 a_(k-2) + g1 d_k + g3 d_(k-1) + g5 d_(k-2)
+template <class T>
+__device__ __forceinline__ void inv_cols(T* S, int n, int m, int lm) {
+    const int h = m >> 1, pairs = m * h;
+    T re[PAIRS], ro[PAIRS];
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int c = idx & (m - 1), k = idx >> lm;
+            const int k1 = (k - 1) & (h - 1), k2 = (k - 2) & (h - 1);
+            const T a0 = S[k * n + c], a1 = S[k1 * n + c], a2 = S[k2 * n + c];
+            const T d0 = S[(h + k) * n + c], d1 = S[(h + k1) * n + c], d2 = S[(h + k2) * n + c];
+            re[it] = tap_h<T>(0) * a0 + tap_h<T>(2) * a1 + tap_h<T>(4) * a2 +
+                     tap_g<T>(0) * d0 + tap_g<T>(2) * d1 + tap_g<T>(4) * d2;
+            ro[it] = tap_h<T>(1) * a0 + tap_h<T>(3) * a1 + tap_h<T>(5) * a2 +
+                     tap_g<T>(1) * d0 + tap_g<T>(3) * d1 + tap_g<T>(5) * d2;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int c = idx & (m - 1), k = idx >> lm;
+            S[(2 * k) * n + c] = re[it];
+            S[(2 * k + 1) * n + c] = ro[it];
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ void inv_rows(T* S, int n, int m, int lm) {
+    const int h = m >> 1, lh = lm - 1, pairs = m * h;
+    T re[PAIRS], ro[PAIRS];
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int r = idx >> lh, k = idx & (h - 1);
+            const int k1 = (k - 1) & (h - 1), k2 = (k - 2) & (h - 1);
+            const T* row = S + r * n;
+            const T a0 = row[k], a1 = row[k1], a2 = row[k2];
+            const T d0 = row[h + k], d1 = row[h + k1], d2 = row[h + k2];
+            re[it] = tap_h<T>(0) * a0 + tap_h<T>(2) * a1 + tap_h<T>(4) * a2 +
+                     tap_g<T>(0) * d0 + tap_g<T>(2) * d1 + tap_g<T>(4) * d2;
+            ro[it] = tap_h<T>(1) * a0 + tap_h<T>(3) * a1 + tap_h<T>(5) * a2 +
+                     tap_g<T>(1) * d0 + tap_g<T>(3) * d1 + tap_g<T>(5) * d2;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PAIRS; ++it) {
+        const int idx = threadIdx.x + it * BLK;
+        if (idx < pairs) {
+            const int r = idx >> lh, k = idx & (h - 1);
+            S[r * n + 2 * k] = re[it];
+            S[r * n + 2 * k + 1] = ro[it];
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ void dwt_forward(T* S, const LayerInfo& L) {
+    for (int lev = 0; lev < L.levels; ++lev) {
+        const int m = L.n >> lev, lm = L.log2n - lev;
+        fwd_rows(S, L.n, m, lm);
+        fwd_cols(S, L.n, m, lm);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void dwt_inverse(T* S, const LayerInfo& L) {
+    for (int lev = L.levels - 1; lev >= 0; --lev) {
+        const int m = L.n >> lev, lm = L.log2n - lev;
+        inv_cols(S, L.n, m, lm);
+        inv_rows(S, L.n, m, lm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG bookkeeping: per-iteration partial inner products in fixed slots.
+// rz of iteration k = sum of rzpart[k * npart + 0 .. npart); p.q of iteration k =
+// sum of pqpart[k * MAXL + 0 .. n_layers).
+// ---------------------------------------------------------------------------
+struct PcgSlots {
+    double* rzpart;
+    double* pqpart;
+    int npart;
+};
+
+// ---------------------------------------------------------------------------
+// Per-layer kernel.  Source: the layer values (SRC_PHI), the adjoint projection of
+// aperture-node vectors (SRC_NODES, P^T as a gather), or the adjoint DM fit
+// (SRC_DM).  Destination: layer values (DST_PHI), wavelet coefficients (DST_COEF),
+// or q = W y + alpha D p with the partial p.q (DST_APPLY).
+// PUPDATE: before use, the CG direction of this layer is advanced, p = z + beta p,
+// beta = rz_k / rz_(k-1) (Sec. 3.3; the update is fused into the first kernel of
+// iteration k).
+// ---------------------------------------------------------------------------
+enum { LSRC_PHI = 0, LSRC_NODES = 1, LSRC_DM = 2, LSRC_COEF = 3 };
+enum { LDST_PHI = 0, LDST_COEF = 1, LDST_APPLY = 2 };
+
+template <class T>
+struct LayerArgs {
+    const T* in;      // source vector
+    const T* pin;     // p of the apply (DST_APPLY)
+    T* out;           // destination vector
+    T* pupd;          // p to advance (PUPDATE), updated in place
+    const T* zupd;    // z of the update
+    PcgSlots pcg;
+    int iter;         // CG iteration of the apply / update
+    int zero_piston;  // data term: the full-depth LL coefficient is exactly 0
+};
+
+template <class T, int SRC, int DST, bool PUPDATE>
+__global__ void __launch_bounds__(BLK) k_layer(const Desc<T> d, const LayerArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);          // 2*NWARP + 4 doubles
+    T* S = reinterpret_cast<T*>(red + 2 * NWARP + 4);
+    const int l = blockIdx.x;
+    const LayerInfo L = d.L[l];
+    const int n = L.n, nn = n * n, off = L.off;
+
+    if (PUPDATE) {
+        const double rz_new = sum_partials(a.pcg.rzpart + a.iter * a.pcg.npart, a.pcg.npart, red);
+        const double rz_old = sum_partials(a.pcg.rzpart + (a.iter - 1) * a.pcg.npart, a.pcg.npart, red);
+        const T beta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
+        for (int k = threadIdx.x; k < nn; k += BLK) {
+            const T p = a.zupd[off + k] + beta * a.pupd[off + k];
+            a.pupd[off + k] = p;
+            S[k] = p;
+        }
+    } else if (SRC == LSRC_PHI || SRC == LSRC_COEF) {
+        for (int k = threadIdx.x; k < nn; k += BLK) S[k] = a.in[off + k];
+    } else if (SRC == LSRC_NODES) {
+        // y(i, j) = sum_g sum_a sum_b wy(a, i) wx(b, j) u_g(a, b): P_g^T as a gather over
+        // the aperture nodes whose bilinear stencil touches layer node (i, j).
+        for (int k = threadIdx.x; k < nn; k += BLK) {
+            const int i = k >> L.log2n, j = k & (n - 1);
+            T acc = T(0);
+            for (int g = 0; g < d.n_wfs; ++g) {
+                const int rb = (g * MAXL + l) * MAXN;
+                const int a0 = d.ry_lo[rb + i], a1 = d.ry_hi[rb + i];
+                const int b0 = d.rx_lo[rb + j], b1 = d.rx_hi[rb + j];
+                if (a0 >= a1 || b0 >= b1) continue;
+                const int tp = (g * MAXL + l) * TAB;
+                const int NP = d.G[g].N + 1;
+                const T* u = a.in + d.G[g].node_off;
+                for (int aa = a0; aa < a1; ++aa) {
+                    const T wy = d.pi0y[tp + aa] == i ? T(1) - d.pfy[tp + aa] : d.pfy[tp + aa];
+                    T row = T(0);
+                    for (int bb = b0; bb < b1; ++bb) {
+                        const T wx = d.pi0x[tp + bb] == j ? T(1) - d.pfx[tp + bb] : d.pfx[tp + bb];
+                        row += wx * u[aa * NP + bb];
+                    }
+                    acc += wy * row;
+                }
+            }
+            S[k] = acc;
+        }
+    } else if (SRC == LSRC_DM) {
+        // adjoint of the DM fit: y(i, j) = sum_m w_lm sum_p sum_q wy(p, i) wx(q, j) a_m(p, q)
+        for (int k = threadIdx.x; k < nn; k += BLK) {
+            const int i = k >> L.log2n, j = k & (n - 1);
+            T acc = T(0);
+            for (int m = 0; m < d.n_dms; ++m) {
+                const T w = d.fitw[m][l];
+                if (w == T(0)) continue;
+                const int rb = (m * MAXL + l) * MAXN;
+                const int p0 = d.dr_lo[rb + i], p1 = d.dr_hi[rb + i];
+                const int q0 = d.dr_lo[rb + j], q1 = d.dr_hi[rb + j];
+                if (p0 >= p1 || q0 >= q1) continue;
+                const int tb = (m * MAXL + l) * MAXNACT;
+                const int na = d.Mi[m].n_act;
+                const T* am = a.in + d.Mi[m].off;
+                T sm = T(0);
+                for (int p = p0; p < p1; ++p) {
+                    const T wy = d.di0[tb + p] == i ? T(1) - d.dfw[tb + p] : d.dfw[tb + p];
+                    T row = T(0);
+                    for (int q = q0; q < q1; ++q) {
+                        const T wx = d.di0[tb + q] == j ? T(1) - d.dfw[tb + q] : d.dfw[tb + q];
+                        row += wx * am[p * na + q];
+                    }
+                    sm += wy * row;
+                }
+                acc += w * sm;
+            }
+            S[k] = acc;
+        }
+    }
+    __syncthreads();
+
+    if (DST == LDST_PHI) {
+        if (SRC == LSRC_COEF || PUPDATE) dwt_inverse(S, L);
+        for (int k = threadIdx.x; k < nn; k += BLK) a.out[off + k] = S[k];
+        return;
+    }
+    dwt_forward(S, L);
+    // The data term has no piston component: Gamma annihilates constants and bilinear
+    // weights sum to one, so (W P^T Gamma^T ...)_LL = 0 exactly at full depth.  Write
+    // that zero instead of the rounding residue of a cancelling sum (it would be
+    // amplified by 1 / (alpha D_LL) in the solve).
+    if (a.zero_piston && L.full && threadIdx.x == 0) S[0] = T(0);
+    __syncthreads();
+    if (DST == LDST_COEF) {
+        for (int k = threadIdx.x; k < nn; k += BLK) a.out[off + k] = S[k];
+        return;
+    }
+    // DST_APPLY: q = W B W^T p + alpha D p, partial p.q in double
+    double dot = 0.0, dummy = 0.0;
+    for (int k = threadIdx.x; k < nn; k += BLK) {
+        const T p = a.pin[off + k];
+        const T q = S[k] + d.alpha * d.D[off + k] * p;
+        a.out[off + k] = q;
+        dot += double(p) * double(q);
+    }
+    block_sum2(dot, dummy, red);
+    if (threadIdx.x == 0) a.pcg.pqpart[a.iter * MAXL + l] = dot;
+}
+
+// ---------------------------------------------------------------------------
+// Per-sensor kernel (one CTA per sensor): projection P_g, Shack-Hartmann slopes
+// Gamma_g, noise weighting C_hat_g^-1 (Eq. 2, Sec. 3.2) and Gamma_g^T, selected by
+// SRC / WEIGHT / DST.  Shared tiles: V (aperture nodes), SX, SY (per subaperture,
+// zero outside the active set).
+// ---------------------------------------------------------------------------
+enum { SSRC_PHI = 0, SSRC_NODES = 1, SSRC_SLOPES = 2 };
+enum { SDST_NODES = 0, SDST_SLOPES = 1, SDST_ADJ = 2 };
+
+template <class T>
+struct SensorArgs {
+    const T* in;
+    T* out;
+    unsigned* status;   // bit 0: a non-finite input slope was seen
+};
+
+template <class T, int SRC, bool WEIGHT, int DST>
+__global__ void __launch_bounds__(BLK) k_sensor(const Desc<T> d, const SensorArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);          // 2*NWARP + 4
+    double* csum = red + 2 * NWARP + 4;                          // 2*MAXCOARSE
+    const int g = blockIdx.x;
+    const WfsInfo W = d.G[g];
+    const int N = W.N, NP = N + 1, NN = N * N, NPP = NP * NP;
+    T* V = reinterpret_cast<T*>(csum + 2 * MAXCOARSE);
+    T* SX = V + NPP;
+    T* SY = SX + NN;
+    const int* sidx = d.sidx + W.mask_off;
+    const T inv = T(W.sig2inv);
+    const T nbinv = T(1) / T(W.nb);
+
+    // ---- source -----------------------------------------------------------
+    if (SRC == SSRC_PHI) {
+        // P_g (Sec. 2): phi_g(x) = sum_l phi_l(s_l x + theta h_l), bilinear
+        for (int k = threadIdx.x; k < NPP; k += BLK) {
+            const int aa = k / NP, bb = k - aa * NP;
+            T v = T(0);
+            for (int l = 0; l < d.n_layers; ++l) {
+                const int tp = (g * MAXL + l) * TAB;
+                const int i0 = d.pi0y[tp + aa], j0 = d.pi0x[tp + bb];
+                const T fy = d.pfy[tp + aa], fx = d.pfx[tp + bb];
+                const int n = d.L[l].n;
+                const T* P = a.in + d.L[l].off + i0 * n + j0;
+                v += (T(1) - fy) * ((T(1) - fx) * P[0] + fx * P[1]) +
+                     fy * ((T(1) - fx) * P[n] + fx * P[n + 1]);
+            }
+            V[k] = v;
+        }
+    } else if (SRC == SSRC_NODES) {
+        for (int k = threadIdx.x; k < NPP; k += BLK) V[k] = a.in[W.node_off + k];
+    } else {
+        // measured slopes -> per-subaperture tiles (coarse: spread over the block, 1/nb)
+        const T* s = a.in + W.soff;
+        bool bad = false;
+        for (int k = threadIdx.x; k < NN; k += BLK) {
+            const int id = sidx[k];
+            T sx = T(0), sy = T(0);
+            if (id >= 0) {
+                sx = s[id];
+                sy = s[W.n_active + id];
+                bad |= !(isfinite(sx) && isfinite(sy));
+                if (W.nb > 1) {
+                    sx *= nbinv;
+                    sy *= nbinv;
+                    if (WEIGHT) {
+                        sx *= inv;
+                        sy *= inv;
+                    }
+                }
+            }
+            SX[k] = sx;
+            SY[k] = sy;
+        }
+        if (bad && a.status) atomicOr(a.status, 1u);
+    }
+    __syncthreads();
+    if (SRC != SSRC_SLOPES && DST == SDST_NODES) {
+        for (int k = threadIdx.x; k < NPP; k += BLK) a.out[W.node_off + k] = V[k];
+        return;
+    }
+
+    // ---- Gamma_g: slopes of the active fine subapertures (Sec. 2, y-slope read as
+    // the mirror of the x-slope) ----------------------------------------------------
+    if (SRC != SSRC_SLOPES) {
+        for (int k = threadIdx.x; k < NN; k += BLK) {
+            const int i = k / N, j = k - i * N;
+            T sx = T(0), sy = T(0);
+            if (sidx[k] >= 0) {
+                const T v00 = V[i * NP + j], v01 = V[i * NP + j + 1];
+                const T v10 = V[(i + 1) * NP + j], v11 = V[(i + 1) * NP + j + 1];
+                sx = T(0.5) * ((v01 - v00) + (v11 - v10));
+                sy = T(0.5) * ((v10 - v00) + (v11 - v01));
+            }
+            SX[k] = sx;
+            SY[k] = sy;
+        }
+        __syncthreads();
+        if (W.nb > 1) {
+            // coarse sensor: slope_K = (1/nb) sum of the active fine slopes in block K
+            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const int ns = W.n_sub, nb = W.nb;
+            for (int blk = w; blk < ns * ns; blk += NWARP) {
+                const int K = d.cidx[W.cmask_off + blk];
+                if (K < 0) continue;
+                const int I = blk / ns, J = blk - I * ns;
+                double sx = 0.0, sy = 0.0;
+                for (int t = lane; t < nb * nb; t += 32) {
+                    const int r = t / nb, c = t - r * nb;
+                    const int k = (I * nb + r) * N + J * nb + c;
+                    sx += double(SX[k]);
+                    sy += double(SY[k]);
+                }
+                sx = warp_sum(sx);
+                sy = warp_sum(sy);
+                if (lane == 0) {
+                    csum[2 * K] = sx / nb;
+                    csum[2 * K + 1] = sy / nb;
+                }
+            }
+            __syncthreads();
+            if (DST == SDST_SLOPES) {
+                for (int K = threadIdx.x; K < W.n_active; K += BLK) {
+                    T cx = T(csum[2 * K]), cy = T(csum[2 * K + 1]);
+                    if (WEIGHT) {
+                        cx *= inv;
+                        cy *= inv;
+                    }
+                    a.out[W.soff + K] = cx;
+                    a.out[W.soff + W.n_active + K] = cy;
+                }
+                return;
+            }
+            // spread the (weighted) coarse slopes back over the fine subapertures:
+            // Gamma_coarse^T puts slope_K / nb on every active fine subaperture of K
+            for (int k = threadIdx.x; k < NN; k += BLK) {
+                const int id = sidx[k];
+                T sx = T(0), sy = T(0);
+                if (id >= 0) {
+                    sx = T(csum[2 * id]) * nbinv;
+                    sy = T(csum[2 * id + 1]) * nbinv;
+                    if (WEIGHT) {
+                        sx *= inv;
+                        sy *= inv;
+                    }
+                }
+                SX[k] = sx;
+                SY[k] = sy;
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- C_hat_g^-1 on fine sensors: LGS (I - T) sigma^-2 (I - T) = sigma^-2 (I - T),
+    // T removing the mean x- and y-slope over the active set (Sec. 3.2); NGS sigma^-2.
+    if (WEIGHT && W.nb == 1) {
+        if (W.lgs) {
+            double tx = 0.0, ty = 0.0;
+            for (int k = threadIdx.x; k < NN; k += BLK) {
+                tx += double(SX[k]);
+                ty += double(SY[k]);
+            }
+            block_sum2(tx, ty, red);
+            const T mx = T(tx / W.n_active), my = T(ty / W.n_active);
+            for (int k = threadIdx.x; k < NN; k += BLK) {
+                if (sidx[k] >= 0) {
+                    SX[k] = inv * (SX[k] - mx);
+                    SY[k] = inv * (SY[k] - my);
+                }
+            }
+        } else {
+            for (int k = threadIdx.x; k < NN; k += BLK) {
+                SX[k] *= inv;
+                SY[k] *= inv;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- destination ------------------------------------------------------------
+    if (DST == SDST_SLOPES) {
+        if (W.nb > 1) {
+            // slopes in -> (weighted) slopes out on a coarse sensor
+            for (int K = threadIdx.x; K < W.n_active; K += BLK) {
+                T cx = a.in[W.soff + K], cy = a.in[W.soff + W.n_active + K];
+                if (WEIGHT) {
+                    cx *= inv;
+                    cy *= inv;
+                }
+                a.out[W.soff + K] = cx;
+                a.out[W.soff + W.n_active + K] = cy;
+            }
+            return;
+        }
+        for (int k = threadIdx.x; k < NN; k += BLK) {
+            const int id = sidx[k];
+            if (id >= 0) {
+                a.out[W.soff + id] = SX[k];
+                a.out[W.soff + W.n_active + id] = SY[k];
+            }
+        }
+        return;
+    }
+    // Gamma_g^T: u(a, b) = 1/2 [sx(a, b-1) - sx(a, b) + sx(a-1, b-1) - sx(a-1, b)]
+    //                    + 1/2 [sy(a-1, b) - sy(a, b) + sy(a-1, b-1) - sy(a, b-1)]
+    for (int k = threadIdx.x; k < NPP; k += BLK) {
+        const int aa = k / NP, bb = k - aa * NP;
+        const bool r0 = aa < N, r1 = aa > 0, c0 = bb < N, c1 = bb > 0;
+        const T x_ab = (r0 && c0) ? SX[aa * N + bb] : T(0);
+        const T x_ab1 = (r0 && c1) ? SX[aa * N + bb - 1] : T(0);
+        const T x_a1b = (r1 && c0) ? SX[(aa - 1) * N + bb] : T(0);
+        const T x_a1b1 = (r1 && c1) ? SX[(aa - 1) * N + bb - 1] : T(0);
+        const T y_ab = (r0 && c0) ? SY[aa * N + bb] : T(0);
+        const T y_ab1 = (r0 && c1) ? SY[aa * N + bb - 1] : T(0);
+        const T y_a1b = (r1 && c0) ? SY[(aa - 1) * N + bb] : T(0);
+        const T y_a1b1 = (r1 && c1) ? SY[(aa - 1) * N + bb - 1] : T(0);
+        a.out[W.node_off + k] =
+            T(0.5) * ((x_ab1 - x_ab) + (x_a1b1 - x_a1b)) + T(0.5) * ((y_a1b - y_ab) + (y_a1b1 - y_ab1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG vector kernels (Sec. 3.3, standard left-preconditioned CG).  Vectors in T,
+// inner products and the scalars alpha = rz/pq, beta = rz_new/rz in double.
+// ---------------------------------------------------------------------------
+template <class T>
+struct VecArgs {
+    T* c;
+    T* r;
+    T* z;
+    T* p;
+    const T* q;
+    const T* b;
+    T* b_prev;
+    const T* Jinv;
+    PcgSlots pcg;
+    int iter;
+};
+
+enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2, V_COPY = 3, V_ZERO = 4 };
+
+template <class T, int PHASE>
+__global__ void __launch_bounds__(PBLK) k_vec(const int n, const VecArgs<T> v) {
+    __shared__ double red[2 * (PBLK / 32) + 4];
+    double alpha = 0.0;
+    if (PHASE == V_UPDATE) {
+        // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final)
+        double rz = 0.0, pq = 0.0;
+        if (threadIdx.x < 32) {
+            double s = 0.0, t = 0.0;
+            for (int i = threadIdx.x; i < v.pcg.npart; i += 32) s += v.pcg.rzpart[v.iter * v.pcg.npart + i];
+            for (int i = threadIdx.x; i < MAXL; i += 32) t += v.pcg.pqpart[v.iter * MAXL + i];
+            s = warp_sum(s);
+            t = warp_sum(t);
+            if (threadIdx.x == 0) {
+                red[0] = s;
+                red[1] = t;
+            }
+        }
+        __syncthreads();
+        rz = red[0];
+        pq = red[1];
+        __syncthreads();
+        alpha = (rz != 0.0 && pq > 0.0) ? rz / pq : 0.0;
+    }
+    const T ta = T(alpha);
+    double dot = 0.0;
+    const int stride = gridDim.x * PBLK;
+    for (int i = blockIdx.x * PBLK + threadIdx.x; i < n; i += stride) {
+        if (PHASE == V_COPY) {
+            v.c[i] = v.b[i];
+            continue;
+        }
+        if (PHASE == V_ZERO) {
+            v.c[i] = T(0);
+            continue;
+        }
+        T r;
+        if (PHASE == V_INIT) {
+            r = v.b[i] - v.q[i];
+            v.b_prev[i] = v.b[i];
+        } else if (PHASE == V_INIT_WARM) {
+            r = (v.b[i] - v.b_prev[i]) + v.r[i];
+            v.b_prev[i] = v.b[i];
+        } else {
+            v.c[i] += ta * v.p[i];
+            r = v.r[i] - ta * v.q[i];
+        }
+        v.r[i] = r;
+        const T z = v.Jinv[i] * r;
+        v.z[i] = z;
+        if (PHASE != V_UPDATE) v.p[i] = z;
+        dot += double(r) * double(z);
+    }
+    if (PHASE == V_COPY || PHASE == V_ZERO) return;
+    double dummy = 0.0;
+    // block_sum2 uses NWARP slots sized for BLK; use a local two-level reduction here
+    dot = warp_sum(dot);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[2 + w] = dot;
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < PBLK / 32 ? red[2 + lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) {
+            const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
+            v.pcg.rzpart[slot * v.pcg.npart + blockIdx.x] = x;
+        }
+    }
+    (void)dummy;
+}
+
+// ---------------------------------------------------------------------------
+// DM fitting (Algorithm 1 fitting step, Table 3): a~_m(p, q) = sum_l w_lm phi_l
+// sampled bilinearly at the actuator, then open-loop gain a = (1-g) a_prev + g a~.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_fit(const Desc<T> d, const T* __restrict__ phi,
+                                              T* __restrict__ a_prev, T* __restrict__ out,
+                                              int apply_gain) {
+    const int idx = blockIdx.x * PBLK + threadIdx.x;
+    if (idx >= d.n_act) return;
+    int m = 0;
+    while (m + 1 < d.n_dms && idx >= d.Mi[m + 1].off) ++m;
+    const int na = d.Mi[m].n_act, loc = idx - d.Mi[m].off;
+    const int p = loc / na, q = loc - p * na;
+    T acc = T(0);
+    for (int l = 0; l < d.n_layers; ++l) {
+        const T w = d.fitw[m][l];
+        if (w == T(0)) continue;
+        const int tb = (m * MAXL + l) * MAXNACT;
+        const int i0 = d.di0[tb + p], j0 = d.di0[tb + q];
+        const T fy = d.dfw[tb + p], fx = d.dfw[tb + q];
+        const int n = d.L[l].n;
+        const T* P = phi + d.L[l].off + i0 * n + j0;
+        acc += w * ((T(1) - fy) * ((T(1) - fx) * P[0] + fx * P[1]) +
+                    fy * ((T(1) - fx) * P[n] + fx * P[n + 1]));
+    }
+    if (apply_gain) {
+        const T a = (T(1) - d.gain) * a_prev[idx] + d.gain * acc;
+        a_prev[idx] = a;
+        out[idx] = a;
+    } else {
+        out[idx] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact Jacobi diagonal of W B W^T (Eq. 7), one warp per wavelet coefficient, in
+// double.  The basis function of coefficient (layer l, row r, col c) is the outer
+// product f_y(i) f_x(j) of 1-D level-j functions (shifted copies of the tables), its
+// bilinear projection on sensor g is (Ry f_y)(Rx f_x)^T, and its slopes are
+// products of 1-D averages and differences:
+//   s^x(i, j) = avg_y(i) dif_x(j),  s^y(i, j) = dif_y(i) avg_x(j).
+// The diagonal is sigma^-2 * (sum of squared active slopes, minus the squared
+// tip/tilt means times |M| for an LGS; or the sum of squared coarse slopes).
+// ---------------------------------------------------------------------------
+struct DiagArgs {
+    const double* basis;
+    const int* basis_off;
+    const double* pfy;   // projection weights in double (same layout as Desc::pfy)
+    const double* pfx;
+    double* out;         // n_c
+};
+
+template <class T>
+__global__ void __launch_bounds__(128) k_jdiag(const Desc<T> d, const DiagArgs a) {
+    __shared__ double sF[4][TAB];
+    __shared__ double sG[4][TAB];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int coef = blockIdx.x * 4 + w;
+    if (coef >= d.n_c) return;
+    int l = 0;
+    while (l + 1 < d.n_layers && coef >= d.L[l + 1].off) ++l;
+    const LayerInfo L = d.L[l];
+    const int n = L.n, k = coef - L.off, r = k >> L.log2n, c = k & (n - 1);
+    const int mx = r > c ? r : c;
+    int j, ky, kx, sy, sx;
+    if (mx < (n >> L.levels)) {
+        j = L.levels;
+        ky = kx = 0;
+        sy = r;
+        sx = c;
+    } else {
+        j = L.log2n - (31 - __clz(mx));
+        const int h = n >> j;
+        ky = r >= h;
+        kx = c >= h;
+        sy = r - ky * h;
+        sx = c - kx * h;
+    }
+    const double* fy = a.basis + a.basis_off[basis_index(l, j, ky)];
+    const double* fx = a.basis + a.basis_off[basis_index(l, j, kx)];
+    const int shy = sy << j, shx = sx << j;
+    double* F = sF[w];
+    double* G = sG[w];
+    double total = 0.0;
+    for (int g = 0; g < d.n_wfs; ++g) {
+        const WfsInfo W = d.G[g];
+        const int N = W.N, NP = N + 1;
+        const int tp = (g * MAXL + l) * TAB;
+        int lo_a = NP, hi_a = -1, lo_b = NP, hi_b = -1;
+        for (int t = lane; t < NP; t += 32) {
+            const int i0 = d.pi0y[tp + t];
+            const double wy = a.pfy[tp + t];
+            const double v = (1.0 - wy) * fy[(i0 - shy) & (n - 1)] + wy * fy[(i0 + 1 - shy) & (n - 1)];
+            F[t] = v;
+            if (v != 0.0) {
+                lo_a = min(lo_a, t);
+                hi_a = max(hi_a, t);
+            }
+            const int j0 = d.pi0x[tp + t];
+            const double wx = a.pfx[tp + t];
+            const double u = (1.0 - wx) * fx[(j0 - shx) & (n - 1)] + wx * fx[(j0 + 1 - shx) & (n - 1)];
+            G[t] = u;
+            if (u != 0.0) {
+                lo_b = min(lo_b, t);
+                hi_b = max(hi_b, t);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            lo_a = min(lo_a, __shfl_xor_sync(0xffffffffu, lo_a, o));
+            hi_a = max(hi_a, __shfl_xor_sync(0xffffffffu, hi_a, o));
+            lo_b = min(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, o));
+            hi_b = max(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, o));
+        }
+        __syncwarp();
+        if (hi_a < 0 || hi_b < 0) {
+            __syncwarp();
+            continue;
+        }
+        // subaperture rows i use nodes i, i+1
+        const int i0 = max(lo_a - 1, 0), i1 = min(hi_a, N - 1);
+        const int j0 = max(lo_b - 1, 0), j1 = min(hi_b, N - 1);
+        const int wi = i1 - i0 + 1, wj = j1 - j0 + 1;
+        const int* sidx = d.sidx + W.mask_off;
+        double contrib = 0.0;
+        if (W.nb == 1) {
+            double s2 = 0.0, tx = 0.0, ty = 0.0;
+            if (wi > 0 && wj > 0) {
+                for (int t = lane; t < wi * wj; t += 32) {
+                    const int i = i0 + t / wj, jj = j0 + t % wj;
+                    if (sidx[i * N + jj] < 0) continue;
+                    const double ya = 0.5 * (F[i] + F[i + 1]), yd = F[i + 1] - F[i];
+                    const double xa = 0.5 * (G[jj] + G[jj + 1]), xd = G[jj + 1] - G[jj];
+                    const double vx = ya * xd, vy = yd * xa;
+                    s2 += vx * vx + vy * vy;
+                    tx += vx;
+                    ty += vy;
+                }
+            }
+            s2 = warp_sum(s2);
+            tx = warp_sum(tx);
+            ty = warp_sum(ty);
+            contrib = s2;
+            if (W.lgs) contrib -= (tx * tx + ty * ty) / W.n_active;
+        } else {
+            const int ns = W.n_sub, nb = W.nb;
+            for (int blk = 0; blk < ns * ns; ++blk) {
+                if (d.cidx[W.cmask_off + blk] < 0) continue;
+                const int I = blk / ns, J = blk - I * ns;
+                const int bi0 = max(i0, I * nb), bi1 = min(i1, I * nb + nb - 1);
+                const int bj0 = max(j0, J * nb), bj1 = min(j1, J * nb + nb - 1);
+                double cx = 0.0, cy = 0.0;
+                if (bi0 <= bi1 && bj0 <= bj1) {
+                    const int bw = bj1 - bj0 + 1, cnt = (bi1 - bi0 + 1) * bw;
+                    for (int t = lane; t < cnt; t += 32) {
+                        const int i = bi0 + t / bw, jj = bj0 + t % bw;
+                        if (sidx[i * N + jj] < 0) continue;
+                        const double ya = 0.5 * (F[i] + F[i + 1]), yd = F[i + 1] - F[i];
+                        const double xa = 0.5 * (G[jj] + G[jj + 1]), xd = G[jj + 1] - G[jj];
+                        cx += ya * xd;
+                        cy += yd * xa;
+                    }
+                }
+                cx = warp_sum(cx) / nb;
+                cy = warp_sum(cy) / nb;
+                contrib += cx * cx + cy * cy;
+            }
+        }
+        total += W.sig2inv * contrib;
+        __syncwarp();
+    }
+    if (lane == 0) a.out[coef] = total;
+}
+
+// J = data diagonal + alpha max(D, tau); Jinv in the handle's type.
+template <class T>
+__global__ void k_jfinish(int n, const double* __restrict__ data, const double* __restrict__ D,
+                          double alpha, double tau, T* __restrict__ Jinv, T* __restrict__ Dt,
+                          double* __restrict__ J) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double j = data[i] + alpha * (D[i] > tau ? D[i] : tau);
+    J[i] = j;
+    Jinv[i] = T(1.0 / j);
+    Dt[i] = T(D[i]);
+}
+
+template <class T, class U>
+__global__ void k_convert(int n, const U* __restrict__ in, T* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = T(in[i]);
+}
+
+}  // namespace fewha

@@ -1,0 +1,297 @@
+"""Python binding of the FEWHA C ABI (include/fewha.h).
+
+Argument marshalling only: every operator runs in the CUDA library
+``libfewha.so`` built in-tree for sm_103a.  PyTorch supplies device memory and
+streams.  There is no CPU fallback: if the library or a CUDA device is missing,
+the constructor raises.
+"""
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfewha.so")
+
+FLAG_GRAPH = 1
+FLAG_WARM_RESIDUAL = 2
+
+ERRORS = {
+    -1: "invalid argument",
+    -2: "geometry",
+    -3: "out of device memory",
+    -4: "CUDA error",
+    -5: "non-finite input",
+    -6: "size limit",
+}
+
+
+class FewhaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("FEWHA error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class Telescope(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("obs", ctypes.c_double)]
+
+
+class Wfs(ctypes.Structure):
+    _fields_ = [("n_sub", ctypes.c_int), ("nb", ctypes.c_int), ("is_lgs", ctypes.c_int),
+                ("theta_x", ctypes.c_double), ("theta_y", ctypes.c_double),
+                ("H", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("cn2_weight", ctypes.c_double),
+                ("spacing", ctypes.c_double), ("n", ctypes.c_int), ("levels", ctypes.c_int)]
+
+
+class Dm(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("spacing", ctypes.c_double), ("n_act", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("gain", ctypes.c_double),
+                ("r0", ctypes.c_double), ("L0", ctypes.c_double), ("iters", ctypes.c_int),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+_VP = ctypes.c_void_p
+_OPS = ["fewha_apply_M", "fewha_rhs", "fewha_dwt", "fewha_idwt", "fewha_project",
+        "fewha_project_adj", "fewha_slopes", "fewha_slopes_adj", "fewha_noise_weight",
+        "fewha_forward", "fewha_forward_adj", "fewha_fit", "fewha_fit_adj"]
+EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_error",
+           "fewha_sizes", "fewha_update_params", "fewha_reset", "fewha_reconstruct",
+           "fewha_reconstruct_f64", "fewha_reconstruct_host", "fewha_reconstruct_host_f64",
+           "fewha_check_input", "fewha_pcg", "fewha_get_diagonals"] + _OPS
+
+_lib = None
+
+
+def lib():
+    """Load libfewha.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfewha.so is missing: run `python -m paper_2202_11945_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    L.fewha_create.argtypes = [ctypes.POINTER(Telescope), ctypes.POINTER(Wfs), ctypes.c_int,
+                               ctypes.POINTER(Layer), ctypes.c_int, ctypes.POINTER(Dm),
+                               ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(_VP)]
+    L.fewha_create.restype = ctypes.c_int
+    L.fewha_destroy.argtypes = [_VP]
+    L.fewha_destroy.restype = None
+    L.fewha_last_error.argtypes = [_VP]
+    L.fewha_last_error.restype = ctypes.c_char_p
+    L.fewha_create_error.argtypes = []
+    L.fewha_create_error.restype = ctypes.c_char_p
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.fewha_sizes.argtypes = [_VP, i64p, i64p, i64p, i64p]
+    L.fewha_update_params.argtypes = [_VP, ctypes.POINTER(Params), _VP, _VP]
+    L.fewha_reset.argtypes = [_VP, _VP]
+    for name in ["fewha_reconstruct", "fewha_reconstruct_f64"]:
+        getattr(L, name).argtypes = [_VP, _VP, _VP, _VP, _VP]
+    for name in ["fewha_reconstruct_host", "fewha_reconstruct_host_f64"]:
+        getattr(L, name).argtypes = [_VP, _VP, _VP, _VP]
+    L.fewha_check_input.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), _VP]
+    L.fewha_pcg.argtypes = [_VP, _VP, _VP, ctypes.c_int, _VP]
+    L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
+    for name in _OPS:
+        getattr(L, name).argtypes = [_VP, _VP, _VP, _VP]
+    for name in EXPORTS:
+        if name not in ("fewha_destroy", "fewha_last_error", "fewha_create_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def structs_from_workload(wl, precision=32, flags=FLAG_GRAPH):
+    """C structs of a workload description (see synth.configs for the dict format)."""
+    tel = Telescope(wl["D"], wl["obs"])
+    wfs = (Wfs * len(wl["wfs"]))(*[
+        Wfs(w["n_sub"], w["nb"], 1 if w["lgs"] else 0, w["theta"][0], w["theta"][1],
+            w["H"] if w["lgs"] else 0.0, w["sigma"]) for w in wl["wfs"]])
+    layers = (Layer * len(wl["layers"]))(*[
+        Layer(L["h"], L["w"], L["delta"], L["n"], L["levels"]) for L in wl["layers"]])
+    dms = (Dm * len(wl["dms"]))(*[Dm(m["h"], m["spacing"], m["n_act"]) for m in wl["dms"]])
+    p = wl["params"]
+    params = Params(p["alpha"], p.get("tau", 0.0), p.get("gain", 1.0), p["r0"], p["L0"],
+                    p["iters"], precision, flags)
+    return tel, wfs, layers, dms, params
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Reconstructor:
+    """One FEWHA instance on the current CUDA device (a handle of the C library)."""
+
+    def __init__(self, wl, precision=32, graph=True, warm_residual=False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("FEWHA needs a CUDA device; there is no CPU path")
+        torch.cuda.init()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.precision = precision
+        self.dtype = torch.float32 if precision == 32 else torch.float64
+        flags = (FLAG_GRAPH if graph else 0) | (FLAG_WARM_RESIDUAL if warm_residual else 0)
+        self._structs = structs_from_workload(wl, precision, flags)
+        tel, wfs, layers, dms, params = self._structs
+        self.L = lib()
+        h = _VP()
+        rc = self.L.fewha_create(ctypes.byref(tel), wfs, len(wfs), layers, len(layers), dms,
+                                 len(dms), ctypes.byref(params), ctypes.byref(h))
+        if rc != 0:
+            raise FewhaError(rc, self.L.fewha_create_error().decode())
+        self.h = h
+        ns, nc, na, nn = (ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64())
+        self._check(self.L.fewha_sizes(h, ctypes.byref(ns), ctypes.byref(nc), ctypes.byref(na),
+                                       ctypes.byref(nn)))
+        self.n_slopes, self.n_coeffs, self.n_act, self.n_nodes = ns.value, nc.value, na.value, nn.value
+
+    # -- plumbing ---------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise FewhaError(rc, self.L.fewha_last_error(self.h).decode())
+
+    def _dev(self, t, n, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype
+                and t.is_contiguous() and t.numel() == n):
+            raise ValueError("%s must be a contiguous %s CUDA tensor of %d elements"
+                             % (name, self.dtype, n))
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _new(self, n):
+        return torch.empty(n, dtype=self.dtype, device=self.device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fewha_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- frame ------------------------------------------------------------------
+    def reconstruct(self, slopes, x_warm=None, dm_out=None, stream=None):
+        """One frame of Algorithm 1 on device tensors; returns the DM commands."""
+        if dm_out is None:
+            dm_out = self._new(self.n_act)
+        s = self._dev(slopes, self.n_slopes, "slopes")
+        x = self._dev(x_warm, self.n_coeffs, "x_warm") if x_warm is not None else None
+        d = self._dev(dm_out, self.n_act, "dm_out")
+        fn = self.L.fewha_reconstruct if self.precision == 32 else self.L.fewha_reconstruct_f64
+        self._check(fn(self.h, s, x, d, _stream(stream)))
+        return dm_out
+
+    def reconstruct_host(self, slopes, dm_out, stream=None):
+        """One frame from and to host tensors (copies inside the call; synchronous)."""
+        for t, n, name in ((slopes, self.n_slopes, "slopes"), (dm_out, self.n_act, "dm_out")):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("%s must be a contiguous host %s tensor of %d" % (name, self.dtype, n))
+        fn = self.L.fewha_reconstruct_host if self.precision == 32 else self.L.fewha_reconstruct_host_f64
+        self._check(fn(self.h, ctypes.c_void_p(slopes.data_ptr()), ctypes.c_void_p(dm_out.data_ptr()),
+                       _stream(stream)))
+        return dm_out
+
+    def check_input(self, stream=None):
+        flag = ctypes.c_int(0)
+        self._check(self.L.fewha_check_input(self.h, ctypes.byref(flag), _stream(stream)))
+        return bool(flag.value)
+
+    def reset(self, stream=None):
+        self._check(self.L.fewha_reset(self.h, _stream(stream)))
+
+    def update_params(self, alpha=None, tau=None, gain=None, r0=None, L0=None, iters=None,
+                      cn2_weights=None, sigmas=None, graph=None, warm_residual=None):
+        tel, wfs, layers, dms, p = self._structs
+        if alpha is not None:
+            p.alpha = alpha
+        if tau is not None:
+            p.tau = tau
+        if gain is not None:
+            p.gain = gain
+        if r0 is not None:
+            p.r0 = r0
+        if L0 is not None:
+            p.L0 = L0
+        if iters is not None:
+            p.iters = iters
+        if graph is not None:
+            p.flags = (p.flags & ~FLAG_GRAPH) | (FLAG_GRAPH if graph else 0)
+        if warm_residual is not None:
+            p.flags = (p.flags & ~FLAG_WARM_RESIDUAL) | (FLAG_WARM_RESIDUAL if warm_residual else 0)
+        w = s = None
+        if cn2_weights is not None:
+            w = (ctypes.c_double * len(layers))(*cn2_weights)
+        if sigmas is not None:
+            s = (ctypes.c_double * len(wfs))(*sigmas)
+        self._check(self.L.fewha_update_params(self.h, ctypes.byref(p), w, s))
+
+    # -- operators ----------------------------------------------------------------
+    def _op(self, name, x, n_in, n_out, out=None, stream=None):
+        if out is None:
+            out = self._new(n_out)
+        self._check(getattr(self.L, name)(self.h, self._dev(x, n_in, "input"),
+                                          self._dev(out, n_out, "output"), _stream(stream)))
+        return out
+
+    def apply_M(self, c, out=None, stream=None):
+        return self._op("fewha_apply_M", c, self.n_coeffs, self.n_coeffs, out, stream)
+
+    def rhs(self, s, out=None, stream=None):
+        return self._op("fewha_rhs", s, self.n_slopes, self.n_coeffs, out, stream)
+
+    def dwt(self, phi, out=None, stream=None):
+        return self._op("fewha_dwt", phi, self.n_coeffs, self.n_coeffs, out, stream)
+
+    def idwt(self, c, out=None, stream=None):
+        return self._op("fewha_idwt", c, self.n_coeffs, self.n_coeffs, out, stream)
+
+    def project(self, phi, out=None, stream=None):
+        return self._op("fewha_project", phi, self.n_coeffs, self.n_nodes, out, stream)
+
+    def project_adj(self, v, out=None, stream=None):
+        return self._op("fewha_project_adj", v, self.n_nodes, self.n_coeffs, out, stream)
+
+    def slopes(self, v, out=None, stream=None):
+        return self._op("fewha_slopes", v, self.n_nodes, self.n_slopes, out, stream)
+
+    def slopes_adj(self, s, out=None, stream=None):
+        return self._op("fewha_slopes_adj", s, self.n_slopes, self.n_nodes, out, stream)
+
+    def noise_weight(self, s, out=None, stream=None):
+        return self._op("fewha_noise_weight", s, self.n_slopes, self.n_slopes, out, stream)
+
+    def forward(self, phi, out=None, stream=None):
+        return self._op("fewha_forward", phi, self.n_coeffs, self.n_slopes, out, stream)
+
+    def forward_adj(self, s, out=None, stream=None):
+        return self._op("fewha_forward_adj", s, self.n_slopes, self.n_coeffs, out, stream)
+
+    def fit(self, c, out=None, stream=None):
+        return self._op("fewha_fit", c, self.n_coeffs, self.n_act, out, stream)
+
+    def fit_adj(self, a, out=None, stream=None):
+        return self._op("fewha_fit_adj", a, self.n_act, self.n_coeffs, out, stream)
+
+    def pcg(self, b, c, iters, stream=None):
+        """`iters` PCG iterations on M c = b, c updated in place."""
+        self._check(self.L.fewha_pcg(self.h, self._dev(b, self.n_coeffs, "b"),
+                                     self._dev(c, self.n_coeffs, "c"), int(iters), _stream(stream)))
+        return c
+
+    def diagonals(self, stream=None):
+        D = self._new(self.n_coeffs)
+        J = self._new(self.n_coeffs)
+        self._check(self.L.fewha_get_diagonals(self.h, self._dev(D, self.n_coeffs, "D"),
+                                               self._dev(J, self.n_coeffs, "J"), _stream(stream)))
+        return D, J

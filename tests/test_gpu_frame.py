@@ -1,0 +1,143 @@
+"""Frame-level parity (Algorithm 1, open loop) of the CUDA path against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from tests.gpu_common import TOL_FRAME, recon, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+SEQ = [("tiny_scao", 64, 20), ("tiny_scao", 32, 20), ("tiny_mcao", 64, 10), ("tiny_mcao", 32, 10),
+       ("maory", 32, 10), ("maory", 64, 3)]
+
+_slopes = {}
+
+
+def slopes(name, t):
+    key = (name, t)
+    if key not in _slopes:
+        wl = synth.workload_by_name(name)
+        if name not in _slopes:
+            _slopes[name] = synth.TruthAtmosphere(wl["truth"])
+        _slopes[key] = synth.simulate_slopes(wl, t, atm=_slopes[name])
+    return _slopes[key]
+
+
+@pytest.mark.parametrize("name,prec,frames", SEQ, ids=lambda x: str(x))
+def test_warm_started_sequence_matches_oracle(name, prec, frames):
+    """Frame 0 cold, then warm-started frames; DM commands within the stated tolerance."""
+    ref = O.Reconstructor(synth.workload_by_name(name))
+    R = recon(name, prec)
+    x = torch.zeros(R.n_coeffs, dtype=R.dtype, device="cuda")
+    worst = 0.0
+    for t in range(frames):
+        s = slopes(name, t)
+        a_ref = ref.frame(s)
+        a = to_np(R.reconstruct(to_dev(s, prec), x_warm=x))
+        err = rel_l2(a, a_ref)
+        worst = max(worst, err)
+        assert err <= TOL_FRAME[prec], (t, err)
+    c_err = rel_l2(to_np(x), ref.c)
+    assert c_err < 1e3 * TOL_FRAME[prec]
+    R.close()
+
+
+def test_graph_and_stream_forms_are_bitwise_identical():
+    A = recon("tiny_mcao", 32, graph=True)
+    B = recon("tiny_mcao", 32, graph=False)
+    for t in range(4):
+        s = to_dev(slopes("tiny_mcao", t), 32)
+        a = to_np(A.reconstruct(s))
+        b = to_np(B.reconstruct(s))
+        assert np.array_equal(a, b), t
+
+
+def test_runs_are_deterministic():
+    outs = []
+    for _ in range(2):
+        R = recon("maory", 32)
+        for t in range(2):
+            a = to_np(R.reconstruct(to_dev(slopes("maory", t), 32)))
+        outs.append(a)
+        R.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_host_entry_matches_device_entry():
+    A = recon("tiny_mcao", 32)
+    B = recon("tiny_mcao", 32)
+    for t in range(3):
+        s = slopes("tiny_mcao", t)
+        a = to_np(A.reconstruct(to_dev(s, 32)))
+        hs = torch.as_tensor(s, dtype=torch.float32).pin_memory()
+        hd = torch.empty(B.n_act, dtype=torch.float32).pin_memory()
+        B.reconstruct_host(hs, hd)
+        assert np.array_equal(a, hd.double().numpy())
+
+
+def test_zero_slopes_and_zero_iterations():
+    R = recon("tiny_mcao", 64)
+    a = to_np(R.reconstruct(torch.zeros(R.n_slopes, dtype=R.dtype, device="cuda")))
+    assert np.all(a == 0)
+    wl = synth.tiny_mcao()
+    wl["params"]["iters"] = 0
+    from paper_2202_11945_gb300 import Reconstructor
+    R0 = Reconstructor(wl, precision=64)
+    a = to_np(R0.reconstruct(to_dev(slopes("tiny_mcao", 0), 64)))
+    assert np.all(a == 0)                      # c stays at the zero warm start
+
+
+def test_nonfinite_slopes_are_flagged():
+    from paper_2202_11945_gb300 import FewhaError
+    R = recon("tiny_scao", 32)
+    s = slopes("tiny_scao", 0).copy()
+    s[5] = np.nan
+    R.reconstruct(to_dev(s, 32))
+    assert R.check_input() is True
+    assert R.check_input() is False            # cleared after reading
+    hs = torch.as_tensor(s, dtype=torch.float32)
+    hd = torch.empty(R.n_act, dtype=torch.float32)
+    with pytest.raises(FewhaError) as e:
+        R.reconstruct_host(hs, hd)
+    assert e.value.code == -5
+
+
+def test_update_params_matches_rebuilt_oracle():
+    wl = synth.tiny_mcao()
+    R = recon("tiny_mcao", 64)
+    new_w = [0.5, 0.3, 0.2]
+    new_sig = [0.15, 0.12, 0.03]
+    R.update_params(alpha=2.5, gain=0.7, cn2_weights=new_w, sigmas=new_sig, iters=3)
+    for L, w in zip(wl["layers"], new_w):
+        L["w"] = w
+    for W, sg in zip(wl["wfs"], new_sig):
+        W["sigma"] = sg
+    wl["params"].update(alpha=2.5, gain=0.7, iters=3)
+    ref = O.Reconstructor(wl)
+    for t in range(3):
+        s = slopes("tiny_mcao", t)
+        a = to_np(R.reconstruct(to_dev(s, 64)))
+        assert rel_l2(a, ref.frame(s)) < TOL_FRAME[64]
+
+
+def test_warm_residual_option():
+    wl = synth.tiny_mcao()
+    ref = O.Reconstructor(wl)
+    R = recon("tiny_mcao", 64, warm_residual=True)
+    for t in range(4):
+        s = slopes("tiny_mcao", t)
+        a_ref = ref.frame(s, warm_residual=True)
+        assert rel_l2(to_np(R.reconstruct(to_dev(s, 64))), a_ref) < TOL_FRAME[64], t
+
+
+def test_external_and_internal_warm_state_agree():
+    A = recon("tiny_scao", 64)
+    B = recon("tiny_scao", 64)
+    x = torch.zeros(A.n_coeffs, dtype=torch.float64, device="cuda")
+    for t in range(3):
+        s = to_dev(slopes("tiny_scao", t), 64)
+        a = to_np(A.reconstruct(s, x_warm=x))
+        b = to_np(B.reconstruct(s))
+        assert np.array_equal(a, b)
