@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""FEWHA benchmark: MAORY-size frames/s and p99 frame latency on GB300.
+
+One step = one frame of Algorithm 1 (right-hand side, explicit initial residual, 4 PCG
+iterations, DM fit and gain) of the MAORY-size instance (39 m, 6 LGS 80x80 + 3 NGS
+2x2, 9 layers, 3 DMs), warm-started from the previous frame, slopes resident on the
+device.  Timed per frame with CUDA events; a 512 MiB memset flushes L2 between frames
+(outside the events).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (single thread) on the same workload.
+With N > 1 (torchrun) every rank runs an independent replica (the path does not
+shard); rank 0 prints the aggregate.
+"""
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")     # the CPU baseline runs single-threaded
+
+import argparse
+import hashlib
+import json
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "FEWHA frames/s and p99 frame latency, MAORY-size, FP32 form vs FP64 plain, 1 GB300"
+UNIT = "frames/s"
+N_FRAMES_INPUT = 8          # distinct seeded frames, cycled through the timed loop
+FLUSH_BYTES = 512 << 20     # > 129 MB L2
+KERNEL_SRC = os.path.join(ROOT, "paper_2202_11945_gb300", "csrc", "fewha_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_maory_fp32.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-frames", type=int, default=20, help="oracle frames of the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(wl):
+    atm = synth.TruthAtmosphere(wl["truth"])
+    return [synth.simulate_slopes(wl, t, atm=atm) for t in range(N_FRAMES_INPUT)]
+
+
+def time_frames(R, S, steps, warmup, flush, dm):
+    """Per-frame device times (ms) of `steps` warm-started frames, L2 flushed between."""
+    n = S.shape[0]
+    for k in range(warmup):
+        R.reconstruct(S[k % n], dm_out=dm)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record()
+        R.reconstruct(S[k % n], dm_out=dm)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def stage_bytes(R, b):
+    """Algorithmic (compulsory) bytes per launch of each hot-path stage."""
+    nc, nn, ns, na = R.n_coeffs, R.n_nodes, R.n_slopes, R.n_act
+    return {
+        "idwt": 4 * nc * b,               # read z, p; write p, phi
+        "sensor": (nc + nn) * b,          # read phi; write aperture-node adjoint u
+        "layer": (nn + 3 * nc) * b,       # read u, p, D; write q
+        "vector": 8 * nc * b,             # read c, p, r, q, J^-1; write c, r, z
+        "rhs": (ns + nn) * b,             # read slopes; write u
+        "fit": (nc + 3 * na) * b,         # read phi, a_prev; write a_prev, dm
+    }
+
+
+def stage_launches(iters):
+    return {"idwt": iters + 2, "sensor": iters + 1, "layer": iters + 2, "vector": iters + 1,
+            "rhs": 1, "fit": 1}
+
+
+def time_stages(R, flush, reps=200):
+    out = {}
+    for st in ("idwt", "sensor", "layer", "vector", "rhs", "fit"):
+        R.bench_stage(st, 3)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.bench_stage(st, reps)
+        b.record()
+        torch.cuda.synchronize()
+        out[st] = a.elapsed_time(b) / reps
+    return out
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary.
+
+    The summary records the SHA-256 of the kernel source it was taken with; a changed
+    kernel makes the figure stale and it is dropped (null).
+    """
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if kv.get("kernel_source_sha256") != sha:
+        return None, kv.get("stage")
+    return float(kv["dram_bytes_per_launch"]), kv.get("stage")
+
+
+def cpu_baseline(wl, frames, S_np, R_gpu_factory):
+    """The FP64 oracle, single thread, on the first `frames` frames; plus parity."""
+    import oracle as O
+    t0 = time.perf_counter()
+    ref = O.Reconstructor(wl)
+    t_setup = time.perf_counter() - t0
+    refs = []
+    t0 = time.perf_counter()
+    for k in range(frames):
+        refs.append(ref.frame(S_np[k % len(S_np)]))
+    t = time.perf_counter() - t0
+    parity = {}
+    for prec in (32, 64):
+        R = R_gpu_factory(prec)
+        dt = torch.float32 if prec == 32 else torch.float64
+        worst = 0.0
+        for k in range(frames):
+            a = R.reconstruct(torch.as_tensor(S_np[k % len(S_np)], dtype=dt, device="cuda"))
+            a = a.double().cpu().numpy()
+            worst = max(worst, float(np.linalg.norm(a - refs[k]) / np.linalg.norm(refs[k])))
+        parity["fp%d_max_rel_l2_dm" % prec] = worst
+        R.close()
+    return {"value": frames / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d warm-started MAORY frames (frame 0 cold), numpy FP64, 1 thread; "
+                      "set-up (D, exact J) %.2f s not timed" % (frames, t_setup)}, parity
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    wl = synth.maory()
+    S_np = make_inputs(wl)
+    ref = O.Reconstructor(wl)
+    # a bounded sample: at most 2 warm-up and 60 timed frames (~0.3-0.5 s each)
+    warm = min(args.warmup, 2)
+    steps = min(args.steps, 60)
+    for k in range(warm):
+        ref.frame(S_np[k % len(S_np)])
+    ts = []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        ref.frame(S_np[(warm + k) % len(S_np)])
+        ts.append(time.perf_counter() - t0)
+    ts = np.array(ts) * 1e3
+    value = 1e3 / ts.mean()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": float(ts.mean()),
+        "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl["name"], "iters": wl["params"]["iters"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d warm-started MAORY frames after %d warm-up (requested "
+                                   "%d/%d), numpy FP64, 1 thread" % (steps, warm, args.steps,
+                                                                      args.warmup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    assert args.warmup >= 3, "at least 3 warm-up frames"
+    torch.cuda.set_device(local)
+    from paper_2202_11945_gb300 import Reconstructor
+
+    wl = synth.maory()
+    S_np = make_inputs(wl)
+    S32 = torch.as_tensor(np.stack(S_np), dtype=torch.float32, device="cuda").contiguous()
+    S64 = torch.as_tensor(np.stack(S_np), dtype=torch.float64, device="cuda").contiguous()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    R32 = Reconstructor(wl, precision=32, graph=True)
+    R64 = Reconstructor(wl, precision=64, graph=False)
+    dm32 = torch.empty(R32.n_act, dtype=torch.float32, device="cuda")
+    dm64 = torch.empty(R64.n_act, dtype=torch.float64, device="cuda")
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t32 = time_frames(R32, S32, args.steps, args.warmup, flush, dm32)
+    torch.cuda.synchronize()
+    t64 = time_frames(R64, S64, args.steps, args.warmup, flush, dm64)
+    torch.cuda.synchronize()
+    # end to end through the host-buffer entry point (pinned buffers, copies inside)
+    Re = Reconstructor(wl, precision=32, graph=True)
+    hs = [torch.as_tensor(s, dtype=torch.float32).pin_memory() for s in S_np]
+    hd = torch.empty(Re.n_act, dtype=torch.float32).pin_memory()
+    for k in range(args.warmup):
+        Re.reconstruct_host(hs[k % len(hs)], hd)
+    e2e_steps = min(args.steps, 1000)
+    te = []
+    for k in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Re.reconstruct_host(hs[k % len(hs)], hd)
+        te.append(time.perf_counter() - t0)
+    te = np.array(te) * 1e3
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    # per-stage kernel times (dedicated handle; back-to-back launches after a flush)
+    Rb = Reconstructor(wl, precision=32, graph=False)
+    Rb.reconstruct(S32[0])
+    st_ms = time_stages(Rb, flush)
+    nbytes = stage_bytes(Rb, 4)
+    launches = stage_launches(wl["params"]["iters"])
+    share = {k: st_ms[k] * launches[k] for k in st_ms}
+    dom = max(share, key=share.get)
+    peak, peak_kind = measured_peaks()
+    achieved = nbytes[dom] / (st_ms[dom] * 1e-3) / 1e9
+    traffic, traffic_stage = recorded_traffic()
+    if traffic_stage is not None and traffic_stage != dom:
+        traffic = None
+    Rb.close()
+
+    total32 = float(t32.sum())
+    total64 = float(t64.sum())
+    tot_e2e = float(te.sum())
+    if world > 1:
+        import torch.distributed as dist
+        v = torch.tensor([total32, total64, tot_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        total32, total64, tot_e2e = [float(x) for x in v.tolist()]
+    value = world * args.steps / (total32 * 1e-3)
+
+    base, parity = (None, None)
+    if rank == 0 and world == 1:
+        base, parity = cpu_baseline(wl, args.cpu_frames, S_np,
+                                    lambda p: Reconstructor(wl, precision=p, graph=(p == 32)))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total32 / args.steps,
+            "p50_ms": float(np.percentile(t32, 50)), "p99_ms": float(np.percentile(t32, 99)),
+            "max_ms": float(t32.max()),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded 35-layer von Karman atmosphere with frozen flow, "
+                    "simulated SH slopes + noise; %d distinct frames cycled" % N_FRAMES_INPUT,
+            "config": {"workload": wl["name"], "n_coeffs": R32.n_coeffs, "n_slopes": R32.n_slopes,
+                       "n_act": R32.n_act, "iters": wl["params"]["iters"], "warm_start": True,
+                       "initial_residual": "explicit b - M c0", "form": "FP32 operators, FP64 "
+                       "dots, CUDA graph", "l2": "512 MiB memset between timed frames",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "fp64_plain": {"value": world * args.steps / (total64 * 1e-3), "unit": UNIT,
+                           "ms_per_step": total64 / args.steps,
+                           "p50_ms": float(np.percentile(t64, 50)),
+                           "p99_ms": float(np.percentile(t64, 99)), "form": "FP64, stream launches"},
+            "clocks": clk,
+            "e2e": {"value": world * e2e_steps / (tot_e2e * 1e-3), "unit": UNIT,
+                    "p99_ms": float(np.percentile(te, 99)),
+                    "h2d_bytes_per_step": R32.n_slopes * 4, "d2h_bytes_per_step": R32.n_act * 4 + 4,
+                    "api": "fewha_reconstruct_host (pinned host buffers, wall clock)"},
+            "gpu_launches": R32.frame_launches() * args.steps,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": nbytes[dom],
+                         "launch_us": st_ms[dom] * 1e3,
+                         "note": "single MAORY frame: L2-resident, latency-bound"},
+            "stages_us": {k: round(v * 1e3, 3) for k, v in st_ms.items()},
+            "stage_share": {k: round(v / sum(share.values()), 4) for k, v in share.items()},
+            "cpu_baseline": base,
+            "parity": parity,
+        }
+        print(json.dumps(line), flush=True)
+    for R in (R32, R64, Re):
+        R.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -212,6 +212,25 @@ int fewha_pcg(fewha_handle* h, const void* d_b, void* d_c, int iters, void* stre
  * D of Sec. 3.1 and J of Eq. (7). */
 int fewha_get_diagonals(fewha_handle* h, void* d_D, void* d_J, void* stream);
 
+/* ---- measurement --------------------------------------------------------------- */
+
+/* Hot-path stages of one PCG iteration and of the frame, for timing one kernel alone. */
+#define FEWHA_STAGE_IDWT 0      /* p = z + beta p and phi = W^T p, one CTA per layer       */
+#define FEWHA_STAGE_SENSOR 1    /* P_g, Gamma_g, C_hat_g^-1, Gamma_g^T, one CTA per sensor  */
+#define FEWHA_STAGE_LAYER 2     /* sum_g P_g^T, W, + alpha D p, p.q, one CTA per layer      */
+#define FEWHA_STAGE_VECTOR 3    /* x += a p, r -= a q, z = J^-1 r, r.z                     */
+#define FEWHA_STAGE_RHS 4       /* C_hat^-1 and Gamma^T of the measured slopes             */
+#define FEWHA_STAGE_FIT 5       /* DM fit and gain                                          */
+#define FEWHA_NUM_STAGES 6
+
+/* Enqueue `reps` back-to-back launches of one stage's kernel on `stream`, working on the
+ * handle's internal buffers (for timing with events around the call).  It overwrites
+ * the handle's warm-start state: use a handle dedicated to measurement, or call
+ * fewha_reset afterwards.  Asynchronous. */
+int fewha_bench_stage(fewha_handle* h, int stage, int reps, void* stream);
+/* Kernel launches one frame enqueues (for the launch count of a timed region). */
+int fewha_frame_launches(const fewha_handle* h, int* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -561,6 +561,53 @@ int op_dispatch(fewha_handle* H, int op, const void* in, void* out, int iters, c
     }
 }
 
+// Back-to-back launches of one hot-path kernel on the internal buffers (timing only).
+template <class T>
+int bench_stage(fewha_handle* H, int stage, int reps, cudaStream_t st) {
+    const Desc<T> d = make_desc<T>(H);
+    T* p = static_cast<T*>(H->p);
+    T* phi = static_cast<T*>(H->phi);
+    T* u = static_cast<T*>(H->u);
+    T* q = static_cast<T*>(H->q);
+    int rc = 0;
+    for (int i = 0; i < reps && rc == 0; ++i) {
+        switch (stage) {
+            case FEWHA_STAGE_IDWT: {
+                LayerArgs<T> a = layer_args<T>(H, p, phi);
+                a.pupd = p;
+                a.zupd = static_cast<const T*>(H->z);
+                a.iter = 1;
+                rc = launch_layer<T, LSRC_COEF, LDST_PHI, true>(H, d, a, st);
+                break;
+            }
+            case FEWHA_STAGE_SENSOR:
+                rc = launch_sensor<T, SSRC_PHI, true, SDST_ADJ>(H, d, phi, u, st);
+                break;
+            case FEWHA_STAGE_LAYER: {
+                LayerArgs<T> a = layer_args<T>(H, u, q);
+                a.pin = p;
+                a.iter = PQ_SCRATCH_SLOT;
+                a.zero_piston = 1;
+                rc = launch_layer<T, LSRC_NODES, LDST_APPLY, false>(H, d, a, st);
+                break;
+            }
+            case FEWHA_STAGE_VECTOR:
+                k_vec<T, V_UPDATE><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, static_cast<T*>(H->c), 0));
+                CK(cudaGetLastError(), "k_vec launch");
+                break;
+            case FEWHA_STAGE_RHS:
+                rc = launch_sensor<T, SSRC_SLOPES, true, SDST_ADJ>(H, d, static_cast<const T*>(H->s_tmp), u, st);
+                break;
+            case FEWHA_STAGE_FIT:
+                k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, static_cast<T*>(H->a_prev),
+                                                                       static_cast<T*>(H->dm_tmp), 1);
+                CK(cudaGetLastError(), "k_fit launch");
+                break;
+        }
+    }
+    return rc;
+}
+
 int op_entry(fewha_handle* H, int op, const void* in, void* out, int iters, void* stream) {
     if (!H) return FEWHA_ERR_INVALID_ARG;
     if (!in || !out) return fail(H, FEWHA_ERR_INVALID_ARG, "null pointer");
@@ -722,6 +769,24 @@ int fewha_fit_adj(fewha_handle* h, const void* dm, void* c, void* st) { return o
 int fewha_pcg(fewha_handle* h, const void* b, void* c, int iters, void* st) {
     if (h && (iters < 0 || iters > FEWHA_MAX_ITERS)) return fail(h, FEWHA_ERR_LIMIT, "iters out of range");
     return op_entry(h, 13, b, c, iters, st);
+}
+
+int fewha_bench_stage(fewha_handle* H, int stage, int reps, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (stage < 0 || stage >= FEWHA_NUM_STAGES || reps < 1)
+        return fail(H, FEWHA_ERR_INVALID_ARG, "bad stage or repetition count");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32 ? bench_stage<float>(H, stage, reps, st)
+                              : bench_stage<double>(H, stage, reps, st);
+}
+
+int fewha_frame_launches(const fewha_handle* H, int* launches) {
+    if (!H || !launches) return FEWHA_ERR_INVALID_ARG;
+    const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
+    // RHS 2, initial residual 4 (explicit) or 1 (warm), 4 per iteration, fit 2
+    *launches = 2 + (warm ? 1 : 4) + 4 * H->params.iters + 2;
+    return FEWHA_OK;
 }
 
 int fewha_get_diagonals(fewha_handle* H, void* d_D, void* d_J, void* stream) {

@@ -65,7 +65,10 @@ _OPS = ["fewha_apply_M", "fewha_rhs", "fewha_dwt", "fewha_idwt", "fewha_project"
 EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_error",
            "fewha_sizes", "fewha_update_params", "fewha_reset", "fewha_reconstruct",
            "fewha_reconstruct_f64", "fewha_reconstruct_host", "fewha_reconstruct_host_f64",
-           "fewha_check_input", "fewha_pcg", "fewha_get_diagonals"] + _OPS
+           "fewha_check_input", "fewha_pcg", "fewha_get_diagonals", "fewha_bench_stage",
+           "fewha_frame_launches"] + _OPS
+
+STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5}
 
 _lib = None
 
@@ -99,6 +102,8 @@ def lib():
     L.fewha_check_input.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), _VP]
     L.fewha_pcg.argtypes = [_VP, _VP, _VP, ctypes.c_int, _VP]
     L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
+    L.fewha_bench_stage.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
+    L.fewha_frame_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
     for name in _OPS:
         getattr(L, name).argtypes = [_VP, _VP, _VP, _VP]
     for name in EXPORTS:
@@ -288,6 +293,15 @@ class Reconstructor:
         self._check(self.L.fewha_pcg(self.h, self._dev(b, self.n_coeffs, "b"),
                                      self._dev(c, self.n_coeffs, "c"), int(iters), _stream(stream)))
         return c
+
+    def bench_stage(self, stage, reps, stream=None):
+        """Enqueue `reps` launches of one hot-path kernel (timing; clobbers the warm state)."""
+        self._check(self.L.fewha_bench_stage(self.h, STAGES[stage], int(reps), _stream(stream)))
+
+    def frame_launches(self):
+        n = ctypes.c_int(0)
+        self._check(self.L.fewha_frame_launches(self.h, ctypes.byref(n)))
+        return n.value
 
     def diagonals(self, stream=None):
         D = self._new(self.n_coeffs)
