@@ -231,6 +231,31 @@ int fewha_bench_stage(fewha_handle* h, int stage, int reps, void* stream);
 /* Kernel launches one frame enqueues (for the launch count of a timed region). */
 int fewha_frame_launches(const fewha_handle* h, int* launches);
 
+/* ---- no-allocation variant ------------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that may not
+ * allocate device memory at the time they need the operator.  A real-time control
+ * loop typically allocates everything at start-up and then forbids cudaMalloc and
+ * cudaFree, which can synchronise the whole device and take unbounded time; a
+ * monitoring thread of such a loop may still want q = M c (for instance to check a
+ * residual) without touching the handle's own scratch, which the frame uses.
+ *
+ * fewha_apply_M_noalloc computes the same q = M c as fewha_apply_M, but its
+ * intermediate layer values, aperture-node vector and p.q partial sums live in one
+ * static device block of FEWHA_NOALLOC_SCRATCH_BYTES inside the library (held by every
+ * GPU that loads the library until the process exits), not in the handle.  It calls
+ * no cudaMalloc, cudaFree or allocating routine.  It returns FEWHA_ERR_LIMIT, doing
+ * nothing, when the instance needs more scratch than the block holds: about
+ * (n_coeffs + n_nodes) elements plus 512 bytes (the MAORY-size instance needs 1.46 MB in
+ * double precision).  The first call on each device looks up the block's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the one block and leave their intermediates in it:
+ * calls whose device work overlaps (different streams, or different handles on one
+ * device) race on it and must be serialised by the caller.  Asynchronous on `stream`;
+ * d_c and d_q are device pointers of the handle's element type. */
+#define FEWHA_NOALLOC_SCRATCH_BYTES (2u << 20)
+#define FEWHA_NOALLOC_MAX_DEVICES 64
+int fewha_apply_M_noalloc(fewha_handle* h, const void* d_c, void* d_q, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -617,6 +618,65 @@ int op_entry(fewha_handle* H, int op, const void* in, void* out, int iters, void
                               : op_dispatch<double>(H, op, in, out, iters, st);
 }
 
+// ---------------------------------------------------------------- no-allocation M-apply
+// Scratch of fewha_apply_M_noalloc: a fixed 2 MiB block in this library's device image.
+// Every GPU that loads the library holds it until the process exits.  In host code the
+// name below is only a host-side stand-in: its device address comes from
+// cudaGetSymbolAddress, taken once per device by noalloc_scratch().
+static __device__ __align__(256) unsigned char fewha_noalloc_scratch[FEWHA_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[FEWHA_NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch block on the current device (set up on first use).
+int noalloc_scratch(fewha_handle* H, unsigned char** out) {
+    if (H->device < 0 || H->device >= FEWHA_NOALLOC_MAX_DEVICES)
+        return fail(H, FEWHA_ERR_LIMIT, "fewha_apply_M_noalloc: device ordinal above the scratch table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[H->device]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, fewha_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(H, e, "fewha_apply_M_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[H->device] = ptr;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[H->device]);
+    return FEWHA_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+template <class T>
+int apply_M_noalloc(fewha_handle* H, const T* x, T* qout, cudaStream_t st) {
+    const size_t b_phi = round256(static_cast<size_t>(H->setup.n_c) * sizeof(T));
+    const size_t b_u = round256(static_cast<size_t>(H->setup.n_nodes) * sizeof(T));
+    const size_t b_pq = round256(static_cast<size_t>(MAXL) * sizeof(double));
+    const size_t need = b_phi + b_u + b_pq;
+    if (need > FEWHA_NOALLOC_SCRATCH_BYTES)
+        return fail(H, FEWHA_ERR_LIMIT,
+                    "fewha_apply_M_noalloc: this instance needs " + std::to_string(need) +
+                        " bytes of scratch, more than the " +
+                        std::to_string(static_cast<size_t>(FEWHA_NOALLOC_SCRATCH_BYTES)) +
+                        "-byte static block; use fewha_apply_M");
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(H, &base);
+    if (rc) return rc;
+    T* phi = reinterpret_cast<T*>(base);
+    T* u = reinterpret_cast<T*>(base + b_phi);
+    double* pq = reinterpret_cast<double*>(base + b_phi + b_u);
+    // the block keeps the previous call's contents; the layer kernel writes only the
+    // p.q slots of the layers present, so clear all slots before use
+    CK(cudaMemsetAsync(pq, 0, b_pq, st), "fewha_apply_M_noalloc: clear partials");
+    const Desc<T> d = make_desc<T>(H);
+    if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, x, phi), st))) return rc;
+    if ((rc = launch_sensor<T, SSRC_PHI, true, SDST_ADJ>(H, d, phi, u, st))) return rc;
+    LayerArgs<T> a = layer_args<T>(H, u, qout);
+    a.pin = x;
+    a.iter = 0;
+    a.zero_piston = 1;
+    a.pcg.pqpart = pq;
+    return launch_layer<T, LSRC_NODES, LDST_APPLY, false>(H, d, a, st);
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -804,6 +864,16 @@ int fewha_get_diagonals(fewha_handle* H, void* d_D, void* d_J, void* stream) {
         }
     }
     return FEWHA_OK;
+}
+
+int fewha_apply_M_noalloc(fewha_handle* H, const void* d_c, void* d_q, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!d_c || !d_q) return fail(H, FEWHA_ERR_INVALID_ARG, "fewha_apply_M_noalloc: null pointer");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32
+               ? apply_M_noalloc<float>(H, static_cast<const float*>(d_c), static_cast<float*>(d_q), st)
+               : apply_M_noalloc<double>(H, static_cast<const double*>(d_c), static_cast<double*>(d_q), st);
 }
 
 }  // extern "C"

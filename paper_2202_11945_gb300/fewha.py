@@ -66,7 +66,7 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_sizes", "fewha_update_params", "fewha_reset", "fewha_reconstruct",
            "fewha_reconstruct_f64", "fewha_reconstruct_host", "fewha_reconstruct_host_f64",
            "fewha_check_input", "fewha_pcg", "fewha_get_diagonals", "fewha_bench_stage",
-           "fewha_frame_launches"] + _OPS
+           "fewha_frame_launches", "fewha_apply_M_noalloc"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5}
 
@@ -104,7 +104,7 @@ def lib():
     L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_bench_stage.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
     L.fewha_frame_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
-    for name in _OPS:
+    for name in _OPS + ["fewha_apply_M_noalloc"]:
         getattr(L, name).argtypes = [_VP, _VP, _VP, _VP]
     for name in EXPORTS:
         if name not in ("fewha_destroy", "fewha_last_error", "fewha_create_error"):
@@ -251,6 +251,10 @@ class Reconstructor:
 
     def apply_M(self, c, out=None, stream=None):
         return self._op("fewha_apply_M", c, self.n_coeffs, self.n_coeffs, out, stream)
+
+    def apply_M_noalloc(self, c, out=None, stream=None):
+        """q = M c with the library's static scratch block (see fewha_apply_M_noalloc)."""
+        return self._op("fewha_apply_M_noalloc", c, self.n_coeffs, self.n_coeffs, out, stream)
 
     def rhs(self, s, out=None, stream=None):
         return self._op("fewha_rhs", s, self.n_slopes, self.n_coeffs, out, stream)
