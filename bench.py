@@ -138,8 +138,10 @@ def stage_bytes(R, b):
     nc, nn, ns, na = R.n_coeffs, R.n_nodes, R.n_slopes, R.n_act
     return {
         "idwt": 4 * nc * b,               # read z, p; write p, phi
-        "sensor": (nc + nn) * b,          # read phi; write aperture-node adjoint u
-        "layer": (nn + 3 * nc) * b,       # read u, p, D; write q
+        "proj": (nc + nn) * b,            # read phi; write P phi on the aperture nodes
+        "sensor": 2 * nn * b,             # read P phi; write the aperture-node adjoint u
+        "projT": (nn + nc) * b,           # read u; write P^T u on the layers
+        "layer": 4 * nc * b,              # read P^T u, p, D; write q
         "vector": 8 * nc * b,             # read c, p, r, q, J^-1; write c, r, z
         "rhs": (ns + nn) * b,             # read slopes; write u
         "fit": (nc + 3 * na) * b,         # read phi, a_prev; write a_prev, dm
@@ -147,18 +149,27 @@ def stage_bytes(R, b):
 
 
 def stage_launches(iters):
-    return {"idwt": iters + 2, "sensor": iters + 1, "layer": iters + 2, "vector": iters + 1,
-            "rhs": 1, "fit": 1}
+    return {"idwt": iters + 2, "proj": iters + 1, "sensor": iters + 1, "projT": iters + 2,
+            "layer": iters + 2, "vector": iters + 1, "rhs": 1, "fit": 1}
 
 
-def time_stages(R, flush, reps=200):
+def time_stages(R, flush, reps=100):
+    """Per-launch device time of each stage's kernel: `reps` back-to-back launches
+    captured in a CUDA graph (so the host launch rate does not pace them), after a flush."""
     out = {}
-    for st in ("idwt", "sensor", "layer", "vector", "rhs", "fit"):
+    cap = torch.cuda.Stream()
+    for st in ("idwt", "proj", "sensor", "projT", "layer", "vector", "rhs", "fit"):
         R.bench_stage(st, 3)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            R.bench_stage(st, reps)
+        g.replay()
+        torch.cuda.synchronize()
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        R.bench_stage(st, reps)
+        g.replay()
         b.record()
         torch.cuda.synchronize()
         out[st] = a.elapsed_time(b) / reps

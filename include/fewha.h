@@ -216,12 +216,14 @@ int fewha_get_diagonals(fewha_handle* h, void* d_D, void* d_J, void* stream);
 
 /* Hot-path stages of one PCG iteration and of the frame, for timing one kernel alone. */
 #define FEWHA_STAGE_IDWT 0      /* p = z + beta p and phi = W^T p, one CTA per layer       */
-#define FEWHA_STAGE_SENSOR 1    /* P_g, Gamma_g, C_hat_g^-1, Gamma_g^T, one CTA per sensor  */
-#define FEWHA_STAGE_LAYER 2     /* sum_g P_g^T, W, + alpha D p, p.q, one CTA per layer      */
+#define FEWHA_STAGE_SENSOR 1    /* sum of the pair terms, Gamma_g, C_hat_g^-1, Gamma_g^T    */
+#define FEWHA_STAGE_LAYER 2     /* sum of the pair terms, W, + alpha D p, p.q               */
 #define FEWHA_STAGE_VECTOR 3    /* x += a p, r -= a q, z = J^-1 r, r.z                     */
 #define FEWHA_STAGE_RHS 4       /* C_hat^-1 and Gamma^T of the measured slopes             */
 #define FEWHA_STAGE_FIT 5       /* DM fit and gain                                          */
-#define FEWHA_NUM_STAGES 6
+#define FEWHA_STAGE_PROJ 6      /* R_y phi_l R_x^T per (sensor, layer) pair                  */
+#define FEWHA_STAGE_PROJT 7     /* R_y^T u_g R_x per (sensor, layer) pair                    */
+#define FEWHA_NUM_STAGES 8
 
 /* Enqueue `reps` back-to-back launches of one stage's kernel on `stream`, working on the
  * handle's internal buffers (for timing with events around the call).  It overwrites

@@ -6,11 +6,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
 
-#include "fewha_kernels.cuh"
+#include "fewha_pair.cuh"
 
 using namespace fewha;
 
@@ -49,8 +50,9 @@ struct fewha_handle {
         *rx_hi = nullptr, *sidx = nullptr, *cidx = nullptr, *di0 = nullptr, *dr_lo = nullptr,
         *dr_hi = nullptr, *basis_off = nullptr;
     double *pfy64 = nullptr, *pfx64 = nullptr, *basis = nullptr, *D64 = nullptr, *Jdata = nullptr,
-           *J64 = nullptr, *rzpart = nullptr, *pqpart = nullptr;
+           *J64 = nullptr, *rzpart = nullptr, *pqpart = nullptr, *rztot = nullptr, *pqtot = nullptr;
     unsigned* status = nullptr;
+    unsigned* count = nullptr;
     int npart = 1;
     // typed device arrays (float or double per precision)
     void *pfy = nullptr, *pfx = nullptr, *dfw = nullptr, *D = nullptr, *Jinv = nullptr;
@@ -67,6 +69,16 @@ struct fewha_handle {
     bool g_warm = false;
     std::string err;
     size_t smem_layer = 0, smem_sensor = 0;
+    // cluster kernels of the hot path
+    ClLayout lay_fwd{}, lay_inv{};
+    SensorLayout lay_sen{};
+    size_t smem_fwd = 0, smem_inv = 0, smem_sen = 0, smem_proj = 0, smem_projT = 0;
+    // (sensor, layer) pair terms of P and P^T
+    int* box = nullptr;
+    std::vector<int> box_host;
+    void* pairV = nullptr;
+    void* pairY = nullptr;
+    int pvs = 0, pvslot = 0, pyslot = 0;
 };
 
 namespace {
@@ -102,7 +114,8 @@ int dalloc(fewha_handle* H, X** ptr, size_t count) {
 
 int talloc(fewha_handle* H, void** ptr, size_t count) {
     void* p = nullptr;
-    const size_t bytes = count * H->esz > 0 ? count * H->esz : 16;
+    // 16 spare elements: the 16-byte staging copies may read up to one chunk past a vector
+    const size_t bytes = (count + 16) * H->esz;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(H, FEWHA_ERR_OOM, "device allocation failed");
@@ -158,6 +171,9 @@ Desc<T> make_desc(const fewha_handle* H) {
     d.dr_hi = H->dr_hi;
     d.D = static_cast<const T*>(H->D);
     d.Jinv = static_cast<const T*>(H->Jinv);
+    for (int g = 0; g < d.n_wfs; ++g)
+        for (int l = 0; l < d.n_layers; ++l)
+            for (int k = 0; k < 4; ++k) d.box[g][l][k] = H->box_host[(g * MAXL + l) * 4 + k];
     return d;
 }
 
@@ -177,6 +193,17 @@ int launch_sensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaSt
     return FEWHA_OK;
 }
 
+PcgSlots pcg_slots(fewha_handle* H) {
+    PcgSlots p;
+    p.rzpart = H->rzpart;
+    p.pqpart = H->pqpart;
+    p.rztot = H->rztot;
+    p.pqtot = H->pqtot;
+    p.count = H->count;
+    p.npart = H->npart;
+    return p;
+}
+
 template <class T>
 VecArgs<T> vec_args(fewha_handle* H, T* c, int iter) {
     VecArgs<T> v;
@@ -188,7 +215,7 @@ VecArgs<T> vec_args(fewha_handle* H, T* c, int iter) {
     v.b = static_cast<const T*>(H->b);
     v.b_prev = static_cast<T*>(H->b_prev);
     v.Jinv = static_cast<const T*>(H->Jinv);
-    v.pcg = PcgSlots{H->rzpart, H->pqpart, H->npart};
+    v.pcg = pcg_slots(H);
     v.iter = iter;
     return v;
 }
@@ -199,43 +226,107 @@ LayerArgs<T> layer_args(fewha_handle* H, const T* in, T* out) {
     std::memset(&a, 0, sizeof(a));
     a.in = in;
     a.out = out;
-    a.pcg = PcgSlots{H->rzpart, H->pqpart, H->npart};
+    a.pcg = pcg_slots(H);
     return a;
 }
 
-// q = M x (Eq. 6) into H->q; the p.q partials go to slot `slot`.
+template <class T>
+ClArgs<T> cl_args(fewha_handle* H, const T* in, T* out) {
+    ClArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.pcg = pcg_slots(H);
+    return a;
+}
+
+template <class T>
+PairBufs<T> pair_bufs(fewha_handle* H) {
+    PairBufs<T> pb;
+    pb.V = static_cast<T*>(H->pairV);
+    pb.Y = static_cast<T*>(H->pairY);
+    pb.vs = H->pvs;
+    pb.vslot = H->pvslot;
+    pb.yslot = H->pyslot;
+    pb.box = H->box;
+    return pb;
+}
+
+template <class T>
+int launch_proj(fewha_handle* H, const Desc<T>& d, const T* phi, cudaStream_t st) {
+    k_proj<T><<<dim3(d.n_wfs, d.n_layers), cblk<T>(), H->smem_proj, st>>>(d, phi, pair_bufs<T>(H));
+    CK(cudaGetLastError(), "k_proj launch");
+    return FEWHA_OK;
+}
+
+template <class T>
+int launch_projT(fewha_handle* H, const Desc<T>& d, const T* u, cudaStream_t st) {
+    k_projT<T><<<dim3(d.n_wfs, d.n_layers), cblk<T>(), H->smem_projT, st>>>(d, u, pair_bufs<T>(H));
+    CK(cudaGetLastError(), "k_projT launch");
+    return FEWHA_OK;
+}
+
+template <class T, int SRC, int DST>
+int launch_fwd(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream_t st) {
+    k_cl_fwd<T, SRC, DST><<<dim3(CL, d.n_layers), cblk<T>(), H->smem_fwd, st>>>(d, a, H->lay_fwd,
+                                                                                   pair_bufs<T>(H));
+    CK(cudaGetLastError(), "k_cl_fwd launch");
+    return FEWHA_OK;
+}
+
+template <class T, bool PUPD>
+int launch_inv(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream_t st) {
+    k_cl_inv<T, PUPD><<<dim3(CL, d.n_layers), cblk<T>(), H->smem_inv, st>>>(d, a, H->lay_inv);
+    CK(cudaGetLastError(), "k_cl_inv launch");
+    return FEWHA_OK;
+}
+
+template <class T, int SRC>
+int launch_csensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaStream_t st) {
+    SensorArgs<T> a{in, out, H->status};
+    k_cl_sensor<T, SRC><<<dim3(CL, d.n_wfs), cblk<T>(), H->smem_sen, st>>>(d, a, H->lay_sen,
+                                                                          pair_bufs<T>(H));
+    CK(cudaGetLastError(), "k_cl_sensor launch");
+    return FEWHA_OK;
+}
+
+// q = M x (Eq. 6); the p.q partials go to slot `slot` (PQ_SLOTS doubles per slot).
+// With pupdate, x is the CG direction p, first advanced to z + beta p (iteration `slot`).
 template <class T>
 int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int slot, bool pupdate,
                   cudaStream_t st) {
     T* phi = static_cast<T*>(H->phi);
     T* u = static_cast<T*>(H->u);
     int rc;
-    LayerArgs<T> a = layer_args<T>(H, x, phi);
+    ClArgs<T> a = cl_args<T>(H, x, phi);
     if (pupdate) {
         a.pupd = static_cast<T*>(H->p);
         a.zupd = static_cast<const T*>(H->z);
         a.iter = slot;
-        rc = launch_layer<T, LSRC_COEF, LDST_PHI, true>(H, d, a, st);
+        rc = launch_inv<T, true>(H, d, a, st);
     } else {
-        rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, a, st);
+        rc = launch_inv<T, false>(H, d, a, st);
     }
     if (rc) return rc;
-    if ((rc = launch_sensor<T, SSRC_PHI, true, SDST_ADJ>(H, d, phi, u, st))) return rc;
-    LayerArgs<T> b = layer_args<T>(H, u, qout);
+    if ((rc = launch_proj<T>(H, d, phi, st))) return rc;
+    if ((rc = launch_csensor<T, SSRC_PHI>(H, d, phi, u, st))) return rc;
+    if ((rc = launch_projT<T>(H, d, u, st))) return rc;
+    ClArgs<T> b = cl_args<T>(H, u, qout);
     b.pin = x;
     b.iter = slot;
     b.zero_piston = 1;
-    return launch_layer<T, LSRC_NODES, LDST_APPLY, false>(H, d, b, st);
+    return launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, b, st);
 }
 
 template <class T>
 int enqueue_rhs(fewha_handle* H, const Desc<T>& d, const T* s, T* bout, cudaStream_t st) {
     T* u = static_cast<T*>(H->u);
     int rc;
-    if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_ADJ>(H, d, s, u, st))) return rc;
-    LayerArgs<T> a = layer_args<T>(H, u, bout);
+    if ((rc = launch_csensor<T, SSRC_SLOPES>(H, d, s, u, st))) return rc;
+    if ((rc = launch_projT<T>(H, d, u, st))) return rc;
+    ClArgs<T> a = cl_args<T>(H, u, bout);
     a.zero_piston = 1;
-    return launch_layer<T, LSRC_NODES, LDST_COEF, false>(H, d, a, st);
+    return launch_fwd<T, LSRC_NODES, LDST_COEF>(H, d, a, st);
 }
 
 int vec_grid(const fewha_handle* H) { return H->npart; }
@@ -265,7 +356,7 @@ template <class T>
 int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain, cudaStream_t st) {
     T* phi = static_cast<T*>(H->phi);
     int rc;
-    if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, c, phi), st))) return rc;
+    if ((rc = launch_inv<T, false>(H, d, cl_args<T>(H, c, phi), st))) return rc;
     k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, static_cast<T*>(H->a_prev), dm,
                                                            gain ? 1 : 0);
     CK(cudaGetLastError(), "k_fit launch");
@@ -370,6 +461,19 @@ int setup_tables(fewha_handle* H) {
     return compute_diagonals<T>(H);
 }
 
+// Let `kernel` use all dynamic shared memory left beside its static shared memory, and
+// check that `need` bytes fit.
+template <class K>
+int allow_smem(fewha_handle* H, K kernel, size_t need) {
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, kernel), "function attributes");
+    const int avail = 227 * 1024 - static_cast<int>(fa.sharedSizeBytes);
+    if (need > static_cast<size_t>(avail))
+        return fail(H, FEWHA_ERR_LIMIT, "cluster shared-memory tile above the per-CTA limit");
+    CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail), "smem attr");
+    return FEWHA_OK;
+}
+
 template <class T>
 int set_smem_limits(fewha_handle* H) {
     const int maxsm = 227 * 1024;
@@ -395,6 +499,118 @@ int set_smem_limits(fewha_handle* H) {
     SETS(SSRC_SLOPES, true, SDST_SLOPES);
     SETS(SSRC_PHI, false, SDST_SLOPES);
 #undef SETS
+    if (H->smem_fwd > static_cast<size_t>(maxsm) || H->smem_inv > static_cast<size_t>(maxsm) ||
+        H->smem_sen > static_cast<size_t>(maxsm))
+        return fail(H, FEWHA_ERR_LIMIT, "cluster shared-memory tile above 227 KB");
+    int rc = 0;
+    if ((rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_APPLY>, H->smem_fwd)) ||
+        (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_COEF>, H->smem_fwd)) ||
+        (rc = allow_smem(H, k_cl_inv<T, false>, H->smem_inv)) ||
+        (rc = allow_smem(H, k_cl_inv<T, true>, H->smem_inv)) ||
+        (rc = allow_smem(H, k_cl_sensor<T, SSRC_PHI>, H->smem_sen)) ||
+        (rc = allow_smem(H, k_cl_sensor<T, SSRC_SLOPES>, H->smem_sen)) ||
+        (rc = allow_smem(H, k_proj<T>, H->smem_proj)) || (rc = allow_smem(H, k_projT<T>, H->smem_projT)))
+        return rc;
+    return FEWHA_OK;
+}
+
+// Shared-memory layouts of the cluster kernels: the largest band over all layers and
+// sensors, element counts in T units after a fixed header; every region starts on a
+// 16-byte boundary (cp.async targets).
+int round4(int x) { return (x + 3) & ~3; }
+
+template <class T>
+int cluster_layouts(fewha_handle* H) {
+    const HostSetup& s = H->setup;
+    constexpr int V = vec16<T>();
+    int ybuf = 0, cbuf = 0, lbuf = 0, kmax = 0;
+    for (size_t l = 0; l < s.L.size(); ++l) {
+        const int n = s.L[l].n, rb = n >= CL ? n / CL : 1, h = n / 2;
+        ybuf = std::max(ybuf, rb * (n + 1));
+        cbuf = std::max(cbuf, n * (rb + 1));
+        if (s.L[l].levels >= 2) lbuf = std::max(lbuf, h * (h + 1));
+        for (size_t g = 0; g < s.G.size(); ++g) {
+            const int rbk = static_cast<int>((g * MAXL + l) * MAXN);
+            for (int i = 0; i < n; ++i) {
+                kmax = std::max(kmax, s.ry_hi[rbk + i] - s.ry_lo[rbk + i]);
+                kmax = std::max(kmax, s.rx_hi[rbk + i] - s.rx_lo[rbk + i]);
+            }
+        }
+    }
+    if (kmax > KMAX) return fail(H, FEWHA_ERR_LIMIT, "more than 8 aperture rows touch one layer row");
+    ybuf = round4(ybuf);
+    cbuf = round4(cbuf);
+    lbuf = round4(lbuf);
+    const size_t hdr_cl = RED_DBL * sizeof(double);
+    ClLayout f{};
+    f.ybuf = 0;
+    f.cbuf = ybuf;
+    f.lbuf = ybuf + cbuf;
+    f.sbuf = f.lbuf + lbuf;
+    f.total = f.sbuf + round4(SMALL * SSTRIDE);
+    H->lay_fwd = f;
+    H->smem_fwd = hdr_cl + static_cast<size_t>(f.total) * sizeof(T);
+    ClLayout v{};
+    v.ybuf = 0;
+    v.cbuf = ybuf;
+    v.lbuf = ybuf + cbuf;
+    v.stage = v.lbuf + lbuf;                               // p and z of the column band
+    v.stage2 = v.stage + 2 * MAXN * (MAXN / CL);           // p and z of the LL quadrant
+    v.sbuf = v.stage2 + 2 * (MAXN / 2) * (MAXN / 2);
+    v.total = v.sbuf + round4(SMALL * SSTRIDE);
+    H->lay_inv = v;
+    H->smem_inv = hdr_cl + static_cast<size_t>(v.total) * sizeof(T);
+    int Vn = 0, SXn = 0, halo = 0;
+    for (size_t g = 0; g < s.G.size(); ++g) {
+        const int N = s.G[g].N, sr = (N + CL - 1) / CL;
+        Vn = std::max(Vn, (sr + 1) * (N + 1));
+        SXn = std::max(SXn, sr * N);
+        halo = std::max(halo, 2 * N + 2 * MAXCOARSE);
+    }
+    SensorLayout q{};
+    q.phsub = 0;
+    q.V = 0;
+    q.SX = q.V + round4(Vn);
+    q.SY = q.SX + round4(SXn);
+    q.halo = q.SY + round4(SXn);
+    q.total = q.halo + round4(halo);
+    H->lay_sen = q;
+    const size_t hdr_s = (RED_DBL + 2 + 2 * MAXCOARSE) * sizeof(double) + (4 * MAXL + 4) * sizeof(int);
+    H->smem_sen = hdr_s + static_cast<size_t>(q.total) * sizeof(T);
+    // pair kernels: footprint boxes (16-byte aligned column supersets) and tile sizes
+    std::vector<int> box(MAXG * MAXL * 4, 0);
+    size_t proj = 0, projT = 0;
+    int yslot = 4;
+    for (size_t g = 0; g < s.G.size(); ++g) {
+        const int N = s.G[g].N, NP = N + 1;
+        for (size_t l = 0; l < s.L.size(); ++l) {
+            const int tp = static_cast<int>((g * MAXL + l) * TAB);
+            const int n = s.L[l].n;
+            const int al = (n % V) == 0 ? V : 1;
+            const int r0 = s.pi0y[tp + 0], rows = s.pi0y[tp + N] + 2 - r0;
+            const int c0 = s.pi0x[tp + 0] & ~(al - 1);
+            const int c1 = (s.pi0x[tp + N] + 2 + al - 1) & ~(al - 1);
+            int* bx = &box[(g * MAXL + l) * 4];
+            bx[0] = r0;
+            bx[1] = rows;
+            bx[2] = c0;
+            bx[3] = c1 - c0;
+            yslot = std::max(yslot, round4(rows * (c1 - c0)));
+            proj = std::max(proj, static_cast<size_t>(round4(rows * (c1 - c0)) + rows * NP));
+            projT = std::max(projT, static_cast<size_t>(round4(V + NP * NP) + NP * (c1 - c0)));
+        }
+    }
+    H->box_host = box;
+    H->smem_proj = proj * sizeof(T);
+    H->smem_projT = projT * sizeof(T);
+    H->pvs = round4(s.max_N + 1);
+    H->pvslot = (s.max_N + 1) * H->pvs;
+    H->pyslot = yslot;
+    int rc;
+    const size_t pairs = s.G.size() * s.L.size();
+    if ((rc = dalloc(H, &H->box, box.size())) || (rc = upload(H, H->box, box)) ||
+        (rc = talloc(H, &H->pairV, pairs * H->pvslot)) || (rc = talloc(H, &H->pairY, pairs * H->pyslot)))
+        return rc;
     return FEWHA_OK;
 }
 
@@ -445,8 +661,10 @@ int typed_create(fewha_handle* H) {
         (rc = dalloc(H, &H->basis, s.basis.size())) || (rc = dalloc(H, &H->D64, s.n_c)) ||
         (rc = dalloc(H, &H->Jdata, s.n_c)) || (rc = dalloc(H, &H->J64, s.n_c)) ||
         (rc = dalloc(H, &H->rzpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * NPART_MAX)) ||
-        (rc = dalloc(H, &H->pqpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * MAXL)) ||
-        (rc = dalloc(H, &H->status, 1)))
+        (rc = dalloc(H, &H->pqpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * PQ_SLOTS)) ||
+        (rc = dalloc(H, &H->rztot, static_cast<size_t>(FEWHA_MAX_ITERS + 2))) ||
+        (rc = dalloc(H, &H->pqtot, static_cast<size_t>(FEWHA_MAX_ITERS + 2))) ||
+        (rc = dalloc(H, &H->count, 2)) || (rc = dalloc(H, &H->status, 1)))
         return rc;
     if ((rc = talloc(H, &H->pfy, tab)) || (rc = talloc(H, &H->pfx, tab)) ||
         (rc = talloc(H, &H->dfw, dtab)) || (rc = talloc(H, &H->D, s.n_c)) ||
@@ -470,6 +688,7 @@ int typed_create(fewha_handle* H) {
     H->smem_layer = (2 * NWARP + 4) * sizeof(double) + static_cast<size_t>(s.max_n) * s.max_n * sizeof(T);
     H->smem_sensor = (2 * NWARP + 4 + 2 * MAXCOARSE) * sizeof(double) +
                      (static_cast<size_t>(s.max_N + 1) * (s.max_N + 1) + 2 * static_cast<size_t>(s.max_N) * s.max_N) * sizeof(T);
+    if ((rc = cluster_layouts<T>(H))) return rc;
     if ((rc = set_smem_limits<T>(H))) return rc;
     return setup_tables<T>(H);
 }
@@ -574,22 +793,22 @@ int bench_stage(fewha_handle* H, int stage, int reps, cudaStream_t st) {
     for (int i = 0; i < reps && rc == 0; ++i) {
         switch (stage) {
             case FEWHA_STAGE_IDWT: {
-                LayerArgs<T> a = layer_args<T>(H, p, phi);
+                ClArgs<T> a = cl_args<T>(H, p, phi);
                 a.pupd = p;
                 a.zupd = static_cast<const T*>(H->z);
                 a.iter = 1;
-                rc = launch_layer<T, LSRC_COEF, LDST_PHI, true>(H, d, a, st);
+                rc = launch_inv<T, true>(H, d, a, st);
                 break;
             }
             case FEWHA_STAGE_SENSOR:
-                rc = launch_sensor<T, SSRC_PHI, true, SDST_ADJ>(H, d, phi, u, st);
+                rc = launch_csensor<T, SSRC_PHI>(H, d, phi, u, st);
                 break;
             case FEWHA_STAGE_LAYER: {
-                LayerArgs<T> a = layer_args<T>(H, u, q);
+                ClArgs<T> a = cl_args<T>(H, u, q);
                 a.pin = p;
                 a.iter = PQ_SCRATCH_SLOT;
                 a.zero_piston = 1;
-                rc = launch_layer<T, LSRC_NODES, LDST_APPLY, false>(H, d, a, st);
+                rc = launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, a, st);
                 break;
             }
             case FEWHA_STAGE_VECTOR:
@@ -597,12 +816,18 @@ int bench_stage(fewha_handle* H, int stage, int reps, cudaStream_t st) {
                 CK(cudaGetLastError(), "k_vec launch");
                 break;
             case FEWHA_STAGE_RHS:
-                rc = launch_sensor<T, SSRC_SLOPES, true, SDST_ADJ>(H, d, static_cast<const T*>(H->s_tmp), u, st);
+                rc = launch_csensor<T, SSRC_SLOPES>(H, d, static_cast<const T*>(H->s_tmp), u, st);
                 break;
             case FEWHA_STAGE_FIT:
                 k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, static_cast<T*>(H->a_prev),
                                                                        static_cast<T*>(H->dm_tmp), 1);
                 CK(cudaGetLastError(), "k_fit launch");
+                break;
+            case FEWHA_STAGE_PROJ:
+                rc = launch_proj<T>(H, d, phi, st);
+                break;
+            case FEWHA_STAGE_PROJT:
+                rc = launch_projT<T>(H, d, u, st);
                 break;
         }
     }
@@ -844,8 +1069,8 @@ int fewha_bench_stage(fewha_handle* H, int stage, int reps, void* stream) {
 int fewha_frame_launches(const fewha_handle* H, int* launches) {
     if (!H || !launches) return FEWHA_ERR_INVALID_ARG;
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
-    // RHS 2, initial residual 4 (explicit) or 1 (warm), 4 per iteration, fit 2
-    *launches = 2 + (warm ? 1 : 4) + 4 * H->params.iters + 2;
+    // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2
+    *launches = 3 + (warm ? 1 : 6) + 6 * H->params.iters + 2;
     return FEWHA_OK;
 }
 

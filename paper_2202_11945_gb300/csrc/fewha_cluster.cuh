@@ -1,0 +1,852 @@
+// Cluster kernels of the FEWHA hot path: one thread-block cluster of CL CTAs per layer
+// (wavelet transforms with the adjoint projection) and per sensor (projection, slopes,
+// noise weighting, adjoint slopes).  The CTAs of a cluster split the work into bands
+// and exchange data through distributed shared memory; every reduction runs in a fixed
+// order, so results stay bitwise reproducible.  Global reads are staged into shared
+// memory with cp.async so that all of a CTA's loads are in flight at once.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "fewha_kernels.cuh"
+
+namespace fewha {
+
+namespace cg = cooperative_groups;
+
+constexpr int CL = 8;        // CTAs per cluster
+constexpr int RMAX = 8;      // wavelet pairs per thread and pass
+constexpr int CWMAX = 16;    // warps per CTA at most
+constexpr int RED_DBL = 520; // reduction scratch at the head of shared memory, in doubles
+
+// Threads per CTA: 512 in single precision (latency hiding), 256 in double precision
+// (the register budget of the sliding windows).
+template <class T>
+__host__ __device__ constexpr int cblk() {
+    return sizeof(T) == 4 ? 512 : 256;
+}
+
+// ---------------------------------------------------------------- cp.async staging
+template <class T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 16-byte copy; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+// Elements per 16-byte chunk.
+template <class T>
+__host__ __device__ constexpr int vec16() {
+    return 16 / static_cast<int>(sizeof(T));
+}
+// Stage `count` elements from src to dst (both 16-byte aligned) in 16-byte chunks by the
+// threads [t0, t0 + nthr); reads up to one chunk past src + count (allocations are padded).
+template <class T>
+__device__ __forceinline__ void stage16(T* dst, const T* src, int count, int t, int nthr) {
+    constexpr int V = vec16<T>();
+    const int chunks = (count + V - 1) / V;
+    for (int c = t; c < chunks; c += nthr) cp_async16(dst + c * V, src + c * V);
+}
+
+// ---------------------------------------------------------------- one db3 step
+// One periodic db3 analysis (INV = false) or synthesis (INV = true) step along an axis
+// of `lines` independent lines of length m, in place.  Element (line, pos) lives at
+// buf[line * ls + pos * ps].  A thread owns a run of R consecutive pairs of one line and
+// keeps a sliding window of the inputs in registers.
+template <class T, bool INV>
+__device__ __forceinline__ void dwt_pass(T* buf, int lines, int m, int ls, int ps) {
+    constexpr int NT = cblk<T>();
+    // lines, m and NT are powers of two
+    const int h = m >> 1;
+    const int ll = __ffs(lines) - 1, lhh = __ffs(h) - 1;
+    const int lnt = __ffs(NT) - 1;
+    const int lruns = min(max(lnt - ll, 0), lhh);
+    const int runs = 1 << lruns;
+    const int R = h >> lruns;
+    const int t = threadIdx.x;
+    const bool act = t < (lines << lruns);
+    const int line = t & (lines - 1), k0 = (t >> ll) * R;
+    T* Lp = buf + line * ls;
+    T o0[RMAX], o1[RMAX];
+    if (act) {
+        if (!INV) {
+            T w[2 * RMAX + 4];
+#pragma unroll
+            for (int s = 0; s < 2 * RMAX + 4; ++s)
+                if (s < 2 * R + 4) w[s] = Lp[((2 * k0 + s) & (m - 1)) * ps];
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) {
+                if (q < R) {
+                    T a = T(0), d = T(0);
+#pragma unroll
+                    for (int tt = 0; tt < 6; ++tt) {
+                        a += tap_h<T>(tt) * w[2 * q + tt];
+                        d += tap_g<T>(tt) * w[2 * q + tt];
+                    }
+                    o0[q] = a;
+                    o1[q] = d;
+                }
+            }
+        } else {
+            T wa[RMAX + 2], wd[RMAX + 2];
+#pragma unroll
+            for (int s = 0; s < RMAX + 2; ++s) {
+                if (s < R + 2) {
+                    const int idx = (k0 - 2 + s) & (h - 1);
+                    wa[s] = Lp[idx * ps];
+                    wd[s] = Lp[(h + idx) * ps];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) {
+                if (q < R) {
+                    o0[q] = tap_h<T>(0) * wa[q + 2] + tap_h<T>(2) * wa[q + 1] + tap_h<T>(4) * wa[q] +
+                            tap_g<T>(0) * wd[q + 2] + tap_g<T>(2) * wd[q + 1] + tap_g<T>(4) * wd[q];
+                    o1[q] = tap_h<T>(1) * wa[q + 2] + tap_h<T>(3) * wa[q + 1] + tap_h<T>(5) * wa[q] +
+                            tap_g<T>(1) * wd[q + 2] + tap_g<T>(3) * wd[q + 1] + tap_g<T>(5) * wd[q];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < RMAX; ++q) {
+            if (q < R) {
+                if (!INV) {
+                    Lp[(k0 + q) * ps] = o0[q];
+                    Lp[(h + k0 + q) * ps] = o1[q];
+                } else {
+                    Lp[(2 * (k0 + q)) * ps] = o0[q];
+                    Lp[(2 * (k0 + q) + 1) * ps] = o1[q];
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Deterministic CTA sum of one double: every thread's value goes to shared memory and
+// warp 0 adds them in a fixed order (few FP64 operations: GB300's FP64 rate is low).
+// `scratch` holds blockDim.x doubles.
+__device__ __forceinline__ double cta_sum(double v, double* scratch) {
+    const int nt = blockDim.x;
+    scratch[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nt; i += 32) s += scratch[i];
+        s = warp_sum(s);
+        if (threadIdx.x == 0) scratch[0] = s;
+    }
+    __syncthreads();
+    const double r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+// Deterministic CTA sum of one float (fixed order); `scratch` holds blockDim.x floats.
+__device__ __forceinline__ float cta_sumf(float v, float* scratch) {
+    const int nt = blockDim.x;
+    scratch[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float s = 0.f;
+        for (int i = threadIdx.x; i < nt; i += 32) s += scratch[i];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) scratch[0] = s;
+    }
+    __syncthreads();
+    const float r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum_t(float v) { return warp_sumf(v); }
+__device__ __forceinline__ double warp_sum_t(double v) { return warp_sum(v); }
+__device__ __forceinline__ float cta_sum_t(float v, double* scratch) {
+    return cta_sumf(v, reinterpret_cast<float*>(scratch));
+}
+__device__ __forceinline__ double cta_sum_t(double v, double* scratch) { return cta_sum(v, scratch); }
+
+constexpr int SMALL = 32;              // side of the spare scratch tile
+constexpr int SSTRIDE = SMALL + 1;
+
+// Forward (analysis) levels lev_begin..levels-1 of the LL block (stride lsd), whole CTA.
+template <class T>
+__device__ __forceinline__ void coarse_forward(T* lbuf, T* sbuf, int n, int lev_begin, int levels,
+                                               int lsd) {
+    (void)sbuf;
+    for (int lev = lev_begin; lev < levels; ++lev) {
+        const int m = n >> lev;
+        dwt_pass<T, false>(lbuf, m, m, lsd, 1);    // rows
+        dwt_pass<T, false>(lbuf, m, m, 1, lsd);    // columns
+    }
+}
+
+// Inverse (synthesis) levels levels-1..lev_end of the LL block.
+template <class T>
+__device__ __forceinline__ void coarse_inverse(T* lbuf, T* sbuf, int n, int lev_end, int levels,
+                                               int lsd) {
+    (void)sbuf;
+    for (int lev = levels - 1; lev >= lev_end; --lev) {
+        const int m = n >> lev;
+        dwt_pass<T, true>(lbuf, m, m, 1, lsd);     // columns
+        dwt_pass<T, true>(lbuf, m, m, lsd, 1);     // rows
+    }
+}
+
+// Band of a layer owned by cluster rank r: rows (and columns) [r * rb, r * rb + rb).
+__device__ __forceinline__ int band_rows(int n) { return n >= CL ? n / CL : 1; }
+
+// Buffers of the (sensor, layer) pair terms of P and P^T, set by the host.
+template <class T>
+struct PairBufs {
+    T* V;             // P_g,l phi_l: slot (g * n_layers + l), N+1 rows of stride vs
+    T* Y;             // R^T u terms: slot (g * n_layers + l), box rows of stride box[3]
+    int vs;           // row stride of a V slot
+    int vslot;        // elements per V slot
+    int yslot;        // elements per Y slot
+    const int* box;   // per pair (g * MAXL + l): row0, rows, col0, cols
+};
+
+// ---------------------------------------------------------------------------
+// Forward layer kernel (cluster per layer).
+//   SRC_NODES: y = sum_g P_g^T u_g (Sec. 2, adjoint), then W y;  SRC_PHI: W phi.
+//   DST_COEF:  write W y (b of Sec. 3.1 when u comes from the measured slopes);
+//   DST_APPLY: write q = W y + alpha D p and p.q (Eq. 6); the grid's last CTA forms
+//              the total p.q in a fixed order.
+// P_g^T is separable, y = R_y^T u R_x: for each sensor, pass X contracts the staged node
+// rows with the column weights, pass Y with the row weights.  The sensors' node rows and
+// tables are staged with cp.async in a double buffer, one sensor ahead of the compute.
+// ---------------------------------------------------------------------------
+template <class T>
+struct ClArgs {
+    const T* in;        // u (nodes), phi, or coefficients
+    const T* pin;       // p of the apply
+    T* out;
+    T* pupd;            // p advanced in place (inverse kernel with update)
+    const T* zupd;
+    PcgSlots pcg;
+    int iter;           // p.q slot of the apply / CG iteration of the update
+    int zero_piston;
+};
+
+struct ClLayout {       // shared-memory offsets set by the host, in T units
+    int ybuf, cbuf, lbuf, stage, stage2, tbuf, sbuf;
+    int total;
+    int umax;           // one staging buffer of the P^T pipeline
+};
+
+constexpr int KMAX = 8;      // aperture rows / columns touching one layer row / column
+
+template <class T, int SRC, int DST>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    k_cl_fwd(const Desc<T> d, const ClArgs<T> a, const ClLayout lay, const PairBufs<T> pb) {
+    constexpr int NT = cblk<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);            // RED_DBL doubles
+    T* sm = reinterpret_cast<T*>(red + RED_DBL);
+    __shared__ bool last;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = static_cast<int>(cluster.block_rank());
+    const int l = blockIdx.y;
+    const LayerInfo L = d.L[l];
+    const int n = L.n, off = L.off, h = n >> 1;
+    const int rb = band_rows(n);
+    const int lrb = L.log2n >= 3 ? L.log2n - 3 : 0;   // log2(rb), CL = 8
+    const int lh = L.log2n - 1;                        // log2(n / 2)
+    const int r0 = r * rb;
+    const bool has_band = r0 < n;
+    const bool coarse = L.levels >= 2;
+    T* ybuf = sm + lay.ybuf;          // rb x (n + 1)
+    T* cbuf = sm + lay.cbuf;          // n x (rb + 1)
+    T* lbuf = sm + lay.lbuf;          // h x (h + 1)
+    const int ys = n + 1, cs = rb + 1, lsd = h + 1;
+
+    // ---- 0. prefetch the epilogue operands of the column band (independent of u) ----
+    constexpr int PF = MAXN * (MAXN / CL) / NT;     // column-band positions per thread
+    const int row_start = (coarse && r0 < h) ? h : 0;
+    const int ecnt = has_band ? (n - row_start) * rb : 0;
+    T pre_p[PF], pre_D[PF];
+    if (DST == LDST_APPLY) {
+#pragma unroll
+        for (int s = 0; s < PF; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < ecnt) {
+                const int pos = off + (row_start + (k >> lrb)) * n + r0 + (k & (rb - 1));
+                pre_p[s] = a.pin[pos];
+                pre_D[s] = d.D[pos];
+            }
+        }
+    }
+
+    // ---- 1. the row band of y ---------------------------------------------------
+    if (has_band) {
+        if (SRC == LSRC_PHI) {
+            for (int k = threadIdx.x; k < rb * n; k += NT) {
+                const int i = (k >> L.log2n), j = k - i * n;
+                cp_async(ybuf + i * ys + j, a.in + off + (r0 + i) * n + j);
+            }
+            cp_async_wait();
+            __syncthreads();
+        } else {
+            // y = sum_g R_y,gl^T u_g R_x,gl: add the pair terms (fixed sensor order) over
+            // this band; a term is zero outside its footprint box
+            // every load is issued unconditionally from a clamped index, then masked, so
+            // that the sensors' loads are in flight together
+            for (int k = threadIdx.x; k < rb * n; k += NT) {
+                const int ii = k >> L.log2n, j = k & (n - 1), i = r0 + ii;
+                T v[MAXG];
+                bool in[MAXG];
+#pragma unroll
+                for (int g = 0; g < MAXG; ++g) {
+                    in[g] = false;
+                    if (g < d.n_wfs) {
+                        const int ri = i - d.box[g][l][0], cj = j - d.box[g][l][2];
+                        in[g] = ri >= 0 && ri < d.box[g][l][1] && cj >= 0 && cj < d.box[g][l][3];
+                        const int rc = min(max(ri, 0), d.box[g][l][1] - 1);
+                        const int cc = min(max(cj, 0), d.box[g][l][3] - 1);
+                        v[g] = pb.Y[(g * d.n_layers + l) * pb.yslot + rc * d.box[g][l][3] + cc];
+                    }
+                }
+                T acc = T(0);
+#pragma unroll
+                for (int g = 0; g < MAXG; ++g)
+                    if (in[g]) acc += v[g];
+                ybuf[ii * ys + j] = acc;
+            }
+            __syncthreads();
+        }
+        // ---- 2. level-0 analysis along the rows of the band --------------------
+        dwt_pass<T, false>(ybuf, rb, n, ys, 1);
+    }
+    cluster.sync();                                                       // #1
+    // ---- 3. column band: gather the band's columns from every row band -------------
+    if (has_band) {
+        constexpr int G = MAXN * (MAXN / CL) / NT;
+        T v[G];
+#pragma unroll
+        for (int s = 0; s < G; ++s) {           // every remote load in flight before any store
+            const int k = threadIdx.x + s * NT;
+            if (k < n * rb) {
+                const int i = (k >> lrb), jj = k - i * rb;
+                const int q = (i >> lrb), ii = i - q * rb;
+                v[s] = cluster.map_shared_rank(ybuf, q)[ii * ys + r0 + jj];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < n * rb) cbuf[((k >> lrb)) * cs + (k & (rb - 1))] = v[s];
+        }
+        __syncthreads();
+        dwt_pass<T, false>(cbuf, rb, n, 1, cs);
+    }
+    cluster.sync();                                                       // #2
+    // ---- 4. the leader gathers the LL quadrant and finishes the coarse levels --------
+    if (coarse && r == 0) {
+        constexpr int G = (MAXN / 2) * (MAXN / 2) / NT;
+        T v[G];
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < h * h) {
+                const int i = (k >> lh), j = k - i * h;
+                const int q = (j >> lrb), jj = j - q * rb;
+                v[s] = cluster.map_shared_rank(cbuf, q)[i * cs + jj];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < h * h) lbuf[((k >> lh)) * lsd + (k & (h - 1))] = v[s];
+        }
+    }
+    cluster.sync();                                                       // #3
+    double dot = 0.0;
+    if (coarse && r == 0) {
+        constexpr int PL = (MAXN / 2) * (MAXN / 2) / NT;     // LL positions per thread
+        T lp[PL], lD[PL];
+        if (DST == LDST_APPLY) {
+#pragma unroll
+            for (int s = 0; s < PL; ++s) {
+                const int k = threadIdx.x + s * NT;
+                if (k < h * h) {
+                    const int pos = off + ((k >> lh)) * n + (k & (h - 1));
+                    lp[s] = a.pin[pos];
+                    lD[s] = d.D[pos];
+                }
+            }
+        }
+        __syncthreads();
+        coarse_forward<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+        // The data term has no piston component: Gamma annihilates constants and bilinear
+        // weights sum to one, so its full-depth LL coefficient is exactly 0.  Write that
+        // zero rather than the rounding residue of a cancelling sum, which the solve would
+        // amplify by 1 / (alpha D_LL).
+        if (a.zero_piston && L.full && threadIdx.x == 0) lbuf[0] = T(0);
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < PL; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < h * h) {
+                const int i = (k >> lh), j = (k & (h - 1));
+                const int pos = off + i * n + j;
+                const T v = lbuf[i * lsd + j];
+                if (DST == LDST_APPLY) {
+                    const T q = v + d.alpha * lD[s] * lp[s];
+                    a.out[pos] = q;
+                    dot += double(lp[s]) * double(q);
+                } else {
+                    a.out[pos] = v;
+                }
+            }
+        }
+    }
+    if (!coarse && a.zero_piston && L.full && r == 0 && threadIdx.x == 0) cbuf[0] = T(0);
+    __syncthreads();
+    // ---- 5. epilogue of the column band (the LL quadrant excluded when coarse) ----------
+#pragma unroll
+    for (int s = 0; s < PF; ++s) {
+        const int k = threadIdx.x + s * NT;
+        if (k < ecnt) {
+            const int i = row_start + (k >> lrb), jj = (k & (rb - 1));
+            const int pos = off + i * n + r0 + jj;
+            const T v = cbuf[i * cs + jj];
+            if (DST == LDST_APPLY) {
+                const T q = v + d.alpha * pre_D[s] * pre_p[s];
+                a.out[pos] = q;
+                dot += double(pre_p[s]) * double(q);
+            } else {
+                a.out[pos] = v;
+            }
+        }
+    }
+    if (DST == LDST_APPLY) {
+        dot = cta_sum(dot, red);
+        double* slots = a.pcg.pqpart + a.iter * PQ_SLOTS;
+        if (threadIdx.x == 0) slots[l * CL + r] = dot;
+        if (last_arrival(a.pcg.count + 1, gridDim.x * gridDim.y, &last) && threadIdx.x < 32) {
+            // fixed order: layer-major, rank-minor over the slots of the layers present
+            const double tot = warp_fixed_sum(slots, d.n_layers * CL);
+            if (threadIdx.x == 0) {
+                a.pcg.pqtot[a.iter] = tot;
+                a.pcg.count[1] = 0;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse layer kernel (cluster per layer): phi = W^T c, optionally advancing the CG
+// direction first (p = z + beta p, beta = rz_k / rz_(k-1), Sec. 3.3).
+// ---------------------------------------------------------------------------
+template <class T, bool PUPD>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    k_cl_inv(const Desc<T> d, const ClArgs<T> a, const ClLayout lay) {
+    constexpr int NT = cblk<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);
+    T* sm = reinterpret_cast<T*>(red + RED_DBL);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = static_cast<int>(cluster.block_rank());
+    const int l = blockIdx.y;
+    const LayerInfo L = d.L[l];
+    const int n = L.n, off = L.off, h = n >> 1;
+    const int rb = band_rows(n);
+    const int lrb = L.log2n >= 3 ? L.log2n - 3 : 0;   // log2(rb), CL = 8
+    const int lh = L.log2n - 1;                        // log2(n / 2)
+    const int r0 = r * rb;
+    const bool has_band = r0 < n;
+    T* ybuf = sm + lay.ybuf;
+    T* cbuf = sm + lay.cbuf;
+    T* lbuf = sm + lay.lbuf;
+    const int ys = n + 1, cs = rb + 1, lsd = h + 1;
+    const bool coarse = L.levels >= 2;
+
+    T beta = T(0);
+    if (PUPD) {
+        const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
+        beta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
+    }
+    const T* src = PUPD ? a.pupd : a.in;
+    // ---- 1. stage this CTA's coefficients: its column band (without the LL quadrant
+    // when coarse) and, for the leader, the LL quadrant.  Rows go through unpadded
+    // staging tiles in 16-byte chunks when aligned, then into the padded tiles.
+    constexpr int V = vec16<T>();
+    const int row_start = (coarse && r0 < h) ? h : 0;
+    const int nrow = n - row_start;
+    T* sp = sm + lay.stage;                     // column band, stride rb: p (or c)
+    T* sz = sp + MAXN * (MAXN / CL);            // column band: z (PUPD)
+    T* lp = sm + lay.stage2;                    // LL quadrant, stride h: p (or c)
+    T* lz = lp + (MAXN / 2) * (MAXN / 2);       // LL quadrant: z (PUPD)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
+    if (has_band) {
+        if ((rb & (V - 1)) == 0) {
+            const int cpr = rb / V;             // chunks per row
+            for (int k = threadIdx.x; k < nrow * cpr; k += NT) {
+                const int i = k / cpr, c = k - i * cpr;
+                const int pos = off + (row_start + i) * n + r0 + c * V;
+                cp_async16(sp + i * rb + c * V, src + pos);
+                if (PUPD) cp_async16(sz + i * rb + c * V, a.zupd + pos);
+            }
+        } else {
+            for (int k = threadIdx.x; k < nrow * rb; k += NT) {
+                const int i = k >> lrb, jj = k & (rb - 1);
+                const int pos = off + (row_start + i) * n + r0 + jj;
+                cp_async(sp + k, src + pos);
+                if (PUPD) cp_async(sz + k, a.zupd + pos);
+            }
+        }
+    }
+    if (coarse && r == 0) {
+        for (int i = warp; i < h; i += nwarp) {
+            const int pos = off + i * n;
+            if ((h & (V - 1)) == 0) {
+                for (int c = lane; c < h / V; c += 32) {
+                    cp_async16(lp + i * h + c * V, src + pos + c * V);
+                    if (PUPD) cp_async16(lz + i * h + c * V, a.zupd + pos + c * V);
+                }
+            } else {
+                for (int j = lane; j < h; j += 32) {
+                    cp_async(lp + i * h + j, src + pos + j);
+                    if (PUPD) cp_async(lz + i * h + j, a.zupd + pos + j);
+                }
+            }
+        }
+    }
+    cp_async_wait();
+    __syncthreads();
+    // p = z + beta p (PUPD) into the padded tiles and back to global
+    if (has_band) {
+        for (int k = threadIdx.x; k < nrow * rb; k += NT) {
+            const int i = k >> lrb, jj = k & (rb - 1);
+            T p = sp[k];
+            if (PUPD) {
+                p = sz[k] + beta * p;
+                a.pupd[off + (row_start + i) * n + r0 + jj] = p;
+            }
+            cbuf[(row_start + i) * cs + jj] = p;
+        }
+    }
+    if (coarse && r == 0) {
+        for (int k = threadIdx.x; k < h * h; k += NT) {
+            const int i = k >> lh, j = k & (h - 1);
+            T p = lp[k];
+            if (PUPD) {
+                p = lz[k] + beta * p;
+                a.pupd[off + i * n + j] = p;
+            }
+            lbuf[i * lsd + j] = p;
+        }
+    }
+    __syncthreads();
+    // ---- 2. the leader synthesises the coarse levels into the LL quadrant ------------
+    if (coarse && r == 0) {
+        coarse_inverse<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+    }
+    cluster.sync();                                                       // #1
+    // ---- 3. column synthesis of level 0 on the column band ------------------------------
+    if (has_band) {
+        if (coarse && r0 < h) {
+            const T* lead = cluster.map_shared_rank(lbuf, 0);
+            constexpr int G = (MAXN / 2) * (MAXN / CL) / NT + 1;
+            T v[G];
+#pragma unroll
+            for (int s = 0; s < G; ++s) {
+                const int k = threadIdx.x + s * NT;
+                if (k < h * rb) v[s] = lead[((k >> lrb)) * lsd + r0 + (k & (rb - 1))];
+            }
+#pragma unroll
+            for (int s = 0; s < G; ++s) {
+                const int k = threadIdx.x + s * NT;
+                if (k < h * rb) cbuf[((k >> lrb)) * cs + (k & (rb - 1))] = v[s];
+            }
+            __syncthreads();
+        }
+        dwt_pass<T, true>(cbuf, rb, n, 1, cs);
+    }
+    cluster.sync();                                                       // #2
+    // ---- 4. row band: gather from every column band, row synthesis, store phi ---------
+    if (has_band) {
+        constexpr int G = MAXN * (MAXN / CL) / NT;
+        T v[G];
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < rb * n) {
+                const int ii = (k >> L.log2n), j = k - ii * n;
+                const int q = (j >> lrb), jj = j - q * rb;
+                v[s] = cluster.map_shared_rank(cbuf, q)[(r0 + ii) * cs + jj];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < rb * n) ybuf[(k >> L.log2n) * ys + (k & (n - 1))] = v[s];
+        }
+        __syncthreads();
+        dwt_pass<T, true>(ybuf, rb, n, ys, 1);
+        for (int k = threadIdx.x; k < rb * n; k += NT) {
+            const int ii = (k >> L.log2n), j = k - ii * n;
+            a.out[off + (r0 + ii) * n + j] = ybuf[ii * ys + j];
+        }
+    }
+    cluster.sync();                                                       // #3: peers done reading
+}
+
+// ---------------------------------------------------------------------------
+// Sensor kernel (cluster per sensor): P_g (Sec. 2), Gamma_g, C_hat_g^-1 (Eq. 2, Sec. 3.2)
+// and Gamma_g^T, each CTA on a band of subaperture rows.  SRC_PHI: slopes of the
+// projected layers (the M-apply); SRC_SLOPES: measured slopes (the right-hand side).
+// ---------------------------------------------------------------------------
+struct SensorLayout {
+    int phsub, V, SX, SY, halo, total;         // T units
+};
+
+template <class T, int SRC>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    k_cl_sensor(const Desc<T> d, const SensorArgs<T> a, const SensorLayout lay, const PairBufs<T> pb) {
+    constexpr int NT = cblk<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* red = reinterpret_cast<double*>(smem_raw);                 // 2*CWMAX + 8
+    double* part = red + RED_DBL;                                 // 2 + 2*MAXCOARSE
+    int* tab = reinterpret_cast<int*>(part + 2 + 2 * MAXCOARSE);       // 4 * MAXL + 4 ints
+    T* sm = reinterpret_cast<T*>(tab + 4 * MAXL + 4);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = static_cast<int>(cluster.block_rank());
+    const int g = blockIdx.y;
+    const WfsInfo W = d.G[g];
+    const int N = W.N, NP = N + 1;
+    const int sr = (N + CL - 1) / CL;
+    const int s0 = r * sr < N ? r * sr : N;
+    const int s1 = (r + 1) * sr < N ? (r + 1) * sr : N;
+    const int rows = s1 - s0;                  // subaperture rows of this CTA (may be 0)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
+    const int* sidx = d.sidx + W.mask_off;
+    const T inv = T(W.sig2inv);
+    const T nbinv = T(1) / T(W.nb);
+    T* V = sm + lay.V;          // (rows + 1) x NP
+    T* SX = sm + lay.SX;        // rows x N
+    T* SY = sm + lay.SY;
+    T* halo = sm + lay.halo;    // 2 x N: weighted slopes of subaperture row s0 - 1
+    T* cw = halo + 2 * N;       // 2 x MAXCOARSE: weighted coarse slopes / nb
+    T* ph = sm + lay.phsub;
+
+    if (SRC == SSRC_PHI && rows > 0) {
+        // ---- stage every layer's sub-block under this band's footprint and the tables --
+        // ---- V = P_g phi = sum_l (pair term of layer l) on node rows [s0, s1] ---------
+        const T* Vb = pb.V + static_cast<size_t>(g * d.n_layers) * pb.vslot;
+        for (int ia = warp; ia < rows + 1; ia += nwarp)
+        for (int b = lane; b < NP; b += 32) {
+            T t[MAXL];
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l)
+                t[l] = l < d.n_layers ? Vb[l * pb.vslot + (s0 + ia) * pb.vs + b] : T(0);
+            T v = T(0);
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l) v += t[l];
+            V[ia * NP + b] = v;
+        }
+        __syncthreads();
+        // ---- Gamma_g on the band's active subapertures -----------------------------------
+        for (int ii = warp; ii < rows; ii += nwarp)
+        for (int j = lane; j < N; j += 32) {
+            const int k = ii * N + j;
+            T sx = T(0), sy = T(0);
+            if (sidx[(s0 + ii) * N + j] >= 0) {
+                const T v00 = V[ii * NP + j], v01 = V[ii * NP + j + 1];
+                const T v10 = V[(ii + 1) * NP + j], v11 = V[(ii + 1) * NP + j + 1];
+                sx = T(0.5) * ((v01 - v00) + (v11 - v10));
+                sy = T(0.5) * ((v10 - v00) + (v11 - v01));
+            }
+            SX[k] = sx;
+            SY[k] = sy;
+        }
+    } else if (SRC == SSRC_SLOPES && rows > 0) {
+        const T* s = a.in + W.soff;
+        bool bad = false;
+        for (int k = threadIdx.x; k < rows * N; k += NT) {
+            const int id = sidx[s0 * N + k];
+            T sx = T(0), sy = T(0);
+            if (id >= 0) {
+                sx = s[id];
+                sy = s[W.n_active + id];
+                bad |= !(isfinite(sx) && isfinite(sy));
+                if (W.nb > 1) {        // coarse: (1/nb) sigma^-2 s_K on each active fine one
+                    sx *= nbinv * inv;
+                    sy *= nbinv * inv;
+                }
+            }
+            SX[k] = sx;
+            SY[k] = sy;
+        }
+        if (bad && a.status) atomicOr(a.status, 1u);
+    }
+    __syncthreads();
+
+    // ---- cluster reductions (fixed order): LGS tip/tilt sums, coarse block sums -------
+    const bool need_tt = W.lgs;
+    const bool need_coarse = (SRC == SSRC_PHI) && W.nb > 1;
+    if (need_tt) {
+        T tx = T(0), ty = T(0);
+        for (int k = threadIdx.x; k < rows * N; k += NT) {
+            tx += SX[k];
+            ty += SY[k];
+        }
+        tx = cta_sum_t(tx, red);
+        ty = cta_sum_t(ty, red);
+        if (threadIdx.x == 0) {
+            part[0] = double(tx);
+            part[1] = double(ty);
+        }
+    }
+    if (need_coarse) {
+        // per coarse block: the band's share of the fine-slope sums (one warp per block)
+        const int ns = W.n_sub, nb = W.nb;
+        for (int blk = warp; blk < ns * ns; blk += nwarp) {
+            const int I = blk / ns, J = blk - I * ns;
+            const int i0 = max(I * nb, s0), i1 = min((I + 1) * nb, s1);
+            T sx = T(0), sy = T(0);
+            if (i0 < i1) {
+                for (int i = i0; i < i1; ++i)
+                    for (int j = J * nb + lane; j < (J + 1) * nb; j += 32) {
+                        sx += SX[(i - s0) * N + j];
+                        sy += SY[(i - s0) * N + j];
+                    }
+            }
+            sx = warp_sum_t(sx);
+            sy = warp_sum_t(sy);
+            if (lane == 0) {
+                part[2 + 2 * blk] = double(sx);
+                part[3 + 2 * blk] = double(sy);
+            }
+        }
+    }
+    if (need_tt || need_coarse) {
+        cluster.sync();                                                   // partials ready
+        if (need_tt) {
+            // warp 0 fetches the CL partials (one remote load per lane), fixed-order sum
+            if (threadIdx.x < 32) {
+                double px = 0.0, py = 0.0;
+                if (lane < CL) {
+                    const double* pp = cluster.map_shared_rank(part, lane);
+                    px = pp[0];
+                    py = pp[1];
+                }
+                T tx = T(0), ty = T(0);
+#pragma unroll
+                for (int q = 0; q < CL; ++q) {
+                    tx += T(__shfl_sync(0xffffffffu, px, q));
+                    ty += T(__shfl_sync(0xffffffffu, py, q));
+                }
+                if (threadIdx.x == 0) {
+                    red[0] = double(tx);
+                    red[1] = double(ty);
+                }
+            }
+            __syncthreads();
+            const T tx = T(red[0]), ty = T(red[1]);
+            const T mx = tx / T(W.n_active), my = ty / T(W.n_active);
+            // C_hat^-1 = (I - T) sigma^-2 (I - T) = sigma^-2 (I - T) for an LGS
+            for (int k = threadIdx.x; k < rows * N; k += NT) {
+                if (sidx[s0 * N + k] >= 0) {
+                    SX[k] = inv * (SX[k] - mx);
+                    SY[k] = inv * (SY[k] - my);
+                }
+            }
+        }
+        if (need_coarse) {
+            const int ns = W.n_sub;
+            for (int blk = threadIdx.x; blk < ns * ns; blk += NT) {
+                T sx = T(0), sy = T(0);
+                for (int q = 0; q < CL; ++q) {
+                    const double* pp = cluster.map_shared_rank(part, q);
+                    sx += T(pp[2 + 2 * blk]);
+                    sy += T(pp[3 + 2 * blk]);
+                }
+                // coarse slope = sum / nb; Gamma_coarse^T spreads sigma^-2 slope / nb
+                cw[2 * blk] = sx * nbinv * inv * nbinv;
+                cw[2 * blk + 1] = sy * nbinv * inv * nbinv;
+            }
+            __syncthreads();
+            for (int ii = warp; ii < rows; ii += nwarp)
+            for (int j = lane; j < N; j += 32) {
+                const int k = ii * N + j;
+                const int i = s0 + ii;
+                T sx = T(0), sy = T(0);
+                if (sidx[i * N + j] >= 0) {
+                    const int blk = (i / W.nb) * W.n_sub + j / W.nb;
+                    sx = cw[2 * blk];
+                    sy = cw[2 * blk + 1];
+                }
+                SX[k] = sx;
+                SY[k] = sy;
+            }
+        }
+    } else if (W.nb == 1) {
+        // NGS: C^-1 = sigma^-2 I
+        for (int k = threadIdx.x; k < rows * N; k += NT) {
+            SX[k] *= inv;
+            SY[k] *= inv;
+        }
+    }
+    cluster.sync();                                                       // weighted slopes ready
+    // ---- Gamma_g^T on node rows [s0, s1) (and row N on the last band) --------------------
+    if (rows > 0) {
+        if (r > 0) {
+            const T* px = cluster.map_shared_rank(SX, r - 1);
+            const T* py = cluster.map_shared_rank(SY, r - 1);
+            const int prow = (s0 - 1) - (r - 1) * sr;     // last row of the previous band
+            for (int j = threadIdx.x; j < N; j += NT) {
+                halo[j] = px[prow * N + j];
+                halo[N + j] = py[prow * N + j];
+            }
+        } else {
+            for (int j = threadIdx.x; j < N; j += NT) {
+                halo[j] = T(0);
+                halo[N + j] = T(0);
+            }
+        }
+        __syncthreads();
+        const int nrows = (s1 == N) ? rows + 1 : rows;
+        for (int ia = warp; ia < nrows; ia += nwarp)
+        for (int b = lane; b < NP; b += 32) {
+            const int aa = s0 + ia;
+            // subaperture row aa (below the node) and aa - 1 (above)
+            const bool has0 = aa < N, c0 = b < N, c1 = b > 0;
+            const T* x0 = SX + ia * N;
+            const T* y0 = SY + ia * N;
+            const T* x1 = ia > 0 ? SX + (ia - 1) * N : halo;
+            const T* y1 = ia > 0 ? SY + (ia - 1) * N : halo + N;
+            const bool has1 = aa > 0;
+            const T x_ab = (has0 && c0) ? x0[b] : T(0);
+            const T x_ab1 = (has0 && c1) ? x0[b - 1] : T(0);
+            const T x_a1b = (has1 && c0) ? x1[b] : T(0);
+            const T x_a1b1 = (has1 && c1) ? x1[b - 1] : T(0);
+            const T y_ab = (has0 && c0) ? y0[b] : T(0);
+            const T y_ab1 = (has0 && c1) ? y0[b - 1] : T(0);
+            const T y_a1b = (has1 && c0) ? y1[b] : T(0);
+            const T y_a1b1 = (has1 && c1) ? y1[b - 1] : T(0);
+            a.out[W.node_off + aa * NP + b] =
+                T(0.5) * ((x_ab1 - x_ab) + (x_a1b1 - x_a1b)) + T(0.5) * ((y_a1b - y_ab) + (y_a1b1 - y_ab1));
+        }
+    }
+    cluster.sync();                                                       // neighbours done reading
+}
+
+}  // namespace fewha

@@ -78,6 +78,9 @@ struct Desc {
     // per-coefficient diagonals
     const T* D;
     const T* Jinv;
+    // footprint box of each (sensor, layer) pair: row0, rows, col0, cols (16-byte aligned
+    // column superset); kept in the descriptor so that warps read it from the constant bank
+    int box[MAXG][MAXL][4];
 };
 
 // Host-side result of geometry set-up (all in double).

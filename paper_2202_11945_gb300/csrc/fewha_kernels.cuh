@@ -12,6 +12,7 @@
 namespace fewha {
 
 constexpr int BLK = 1024;   // threads of the per-layer and per-sensor kernels
+constexpr int PQ_SLOTS = MAXL * 8;   // p.q partial slots per CG iteration (layer x cluster rank)
 constexpr int PBLK = 256;   // threads of the vector (PCG) kernels
 constexpr int NWARP = BLK / 32;
 
@@ -240,10 +241,43 @@ __device__ __forceinline__ void dwt_inverse(T* S, const LayerInfo& L) {
 // sum of pqpart[k * MAXL + 0 .. n_layers).
 // ---------------------------------------------------------------------------
 struct PcgSlots {
-    double* rzpart;
-    double* pqpart;
+    double* rzpart;     // [slot * npart + cta]: partial r.z
+    double* pqpart;     // [slot * PQ_SLOTS + l * 8 + rank]: partial p.q
+    double* rztot;      // [slot]: r.z in fixed summation order (slot 0: initial residual)
+    double* pqtot;      // [slot]: p.q of iteration slot
+    unsigned* count;    // [2]: arrival counters of the reducing grids, reset by the last CTA
     int npart;
 };
+
+// Fixed-order sum of cnt <= 512 doubles written by other CTAs of this grid, by one warp:
+// every lane issues its loads at once (L2, bypassing L1), then a fixed shuffle tree.
+__device__ __forceinline__ double warp_fixed_sum(const double* p, int cnt) {
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = (threadIdx.x & 31) + 32 * k;
+        v[k] = i < cnt ? __ldcg(p + i) : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s += v[k];
+    return warp_sum(s);
+}
+
+// Arrival of one CTA of a reducing grid; true in the CTA that arrives last.  Its
+// partial must already be stored; the fence orders it before the count.
+__device__ __forceinline__ bool last_arrival(unsigned* count, unsigned ctas, bool* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(count, 1u);
+        *flag = (prev == ctas - 1);
+    }
+    __syncthreads();
+    const bool last = *flag;
+    if (last) __threadfence();
+    return last;
+}
 
 // ---------------------------------------------------------------------------
 // Per-layer kernel.  Source: the layer values (SRC_PHI), the adjoint projection of
@@ -613,77 +647,88 @@ struct VecArgs {
     int iter;
 };
 
-enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2, V_COPY = 3, V_ZERO = 4 };
+enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2 };
+
+constexpr int PVEC = 4;     // elements per thread and pass of the vector kernels
 
 template <class T, int PHASE>
 __global__ void __launch_bounds__(PBLK) k_vec(const int n, const VecArgs<T> v) {
-    __shared__ double red[2 * (PBLK / 32) + 4];
+    __shared__ bool last;
     double alpha = 0.0;
     if (PHASE == V_UPDATE) {
         // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final)
-        double rz = 0.0, pq = 0.0;
-        if (threadIdx.x < 32) {
-            double s = 0.0, t = 0.0;
-            for (int i = threadIdx.x; i < v.pcg.npart; i += 32) s += v.pcg.rzpart[v.iter * v.pcg.npart + i];
-            for (int i = threadIdx.x; i < MAXL; i += 32) t += v.pcg.pqpart[v.iter * MAXL + i];
-            s = warp_sum(s);
-            t = warp_sum(t);
-            if (threadIdx.x == 0) {
-                red[0] = s;
-                red[1] = t;
-            }
-        }
-        __syncthreads();
-        rz = red[0];
-        pq = red[1];
-        __syncthreads();
+        const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
         alpha = (rz != 0.0 && pq > 0.0) ? rz / pq : 0.0;
     }
     const T ta = T(alpha);
     double dot = 0.0;
-    const int stride = gridDim.x * PBLK;
-    for (int i = blockIdx.x * PBLK + threadIdx.x; i < n; i += stride) {
-        if (PHASE == V_COPY) {
-            v.c[i] = v.b[i];
-            continue;
+    for (int base = blockIdx.x * PBLK * PVEC; base < n; base += gridDim.x * PBLK * PVEC) {
+        // issue every load of the batch before the arithmetic
+        T b[PVEC], q[PVEC], r[PVEC], p[PVEC], c[PVEC], bp[PVEC], jv[PVEC];
+#pragma unroll
+        for (int k = 0; k < PVEC; ++k) {
+            const int i = base + k * PBLK + threadIdx.x;
+            if (i < n) {
+                jv[k] = v.Jinv[i];
+                if (PHASE == V_INIT) {
+                    b[k] = v.b[i];
+                    q[k] = v.q[i];
+                } else if (PHASE == V_INIT_WARM) {
+                    b[k] = v.b[i];
+                    bp[k] = v.b_prev[i];
+                    r[k] = v.r[i];
+                } else {
+                    c[k] = v.c[i];
+                    p[k] = v.p[i];
+                    r[k] = v.r[i];
+                    q[k] = v.q[i];
+                }
+            }
         }
-        if (PHASE == V_ZERO) {
-            v.c[i] = T(0);
-            continue;
+#pragma unroll
+        for (int k = 0; k < PVEC; ++k) {
+            const int i = base + k * PBLK + threadIdx.x;
+            if (i < n) {
+                T rr;
+                if (PHASE == V_INIT) {
+                    rr = b[k] - q[k];
+                    v.b_prev[i] = b[k];
+                } else if (PHASE == V_INIT_WARM) {
+                    rr = (b[k] - bp[k]) + r[k];
+                    v.b_prev[i] = b[k];
+                } else {
+                    v.c[i] = c[k] + ta * p[k];
+                    rr = r[k] - ta * q[k];
+                }
+                v.r[i] = rr;
+                const T z = jv[k] * rr;
+                v.z[i] = z;
+                if (PHASE != V_UPDATE) v.p[i] = z;
+                dot += double(rr) * double(z);
+            }
         }
-        T r;
-        if (PHASE == V_INIT) {
-            r = v.b[i] - v.q[i];
-            v.b_prev[i] = v.b[i];
-        } else if (PHASE == V_INIT_WARM) {
-            r = (v.b[i] - v.b_prev[i]) + v.r[i];
-            v.b_prev[i] = v.b[i];
-        } else {
-            v.c[i] += ta * v.p[i];
-            r = v.r[i] - ta * v.q[i];
-        }
-        v.r[i] = r;
-        const T z = v.Jinv[i] * r;
-        v.z[i] = z;
-        if (PHASE != V_UPDATE) v.p[i] = z;
-        dot += double(r) * double(z);
     }
-    if (PHASE == V_COPY || PHASE == V_ZERO) return;
-    double dummy = 0.0;
-    // block_sum2 uses NWARP slots sized for BLK; use a local two-level reduction here
-    dot = warp_sum(dot);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[2 + w] = dot;
+    // CTA partial of r.z (thread values summed by warp 0 in a fixed order: few FP64
+    // additions), then the last CTA forms the total in a fixed order
+    __shared__ double part[PBLK];
+    part[threadIdx.x] = dot;
     __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
     if (w == 0) {
-        double x = lane < PBLK / 32 ? red[2 + lane] : 0.0;
+        double x = 0.0;
+#pragma unroll
+        for (int i = 0; i < PBLK / 32; ++i) x += part[lane + 32 * i];
         x = warp_sum(x);
+        if (lane == 0) v.pcg.rzpart[slot * v.pcg.npart + blockIdx.x] = x;
+    }
+    if (last_arrival(v.pcg.count, gridDim.x, &last) && w == 0) {
+        const double tot = warp_fixed_sum(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart);
         if (lane == 0) {
-            const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
-            v.pcg.rzpart[slot * v.pcg.npart + blockIdx.x] = x;
+            v.pcg.rztot[slot] = tot;
+            v.pcg.count[0] = 0;
         }
     }
-    (void)dummy;
 }
 
 // ---------------------------------------------------------------------------

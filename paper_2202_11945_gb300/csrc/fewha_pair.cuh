@@ -1,0 +1,128 @@
+// Per (sensor, layer) pair kernels: the bilinear projection P_g (Sec. 2) is a sum over
+// layers of separable interpolations, P_g phi = sum_l R_y,gl phi_l R_x,gl^T, and its
+// adjoint is sum_g R_y,gl^T u_g R_x,gl.  One CTA per pair computes its term with two
+// separable passes in shared memory; the sensor and layer kernels add the terms up.
+// No reduction crosses CTAs here, so the sums stay in a fixed order.
+#pragma once
+
+#include "fewha_cluster.cuh"
+
+namespace fewha {
+
+// V_gl(a, b) = sum_{i,j} wy(a, i) wx(b, j) phi_l(i, j) over the pair's footprint box.
+template <class T>
+__global__ void __launch_bounds__(cblk<T>(), 1) k_proj(const Desc<T> d, const T* __restrict__ phi,
+                                                       const PairBufs<T> pb) {
+    constexpr int NT = cblk<T>();
+    constexpr int V = vec16<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* F = reinterpret_cast<T*>(smem_raw);       // footprint of phi_l: rows x cols
+    const int g = blockIdx.x, l = blockIdx.y;
+    const int N = d.G[g].N, NP = N + 1;
+    const int tp = (g * MAXL + l) * TAB;
+    const int r0 = d.box[g][l][0], rows = d.box[g][l][1], c0 = d.box[g][l][2], cols = d.box[g][l][3];
+    const int n = d.L[l].n;
+    T* Tm = F + rows * cols;                      // pass X result: rows x NP
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
+    const T* src = phi + d.L[l].off + r0 * n + c0;
+    if ((n & (V - 1)) == 0) {
+        const int cpr = cols / V;
+        for (int i = warp; i < rows; i += nwarp)
+            for (int c = lane; c < cpr; c += 32) cp_async16(F + i * cols + c * V, src + i * n + c * V);
+    } else {
+        for (int i = warp; i < rows; i += nwarp)
+            for (int j = lane; j < cols; j += 32) cp_async(F + i * cols + j, src + i * n + j);
+    }
+    cp_async_wait();
+    __syncthreads();
+    // pass X: Tm(i, b) = (1 - fx_b) F(i, j0_b) + fx_b F(i, j0_b + 1); thread per column b
+    {
+        const int b = threadIdx.x % NP, rg = threadIdx.x / NP, groups = NT / NP;
+        if (rg < groups) {
+            const int j0 = d.pi0x[tp + b] - c0;
+            const T fx = d.pfx[tp + b];
+            for (int i = rg; i < rows; i += groups)
+                Tm[i * NP + b] = (T(1) - fx) * F[i * cols + j0] + fx * F[i * cols + j0 + 1];
+        }
+    }
+    __syncthreads();
+    // pass Y: V(a, b) = (1 - fy_a) Tm(i0_a, b) + fy_a Tm(i0_a + 1, b)
+    T* out = pb.V + static_cast<size_t>(g * d.n_layers + l) * pb.vslot;
+    for (int a = warp; a < NP; a += nwarp) {
+        const int i0 = d.pi0y[tp + a] - r0;
+        const T fy = d.pfy[tp + a];
+        for (int b = lane; b < NP; b += 32)
+            out[a * pb.vs + b] = (T(1) - fy) * Tm[i0 * NP + b] + fy * Tm[(i0 + 1) * NP + b];
+    }
+}
+
+// Y_gl(i, j) = sum_{a,b} wy(a, i) wx(b, j) u_g(a, b) on the pair's footprint box.
+template <class T>
+__global__ void __launch_bounds__(cblk<T>(), 1) k_projT(const Desc<T> d, const T* __restrict__ u,
+                                                        const PairBufs<T> pb) {
+    constexpr int NT = cblk<T>();
+    constexpr int V = vec16<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* U = reinterpret_cast<T*>(smem_raw);       // u_g, (N+1)^2 (+ alignment shift)
+    const int g = blockIdx.x, l = blockIdx.y;
+    const int N = d.G[g].N, NP = N + 1;
+    const int tp = (g * MAXL + l) * TAB, rbk = (g * MAXL + l) * MAXN;
+    const int r0 = d.box[g][l][0], rows = d.box[g][l][1], c0 = d.box[g][l][2], cols = d.box[g][l][3];
+    const int start = d.G[g].node_off, s0a = start & ~(V - 1);
+    const int ushift = start - s0a;
+    T* Tx = U + ((ushift + NP * NP + V - 1) & ~(V - 1));   // pass X result: NP x cols
+    stage16(U, u + s0a, ushift + NP * NP, threadIdx.x, NT);
+    cp_async_wait();
+    __syncthreads();
+    const T* Us = U + ushift;
+    // pass X: Tx(a, j) = sum_{b touching j} wx(b, j) u(a, b); thread per box column j
+    {
+        const int groups = NT / cols;
+        const int jj = threadIdx.x % cols, rg = threadIdx.x / cols;
+        if (rg < groups) {
+            const int j = c0 + jj;
+            const int n = d.L[l].n;
+            int b0 = 0, c = 0;
+            if (j < n) {
+                b0 = d.rx_lo[rbk + j];
+                c = d.rx_hi[rbk + j] - b0;
+            }
+            T w[KMAX];
+#pragma unroll
+            for (int q = 0; q < KMAX; ++q) {
+                w[q] = T(0);
+                if (q < c) {
+                    const T f = d.pfx[tp + b0 + q];
+                    w[q] = d.pi0x[tp + b0 + q] == j ? T(1) - f : f;
+                }
+            }
+            for (int a = rg; a < NP; a += groups) {
+                const T* urow = Us + a * NP + b0;
+                T acc = T(0);
+#pragma unroll
+                for (int q = 0; q < KMAX; ++q)
+                    if (q < c) acc += w[q] * urow[q];
+                Tx[a * cols + jj] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // pass Y: Y(i, j) = sum_{a touching i} wy(a, i) Tx(a, j); warp per box row i
+    T* out = pb.Y + static_cast<size_t>(g * d.n_layers + l) * pb.yslot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
+    for (int ii = warp; ii < rows; ii += nwarp) {
+        const int i = r0 + ii;
+        const int a0 = d.ry_lo[rbk + i], a1 = d.ry_hi[rbk + i];
+        for (int jj = lane; jj < cols; jj += 32) {
+            T acc = T(0);
+            for (int a = a0; a < a1; ++a) {
+                const T f = d.pfy[tp + a];
+                const T wv = d.pi0y[tp + a] == i ? T(1) - f : f;
+                acc += wv * Tx[a * cols + jj];
+            }
+            out[ii * cols + jj] = acc;
+        }
+    }
+}
+
+}  // namespace fewha

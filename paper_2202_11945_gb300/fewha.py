@@ -68,7 +68,8 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_check_input", "fewha_pcg", "fewha_get_diagonals", "fewha_bench_stage",
            "fewha_frame_launches", "fewha_apply_M_noalloc"] + _OPS
 
-STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5}
+STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
+          "projT": 7}
 
 _lib = None
 
