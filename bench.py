@@ -38,7 +38,11 @@ METRIC = "FEWHA frames/s and p99 frame latency, MAORY-size, FP32 form vs FP64 pl
 UNIT = "frames/s"
 N_FRAMES_INPUT = 8          # distinct seeded frames, cycled through the timed loop
 FLUSH_BYTES = 512 << 20     # > 129 MB L2
-KERNEL_SRC = os.path.join(ROOT, "paper_2202_11945_gb300", "csrc", "fewha_kernels.cuh")
+_CSRC = os.path.join(ROOT, "paper_2202_11945_gb300", "csrc")
+# source file of each stage's kernel (the traffic record is tied to its hash)
+STAGE_SRC = {"idwt": "fewha_cluster.cuh", "sensor": "fewha_cluster.cuh", "layer": "fewha_cluster.cuh",
+             "rhs": "fewha_cluster.cuh", "proj": "fewha_pair.cuh", "projT": "fewha_pair.cuh",
+             "vector": "fewha_kernels.cuh", "fit": "fewha_kernels.cuh"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_maory_fp32.txt")
 
 
@@ -49,6 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-frames", type=int, default=20, help="oracle frames of the CPU baseline")
+    ap.add_argument("--loop-frames", type=int, default=2000,
+                    help="frames of the 1 kHz real-time loop (8 m single-conjugate geometry)")
     return ap.parse_args()
 
 
@@ -189,7 +195,10 @@ def recorded_traffic():
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    stage = kv.get("stage")
+    if stage not in STAGE_SRC:
+        return None, stage
+    sha = hashlib.sha256(open(os.path.join(_CSRC, STAGE_SRC[stage]), "rb").read()).hexdigest()
     if kv.get("kernel_source_sha256") != sha:
         return None, kv.get("stage")
     return float(kv["dram_bytes_per_launch"]), kv.get("stage")
@@ -220,6 +229,46 @@ def cpu_baseline(wl, frames, S_np, R_gpu_factory):
     return {"value": frames / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d warm-started MAORY frames (frame 0 cold), numpy FP64, 1 thread; "
                       "set-up (D, exact J) %.2f s not timed" % (frames, t_setup)}, parity
+
+
+def time_loop(frames, warmup=100, period_us=1000.0):
+    """The real-time loop: the 8 m single-conjugate geometry, frozen flow, frames released
+    every `period_us` from pinned host slopes, commands back on the host per frame."""
+    from paper_2202_11945_gb300 import Reconstructor
+    wl = synth.realtime_loop()
+    S = synth.slope_sequence(wl, frames)
+    R = Reconstructor(wl, precision=32, graph=True)
+    R.run_loop(S[:min(warmup, frames)], period_us=0.0)
+    R.reset()
+    dm, wall, dev, late = R.run_loop(S, period_us=period_us)
+    Rw = Reconstructor(wl, precision=32, graph=True, warm_residual=True)
+    dmw, _, _, _ = Rw.run_loop(S, period_us=0.0)
+    R.close()
+    Rw.close()
+    wall, dev = wall.numpy().astype(float), dev.numpy().astype(float)
+    out = {"workload": wl["name"], "frames": frames, "period_us": period_us,
+           "form": "FP32 operators, FP64 dots, CUDA graph; host slopes in, host commands out",
+           "latency_us": {"p50": float(np.percentile(wall, 50)), "p99": float(np.percentile(wall, 99)),
+                          "max": float(wall.max())},
+           "device_us": {"p50": float(np.percentile(dev, 50)), "p99": float(np.percentile(dev, 99))},
+           "late_frames": late}
+    return out, wl, S, dm.double().numpy(), dmw.double().numpy()
+
+
+def loop_parity(wl, S, dm, dmw):
+    """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
+    the same sequence (explicit initial residual), and the oracle's own frame rate."""
+    import oracle as O
+    ref = O.Reconstructor(wl)
+    t0 = time.perf_counter()
+    a = np.stack([ref.frame(s) for s in S])
+    t = time.perf_counter() - t0
+    e = np.array([np.linalg.norm(x - y) / np.linalg.norm(y) for x, y in zip(dm, a)])
+    ew = np.array([np.linalg.norm(x - y) / np.linalg.norm(y) for x, y in zip(dmw, a)])
+    return {"max_rel_l2_dm": float(e.max()), "p99_rel_l2_dm": float(np.percentile(e, 99)),
+            "warm_residual_max_rel_l2_dm": float(ew.max()),
+            "warm_residual_last_rel_l2_dm": float(ew[-1]),
+            "oracle_frames_per_s": len(S) / t}
 
 
 def run_reference(args, world, rank):
@@ -327,6 +376,8 @@ def main():
         traffic = None
     Rb.close()
 
+    loop, wl3, S3, dm3, dm3w = time_loop(args.loop_frames)
+
     total32 = float(t32.sum())
     total64 = float(t64.sum())
     tot_e2e = float(te.sum())
@@ -341,6 +392,7 @@ def main():
     if rank == 0 and world == 1:
         base, parity = cpu_baseline(wl, args.cpu_frames, S_np,
                                     lambda p: Reconstructor(wl, precision=p, graph=(p == 32)))
+        loop["parity"] = loop_parity(wl3, S3, dm3, dm3w)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -374,6 +426,7 @@ def main():
             "stage_share": {k: round(v / sum(share.values()), 4) for k, v in share.items()},
             "cpu_baseline": base,
             "parity": parity,
+            "realtime_loop": loop,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

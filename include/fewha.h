@@ -178,6 +178,28 @@ int fewha_reconstruct_host(fewha_handle* h, const float* h_slopes, float* h_dm_o
 int fewha_reconstruct_host_f64(fewha_handle* h, const double* h_slopes, double* h_dm_out,
                                void* stream);
 
+/* Real-time frame loop (Algorithm 1 run frame after frame, open loop): frame k reads
+ * the host slopes h_slopes + k * n_slopes, is warm-started from frame k - 1 (the
+ * handle's internal state, so frame 0 continues from whatever the handle holds), and
+ * writes its commands to h_dm_out + k * n_act.  Each frame is one host->device copy,
+ * one replay of the captured frame graph (with FEWHA_FLAG_GRAPH) and one
+ * device->host copy, then a synchronise: the frame's commands are on the host when
+ * its latency sample is taken.  Frame k is released at t0 + k * period_us (t0 = the
+ * call; the host busy-waits until then); period_us = 0 runs the frames back to back.
+ * Per frame, wall_us (nullable, n_frames floats) gets the host-clock time from the
+ * later of the frame's release and the end of the previous frame to its commands
+ * being on the host, and device_us (nullable) the CUDA-event time from the start of
+ * the slope copy to the end of the command copy.  *n_late (nullable) counts frames
+ * whose commands arrived after the next frame's release.  Host buffers should be
+ * pinned for the copies to be asynchronous.  A frame whose slopes hold a NaN or Inf
+ * still runs; the call then returns FEWHA_ERR_NONFINITE after the last frame, naming
+ * the first such frame in fewha_last_error.  Synchronous on `stream`. */
+int fewha_run_loop(fewha_handle* h, const float* h_slopes, int n_frames, float* h_dm_out,
+                   double period_us, float* wall_us, float* device_us, int* n_late, void* stream);
+int fewha_run_loop_f64(fewha_handle* h, const double* h_slopes, int n_frames, double* h_dm_out,
+                       double period_us, float* wall_us, float* device_us, int* n_late,
+                       void* stream);
+
 /* Non-finite flag of the slopes read by frames since the last call (1 if any NaN or
  * Inf was seen), then cleared.  Synchronises on `stream`. */
 int fewha_check_input(fewha_handle* h, int* nonfinite, void* stream);

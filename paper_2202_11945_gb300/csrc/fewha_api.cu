@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -710,6 +711,28 @@ int reconstruct_dev(fewha_handle* H, const T* s, T* x, T* dm, void* stream) {
     return run_frame<T>(H, s, x ? x : static_cast<T*>(H->c), dm, static_cast<cudaStream_t>(stream));
 }
 
+// Enqueue one frame from and to host memory; *flag receives the non-finite status.
+template <class T>
+int enqueue_host_frame(fewha_handle* H, const T* hs, T* hdm, unsigned* flag, cudaStream_t st) {
+    const HostSetup& s = H->setup;
+    int rc;
+    CK(cudaMemcpyAsync(H->s_tmp, hs, s.n_s * sizeof(T), cudaMemcpyHostToDevice, st), "slopes H2D");
+    if ((rc = run_frame<T>(H, static_cast<const T*>(H->s_tmp), static_cast<T*>(H->c),
+                           static_cast<T*>(H->dm_tmp), st)))
+        return rc;
+    CK(cudaMemcpyAsync(hdm, H->dm_tmp, s.n_act * sizeof(T), cudaMemcpyDeviceToHost, st), "DM D2H");
+    CK(cudaMemcpyAsync(flag, H->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "status");
+    return FEWHA_OK;
+}
+
+// After the stream has synchronised: clear a raised non-finite flag.
+int clear_flag(fewha_handle* H, unsigned flag, cudaStream_t st) {
+    if (!flag) return FEWHA_OK;
+    cudaMemsetAsync(H->status, 0, sizeof(unsigned), st);
+    cudaStreamSynchronize(st);
+    return fail(H, FEWHA_ERR_NONFINITE, "non-finite value in the input slopes");
+}
+
 template <class T>
 int reconstruct_host(fewha_handle* H, const T* hs, T* hdm, void* stream) {
     int rc;
@@ -717,20 +740,70 @@ int reconstruct_host(fewha_handle* H, const T* hs, T* hdm, void* stream) {
     if (!hs || !hdm) return fail(H, FEWHA_ERR_INVALID_ARG, "null host pointer");
     DeviceGuard g(H->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const HostSetup& s = H->setup;
-    CK(cudaMemcpyAsync(H->s_tmp, hs, s.n_s * sizeof(T), cudaMemcpyHostToDevice, st), "slopes H2D");
-    if ((rc = run_frame<T>(H, static_cast<const T*>(H->s_tmp), static_cast<T*>(H->c),
-                           static_cast<T*>(H->dm_tmp), st)))
-        return rc;
-    CK(cudaMemcpyAsync(hdm, H->dm_tmp, s.n_act * sizeof(T), cudaMemcpyDeviceToHost, st), "DM D2H");
     unsigned flag = 0;
-    CK(cudaMemcpyAsync(&flag, H->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "status");
+    if ((rc = enqueue_host_frame<T>(H, hs, hdm, &flag, st))) return rc;
     CK(cudaStreamSynchronize(st), "host frame");
-    if (flag) {
-        cudaMemsetAsync(H->status, 0, sizeof(unsigned), st);
-        cudaStreamSynchronize(st);
-        return fail(H, FEWHA_ERR_NONFINITE, "non-finite value in the input slopes");
+    return clear_flag(H, flag, st);
+}
+
+// Frames released on a fixed period from host buffers; see fewha_run_loop.
+template <class T>
+int run_loop(fewha_handle* H, const T* hs, int n_frames, T* hdm, double period_us, float* wall_us,
+             float* device_us, int* n_late, void* stream) {
+    int rc;
+    if ((rc = check_type<T>(H))) return rc;
+    if (n_frames < 0 || (n_frames > 0 && (!hs || !hdm)) || !(period_us >= 0.0))
+        return fail(H, FEWHA_ERR_INVALID_ARG, "bad frame count, host pointer or period");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const HostSetup& s = H->setup;
+    using clock = std::chrono::steady_clock;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(H, FEWHA_ERR_CUDA, "event");
     }
+    int late = 0, first_bad = -1;
+    rc = FEWHA_OK;
+    const clock::time_point t0 = clock::now();
+    clock::time_point prev_end = t0;
+    for (int k = 0; k < n_frames && rc == FEWHA_OK; ++k) {
+        const clock::time_point release =
+            t0 + std::chrono::duration_cast<clock::duration>(std::chrono::duration<double, std::micro>(period_us * k));
+        while (clock::now() < release) {
+        }
+        const clock::time_point start = std::max(release, prev_end);
+        unsigned flag = 0;
+        cudaEventRecord(e0, st);
+        if ((rc = enqueue_host_frame<T>(H, hs + static_cast<size_t>(k) * s.n_s,
+                                        hdm + static_cast<size_t>(k) * s.n_act, &flag, st)))
+            break;
+        cudaEventRecord(e1, st);
+        const cudaError_t se = cudaStreamSynchronize(st);
+        if (se != cudaSuccess) {
+            rc = cuda_fail(H, se, "loop frame");
+            break;
+        }
+        const clock::time_point end = clock::now();
+        if (clear_flag(H, flag, st) && first_bad < 0) first_bad = k;
+        if (wall_us) wall_us[k] = static_cast<float>(std::chrono::duration<double, std::micro>(end - start).count());
+        if (device_us) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            device_us[k] = 1e3f * ms;
+        }
+        if (period_us > 0.0 && end > release + std::chrono::duration_cast<clock::duration>(
+                                                   std::chrono::duration<double, std::micro>(period_us)))
+            ++late;
+        prev_end = end;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_late) *n_late = late;
+    if (rc) return rc;
+    if (first_bad >= 0)
+        return fail(H, FEWHA_ERR_NONFINITE, "non-finite value in the slopes of frame " + std::to_string(first_bad));
     return FEWHA_OK;
 }
 
@@ -1024,6 +1097,15 @@ int fewha_reconstruct_host(fewha_handle* h, const float* s, float* dm, void* str
 }
 int fewha_reconstruct_host_f64(fewha_handle* h, const double* s, double* dm, void* stream) {
     return reconstruct_host<double>(h, s, dm, stream);
+}
+
+int fewha_run_loop(fewha_handle* h, const float* s, int n_frames, float* dm, double period_us,
+                   float* wall_us, float* device_us, int* n_late, void* stream) {
+    return run_loop<float>(h, s, n_frames, dm, period_us, wall_us, device_us, n_late, stream);
+}
+int fewha_run_loop_f64(fewha_handle* h, const double* s, int n_frames, double* dm, double period_us,
+                       float* wall_us, float* device_us, int* n_late, void* stream) {
+    return run_loop<double>(h, s, n_frames, dm, period_us, wall_us, device_us, n_late, stream);
 }
 
 int fewha_check_input(fewha_handle* H, int* nonfinite, void* stream) {

@@ -66,7 +66,8 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_sizes", "fewha_update_params", "fewha_reset", "fewha_reconstruct",
            "fewha_reconstruct_f64", "fewha_reconstruct_host", "fewha_reconstruct_host_f64",
            "fewha_check_input", "fewha_pcg", "fewha_get_diagonals", "fewha_bench_stage",
-           "fewha_frame_launches", "fewha_apply_M_noalloc"] + _OPS
+           "fewha_frame_launches", "fewha_apply_M_noalloc", "fewha_run_loop",
+           "fewha_run_loop_f64"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -105,6 +106,9 @@ def lib():
     L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_bench_stage.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
     L.fewha_frame_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    for name in ["fewha_run_loop", "fewha_run_loop_f64"]:
+        getattr(L, name).argtypes = [_VP, _VP, ctypes.c_int, _VP, ctypes.c_double, _VP, _VP,
+                                     ctypes.POINTER(ctypes.c_int), _VP]
     for name in _OPS + ["fewha_apply_M_noalloc"]:
         getattr(L, name).argtypes = [_VP, _VP, _VP, _VP]
     for name in EXPORTS:
@@ -207,6 +211,30 @@ class Reconstructor:
         self._check(fn(self.h, ctypes.c_void_p(slopes.data_ptr()), ctypes.c_void_p(dm_out.data_ptr()),
                        _stream(stream)))
         return dm_out
+
+    def run_loop(self, slopes, period_us=1000.0, stream=None):
+        """Frames of a real-time loop from host slopes (n_frames x n_slopes, any layout that
+        converts to a contiguous host tensor of the handle's dtype), released every
+        `period_us` (0: back to back), each warm-started from the previous one.
+
+        Returns (dm [n_frames, n_act] host tensor, wall_us, device_us, n_late): per-frame
+        host-clock latency from release to commands on the host, the CUDA-event time of
+        the frame's copies and kernels, and the number of frames that missed the next
+        release."""
+        s = torch.as_tensor(slopes, dtype=self.dtype).contiguous()
+        if s.is_cuda or s.dim() != 2 or s.shape[1] != self.n_slopes:
+            raise ValueError("slopes must be a host array of shape [n_frames, %d]" % self.n_slopes)
+        F = s.shape[0]
+        s = s.pin_memory()
+        dm = torch.empty((F, self.n_act), dtype=self.dtype).pin_memory()
+        wall = torch.zeros(F, dtype=torch.float32)
+        dev = torch.zeros(F, dtype=torch.float32)
+        late = ctypes.c_int(0)
+        fn = self.L.fewha_run_loop if self.precision == 32 else self.L.fewha_run_loop_f64
+        self._check(fn(self.h, ctypes.c_void_p(s.data_ptr()), int(F), ctypes.c_void_p(dm.data_ptr()),
+                       float(period_us), ctypes.c_void_p(wall.data_ptr()),
+                       ctypes.c_void_p(dev.data_ptr()), ctypes.byref(late), _stream(stream)))
+        return dm, wall, dev, late.value
 
     def check_input(self, stream=None):
         flag = ctypes.c_int(0)

@@ -16,4 +16,4 @@ from .configs import (  # noqa: F401
     workload_by_name, arcsec,
 )
 from .atmosphere import TruthAtmosphere  # noqa: F401
-from .sensor import simulate_slopes, slope_counts  # noqa: F401
+from .sensor import simulate_slopes, slope_counts, slope_sequence, true_phase_at  # noqa: F401

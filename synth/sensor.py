@@ -80,3 +80,10 @@ def true_phase_at(wl, x, y, frame=0, atm=None):
     if atm is None:
         atm = TruthAtmosphere(wl["truth"])
     return atm.phase(np.asarray(x, float), np.asarray(y, float), (0.0, 0.0), 0.0, frame)
+
+
+def slope_sequence(wl, n_frames, atm=None, first=0):
+    """Measurement vectors of frames first .. first + n_frames - 1 as rows (float64)."""
+    if atm is None:
+        atm = TruthAtmosphere(wl["truth"])
+    return np.stack([simulate_slopes(wl, first + t, atm=atm) for t in range(n_frames)])
