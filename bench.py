@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-frames", type=int, default=20, help="oracle frames of the CPU baseline")
+    ap.add_argument("--batch-count", type=int, default=64, help="instances of the batched workload")
+    ap.add_argument("--batch-steps", type=int, default=50, help="timed batched frames")
     ap.add_argument("--loop-frames", type=int, default=2000,
                     help="frames of the 1 kHz real-time loop (8 m single-conjugate geometry)")
     return ap.parse_args()
@@ -255,6 +257,76 @@ def time_loop(frames, warmup=100, period_us=1000.0):
     return out, wl, S, dm.double().numpy(), dmw.double().numpy()
 
 
+def frame_bytes(R, b=4):
+    """Algorithmic bytes of one frame of an instance (stage bytes x launches per frame)."""
+    nb = stage_bytes(R, b)
+    la = stage_launches(R.iters)
+    return sum(nb[k] * la[k] for k in nb)
+
+
+def time_batched(count, steps, warmup, flush):
+    """Uneven instances: one-by-one frames (each instance's own graph, one after another)
+    against the batched frame (one launch per step over all instances), autotuned."""
+    from paper_2202_11945_gb300 import Batch, Reconstructor
+    wls = synth.batched_instances(count)
+    S = []
+    for wl in wls:
+        atm = synth.TruthAtmosphere(wl["truth"])
+        S.append([torch.as_tensor(synth.simulate_slopes(wl, t, atm=atm), dtype=torch.float32,
+                                  device="cuda") for t in range(2)])
+    solo = [Reconstructor(wl, precision=32, graph=True) for wl in wls]
+    mem = [Reconstructor(wl, precision=32, graph=True) for wl in wls]
+    B = Batch(mem)
+    cfg, tuned_us = B.autotune([s[0] for s in S], reps=5)
+    for R in mem:
+        R.reset()
+    torch.cuda.synchronize()
+
+    def run(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record()
+            fn(k)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ev])
+
+    dm_solo = [torch.empty(R.n_act, dtype=torch.float32, device="cuda") for R in solo]
+    dm_b = [torch.empty(R.n_act, dtype=torch.float32, device="cuda") for R in mem]
+
+    def one_by_one(k):
+        for i, R in enumerate(solo):
+            R.reconstruct(S[i][k % 2], dm_out=dm_solo[i])
+
+    def batched(k):
+        B.reconstruct([s[k % 2] for s in S], dm_out=dm_b)
+
+    run(one_by_one, warmup)
+    run(batched, warmup)
+    t1 = run(one_by_one, steps)
+    tb = run(batched, steps)
+    # same frame count on both sides and the same inputs: compare the last commands
+    diff = max(float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
+               for a, b in zip(dm_b, dm_solo))
+    nbytes = sum(frame_bytes(R) for R in mem)
+    out = {"workload": "batched_%d_uneven_instances" % count, "instances": count,
+           "frames_per_s": count / (tb.mean() * 1e-3),
+           "one_by_one_frames_per_s": count / (t1.mean() * 1e-3),
+           "speedup": float(t1.mean() / tb.mean()),
+           "ms_per_batch": float(tb.mean()), "p99_ms_per_batch": float(np.percentile(tb, 99)),
+           "ms_one_by_one": float(t1.mean()),
+           "config": cfg, "autotune_us": tuned_us,
+           "max_rel_l2_vs_one_by_one": diff,
+           "algorithmic_gb_s": nbytes / (tb.mean() * 1e-3) / 1e9,
+           "l2": "512 MiB memset between timed batches", "steps": steps}
+    B.close()
+    for R in solo + mem:
+        R.close()
+    return out
+
+
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
     the same sequence (explicit initial residual), and the oracle's own frame rate."""
@@ -377,6 +449,7 @@ def main():
     Rb.close()
 
     loop, wl3, S3, dm3, dm3w = time_loop(args.loop_frames)
+    batched = time_batched(args.batch_count, args.batch_steps, 3, flush) if args.batch_count > 0 else None
 
     total32 = float(t32.sum())
     total64 = float(t64.sum())
@@ -427,6 +500,7 @@ def main():
             "cpu_baseline": base,
             "parity": parity,
             "realtime_loop": loop,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

@@ -178,6 +178,13 @@ int fewha_reconstruct_host(fewha_handle* h, const float* h_slopes, float* h_dm_o
 int fewha_reconstruct_host_f64(fewha_handle* h, const double* h_slopes, double* h_dm_out,
                                void* stream);
 
+/* Warm-start state of the frame loop (checkpoint / resume): the wavelet coefficients c
+ * (n_coeffs) and the previous commands a_prev (n_act), device pointers of the handle's
+ * element type, either may be NULL.  set_state also discards the warm residual (the next
+ * frame forms r0 = b - M c explicitly).  Stream-ordered. */
+int fewha_get_state(fewha_handle* h, void* d_c, void* d_a_prev, void* stream);
+int fewha_set_state(fewha_handle* h, const void* d_c, const void* d_a_prev, void* stream);
+
 /* Real-time frame loop (Algorithm 1 run frame after frame, open loop): frame k reads
  * the host slopes h_slopes + k * n_slopes, is warm-started from frame k - 1 (the
  * handle's internal state, so frame 0 continues from whatever the handle holds), and
@@ -254,6 +261,61 @@ int fewha_get_diagonals(fewha_handle* h, void* d_D, void* d_J, void* stream);
 int fewha_bench_stage(fewha_handle* h, int stage, int reps, void* stream);
 /* Kernel launches one frame enqueues (for the launch count of a timed region). */
 int fewha_frame_launches(const fewha_handle* h, int* launches);
+
+/* ---- batched frames of many instances ------------------------------------------
+ * Independent instances of uneven size (telescope, sensors, layers, DMs) reconstruct one
+ * frame each in one CUDA-graph replay.  The frame of Algorithm 1 is the same sequence of
+ * steps for every instance (right-hand side, initial residual, `iters` PCG iterations,
+ * fit), so each step runs as ONE kernel launch over a work list of (instance, unit)
+ * items, a unit being a layer, a sensor, a (sensor, layer) pair or a CTA of the vector
+ * and fit kernels.  Results are bit-identical to the instances' own fewha_reconstruct.
+ * All instances must share the device, precision, iteration count and warm-residual
+ * mode; each runs on its own internal warm state (as fewha_reconstruct with
+ * d_x_warm = NULL).  A handle may belong to several batches but not twice to one; a
+ * batch whose member was destroyed fails with FEWHA_ERR_INVALID_ARG.  A batch is not
+ * thread-safe, and no member may run other work concurrently with it. */
+typedef struct fewha_batch fewha_batch;
+
+/* Launch shape of a batch (what the autotuner chooses). */
+typedef struct {
+    int order;       /* 0: work items in the given instance order; 1: costliest instance first */
+    int groups;      /* 1..FEWHA_BATCH_MAX_GROUPS: instances split (by balanced cost) into this
+                        many independent launch chains that run concurrently */
+    int vec_passes;  /* 1..8: 1024-element passes per CTA of the vector kernel */
+} fewha_batch_config;
+
+#define FEWHA_BATCH_MAX_GROUPS 8
+#define FEWHA_BATCH_MAX_COUNT 4096
+
+int fewha_batch_create(fewha_handle* const* handles, int count, fewha_batch** out);
+void fewha_batch_destroy(fewha_batch* b);
+const char* fewha_batch_last_error(const fewha_batch* b);
+int fewha_batch_set_config(fewha_batch* b, const fewha_batch_config* cfg);
+int fewha_batch_get_config(const fewha_batch* b, fewha_batch_config* cfg);
+
+/* One frame of every instance: d_slopes[i] (device, the handle's element type) ->
+ * d_dm_out[i].  Asynchronous on `stream`.  The graph is captured on the first call and
+ * re-captured when the configuration, the warm-residual state or a member's parameters
+ * change; new slope / command pointers only refresh a device argument table (uploaded on
+ * `stream`). */
+int fewha_batch_reconstruct(fewha_batch* b, const void* const* d_slopes, void* const* d_dm_out,
+                            void* stream);
+
+/* Autotuner: times every candidate configuration (order x groups x vec_passes) on
+ * `reps` batched frames of the given slopes (CUDA events on `stream`), keeps the fastest
+ * in the batch and in a process-wide table keyed by the instances' shapes (a later batch
+ * of the same shapes starts from it), and restores every member's warm state afterwards.
+ * *best_us (nullable) receives the chosen configuration's mean frame time.  Synchronous. */
+int fewha_batch_autotune(fewha_batch* b, const void* const* d_slopes, void* const* d_dm_out,
+                         int reps, float* best_us, void* stream);
+
+/* The same frame without a batch object: a batch for this exact handle list is created on
+ * first use and cached (dropped when a member is destroyed). */
+int fewha_reconstruct_batched(fewha_handle* const* handles, int count, const float* const* d_slopes,
+                              float* const* d_dm_out, void* stream);
+int fewha_reconstruct_batched_f64(fewha_handle* const* handles, int count,
+                                  const double* const* d_slopes, double* const* d_dm_out,
+                                  void* stream);
 
 /* ---- no-allocation variant ------------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that may not

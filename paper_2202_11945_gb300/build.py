@@ -1,6 +1,7 @@
 """Build the in-tree CUDA library ``libfewha.so`` for sm_103a.
 
-Two translation units (the CUDA C-ABI with its kernels, and the host set-up code)
+Three translation units (the CUDA C-ABI with its kernels, the batched kernels, and the
+host set-up code)
 are compiled in parallel with nvcc and linked into one shared library next to
 this file.  Run as ``python -m paper_2202_11945_gb300.build`` or via
 ``__graft_entry__.build()``.
@@ -18,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfewha.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
-SOURCES = ["fewha_api.cu", "fewha_setup.cpp"]
+SOURCES = ["fewha_api.cu", "fewha_batch.cu", "fewha_setup.cpp"]
 
 
 def nvcc():

@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "fewha_pair.cuh"
+#include "fewha_batch.h"
 
 using namespace fewha;
 
@@ -80,6 +80,32 @@ struct fewha_handle {
     void* pairV = nullptr;
     void* pairY = nullptr;
     int pvs = 0, pvslot = 0, pyslot = 0;
+    // batches this instance belongs to, and a counter of parameter updates (a batch
+    // rebuilds its copy of the descriptor when it changes)
+    std::vector<fewha_batch*> batches;
+    unsigned version = 0;
+};
+
+struct fewha_batch {
+    std::vector<fewha_handle*> h;   // members (an entry is cleared when its handle is destroyed)
+    std::vector<unsigned> ver;      // member versions the plan was built with
+    int precision = 32;
+    int device = 0;
+    bool dead = false;
+    bool registry = false;          // owned by the fewha_reconstruct_batched cache
+    std::string err;
+    fewha_batch_config cfg{0, 1, 1};
+    // current plan: one device block [instances | work lists | argument table] and a graph
+    bool have_plan = false;
+    bool plan_warm = false;
+    fewha_batch_config plan_cfg{0, 0, 0};
+    void* dev = nullptr;
+    size_t args_off = 0;
+    std::vector<unsigned char> args_host;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaStream_t branch[FEWHA_BATCH_MAX_GROUPS] = {};
+    cudaEvent_t ev[FEWHA_BATCH_MAX_GROUPS] = {};
 };
 
 namespace {
@@ -178,6 +204,41 @@ Desc<T> make_desc(const fewha_handle* H) {
     return d;
 }
 
+// ---------------------------------------------------------------- step recording
+// A batched frame runs the single-instance frame sequence of every instance: while a
+// recorder is set on this thread, the launchers below append their step (kind and
+// arguments) to it instead of launching.
+template <class T>
+struct BStep {
+    int kind;
+    ClArgs<T> cl;
+    SensorArgs<T> sa;
+    VecArgs<T> va;
+    const T* ptr;
+    FitArgs<T> fa;
+};
+
+template <class T>
+struct Recorder {
+    std::vector<BStep<T>> steps;
+};
+
+thread_local void* g_recorder = nullptr;
+
+template <class T>
+Recorder<T>* recorder() {
+    return static_cast<Recorder<T>*>(g_recorder);
+}
+
+template <class T>
+BStep<T>& record(int kind) {
+    BStep<T> st;
+    std::memset(&st, 0, sizeof(st));
+    st.kind = kind;
+    recorder<T>()->steps.push_back(st);
+    return recorder<T>()->steps.back();
+}
+
 // ---------------------------------------------------------------- launchers
 template <class T, int SRC, int DST, bool PUPD>
 int launch_layer(fewha_handle* H, const Desc<T>& d, const LayerArgs<T>& a, cudaStream_t st) {
@@ -255,6 +316,10 @@ PairBufs<T> pair_bufs(fewha_handle* H) {
 
 template <class T>
 int launch_proj(fewha_handle* H, const Desc<T>& d, const T* phi, cudaStream_t st) {
+    if (recorder<T>()) {
+        record<T>(BK_PROJ).ptr = phi;
+        return FEWHA_OK;
+    }
     k_proj<T><<<dim3(d.n_wfs, d.n_layers), cblk<T>(), H->smem_proj, st>>>(d, phi, pair_bufs<T>(H));
     CK(cudaGetLastError(), "k_proj launch");
     return FEWHA_OK;
@@ -262,6 +327,10 @@ int launch_proj(fewha_handle* H, const Desc<T>& d, const T* phi, cudaStream_t st
 
 template <class T>
 int launch_projT(fewha_handle* H, const Desc<T>& d, const T* u, cudaStream_t st) {
+    if (recorder<T>()) {
+        record<T>(BK_PROJT).ptr = u;
+        return FEWHA_OK;
+    }
     k_projT<T><<<dim3(d.n_wfs, d.n_layers), cblk<T>(), H->smem_projT, st>>>(d, u, pair_bufs<T>(H));
     CK(cudaGetLastError(), "k_projT launch");
     return FEWHA_OK;
@@ -269,6 +338,12 @@ int launch_projT(fewha_handle* H, const Desc<T>& d, const T* u, cudaStream_t st)
 
 template <class T, int SRC, int DST>
 int launch_fwd(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream_t st) {
+    if (recorder<T>()) {
+        if (SRC != LSRC_NODES || (DST != LDST_APPLY && DST != LDST_COEF))
+            return fail(H, FEWHA_ERR_INVALID_ARG, "step without a batched form");
+        record<T>(DST == LDST_APPLY ? BK_FWD_APPLY : BK_FWD_COEF).cl = a;
+        return FEWHA_OK;
+    }
     k_cl_fwd<T, SRC, DST><<<dim3(CL, d.n_layers), cblk<T>(), H->smem_fwd, st>>>(d, a, H->lay_fwd,
                                                                                    pair_bufs<T>(H));
     CK(cudaGetLastError(), "k_cl_fwd launch");
@@ -277,6 +352,10 @@ int launch_fwd(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream
 
 template <class T, bool PUPD>
 int launch_inv(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream_t st) {
+    if (recorder<T>()) {
+        record<T>(PUPD ? BK_INV_UPD : BK_INV).cl = a;
+        return FEWHA_OK;
+    }
     k_cl_inv<T, PUPD><<<dim3(CL, d.n_layers), cblk<T>(), H->smem_inv, st>>>(d, a, H->lay_inv);
     CK(cudaGetLastError(), "k_cl_inv launch");
     return FEWHA_OK;
@@ -285,6 +364,10 @@ int launch_inv(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream
 template <class T, int SRC>
 int launch_csensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaStream_t st) {
     SensorArgs<T> a{in, out, H->status};
+    if (recorder<T>()) {
+        record<T>(SRC == SSRC_PHI ? BK_SEN_PHI : BK_SEN_SLOPES).sa = a;
+        return FEWHA_OK;
+    }
     k_cl_sensor<T, SRC><<<dim3(CL, d.n_wfs), cblk<T>(), H->smem_sen, st>>>(d, a, H->lay_sen,
                                                                           pair_bufs<T>(H));
     CK(cudaGetLastError(), "k_cl_sensor launch");
@@ -332,23 +415,42 @@ int enqueue_rhs(fewha_handle* H, const Desc<T>& d, const T* s, T* bout, cudaStre
 
 int vec_grid(const fewha_handle* H) { return H->npart; }
 
+template <class T, int PHASE>
+int launch_vec(fewha_handle* H, int n, const VecArgs<T>& v, cudaStream_t st) {
+    if (recorder<T>()) {
+        record<T>(PHASE == V_INIT ? BK_VEC_INIT : PHASE == V_INIT_WARM ? BK_VEC_WARM : BK_VEC_UPDATE).va = v;
+        return FEWHA_OK;
+    }
+    k_vec<T, PHASE><<<vec_grid(H), PBLK, 0, st>>>(n, v);
+    CK(cudaGetLastError(), "k_vec launch");
+    return FEWHA_OK;
+}
+
+template <class T>
+int launch_fit(fewha_handle* H, const Desc<T>& d, const T* phi, T* a_prev, T* dm, int gain, cudaStream_t st) {
+    if (recorder<T>()) {
+        record<T>(BK_FIT).fa = FitArgs<T>{phi, a_prev, dm, gain};
+        return FEWHA_OK;
+    }
+    k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, a_prev, dm, gain);
+    CK(cudaGetLastError(), "k_fit launch");
+    return FEWHA_OK;
+}
+
 // `iters` PCG iterations on M c = b (b in H->b), r0 explicit or warm.
 template <class T>
 int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, cudaStream_t st) {
     int rc;
     if (warm) {
-        k_vec<T, V_INIT_WARM><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, c, 0));
-        CK(cudaGetLastError(), "k_vec init");
+        if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
     } else {
         if ((rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
-        k_vec<T, V_INIT><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, c, 0));
-        CK(cudaGetLastError(), "k_vec init");
+        if ((rc = launch_vec<T, V_INIT>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
     }
     T* p = static_cast<T*>(H->p);
     for (int k = 0; k < iters; ++k) {
         if ((rc = enqueue_apply<T>(H, d, p, static_cast<T*>(H->q), k, k > 0, st))) return rc;
-        k_vec<T, V_UPDATE><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, c, k));
-        CK(cudaGetLastError(), "k_vec update");
+        if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, vec_args<T>(H, c, k), st))) return rc;
     }
     return FEWHA_OK;
 }
@@ -358,10 +460,7 @@ int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain,
     T* phi = static_cast<T*>(H->phi);
     int rc;
     if ((rc = launch_inv<T, false>(H, d, cl_args<T>(H, c, phi), st))) return rc;
-    k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, static_cast<T*>(H->a_prev), dm,
-                                                           gain ? 1 : 0);
-    CK(cudaGetLastError(), "k_fit launch");
-    return FEWHA_OK;
+    return launch_fit<T>(H, d, phi, static_cast<T*>(H->a_prev), dm, gain ? 1 : 0, st);
 }
 
 // One frame of Algorithm 1 (open loop).
@@ -807,6 +906,493 @@ int run_loop(fewha_handle* H, const T* hs, int n_frames, T* hdm, double period_u
     return FEWHA_OK;
 }
 
+// ---------------------------------------------------------------- batched frames
+int bfail(fewha_batch* B, int code, const std::string& msg) {
+    if (B) B->err = msg;
+    return code;
+}
+
+#define BCK(call, where)                                                                      \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return bfail(B, FEWHA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t round16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+template <class T>
+size_t barg_size(int kind) {
+    switch (kind) {
+        case BK_INV: case BK_INV_UPD: case BK_FWD_APPLY: case BK_FWD_COEF: return sizeof(ClArgs<T>);
+        case BK_SEN_PHI: case BK_SEN_SLOPES: return sizeof(SensorArgs<T>);
+        case BK_PROJ: case BK_PROJT: return sizeof(const T*);
+        case BK_FIT: return sizeof(FitArgs<T>);
+        default: return sizeof(VecArgs<T>);
+    }
+}
+
+size_t bsmem(const fewha_handle* H, int kind) {
+    switch (kind) {
+        case BK_INV: case BK_INV_UPD: return H->smem_inv;
+        case BK_FWD_APPLY: case BK_FWD_COEF: return H->smem_fwd;
+        case BK_SEN_PHI: case BK_SEN_SLOPES: return H->smem_sen;
+        case BK_PROJ: return H->smem_proj;
+        case BK_PROJT: return H->smem_projT;
+        default: return 0;
+    }
+}
+
+// Relative work of one instance's frame: the wavelet transforms scale with n_c, the
+// projections with layers x aperture nodes.
+double bcost(const fewha_handle* H) {
+    return 2.0 * H->setup.n_c + static_cast<double>(H->setup.L.size()) * H->setup.n_nodes;
+}
+
+int bnparts(const fewha_handle* H, int vec_passes) {
+    const int per = PBLK * PVEC * vec_passes;
+    int n = (H->setup.n_c + per - 1) / per;
+    return n < 1 ? 1 : (n > NPART_MAX ? NPART_MAX : n);
+}
+
+// Record every member's frame (host only) and check that the step sequences agree.
+template <class T>
+int batch_record(fewha_batch* B, const T* const* s, T* const* dm, bool warm, std::vector<Recorder<T>>& recs) {
+    const size_t n = B->h.size();
+    recs.assign(n, Recorder<T>());
+    for (size_t i = 0; i < n; ++i) {
+        fewha_handle* H = B->h[i];
+        if (!s[i] || !dm[i]) return bfail(B, FEWHA_ERR_INVALID_ARG, "null slope or DM pointer of instance " + std::to_string(i));
+        g_recorder = &recs[i];
+        const int rc = enqueue_frame<T>(H, s[i], static_cast<T*>(H->c), dm[i], warm, nullptr);
+        g_recorder = nullptr;
+        if (rc) return bfail(B, rc, "instance " + std::to_string(i) + ": " + H->err);
+        bool same = recs[i].steps.size() == recs[0].steps.size();
+        for (size_t j = 0; same && j < recs[i].steps.size(); ++j) same = recs[i].steps[j].kind == recs[0].steps[j].kind;
+        if (!same) return bfail(B, FEWHA_ERR_INVALID_ARG, "instances differ in iteration count or residual mode");
+    }
+    return FEWHA_OK;
+}
+
+// Argument table: per step, one entry per instance, each step's array 16-byte aligned.
+template <class T>
+void batch_pack(const std::vector<Recorder<T>>& recs, const std::vector<int>& nparts,
+                std::vector<unsigned char>& out, std::vector<size_t>& offs) {
+    const size_t n = recs.size(), S = recs[0].steps.size();
+    offs.assign(S, 0);
+    size_t off = 0;
+    for (size_t j = 0; j < S; ++j) {
+        offs[j] = off;
+        off += round16(n * barg_size<T>(recs[0].steps[j].kind));
+    }
+    out.assign(off, 0);
+    for (size_t j = 0; j < S; ++j) {
+        const int kind = recs[0].steps[j].kind;
+        const size_t sz = barg_size<T>(kind);
+        for (size_t i = 0; i < n; ++i) {
+            const BStep<T>& st = recs[i].steps[j];
+            unsigned char* dst = out.data() + offs[j] + i * sz;
+            switch (bkind_list(kind)) {
+                case BL_LAYER: std::memcpy(dst, &st.cl, sz); break;
+                case BL_SENSOR: std::memcpy(dst, &st.sa, sz); break;
+                case BL_PAIR: std::memcpy(dst, &st.ptr, sz); break;
+                case BL_FIT: std::memcpy(dst, &st.fa, sz); break;
+                default: {
+                    VecArgs<T> v = st.va;
+                    v.pcg.npart = nparts[i];
+                    std::memcpy(dst, &v, sz);
+                }
+            }
+        }
+    }
+}
+
+void batch_drop_plan(fewha_batch* B) {
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+    if (B->dev) cudaFree(B->dev);
+    B->dev = nullptr;
+    B->have_plan = false;
+}
+
+// Build the device block and capture the graph of one batched frame.
+template <class T>
+int batch_build(fewha_batch* B, const std::vector<Recorder<T>>& recs, const std::vector<int>& nparts,
+                const std::vector<unsigned char>& args, const std::vector<size_t>& offs, bool warm) {
+    const int n = static_cast<int>(B->h.size());
+    const fewha_batch_config cfg = B->cfg;
+    BCK(cudaDeviceSynchronize(), "batch sync");
+    batch_drop_plan(B);
+    // order and groups (greedy balanced partition by cost, costliest first)
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) cost[i] = bcost(B->h[i]);
+    std::vector<int> byc(n);
+    for (int i = 0; i < n; ++i) byc[i] = i;
+    std::stable_sort(byc.begin(), byc.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    const int G = std::max(1, std::min(cfg.groups, n));
+    std::vector<int> grp(n, 0);
+    std::vector<double> load(G, 0.0);
+    for (int i : byc) {
+        const int g = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+        grp[i] = g;
+        load[g] += cost[i];
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = cfg.order == 1 ? byc[i] : i;
+    // work lists per group
+    std::vector<std::vector<BItem>> lists(G * BL_COUNT);
+    for (int i : order) {
+        const fewha_handle* H = B->h[i];
+        const int g = grp[i], nl = static_cast<int>(H->setup.L.size()), nw = static_cast<int>(H->setup.G.size());
+        for (int l = 0; l < nl; ++l) lists[g * BL_COUNT + BL_LAYER].push_back({i, l});
+        for (int w = 0; w < nw; ++w) lists[g * BL_COUNT + BL_SENSOR].push_back({i, w});
+        for (int w = 0; w < nw; ++w)
+            for (int l = 0; l < nl; ++l) lists[g * BL_COUNT + BL_PAIR].push_back({i, w * MAXL + l});
+        for (int k = 0; k < nparts[i]; ++k) lists[g * BL_COUNT + BL_VEC].push_back({i, k});
+        for (int k = 0; k < (H->setup.n_act + PBLK - 1) / PBLK; ++k) lists[g * BL_COUNT + BL_FIT].push_back({i, k});
+    }
+    // instances
+    std::vector<BInst<T>> inst(n);
+    for (int i = 0; i < n; ++i) {
+        fewha_handle* H = B->h[i];
+        BInst<T>& I = inst[i];
+        std::memset(&I, 0, sizeof(I));
+        I.d = make_desc<T>(H);
+        I.lay_fwd = H->lay_fwd;
+        I.lay_inv = H->lay_inv;
+        I.lay_sen = H->lay_sen;
+        I.pb = pair_bufs<T>(H);
+        I.desc_bytes = static_cast<int>(offsetof(Desc<T>, box) + static_cast<size_t>(I.d.n_wfs) * MAXL * 4 * sizeof(int));
+        I.ctas_layer = static_cast<unsigned>(CL * I.d.n_layers);
+        I.nparts = nparts[i];
+    }
+    // device block
+    const size_t inst_bytes = round16(sizeof(BInst<T>) * n);
+    std::vector<size_t> loff(lists.size());
+    size_t off = inst_bytes;
+    for (size_t k = 0; k < lists.size(); ++k) {
+        loff[k] = off;
+        off += round16(lists[k].size() * sizeof(BItem));
+    }
+    B->args_off = off;
+    const size_t total = off + args.size();
+    cudaError_t e = cudaMalloc(&B->dev, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        B->dev = nullptr;
+        return bfail(B, FEWHA_ERR_OOM, "batch allocation failed");
+    }
+    unsigned char* base = static_cast<unsigned char*>(B->dev);
+    BCK(cudaMemcpy(base, inst.data(), sizeof(BInst<T>) * n, cudaMemcpyHostToDevice), "batch upload");
+    for (size_t k = 0; k < lists.size(); ++k)
+        if (!lists[k].empty())
+            BCK(cudaMemcpy(base + loff[k], lists[k].data(), lists[k].size() * sizeof(BItem), cudaMemcpyHostToDevice),
+                "batch upload");
+    BCK(cudaMemcpy(base + B->args_off, args.data(), args.size(), cudaMemcpyHostToDevice), "batch upload");
+    B->args_host = args;
+    // shared memory per (group, kind) and its limit
+    const size_t S = recs[0].steps.size();
+    std::vector<size_t> smem(G * BK_COUNT, 0);
+    for (int i = 0; i < n; ++i)
+        for (int kind = 0; kind < BK_COUNT; ++kind)
+            smem[grp[i] * BK_COUNT + kind] = std::max(smem[grp[i] * BK_COUNT + kind], bsmem(B->h[i], kind));
+    for (int kind = 0; kind < BK_COUNT; ++kind) {
+        size_t lim = 0;
+        BCK(batch_smem_limit<T>(kind, &lim), "batch smem attribute");
+        for (int g = 0; g < G; ++g)
+            if (bkind_list(kind) != BL_VEC && smem[g * BK_COUNT + kind] > lim)
+                return bfail(B, FEWHA_ERR_LIMIT, "batched tile above the per-CTA shared-memory limit");
+    }
+    BCK(batch_set_taps(B->h[0]->setup.taps_h, B->h[0]->setup.taps_g), "batch taps");
+    // capture
+    BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "batch capture");
+    cudaError_t le = cudaSuccess;
+    if (G > 1) {
+        le = cudaEventRecord(B->ev[0], B->cap);
+        for (int g = 1; g < G && le == cudaSuccess; ++g) le = cudaStreamWaitEvent(B->branch[g], B->ev[0], 0);
+    }
+    for (int g = 0; g < G && le == cudaSuccess; ++g) {
+        cudaStream_t st = g == 0 ? B->cap : B->branch[g];
+        for (size_t j = 0; j < S && le == cudaSuccess; ++j) {
+            const int kind = recs[0].steps[j].kind;
+            const int li = g * BL_COUNT + bkind_list(kind);
+            BLaunch L;
+            L.kind = kind;
+            L.inst = base;
+            L.args = base + B->args_off + offs[j];
+            L.items = reinterpret_cast<const BItem*>(base + loff[li]);
+            L.n_items = static_cast<int>(lists[li].size());
+            L.smem = smem[g * BK_COUNT + kind];
+            le = batch_launch<T>(L, st);
+        }
+    }
+    if (G > 1)
+        for (int g = 1; g < G && le == cudaSuccess; ++g) {
+            le = cudaEventRecord(B->ev[g], B->branch[g]);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(B->cap, B->ev[g], 0);
+        }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(B->cap, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bfail(B, FEWHA_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(le != cudaSuccess ? le : e));
+    }
+    e = cudaGraphInstantiate(&B->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        B->gexec = nullptr;
+        return bfail(B, FEWHA_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    }
+    B->have_plan = true;
+    B->plan_warm = warm;
+    B->plan_cfg = cfg;
+    for (int i = 0; i < n; ++i) B->ver[i] = B->h[i]->version;
+    return FEWHA_OK;
+}
+
+bool same_cfg(const fewha_batch_config& a, const fewha_batch_config& b) {
+    return a.order == b.order && a.groups == b.groups && a.vec_passes == b.vec_passes;
+}
+
+template <class T>
+int batch_run(fewha_batch* B, const void* const* s_in, void* const* dm_in, void* stream) {
+    if (!B) return FEWHA_ERR_INVALID_ARG;
+    if (B->dead) return bfail(B, FEWHA_ERR_INVALID_ARG, "a member of the batch was destroyed");
+    if (static_cast<int>(sizeof(T) * 8) != B->precision)
+        return bfail(B, FEWHA_ERR_INVALID_ARG, "element type does not match the batch's precision");
+    if (!s_in || !dm_in) return bfail(B, FEWHA_ERR_INVALID_ARG, "null pointer table");
+    DeviceGuard g(B->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t n = B->h.size();
+    bool warm = false;
+    for (size_t i = 0; i < n; ++i) {
+        const fewha_handle* H = B->h[i];
+        const bool w = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) && H->have_prev;
+        if (i == 0) warm = w;
+        if (w != warm) return bfail(B, FEWHA_ERR_INVALID_ARG, "members differ in warm-residual state (reset them)");
+    }
+    const T* const* s = reinterpret_cast<const T* const*>(s_in);
+    T* const* dm = reinterpret_cast<T* const*>(dm_in);
+    std::vector<Recorder<T>> recs;
+    int rc;
+    if ((rc = batch_record<T>(B, s, dm, warm, recs))) return rc;
+    std::vector<int> nparts(n);
+    for (size_t i = 0; i < n; ++i) nparts[i] = bnparts(B->h[i], B->cfg.vec_passes);
+    std::vector<unsigned char> args;
+    std::vector<size_t> offs;
+    batch_pack<T>(recs, nparts, args, offs);
+    bool rebuild = !B->have_plan || B->plan_warm != warm || !same_cfg(B->plan_cfg, B->cfg) ||
+                   args.size() != B->args_host.size();
+    for (size_t i = 0; i < n && !rebuild; ++i) rebuild = B->ver[i] != B->h[i]->version;
+    if (rebuild) {
+        if ((rc = batch_build<T>(B, recs, nparts, args, offs, warm))) return rc;
+    } else if (args != B->args_host) {
+        B->args_host = args;
+        BCK(cudaMemcpyAsync(static_cast<unsigned char*>(B->dev) + B->args_off, B->args_host.data(), args.size(),
+                            cudaMemcpyHostToDevice, st),
+            "batch arguments");
+    }
+    BCK(cudaGraphLaunch(B->gexec, st), "batch graph launch");
+    for (size_t i = 0; i < n; ++i) B->h[i]->have_prev = true;
+    return FEWHA_OK;
+}
+
+std::mutex g_tune_mutex;
+std::vector<std::pair<std::string, fewha_batch_config>> g_tuned;   // shape signature -> config
+
+std::string batch_signature(const fewha_batch* B) {
+    std::string k = std::to_string(B->precision);
+    for (const fewha_handle* H : B->h) {
+        k += "|" + std::to_string(H->params.iters) + ":" + std::to_string(H->setup.n_act);
+        for (const auto& L : H->setup.L) k += "," + std::to_string(L.n);
+        k += ";";
+        for (const auto& W : H->setup.G) k += "," + std::to_string(W.N);
+    }
+    return k;
+}
+
+template <class T>
+int batch_autotune(fewha_batch* B, const void* const* s, void* const* dm, int reps, float* best_us, void* stream) {
+    if (!B) return FEWHA_ERR_INVALID_ARG;
+    if (B->dead) return bfail(B, FEWHA_ERR_INVALID_ARG, "a member of the batch was destroyed");
+    if (reps < 1 || reps > 10000) return bfail(B, FEWHA_ERR_INVALID_ARG, "reps out of range");
+    DeviceGuard g(B->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t n = B->h.size();
+    // snapshot of the warm state
+    size_t per = 0;
+    for (const fewha_handle* H : B->h) per += (3 * static_cast<size_t>(H->setup.n_c) + H->setup.n_act) * sizeof(T);
+    void* snap = nullptr;
+    if (cudaMalloc(&snap, per) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(B, FEWHA_ERR_OOM, "autotune snapshot allocation failed");
+    }
+    std::vector<bool> had(n);
+    auto copy_state = [&](bool save) {
+        unsigned char* p = static_cast<unsigned char*>(snap);
+        for (size_t i = 0; i < n; ++i) {
+            fewha_handle* H = B->h[i];
+            void* v[4] = {H->c, H->r, H->b_prev, H->a_prev};
+            const size_t sz[4] = {H->setup.n_c * sizeof(T), H->setup.n_c * sizeof(T), H->setup.n_c * sizeof(T),
+                                  H->setup.n_act * sizeof(T)};
+            for (int k = 0; k < 4; ++k) {
+                cudaMemcpyAsync(save ? p : v[k], save ? v[k] : p, sz[k], cudaMemcpyDeviceToDevice, st);
+                p += sz[k];
+            }
+            if (save) had[i] = H->have_prev;
+            else H->have_prev = had[i];
+        }
+    };
+    copy_state(true);
+    const fewha_batch_config start = B->cfg;
+    fewha_batch_config best = start;
+    float best_t = -1.f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = FEWHA_OK;
+    const int groups[] = {1, 2, 4, 8};
+    const int vps[] = {1, 4};
+    for (int order = 0; order < 2 && rc == FEWHA_OK; ++order)
+        for (int gi = 0; gi < 4 && rc == FEWHA_OK; ++gi) {
+            if (groups[gi] > static_cast<int>(n)) continue;
+            for (int vi = 0; vi < 2 && rc == FEWHA_OK; ++vi) {
+                B->cfg = fewha_batch_config{order, groups[gi], vps[vi]};
+                for (int w = 0; w < 2 && rc == FEWHA_OK; ++w) rc = batch_run<T>(B, s, dm, stream);
+                if (rc) break;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < reps && rc == FEWHA_OK; ++r) rc = batch_run<T>(B, s, dm, stream);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = bfail(B, FEWHA_ERR_CUDA, "autotune timing");
+                if (rc) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const float us = 1e3f * ms / reps;
+                if (best_t < 0.f || us < best_t) {
+                    best_t = us;
+                    best = B->cfg;
+                }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    copy_state(false);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    cudaFree(snap);
+    if (rc) {
+        B->cfg = start;
+        return rc;
+    }
+    if (se != cudaSuccess) return bfail(B, FEWHA_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(se));
+    B->cfg = best;
+    if (best_us) *best_us = best_t;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    const std::string key = batch_signature(B);
+    bool found = false;
+    for (auto& kv : g_tuned)
+        if (kv.first == key) {
+            kv.second = best;
+            found = true;
+        }
+    if (!found) g_tuned.emplace_back(key, best);
+    return FEWHA_OK;
+}
+
+void batch_free(fewha_batch* B) {
+    if (!B) return;
+    DeviceGuard g(B->device);
+    cudaDeviceSynchronize();
+    batch_drop_plan(B);
+    for (fewha_handle* H : B->h)
+        if (H) H->batches.erase(std::remove(H->batches.begin(), H->batches.end(), B), H->batches.end());
+    if (B->cap) cudaStreamDestroy(B->cap);
+    for (int g2 = 0; g2 < FEWHA_BATCH_MAX_GROUPS; ++g2) {
+        if (B->branch[g2]) cudaStreamDestroy(B->branch[g2]);
+        if (B->ev[g2]) cudaEventDestroy(B->ev[g2]);
+    }
+    delete B;
+}
+
+int batch_create(fewha_handle* const* hs, int count, fewha_batch** out) {
+    if (!out) return FEWHA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!hs || count < 1 || count > FEWHA_BATCH_MAX_COUNT) return FEWHA_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i]) return FEWHA_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(hs[i], FEWHA_ERR_INVALID_ARG, "a handle appears twice in a batch");
+        if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision)
+            return fail(hs[i], FEWHA_ERR_INVALID_ARG, "batch members differ in device or precision");
+    }
+    fewha_batch* B = new fewha_batch();
+    B->h.assign(hs, hs + count);
+    B->ver.assign(count, 0);
+    B->precision = hs[0]->precision;
+    B->device = hs[0]->device;
+    DeviceGuard g(B->device);
+    bool ok = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int g2 = 0; g2 < FEWHA_BATCH_MAX_GROUPS && ok; ++g2) {
+        ok = cudaStreamCreateWithFlags(&B->branch[g2], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&B->ev[g2], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        B->h.clear();
+        batch_free(B);
+        return FEWHA_ERR_CUDA;
+    }
+    for (fewha_handle* H : B->h) H->batches.push_back(B);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        const std::string key = batch_signature(B);
+        for (const auto& kv : g_tuned)
+            if (kv.first == key) B->cfg = kv.second;
+    }
+    *out = B;
+    return FEWHA_OK;
+}
+
+std::mutex g_registry_mutex;
+std::vector<fewha_batch*> g_registry;   // batches of fewha_reconstruct_batched
+
+template <class T>
+int reconstruct_batched(fewha_handle* const* hs, int count, const T* const* s, T* const* dm, void* stream) {
+    if (!hs || count < 1 || count > FEWHA_BATCH_MAX_COUNT) return FEWHA_ERR_INVALID_ARG;
+    fewha_batch* B = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_registry_mutex);
+        for (fewha_batch* b : g_registry)
+            if (!b->dead && static_cast<int>(b->h.size()) == count && std::equal(b->h.begin(), b->h.end(), hs)) B = b;
+    }
+    if (!B) {
+        const int rc = batch_create(hs, count, &B);
+        if (rc) return rc;
+        B->registry = true;
+        std::lock_guard<std::mutex> lk(g_registry_mutex);
+        g_registry.push_back(B);
+    }
+    const int rc = batch_run<T>(B, reinterpret_cast<const void* const*>(s), reinterpret_cast<void* const*>(dm), stream);
+    if (rc) fail(hs[0], rc, B->err);
+    return rc;
+}
+
+// A member handle is being destroyed: cached batches go, user batches are disabled.
+void batches_forget(fewha_handle* H) {
+    std::vector<fewha_batch*> bs = H->batches;
+    for (fewha_batch* B : bs) {
+        B->dead = true;
+        for (auto& m : B->h)
+            if (m == H) m = nullptr;
+        if (B->registry) {
+            {
+                std::lock_guard<std::mutex> lk(g_registry_mutex);
+                g_registry.erase(std::remove(g_registry.begin(), g_registry.end(), B), g_registry.end());
+            }
+            batch_free(B);
+        }
+    }
+    H->batches.clear();
+}
+
 // ---------------------------------------------------------------- operators
 template <class T>
 int op_dispatch(fewha_handle* H, int op, const void* in, void* out, int iters, cudaStream_t st) {
@@ -1033,6 +1619,7 @@ void fewha_destroy(fewha_handle* h) {
     if (!h) return;
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
+    batches_forget(h);
     free_handle(h);
 }
 
@@ -1071,6 +1658,7 @@ int fewha_update_params(fewha_handle* H, const fewha_params* params, const doubl
     H->params = *params;
     drop_graph(H);
     H->have_prev = false;
+    ++H->version;
     return H->precision == 32 ? compute_diagonals<float>(H) : compute_diagonals<double>(H);
 }
 
@@ -1106,6 +1694,70 @@ int fewha_run_loop(fewha_handle* h, const float* s, int n_frames, float* dm, dou
 int fewha_run_loop_f64(fewha_handle* h, const double* s, int n_frames, double* dm, double period_us,
                        float* wall_us, float* device_us, int* n_late, void* stream) {
     return run_loop<double>(h, s, n_frames, dm, period_us, wall_us, device_us, n_late, stream);
+}
+
+int fewha_batch_create(fewha_handle* const* handles, int count, fewha_batch** out) {
+    return batch_create(handles, count, out);
+}
+void fewha_batch_destroy(fewha_batch* b) {
+    if (!b) return;
+    if (b->registry) return;   // owned by the fewha_reconstruct_batched cache
+    batch_free(b);
+}
+const char* fewha_batch_last_error(const fewha_batch* b) { return b ? b->err.c_str() : "null batch"; }
+int fewha_batch_set_config(fewha_batch* b, const fewha_batch_config* cfg) {
+    if (!b || !cfg) return FEWHA_ERR_INVALID_ARG;
+    if (cfg->order < 0 || cfg->order > 1 || cfg->groups < 1 || cfg->groups > FEWHA_BATCH_MAX_GROUPS ||
+        cfg->vec_passes < 1 || cfg->vec_passes > 8)
+        return bfail(b, FEWHA_ERR_INVALID_ARG, "configuration out of range");
+    b->cfg = *cfg;
+    return FEWHA_OK;
+}
+int fewha_batch_get_config(const fewha_batch* b, fewha_batch_config* cfg) {
+    if (!b || !cfg) return FEWHA_ERR_INVALID_ARG;
+    *cfg = b->cfg;
+    return FEWHA_OK;
+}
+int fewha_batch_reconstruct(fewha_batch* b, const void* const* s, void* const* dm, void* stream) {
+    if (!b) return FEWHA_ERR_INVALID_ARG;
+    return b->precision == 32 ? batch_run<float>(b, s, dm, stream) : batch_run<double>(b, s, dm, stream);
+}
+int fewha_batch_autotune(fewha_batch* b, const void* const* s, void* const* dm, int reps, float* best_us,
+                         void* stream) {
+    if (!b) return FEWHA_ERR_INVALID_ARG;
+    return b->precision == 32 ? batch_autotune<float>(b, s, dm, reps, best_us, stream)
+                              : batch_autotune<double>(b, s, dm, reps, best_us, stream);
+}
+int fewha_reconstruct_batched(fewha_handle* const* hs, int count, const float* const* s, float* const* dm,
+                              void* stream) {
+    if (hs && count > 0 && hs[0] && hs[0]->precision != 32) return fail(hs[0], FEWHA_ERR_INVALID_ARG, "precision mismatch");
+    return reconstruct_batched<float>(hs, count, s, dm, stream);
+}
+int fewha_reconstruct_batched_f64(fewha_handle* const* hs, int count, const double* const* s, double* const* dm,
+                                  void* stream) {
+    if (hs && count > 0 && hs[0] && hs[0]->precision != 64) return fail(hs[0], FEWHA_ERR_INVALID_ARG, "precision mismatch");
+    return reconstruct_batched<double>(hs, count, s, dm, stream);
+}
+
+int fewha_get_state(fewha_handle* H, void* c, void* a_prev, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (c) CK(cudaMemcpyAsync(c, H->c, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get state");
+    if (a_prev)
+        CK(cudaMemcpyAsync(a_prev, H->a_prev, H->setup.n_act * H->esz, cudaMemcpyDeviceToDevice, st), "get state");
+    return FEWHA_OK;
+}
+
+int fewha_set_state(fewha_handle* H, const void* c, const void* a_prev, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (c) CK(cudaMemcpyAsync(H->c, c, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "set state");
+    if (a_prev)
+        CK(cudaMemcpyAsync(H->a_prev, a_prev, H->setup.n_act * H->esz, cudaMemcpyDeviceToDevice, st), "set state");
+    H->have_prev = false;
+    return FEWHA_OK;
 }
 
 int fewha_check_input(fewha_handle* H, int* nonfinite, void* stream) {

@@ -1,0 +1,217 @@
+// Batched kernels: thin wrappers that run the single-instance kernel bodies on work items
+// of many instances in one launch.  A CTA first copies its instance's descriptor into
+// shared memory (the bodies then read it from there, as the single-instance kernels read
+// theirs from the constant bank), then runs the body on its unit.
+#include "fewha_batch.h"
+
+namespace fewha {
+
+namespace {
+
+// Copy the leading desc_bytes of the instance's descriptor into shared memory.
+template <class T>
+__device__ __forceinline__ void load_desc(Desc<T>& sd, const BInst<T>* __restrict__ I) {
+    const int4* src = reinterpret_cast<const int4*>(&I->d);
+    int4* dst = reinterpret_cast<int4*>(&sd);
+    const int nb = (I->desc_bytes + 15) >> 4;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
+template <class T, bool PUPD>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    kb_cl_inv(const BInst<T>* __restrict__ inst, const ClArgs<T>* __restrict__ args,
+              const BItem* __restrict__ items) {
+    __shared__ __align__(16) Desc<T> sd;
+    const BItem it = items[blockIdx.y];
+    const BInst<T>* I = inst + it.inst;
+    load_desc<T>(sd, I);
+    const ClArgs<T> a = args[it.inst];
+    const ClLayout lay = I->lay_inv;
+    cl_inv_body<T, PUPD>(sd, a, lay, it.unit);
+}
+
+template <class T, int DST>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    kb_cl_fwd(const BInst<T>* __restrict__ inst, const ClArgs<T>* __restrict__ args,
+              const BItem* __restrict__ items) {
+    __shared__ __align__(16) Desc<T> sd;
+    const BItem it = items[blockIdx.y];
+    const BInst<T>* I = inst + it.inst;
+    load_desc<T>(sd, I);
+    const ClArgs<T> a = args[it.inst];
+    const ClLayout lay = I->lay_fwd;
+    const PairBufs<T> pb = I->pb;
+    cl_fwd_body<T, LSRC_NODES, DST>(sd, a, lay, pb, it.unit, I->ctas_layer);
+}
+
+template <class T, int SRC>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    kb_cl_sensor(const BInst<T>* __restrict__ inst, const SensorArgs<T>* __restrict__ args,
+                 const BItem* __restrict__ items) {
+    __shared__ __align__(16) Desc<T> sd;
+    const BItem it = items[blockIdx.y];
+    const BInst<T>* I = inst + it.inst;
+    load_desc<T>(sd, I);
+    const SensorArgs<T> a = args[it.inst];
+    const SensorLayout lay = I->lay_sen;
+    const PairBufs<T> pb = I->pb;
+    cl_sensor_body<T, SRC>(sd, a, lay, pb, it.unit);
+}
+
+template <class T>
+__global__ void __launch_bounds__(cblk<T>(), 1)
+    kb_proj(const BInst<T>* __restrict__ inst, const T* const* __restrict__ args,
+            const BItem* __restrict__ items) {
+    __shared__ __align__(16) Desc<T> sd;
+    const BItem it = items[blockIdx.x];
+    const BInst<T>* I = inst + it.inst;
+    load_desc<T>(sd, I);
+    const PairBufs<T> pb = I->pb;
+    proj_body<T>(sd, args[it.inst], pb, it.unit / MAXL, it.unit % MAXL);
+}
+
+template <class T>
+__global__ void __launch_bounds__(cblk<T>(), 1)
+    kb_projT(const BInst<T>* __restrict__ inst, const T* const* __restrict__ args,
+             const BItem* __restrict__ items) {
+    __shared__ __align__(16) Desc<T> sd;
+    const BItem it = items[blockIdx.x];
+    const BInst<T>* I = inst + it.inst;
+    load_desc<T>(sd, I);
+    const PairBufs<T> pb = I->pb;
+    projT_body<T>(sd, args[it.inst], pb, it.unit / MAXL, it.unit % MAXL);
+}
+
+template <class T, int PHASE>
+__global__ void __launch_bounds__(PBLK)
+    kb_vec(const BInst<T>* __restrict__ inst, const VecArgs<T>* __restrict__ args,
+           const BItem* __restrict__ items) {
+    const BItem it = items[blockIdx.x];
+    const BInst<T>* I = inst + it.inst;
+    const VecArgs<T> v = args[it.inst];
+    vec_body<T, PHASE>(I->d.n_c, v, it.unit, I->nparts);
+}
+
+template <class T>
+__global__ void __launch_bounds__(PBLK)
+    kb_fit(const BInst<T>* __restrict__ inst, const FitArgs<T>* __restrict__ args,
+           const BItem* __restrict__ items) {
+    __shared__ __align__(16) Desc<T> sd;
+    const BItem it = items[blockIdx.x];
+    const BInst<T>* I = inst + it.inst;
+    load_desc<T>(sd, I);
+    const FitArgs<T> f = args[it.inst];
+    fit_body<T>(sd, f.phi, f.a_prev, f.out, f.apply_gain, it.unit);
+}
+
+template <class T>
+const void* kernel_of(int kind) {
+    switch (kind) {
+        case BK_INV: return reinterpret_cast<const void*>(kb_cl_inv<T, false>);
+        case BK_INV_UPD: return reinterpret_cast<const void*>(kb_cl_inv<T, true>);
+        case BK_PROJ: return reinterpret_cast<const void*>(kb_proj<T>);
+        case BK_SEN_PHI: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_PHI>);
+        case BK_SEN_SLOPES: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_SLOPES>);
+        case BK_PROJT: return reinterpret_cast<const void*>(kb_projT<T>);
+        case BK_FWD_APPLY: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_APPLY>);
+        case BK_FWD_COEF: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_COEF>);
+        case BK_VEC_INIT: return reinterpret_cast<const void*>(kb_vec<T, V_INIT>);
+        case BK_VEC_WARM: return reinterpret_cast<const void*>(kb_vec<T, V_INIT_WARM>);
+        case BK_VEC_UPDATE: return reinterpret_cast<const void*>(kb_vec<T, V_UPDATE>);
+        case BK_FIT: return reinterpret_cast<const void*>(kb_fit<T>);
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+cudaError_t batch_set_taps(const double* h, const double* g) {
+    float h32[6], g32[6];
+    for (int k = 0; k < 6; ++k) {
+        h32[k] = static_cast<float>(h[k]);
+        g32[k] = static_cast<float>(g[k]);
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_h32, h32, sizeof(h32));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_g32, g32, sizeof(g32));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_h64, h, 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_g64, g, 6 * sizeof(double));
+    return e;
+}
+
+template <class T>
+cudaError_t batch_smem_limit(int kind, size_t* bytes) {
+    const void* k = kernel_of<T>(kind);
+    if (!k) return cudaErrorInvalidValue;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    const int avail = 227 * 1024 - static_cast<int>(fa.sharedSizeBytes);
+    if (bkind_list(kind) == BL_VEC) {
+        *bytes = 0;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
+    *bytes = static_cast<size_t>(avail);
+    return e;
+}
+
+template <class T>
+cudaError_t batch_launch(const BLaunch& L, cudaStream_t st) {
+    if (L.n_items <= 0) return cudaSuccess;
+    const BInst<T>* I = static_cast<const BInst<T>*>(L.inst);
+    const int n = L.n_items;
+    constexpr int NT = cblk<T>();
+    switch (L.kind) {
+        case BK_INV:
+            kb_cl_inv<T, false><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args), L.items);
+            break;
+        case BK_INV_UPD:
+            kb_cl_inv<T, true><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args), L.items);
+            break;
+        case BK_FWD_APPLY:
+            kb_cl_fwd<T, LDST_APPLY><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args),
+                                                                     L.items);
+            break;
+        case BK_FWD_COEF:
+            kb_cl_fwd<T, LDST_COEF><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args),
+                                                                    L.items);
+            break;
+        case BK_SEN_PHI:
+            kb_cl_sensor<T, SSRC_PHI><<<dim3(CL, n), NT, L.smem, st>>>(
+                I, static_cast<const SensorArgs<T>*>(L.args), L.items);
+            break;
+        case BK_SEN_SLOPES:
+            kb_cl_sensor<T, SSRC_SLOPES><<<dim3(CL, n), NT, L.smem, st>>>(
+                I, static_cast<const SensorArgs<T>*>(L.args), L.items);
+            break;
+        case BK_PROJ:
+            kb_proj<T><<<n, NT, L.smem, st>>>(I, static_cast<const T* const*>(L.args), L.items);
+            break;
+        case BK_PROJT:
+            kb_projT<T><<<n, NT, L.smem, st>>>(I, static_cast<const T* const*>(L.args), L.items);
+            break;
+        case BK_VEC_INIT:
+            kb_vec<T, V_INIT><<<n, PBLK, 0, st>>>(I, static_cast<const VecArgs<T>*>(L.args), L.items);
+            break;
+        case BK_VEC_WARM:
+            kb_vec<T, V_INIT_WARM><<<n, PBLK, 0, st>>>(I, static_cast<const VecArgs<T>*>(L.args), L.items);
+            break;
+        case BK_VEC_UPDATE:
+            kb_vec<T, V_UPDATE><<<n, PBLK, 0, st>>>(I, static_cast<const VecArgs<T>*>(L.args), L.items);
+            break;
+        case BK_FIT:
+            kb_fit<T><<<n, PBLK, L.smem, st>>>(I, static_cast<const FitArgs<T>*>(L.args), L.items);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t batch_launch<float>(const BLaunch&, cudaStream_t);
+template cudaError_t batch_launch<double>(const BLaunch&, cudaStream_t);
+template cudaError_t batch_smem_limit<float>(int, size_t*);
+template cudaError_t batch_smem_limit<double>(int, size_t*);
+
+}  // namespace fewha

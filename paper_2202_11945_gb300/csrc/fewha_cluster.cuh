@@ -253,9 +253,11 @@ struct ClLayout {       // shared-memory offsets set by the host, in T units
 
 constexpr int KMAX = 8;      // aperture rows / columns touching one layer row / column
 
+// Body of the forward layer kernel for layer l; `ctas` = CTAs of the instance's grid
+// (the p.q total is formed by the last of them to arrive).
 template <class T, int SRC, int DST>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
-    k_cl_fwd(const Desc<T> d, const ClArgs<T> a, const ClLayout lay, const PairBufs<T> pb) {
+__device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a, const ClLayout& lay,
+                                            const PairBufs<T>& pb, const int l, const unsigned ctas) {
     constexpr int NT = cblk<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);            // RED_DBL doubles
@@ -263,7 +265,6 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     __shared__ bool last;
     cg::cluster_group cluster = cg::this_cluster();
     const int r = static_cast<int>(cluster.block_rank());
-    const int l = blockIdx.y;
     const LayerInfo L = d.L[l];
     const int n = L.n, off = L.off, h = n >> 1;
     const int rb = band_rows(n);
@@ -440,7 +441,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
         dot = cta_sum(dot, red);
         double* slots = a.pcg.pqpart + a.iter * PQ_SLOTS;
         if (threadIdx.x == 0) slots[l * CL + r] = dot;
-        if (last_arrival(a.pcg.count + 1, gridDim.x * gridDim.y, &last) && threadIdx.x < 32) {
+        if (last_arrival(a.pcg.count + 1, ctas, &last) && threadIdx.x < 32) {
             // fixed order: layer-major, rank-minor over the slots of the layers present
             const double tot = warp_fixed_sum(slots, d.n_layers * CL);
             if (threadIdx.x == 0) {
@@ -451,20 +452,26 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     }
 }
 
+template <class T, int SRC, int DST>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    k_cl_fwd(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
+             __grid_constant__ const ClLayout lay, __grid_constant__ const PairBufs<T> pb) {
+    cl_fwd_body<T, SRC, DST>(d, a, lay, pb, blockIdx.y, gridDim.x * gridDim.y);
+}
+
 // ---------------------------------------------------------------------------
 // Inverse layer kernel (cluster per layer): phi = W^T c, optionally advancing the CG
 // direction first (p = z + beta p, beta = rz_k / rz_(k-1), Sec. 3.3).
 // ---------------------------------------------------------------------------
 template <class T, bool PUPD>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
-    k_cl_inv(const Desc<T> d, const ClArgs<T> a, const ClLayout lay) {
+__device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a, const ClLayout& lay,
+                                            const int l) {
     constexpr int NT = cblk<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);
     T* sm = reinterpret_cast<T*>(red + RED_DBL);
     cg::cluster_group cluster = cg::this_cluster();
     const int r = static_cast<int>(cluster.block_rank());
-    const int l = blockIdx.y;
     const LayerInfo L = d.L[l];
     const int n = L.n, off = L.off, h = n >> 1;
     const int rb = band_rows(n);
@@ -609,6 +616,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     cluster.sync();                                                       // #3: peers done reading
 }
 
+template <class T, bool PUPD>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    k_cl_inv(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
+             __grid_constant__ const ClLayout lay) {
+    cl_inv_body<T, PUPD>(d, a, lay, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Sensor kernel (cluster per sensor): P_g (Sec. 2), Gamma_g, C_hat_g^-1 (Eq. 2, Sec. 3.2)
 // and Gamma_g^T, each CTA on a band of subaperture rows.  SRC_PHI: slopes of the
@@ -619,8 +633,9 @@ struct SensorLayout {
 };
 
 template <class T, int SRC>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
-    k_cl_sensor(const Desc<T> d, const SensorArgs<T> a, const SensorLayout lay, const PairBufs<T> pb) {
+__device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArgs<T>& a,
+                                               const SensorLayout& lay, const PairBufs<T>& pb,
+                                               const int g) {
     constexpr int NT = cblk<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);                 // 2*CWMAX + 8
@@ -629,7 +644,6 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     T* sm = reinterpret_cast<T*>(tab + 4 * MAXL + 4);
     cg::cluster_group cluster = cg::this_cluster();
     const int r = static_cast<int>(cluster.block_rank());
-    const int g = blockIdx.y;
     const WfsInfo W = d.G[g];
     const int N = W.N, NP = N + 1;
     const int sr = (N + CL - 1) / CL;
@@ -847,6 +861,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
         }
     }
     cluster.sync();                                                       // neighbours done reading
+}
+
+template <class T, int SRC>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
+    k_cl_sensor(__grid_constant__ const Desc<T> d, __grid_constant__ const SensorArgs<T> a,
+                __grid_constant__ const SensorLayout lay, __grid_constant__ const PairBufs<T> pb) {
+    cl_sensor_body<T, SRC>(d, a, lay, pb, blockIdx.y);
 }
 
 }  // namespace fewha

@@ -46,7 +46,7 @@ struct DmInfo {
 
 // Everything a kernel needs about one instance, passed by value.
 template <class T>
-struct Desc {
+struct alignas(16) Desc {   // 16-byte multiple: batched kernels copy it in 16-byte chunks
     int n_layers, n_wfs, n_dms;
     int n_c, n_s, n_nodes, n_act;
     int max_n, max_N;

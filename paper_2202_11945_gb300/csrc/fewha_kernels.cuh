@@ -651,8 +651,10 @@ enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2 };
 
 constexpr int PVEC = 4;     // elements per thread and pass of the vector kernels
 
+// Body of the vector kernel: CTA `cta` of the `nparts` sharing the instance's vectors.
 template <class T, int PHASE>
-__global__ void __launch_bounds__(PBLK) k_vec(const int n, const VecArgs<T> v) {
+__device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const int cta,
+                                         const int nparts) {
     __shared__ bool last;
     double alpha = 0.0;
     if (PHASE == V_UPDATE) {
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(PBLK) k_vec(const int n, const VecArgs<T> v) {
     }
     const T ta = T(alpha);
     double dot = 0.0;
-    for (int base = blockIdx.x * PBLK * PVEC; base < n; base += gridDim.x * PBLK * PVEC) {
+    for (int base = cta * PBLK * PVEC; base < n; base += nparts * PBLK * PVEC) {
         // issue every load of the batch before the arithmetic
         T b[PVEC], q[PVEC], r[PVEC], p[PVEC], c[PVEC], bp[PVEC], jv[PVEC];
 #pragma unroll
@@ -720,9 +722,9 @@ __global__ void __launch_bounds__(PBLK) k_vec(const int n, const VecArgs<T> v) {
 #pragma unroll
         for (int i = 0; i < PBLK / 32; ++i) x += part[lane + 32 * i];
         x = warp_sum(x);
-        if (lane == 0) v.pcg.rzpart[slot * v.pcg.npart + blockIdx.x] = x;
+        if (lane == 0) v.pcg.rzpart[slot * v.pcg.npart + cta] = x;
     }
-    if (last_arrival(v.pcg.count, gridDim.x, &last) && w == 0) {
+    if (last_arrival(v.pcg.count, nparts, &last) && w == 0) {
         const double tot = warp_fixed_sum(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart);
         if (lane == 0) {
             v.pcg.rztot[slot] = tot;
@@ -731,15 +733,20 @@ __global__ void __launch_bounds__(PBLK) k_vec(const int n, const VecArgs<T> v) {
     }
 }
 
+template <class T, int PHASE>
+__global__ void __launch_bounds__(PBLK) k_vec(const int n, __grid_constant__ const VecArgs<T> v) {
+    vec_body<T, PHASE>(n, v, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // DM fitting (Algorithm 1 fitting step, Table 3): a~_m(p, q) = sum_l w_lm phi_l
 // sampled bilinearly at the actuator, then open-loop gain a = (1-g) a_prev + g a~.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(PBLK) k_fit(const Desc<T> d, const T* __restrict__ phi,
-                                              T* __restrict__ a_prev, T* __restrict__ out,
-                                              int apply_gain) {
-    const int idx = blockIdx.x * PBLK + threadIdx.x;
+__device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__ phi,
+                                         T* __restrict__ a_prev, T* __restrict__ out, int apply_gain,
+                                         const int blk) {
+    const int idx = blk * PBLK + threadIdx.x;
     if (idx >= d.n_act) return;
     int m = 0;
     while (m + 1 < d.n_dms && idx >= d.Mi[m + 1].off) ++m;
@@ -764,6 +771,13 @@ __global__ void __launch_bounds__(PBLK) k_fit(const Desc<T> d, const T* __restri
     } else {
         out[idx] = acc;
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_fit(__grid_constant__ const Desc<T> d, const T* __restrict__ phi,
+                                              T* __restrict__ a_prev, T* __restrict__ out,
+                                              int apply_gain) {
+    fit_body<T>(d, phi, a_prev, out, apply_gain, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -11,13 +11,12 @@ namespace fewha {
 
 // V_gl(a, b) = sum_{i,j} wy(a, i) wx(b, j) phi_l(i, j) over the pair's footprint box.
 template <class T>
-__global__ void __launch_bounds__(cblk<T>(), 1) k_proj(const Desc<T> d, const T* __restrict__ phi,
-                                                       const PairBufs<T> pb) {
+__device__ __forceinline__ void proj_body(const Desc<T>& d, const T* __restrict__ phi,
+                                          const PairBufs<T>& pb, const int g, const int l) {
     constexpr int NT = cblk<T>();
     constexpr int V = vec16<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* F = reinterpret_cast<T*>(smem_raw);       // footprint of phi_l: rows x cols
-    const int g = blockIdx.x, l = blockIdx.y;
     const int N = d.G[g].N, NP = N + 1;
     const int tp = (g * MAXL + l) * TAB;
     const int r0 = d.box[g][l][0], rows = d.box[g][l][1], c0 = d.box[g][l][2], cols = d.box[g][l][3];
@@ -56,15 +55,21 @@ __global__ void __launch_bounds__(cblk<T>(), 1) k_proj(const Desc<T> d, const T*
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(cblk<T>(), 1) k_proj(__grid_constant__ const Desc<T> d,
+                                                       const T* __restrict__ phi,
+                                                       __grid_constant__ const PairBufs<T> pb) {
+    proj_body<T>(d, phi, pb, blockIdx.x, blockIdx.y);
+}
+
 // Y_gl(i, j) = sum_{a,b} wy(a, i) wx(b, j) u_g(a, b) on the pair's footprint box.
 template <class T>
-__global__ void __launch_bounds__(cblk<T>(), 1) k_projT(const Desc<T> d, const T* __restrict__ u,
-                                                        const PairBufs<T> pb) {
+__device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict__ u,
+                                           const PairBufs<T>& pb, const int g, const int l) {
     constexpr int NT = cblk<T>();
     constexpr int V = vec16<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = reinterpret_cast<T*>(smem_raw);       // u_g, (N+1)^2 (+ alignment shift)
-    const int g = blockIdx.x, l = blockIdx.y;
     const int N = d.G[g].N, NP = N + 1;
     const int tp = (g * MAXL + l) * TAB, rbk = (g * MAXL + l) * MAXN;
     const int r0 = d.box[g][l][0], rows = d.box[g][l][1], c0 = d.box[g][l][2], cols = d.box[g][l][3];
@@ -123,6 +128,13 @@ __global__ void __launch_bounds__(cblk<T>(), 1) k_projT(const Desc<T> d, const T
             out[ii * cols + jj] = acc;
         }
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(cblk<T>(), 1) k_projT(__grid_constant__ const Desc<T> d,
+                                                        const T* __restrict__ u,
+                                                        __grid_constant__ const PairBufs<T> pb) {
+    projT_body<T>(d, u, pb, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace fewha

@@ -58,6 +58,10 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("groups", ctypes.c_int), ("vec_passes", ctypes.c_int)]
+
+
 _VP = ctypes.c_void_p
 _OPS = ["fewha_apply_M", "fewha_rhs", "fewha_dwt", "fewha_idwt", "fewha_project",
         "fewha_project_adj", "fewha_slopes", "fewha_slopes_adj", "fewha_noise_weight",
@@ -67,7 +71,10 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_reconstruct_f64", "fewha_reconstruct_host", "fewha_reconstruct_host_f64",
            "fewha_check_input", "fewha_pcg", "fewha_get_diagonals", "fewha_bench_stage",
            "fewha_frame_launches", "fewha_apply_M_noalloc", "fewha_run_loop",
-           "fewha_run_loop_f64"] + _OPS
+           "fewha_run_loop_f64", "fewha_batch_create", "fewha_batch_destroy",
+           "fewha_batch_last_error", "fewha_batch_set_config", "fewha_batch_get_config",
+           "fewha_batch_reconstruct", "fewha_batch_autotune", "fewha_reconstruct_batched",
+           "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -106,13 +113,29 @@ def lib():
     L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_bench_stage.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
     L.fewha_frame_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    L.fewha_get_state.argtypes = [_VP, _VP, _VP, _VP]
+    L.fewha_set_state.argtypes = [_VP, _VP, _VP, _VP]
     for name in ["fewha_run_loop", "fewha_run_loop_f64"]:
         getattr(L, name).argtypes = [_VP, _VP, ctypes.c_int, _VP, ctypes.c_double, _VP, _VP,
                                      ctypes.POINTER(ctypes.c_int), _VP]
     for name in _OPS + ["fewha_apply_M_noalloc"]:
         getattr(L, name).argtypes = [_VP, _VP, _VP, _VP]
+    L.fewha_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]
+    L.fewha_batch_destroy.argtypes = [_VP]
+    L.fewha_batch_destroy.restype = None
+    L.fewha_batch_last_error.argtypes = [_VP]
+    L.fewha_batch_last_error.restype = ctypes.c_char_p
+    L.fewha_batch_set_config.argtypes = [_VP, ctypes.POINTER(BatchConfig)]
+    L.fewha_batch_get_config.argtypes = [_VP, ctypes.POINTER(BatchConfig)]
+    L.fewha_batch_reconstruct.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]
+    L.fewha_batch_autotune.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_float), _VP]
+    for name in ["fewha_reconstruct_batched", "fewha_reconstruct_batched_f64"]:
+        getattr(L, name).argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP),
+                                     ctypes.POINTER(_VP), _VP]
     for name in EXPORTS:
-        if name not in ("fewha_destroy", "fewha_last_error", "fewha_create_error"):
+        if name not in ("fewha_destroy", "fewha_last_error", "fewha_create_error",
+                        "fewha_batch_destroy", "fewha_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -163,6 +186,11 @@ class Reconstructor:
         self._check(self.L.fewha_sizes(h, ctypes.byref(ns), ctypes.byref(nc), ctypes.byref(na),
                                        ctypes.byref(nn)))
         self.n_slopes, self.n_coeffs, self.n_act, self.n_nodes = ns.value, nc.value, na.value, nn.value
+
+    @property
+    def iters(self):
+        """PCG iterations per frame."""
+        return self._structs[4].iters
 
     # -- plumbing ---------------------------------------------------------------
     def _check(self, rc):
@@ -235,6 +263,20 @@ class Reconstructor:
                        float(period_us), ctypes.c_void_p(wall.data_ptr()),
                        ctypes.c_void_p(dev.data_ptr()), ctypes.byref(late), _stream(stream)))
         return dm, wall, dev, late.value
+
+    def get_state(self, stream=None):
+        """(c, a_prev): copies of the warm-start coefficients and previous commands."""
+        c, a = self._new(self.n_coeffs), self._new(self.n_act)
+        self._check(self.L.fewha_get_state(self.h, self._dev(c, self.n_coeffs, "c"),
+                                           self._dev(a, self.n_act, "a_prev"), _stream(stream)))
+        return c, a
+
+    def set_state(self, c=None, a_prev=None, stream=None):
+        """Restore a saved state (either part may be None); the next frame forms its
+        initial residual explicitly."""
+        cp = self._dev(c, self.n_coeffs, "c") if c is not None else None
+        ap = self._dev(a_prev, self.n_act, "a_prev") if a_prev is not None else None
+        self._check(self.L.fewha_set_state(self.h, cp, ap, _stream(stream)))
 
     def check_input(self, stream=None):
         flag = ctypes.c_int(0)
@@ -342,3 +384,93 @@ class Reconstructor:
         self._check(self.L.fewha_get_diagonals(self.h, self._dev(D, self.n_coeffs, "D"),
                                                self._dev(J, self.n_coeffs, "J"), _stream(stream)))
         return D, J
+
+
+def _ptr_array(ts):
+    return (_VP * len(ts))(*[ctypes.c_void_p(t.data_ptr()) for t in ts])
+
+
+class Batch:
+    """Many Reconstructor instances (uneven sizes) reconstructing one frame each in one
+    graph replay: every step of the frame is one launch over all instances' work items."""
+
+    def __init__(self, recons):
+        self.recons = list(recons)          # keeps the members alive
+        if not self.recons:
+            raise ValueError("empty batch")
+        self.L = lib()
+        hs = (_VP * len(self.recons))(*[r.h for r in self.recons])
+        b = _VP()
+        rc = self.L.fewha_batch_create(hs, len(self.recons), ctypes.byref(b))
+        if rc != 0:
+            raise FewhaError(rc, self.recons[0].L.fewha_last_error(self.recons[0].h).decode())
+        self.b = b
+        self.dtype = self.recons[0].dtype
+
+    def _check(self, rc):
+        if rc != 0:
+            raise FewhaError(rc, self.L.fewha_batch_last_error(self.b).decode())
+
+    def _tables(self, slopes, dms):
+        if len(slopes) != len(self.recons):
+            raise ValueError("one slope vector per instance")
+        if dms is None:
+            dms = [r._new(r.n_act) for r in self.recons]
+        for r, s, d in zip(self.recons, slopes, dms):
+            r._dev(s, r.n_slopes, "slopes")
+            r._dev(d, r.n_act, "dm_out")
+        return dms, _ptr_array(slopes), _ptr_array(dms)
+
+    @property
+    def config(self):
+        c = BatchConfig()
+        self._check(self.L.fewha_batch_get_config(self.b, ctypes.byref(c)))
+        return {"order": c.order, "groups": c.groups, "vec_passes": c.vec_passes}
+
+    @config.setter
+    def config(self, cfg):
+        c = BatchConfig(cfg["order"], cfg["groups"], cfg["vec_passes"])
+        self._check(self.L.fewha_batch_set_config(self.b, ctypes.byref(c)))
+
+    def reconstruct(self, slopes, dm_out=None, stream=None):
+        """One frame of every instance (device tensors); returns the DM command tensors."""
+        dms, sp, dp = self._tables(slopes, dm_out)
+        self._check(self.L.fewha_batch_reconstruct(self.b, sp, dp, _stream(stream)))
+        return dms
+
+    def autotune(self, slopes, dm_out=None, reps=10, stream=None):
+        """Time every launch configuration on these slopes and keep the fastest; the
+        members' warm state is restored.  Returns (config, mean frame time in us)."""
+        dms, sp, dp = self._tables(slopes, dm_out)
+        us = ctypes.c_float(0.0)
+        self._check(self.L.fewha_batch_autotune(self.b, sp, dp, int(reps), ctypes.byref(us),
+                                                _stream(stream)))
+        return self.config, us.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.L.fewha_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reconstruct_batched(recons, slopes, dm_out=None, stream=None):
+    """fewha_reconstruct_batched: the batched frame through the library's own batch cache."""
+    recons = list(recons)
+    if dm_out is None:
+        dm_out = [r._new(r.n_act) for r in recons]
+    for r, s, d in zip(recons, slopes, dm_out):
+        r._dev(s, r.n_slopes, "slopes")
+        r._dev(d, r.n_act, "dm_out")
+    L = lib()
+    hs = (_VP * len(recons))(*[r.h for r in recons])
+    fn = L.fewha_reconstruct_batched if recons[0].precision == 32 else L.fewha_reconstruct_batched_f64
+    rc = fn(hs, len(recons), _ptr_array(slopes), _ptr_array(dm_out), _stream(stream))
+    if rc != 0:
+        raise FewhaError(rc, L.fewha_last_error(recons[0].h).decode())
+    return dm_out
