@@ -265,7 +265,7 @@ class Geometry:
                     Rs.append(_interp_matrix(xa / L["delta"] + L["n"] / 2, L["n"]))
                 else:
                     Rs.append(None)
-            self.dms.append(dict(n_act=na, off=aoff, R=Rs, w=fw[:, mi]))
+            self.dms.append(dict(n_act=na, off=aoff, R=Rs, w=fw[:, mi], spacing=float(m["spacing"])))
             aoff += na * na
         self.n_a = aoff
 
