@@ -327,6 +327,59 @@ def time_batched(count, steps, warmup, flush):
     return out
 
 
+def time_backward(frames=8):
+    """The differentiable 8 m workload: converged reconstruction and backward (adjoint PCG
+    and adjoint operator kernels) of J = ||Pi (a~ - true on-axis phase)||^2 (Pi removes the
+    piston) per frame, FP32 and FP64, solves warm-started from the previous frame; wall
+    time of each synchronous call, and the FP32 gradients against the FP64 ones."""
+    from paper_2202_11945_gb300 import Reconstructor
+    wl = synth.differentiable()
+    atm = synth.TruthAtmosphere(wl["truth"])
+    na = sum(m["n_act"] ** 2 for m in wl["dms"])
+    xs, ys = [], []
+    for m in wl["dms"]:
+        k = (np.arange(m["n_act"]) - (m["n_act"] - 1) / 2.0) * m["spacing"]
+        X, Y = np.meshgrid(k, k)
+        xs.append(X.ravel())
+        ys.append(Y.ravel())
+    xa, ya = np.concatenate(xs), np.concatenate(ys)
+    assert len(xa) == na
+    out = {"workload": wl["name"], "frames": frames,
+           "objective": "||a~ - true on-axis phase||^2 over the actuators, piston removed"}
+    grads = {}
+    for prec, dt in ((32, torch.float32), (64, torch.float64)):
+        R = Reconstructor(wl, precision=prec, graph=False)
+        tf, tb, its, gl = [], [], [], []
+        for t in range(frames + 1):
+            s = torch.as_tensor(synth.simulate_slopes(wl, t, atm=atm), dtype=dt, device="cuda")
+            target = synth.true_phase_at(wl, xa, ya, t, atm=atm)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dm, it, rel = R.reconstruct_converged(s)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            d = dm.double().cpu().numpy() - target
+            g = torch.as_tensor(2.0 * (d - d.mean()), dtype=dt, device="cuda")
+            t2 = time.perf_counter()
+            gs, ga, gw = R.backward(g)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            gl.append((gs.double().cpu().numpy(), ga, np.array(gw)))
+            if t > 0:                       # frame 0 starts cold
+                tf.append(t1 - t0)
+                tb.append(t3 - t2)
+                its.append(it)
+        grads[prec] = gl
+        out["fp%d" % prec] = {"forward_ms": 1e3 * float(np.mean(tf)), "backward_ms": 1e3 * float(np.mean(tb)),
+                              "forward_iters": float(np.mean(its)), "tol": R.default_tol()}
+        R.close()
+    e = [(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]), abs(a[1] - b[1]) / abs(b[1]),
+          np.linalg.norm(a[2] - b[2]) / np.linalg.norm(b[2])) for a, b in zip(grads[32], grads[64])]
+    out["fp32_vs_fp64_max_rel"] = {"slopes": float(max(x[0] for x in e)), "alpha": float(max(x[1] for x in e)),
+                                   "cn2": float(max(x[2] for x in e))}
+    return out
+
+
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
     the same sequence (explicit initial residual), and the oracle's own frame rate."""
@@ -450,6 +503,7 @@ def main():
 
     loop, wl3, S3, dm3, dm3w = time_loop(args.loop_frames)
     batched = time_batched(args.batch_count, args.batch_steps, 3, flush) if args.batch_count > 0 else None
+    backward = time_backward()
 
     total32 = float(t32.sum())
     total64 = float(t64.sum())
@@ -501,6 +555,7 @@ def main():
             "parity": parity,
             "realtime_loop": loop,
             "batched": batched,
+            "backward": backward,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

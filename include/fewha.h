@@ -262,6 +262,37 @@ int fewha_bench_stage(fewha_handle* h, int stage, int reps, void* stream);
 /* Kernel launches one frame enqueues (for the launch count of a timed region). */
 int fewha_frame_launches(const fewha_handle* h, int* launches);
 
+/* ---- differentiable reconstruction (a build addition: the paper has no gradients) --
+ * The differentiable map is the CONVERGED reconstruction: c* solves M c = b (Eq. 6) to a
+ * tolerance, the MAP estimate of Sec. 3.1, and a~ = F W^T c* (no gain).  Gradients follow
+ * from implicit differentiation: lambda = M^-1 (F W^T)^T g_a by a second PCG on the
+ * symmetric M, then dJ/ds = C_hat^-1 Gamma P W^T lambda, dJ/dalpha = -lambda^T D c* and
+ * dJ/dw_l = alpha lambda_l^T D_l c*_l / w_l (D_l is proportional to 1 / w_l).
+ * These calls use the frame's work vectors: they discard the warm residual (the next
+ * frame forms r0 = b - M c explicitly) but keep the frame's warm start c.  Synchronous. */
+
+/* x = M^-1 b by PCG from x = 0 (one recurrence, no restarts), until
+ * sqrt(r^T J^-1 r / b^T J^-1 b) <= tol (r the recursively updated residual) or max_iters
+ * iterations; the test is made every FEWHA_MAX_ITERS - 1 iterations.  *iters_done and *rel_residual (nullable) report the outcome; reaching
+ * max_iters is not an error.  Device pointers of the handle's element type. */
+int fewha_solve(fewha_handle* h, const void* d_b, void* d_x, double tol, int max_iters,
+                int* iters_done, double* rel_residual, void* stream);
+
+/* a~ = F W^T M^-1 b(s) with the solve above; the handle keeps c* for fewha_backward.
+ * The solve (and the adjoint solve of fewha_backward) starts from the handle's previous
+ * solution, if any: a nearby b or M (parameter sweeps, consecutive frames) converges in
+ * fewer iterations. */
+int fewha_reconstruct_converged(fewha_handle* h, const void* d_slopes, void* d_dm_out, double tol,
+                                int max_iters, int* iters_done, double* rel_residual, void* stream);
+
+/* Given d_grad_dm = dJ/da~ (n_act), the gradients of J at the last converged
+ * reconstruction: d_grad_slopes (n_slopes, nullable), *grad_alpha (nullable) and
+ * grad_cn2[n_layers] (nullable), the adjoint solve using the same tolerance and
+ * iteration limit.  FEWHA_ERR_INVALID_ARG if no converged reconstruction is held (none
+ * yet, or fewha_update_params since). */
+int fewha_backward(fewha_handle* h, const void* d_grad_dm, void* d_grad_slopes, double* grad_alpha,
+                   double* grad_cn2, void* stream);
+
 /* ---- batched frames of many instances ------------------------------------------
  * Independent instances of uneven size (telescope, sensors, layers, DMs) reconstruct one
  * frame each in one CUDA-graph replay.  The frame of Algorithm 1 is the same sequence of

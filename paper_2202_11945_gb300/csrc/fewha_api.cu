@@ -59,7 +59,13 @@ struct fewha_handle {
     void *pfy = nullptr, *pfx = nullptr, *dfw = nullptr, *D = nullptr, *Jinv = nullptr;
     void *c = nullptr, *b = nullptr, *b_prev = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
          *q = nullptr, *phi = nullptr, *u = nullptr, *a_prev = nullptr, *dm_tmp = nullptr,
-         *s_tmp = nullptr, *c_tmp = nullptr;
+         *s_tmp = nullptr, *c_tmp = nullptr, *cgrad = nullptr, *lam = nullptr;
+    double* gdot = nullptr;           // per-layer sums of the backward pass
+    bool grad_ready = false;          // a converged reconstruction is held in cgrad
+    bool have_cgrad = false;          // cgrad / lam hold earlier solutions (warm starts)
+    bool have_lam = false;
+    double grad_tol = 0.0;
+    int grad_max_iters = 0;
     bool have_prev = false;
     // frame-graph cache
     cudaStream_t cap_stream = nullptr;
@@ -774,7 +780,9 @@ int typed_create(fewha_handle* H) {
         (rc = talloc(H, &H->p, s.n_c)) || (rc = talloc(H, &H->q, s.n_c)) ||
         (rc = talloc(H, &H->phi, s.n_c)) || (rc = talloc(H, &H->c_tmp, s.n_c)) ||
         (rc = talloc(H, &H->u, s.n_nodes)) || (rc = talloc(H, &H->a_prev, s.n_act)) ||
-        (rc = talloc(H, &H->dm_tmp, s.n_act)) || (rc = talloc(H, &H->s_tmp, s.n_s)))
+        (rc = talloc(H, &H->dm_tmp, s.n_act)) || (rc = talloc(H, &H->s_tmp, s.n_s)) ||
+        (rc = talloc(H, &H->cgrad, s.n_c)) || (rc = talloc(H, &H->lam, s.n_c)) ||
+        (rc = dalloc(H, &H->gdot, MAXL + 1)))
         return rc;
     if ((rc = upload(H, H->pi0y, s.pi0y)) || (rc = upload(H, H->pi0x, s.pi0x)) ||
         (rc = upload(H, H->pfy64, s.pfy)) || (rc = upload(H, H->pfx64, s.pfx)) ||
@@ -903,6 +911,114 @@ int run_loop(fewha_handle* H, const T* hs, int n_frames, T* hdm, double period_u
     if (rc) return rc;
     if (first_bad >= 0)
         return fail(H, FEWHA_ERR_NONFINITE, "non-finite value in the slopes of frame " + std::to_string(first_bad));
+    return FEWHA_OK;
+}
+
+// ---------------------------------------------------------------- converged solve and gradients
+// x = M^-1 b by PCG until sqrt(r.J^-1 r / b.J^-1 b) <= tol or max_iters, from x = 0 or
+// (warm) from the x given.  The iterations run in chunks (the scalar slots hold
+// FEWHA_MAX_ITERS + 2 values); between chunks the last two r.z totals are moved to slots
+// 0 and 1 and the next chunk resumes at iteration 1, whose fused direction update
+// p = z + beta p continues the same CG recurrence (no restart).  Uses the frame's work
+// vectors (b, r, z, p, q, b_prev), so the warm residual is discarded.  Synchronous.
+template <class T>
+int solve_converged(fewha_handle* H, const T* b, T* x, bool warm, double tol, int max_iters, cudaStream_t st,
+                    int* iters_out, double* rel_out) {
+    const Desc<T> d = make_desc<T>(H);
+    int rc;
+    if (b != static_cast<const T*>(H->b))
+        CK(cudaMemcpyAsync(H->b, b, d.n_c * sizeof(T), cudaMemcpyDeviceToDevice, st), "solve rhs");
+    if (!warm) CK(cudaMemsetAsync(x, 0, d.n_c * sizeof(T), st), "solve start");
+    k_wnorm<T><<<1, PBLK, 0, st>>>(d.n_c, static_cast<const T*>(H->b), d.Jinv, H->gdot + MAXL);
+    CK(cudaGetLastError(), "k_wnorm launch");
+    double rzb = 0.0, rz = 0.0;
+    CK(cudaMemcpyAsync(&rzb, H->gdot + MAXL, sizeof(double), cudaMemcpyDeviceToHost, st), "solve norm");
+    int done = 0;
+    T* p = static_cast<T*>(H->p);
+    T* q = static_cast<T*>(H->q);
+    while (done < max_iters) {
+        int last;                                // slot of the newest r.z total
+        if (done == 0) {
+            const int k = std::min(FEWHA_MAX_ITERS, max_iters);
+            if ((rc = enqueue_pcg<T>(H, d, x, k, false, st))) return rc;
+            done = k;
+            last = k;
+        } else {
+            // resume: slots (K-1, K) -> (0, 1), then iterations 1 .. k of the recurrence
+            CK(cudaMemcpyAsync(H->rztot, H->rztot + FEWHA_MAX_ITERS - 1, 2 * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st), "solve resume");
+            const int k = std::min(FEWHA_MAX_ITERS - 1, max_iters - done);
+            for (int j = 1; j <= k; ++j) {
+                if ((rc = enqueue_apply<T>(H, d, p, q, j, true, st))) return rc;
+                if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, vec_args<T>(H, x, j), st))) return rc;
+            }
+            done += k;
+            last = k + 1;
+        }
+        CK(cudaMemcpyAsync(&rz, H->rztot + last, sizeof(double), cudaMemcpyDeviceToHost, st), "solve residual");
+        CK(cudaStreamSynchronize(st), "solve residual");
+        if (!(rzb > 0.0) || !(rz > 0.0) || std::sqrt(rz / rzb) <= tol) break;
+        if (last != FEWHA_MAX_ITERS) break;      // the chunk was cut short by max_iters
+    }
+    if (max_iters == 0) CK(cudaStreamSynchronize(st), "solve");
+    H->have_prev = false;
+    if (iters_out) *iters_out = done;
+    if (rel_out) *rel_out = rzb > 0.0 ? std::sqrt(std::max(rz, 0.0) / rzb) : 0.0;
+    if (!std::isfinite(rz)) return fail(H, FEWHA_ERR_NONFINITE, "non-finite residual in the converged solve");
+    return FEWHA_OK;
+}
+
+template <class T>
+int reconstruct_converged(fewha_handle* H, const T* s, T* dm, double tol, int max_iters, int* iters,
+                          double* rel, cudaStream_t st) {
+    const Desc<T> d = make_desc<T>(H);
+    int rc;
+    H->grad_ready = false;
+    if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
+    // warm start from the previous converged solution (a nearby M or b)
+    if ((rc = solve_converged<T>(H, static_cast<const T*>(H->b), static_cast<T*>(H->cgrad), H->have_cgrad, tol,
+                                 max_iters, st, iters, rel)))
+        return rc;
+    H->have_cgrad = true;
+    if ((rc = enqueue_fit<T>(H, d, static_cast<const T*>(H->cgrad), dm, false, st))) return rc;
+    H->grad_ready = true;
+    H->grad_tol = tol;
+    H->grad_max_iters = max_iters;
+    return FEWHA_OK;
+}
+
+// Gradients of J(a~) at the last converged reconstruction, given g_a = dJ/da~:
+//   lambda = M^-1 (F W^T)^T g_a,  dJ/ds = C_hat^-1 Gamma P W^T lambda,
+//   dJ/dalpha = -lambda^T D c*,   dJ/dw_l = alpha lambda_l^T D_l c*_l / w_l.
+template <class T>
+int backward(fewha_handle* H, const T* g_a, T* g_s, double* g_alpha, double* g_w, cudaStream_t st) {
+    if (!H->grad_ready) return fail(H, FEWHA_ERR_INVALID_ARG, "no converged reconstruction to differentiate");
+    const Desc<T> d = make_desc<T>(H);
+    int rc;
+    T* b = static_cast<T*>(H->b);
+    T* lam = static_cast<T*>(H->lam);
+    T* phi = static_cast<T*>(H->phi);
+    T* st_s = static_cast<T*>(H->s_tmp);
+    if ((rc = launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, g_a, b), st))) return rc;
+    int it = 0;
+    double rel = 0.0;
+    if ((rc = solve_converged<T>(H, b, lam, H->have_lam, H->grad_tol, H->grad_max_iters, st, &it, &rel))) return rc;
+    H->have_lam = true;
+    if (g_s) {
+        if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, lam, phi), st))) return rc;
+        if ((rc = launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, phi, st_s, st))) return rc;
+        if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, st_s, g_s, st))) return rc;
+    }
+    k_layer_dots<T><<<d.n_layers, PBLK, 0, st>>>(d, lam, static_cast<const T*>(H->cgrad), H->gdot);
+    CK(cudaGetLastError(), "k_layer_dots launch");
+    double S[MAXL];
+    CK(cudaMemcpyAsync(S, H->gdot, d.n_layers * sizeof(double), cudaMemcpyDeviceToHost, st), "layer sums");
+    CK(cudaStreamSynchronize(st), "backward");
+    double tot = 0.0;
+    for (int l = 0; l < d.n_layers; ++l) tot += S[l];
+    if (g_alpha) *g_alpha = -tot;
+    if (g_w)
+        for (int l = 0; l < d.n_layers; ++l) g_w[l] = H->params.alpha * S[l] / H->weights[l];
     return FEWHA_OK;
 }
 
@@ -1659,6 +1775,7 @@ int fewha_update_params(fewha_handle* H, const fewha_params* params, const doubl
     drop_graph(H);
     H->have_prev = false;
     ++H->version;
+    H->grad_ready = false;
     return H->precision == 32 ? compute_diagonals<float>(H) : compute_diagonals<double>(H);
 }
 
@@ -1758,6 +1875,43 @@ int fewha_set_state(fewha_handle* H, const void* c, const void* a_prev, void* st
         CK(cudaMemcpyAsync(H->a_prev, a_prev, H->setup.n_act * H->esz, cudaMemcpyDeviceToDevice, st), "set state");
     H->have_prev = false;
     return FEWHA_OK;
+}
+
+int fewha_solve(fewha_handle* H, const void* b, void* x, double tol, int max_iters, int* iters,
+                double* rel, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!b || !x || !(tol >= 0.0) || max_iters < 0) return fail(H, FEWHA_ERR_INVALID_ARG, "bad solve arguments");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32
+               ? solve_converged<float>(H, static_cast<const float*>(b), static_cast<float*>(x), false, tol,
+                                        max_iters, st, iters, rel)
+               : solve_converged<double>(H, static_cast<const double*>(b), static_cast<double*>(x), false, tol,
+                                         max_iters, st, iters, rel);
+}
+
+int fewha_reconstruct_converged(fewha_handle* H, const void* s, void* dm, double tol, int max_iters,
+                                int* iters, double* rel, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!s || !dm || !(tol >= 0.0) || max_iters < 0) return fail(H, FEWHA_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32
+               ? reconstruct_converged<float>(H, static_cast<const float*>(s), static_cast<float*>(dm), tol,
+                                              max_iters, iters, rel, st)
+               : reconstruct_converged<double>(H, static_cast<const double*>(s), static_cast<double*>(dm), tol,
+                                               max_iters, iters, rel, st);
+}
+
+int fewha_backward(fewha_handle* H, const void* g_dm, void* g_s, double* g_alpha, double* g_cn2, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!g_dm) return fail(H, FEWHA_ERR_INVALID_ARG, "null gradient of the commands");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32
+               ? backward<float>(H, static_cast<const float*>(g_dm), static_cast<float*>(g_s), g_alpha, g_cn2, st)
+               : backward<double>(H, static_cast<const double*>(g_dm), static_cast<double*>(g_s), g_alpha, g_cn2,
+                                  st);
 }
 
 int fewha_check_input(fewha_handle* H, int* nonfinite, void* stream) {

@@ -781,6 +781,49 @@ __global__ void __launch_bounds__(PBLK) k_fit(__grid_constant__ const Desc<T> d,
 }
 
 // ---------------------------------------------------------------------------
+// Per-layer sums S_l = sum over layer l of lambda_i D_i c_i, in double, one CTA per
+// layer in a fixed order: the gradients of the converged reconstruction with respect to
+// alpha (-sum_l S_l) and to the layer Cn2 weights (alpha S_l / w_l), since
+// dM/dalpha = D and D_l is proportional to 1 / w_l (Sec. 3.1 prior).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_layer_dots(__grid_constant__ const Desc<T> d, const T* __restrict__ lam,
+                                                     const T* __restrict__ c, double* __restrict__ out) {
+    __shared__ double part[PBLK];
+    const int l = blockIdx.x;
+    const int off = d.L[l].off, n2 = d.L[l].n * d.L[l].n;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n2; i += PBLK)
+        acc += double(lam[off + i]) * double(d.D[off + i]) * double(c[off + i]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double x = 0.0;
+        for (int k = threadIdx.x; k < PBLK; k += 32) x += part[k];
+        x = warp_sum(x);
+        if (threadIdx.x == 0) out[l] = x;
+    }
+}
+
+// b^T J^-1 b in double, one CTA, fixed order (the reference of a warm-started solve's
+// relative residual).
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_wnorm(const int n, const T* __restrict__ b, const T* __restrict__ jinv,
+                                                double* __restrict__ out) {
+    __shared__ double part[PBLK];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += PBLK) acc += double(b[i]) * double(b[i]) * double(jinv[i]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double x = 0.0;
+        for (int k = threadIdx.x; k < PBLK; k += 32) x += part[k];
+        x = warp_sum(x);
+        if (threadIdx.x == 0) *out = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Exact Jacobi diagonal of W B W^T (Eq. 7), one warp per wavelet coefficient, in
 // double.  The basis function of coefficient (layer l, row r, col c) is the outer
 // product f_y(i) f_x(j) of 1-D level-j functions (shifted copies of the tables), its

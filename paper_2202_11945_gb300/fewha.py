@@ -74,7 +74,8 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_run_loop_f64", "fewha_batch_create", "fewha_batch_destroy",
            "fewha_batch_last_error", "fewha_batch_set_config", "fewha_batch_get_config",
            "fewha_batch_reconstruct", "fewha_batch_autotune", "fewha_reconstruct_batched",
-           "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state"] + _OPS
+           "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state", "fewha_solve",
+           "fewha_reconstruct_converged", "fewha_backward"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -113,6 +114,10 @@ def lib():
     L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_bench_stage.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
     L.fewha_frame_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    for name in ["fewha_solve", "fewha_reconstruct_converged"]:
+        getattr(L, name).argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ip, dp, _VP]
+    L.fewha_backward.argtypes = [_VP, _VP, _VP, dp, dp, _VP]
     L.fewha_get_state.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_set_state.argtypes = [_VP, _VP, _VP, _VP]
     for name in ["fewha_run_loop", "fewha_run_loop_f64"]:
@@ -368,6 +373,46 @@ class Reconstructor:
         self._check(self.L.fewha_pcg(self.h, self._dev(b, self.n_coeffs, "b"),
                                      self._dev(c, self.n_coeffs, "c"), int(iters), _stream(stream)))
         return c
+
+    # -- converged solve and gradients ------------------------------------------------
+    def default_tol(self):
+        """Relative residual of the converged solves: 1e-10 in FP64, 1e-6 in FP32 (FP32
+        operators cannot resolve M's weakly determined modes much further)."""
+        return 1e-10 if self.precision == 64 else 1e-6
+
+    def solve(self, b, tol=None, max_iters=20000, stream=None):
+        """x = M^-1 b (PCG to a relative preconditioned residual); returns (x, iters, rel)."""
+        x = self._new(self.n_coeffs)
+        it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.L.fewha_solve(self.h, self._dev(b, self.n_coeffs, "b"),
+                                       self._dev(x, self.n_coeffs, "x"),
+                                       self.default_tol() if tol is None else float(tol),
+                                       int(max_iters), ctypes.byref(it), ctypes.byref(rel),
+                                       _stream(stream)))
+        return x, it.value, rel.value
+
+    def reconstruct_converged(self, slopes, tol=None, max_iters=20000, dm_out=None, stream=None):
+        """a~ = F W^T M^-1 b(s) (no gain); kept for backward().  Returns (a~, iters, rel)."""
+        if dm_out is None:
+            dm_out = self._new(self.n_act)
+        it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.L.fewha_reconstruct_converged(
+            self.h, self._dev(slopes, self.n_slopes, "slopes"), self._dev(dm_out, self.n_act, "dm_out"),
+            self.default_tol() if tol is None else float(tol), int(max_iters), ctypes.byref(it),
+            ctypes.byref(rel), _stream(stream)))
+        return dm_out, it.value, rel.value
+
+    def backward(self, grad_dm, stream=None):
+        """Gradients (slopes tensor, alpha, per-layer Cn2 weights) of J with dJ/da~ = grad_dm
+        at the last converged reconstruction."""
+        gs = self._new(self.n_slopes)
+        ga = ctypes.c_double(0.0)
+        nl = len(self._structs[2])
+        gw = (ctypes.c_double * nl)()
+        self._check(self.L.fewha_backward(self.h, self._dev(grad_dm, self.n_act, "grad_dm"),
+                                          self._dev(gs, self.n_slopes, "grad_slopes"),
+                                          ctypes.byref(ga), gw, _stream(stream)))
+        return gs, ga.value, list(gw)
 
     def bench_stage(self, stage, reps, stream=None):
         """Enqueue `reps` launches of one hot-path kernel (timing; clobbers the warm state)."""
