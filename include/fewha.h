@@ -75,6 +75,10 @@ extern "C" {
 
 #define FEWHA_FLAG_GRAPH 1u         /* replay each frame as a captured CUDA graph    */
 #define FEWHA_FLAG_WARM_RESIDUAL 2u /* r0 = (b - b_prev) + r_prev (Algorithm 1)     */
+#define FEWHA_FLAG_PDL 4u           /* programmatic dependent launch: each kernel lets
+                                       the next one launch its CTAs early, which wait on
+                                       the device for it to finish (off by default: on
+                                       GB300 it slows the graph-replayed frame)        */
 
 /* Telescope aperture: diameter D [m], central obstruction as a diameter ratio. */
 typedef struct fewha_telescope {

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fewha_batch.h"
@@ -210,6 +211,24 @@ Desc<T> make_desc(const fewha_handle* H) {
     return d;
 }
 
+// Launch of a hot-path kernel, with programmatic stream serialization if the handle asks
+// for it (FEWHA_FLAG_PDL; the kernels then wait for their predecessor on the device).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(const fewha_handle* H, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = (H->params.flags & FEWHA_FLAG_PDL) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------- step recording
 // A batched frame runs the single-instance frame sequence of every instance: while a
 // recorder is set on this thread, the launchers below append their step (kind and
@@ -326,8 +345,9 @@ int launch_proj(fewha_handle* H, const Desc<T>& d, const T* phi, cudaStream_t st
         record<T>(BK_PROJ).ptr = phi;
         return FEWHA_OK;
     }
-    k_proj<T><<<dim3(d.n_wfs, d.n_layers), cblk<T>(), H->smem_proj, st>>>(d, phi, pair_bufs<T>(H));
-    CK(cudaGetLastError(), "k_proj launch");
+    CK(launch_k(H, k_proj<T>, dim3(d.n_wfs, d.n_layers), dim3(cblk<T>()), H->smem_proj, st, d, phi,
+                pair_bufs<T>(H)),
+       "k_proj launch");
     return FEWHA_OK;
 }
 
@@ -337,8 +357,9 @@ int launch_projT(fewha_handle* H, const Desc<T>& d, const T* u, cudaStream_t st)
         record<T>(BK_PROJT).ptr = u;
         return FEWHA_OK;
     }
-    k_projT<T><<<dim3(d.n_wfs, d.n_layers), cblk<T>(), H->smem_projT, st>>>(d, u, pair_bufs<T>(H));
-    CK(cudaGetLastError(), "k_projT launch");
+    CK(launch_k(H, k_projT<T>, dim3(d.n_wfs, d.n_layers), dim3(cblk<T>()), H->smem_projT, st, d, u,
+                pair_bufs<T>(H)),
+       "k_projT launch");
     return FEWHA_OK;
 }
 
@@ -350,9 +371,9 @@ int launch_fwd(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream
         record<T>(DST == LDST_APPLY ? BK_FWD_APPLY : BK_FWD_COEF).cl = a;
         return FEWHA_OK;
     }
-    k_cl_fwd<T, SRC, DST><<<dim3(CL, d.n_layers), cblk<T>(), H->smem_fwd, st>>>(d, a, H->lay_fwd,
-                                                                                   pair_bufs<T>(H));
-    CK(cudaGetLastError(), "k_cl_fwd launch");
+    CK(launch_k(H, k_cl_fwd<T, SRC, DST>, dim3(CL, d.n_layers), dim3(cblk<T>()), H->smem_fwd, st, d, a,
+                H->lay_fwd, pair_bufs<T>(H)),
+       "k_cl_fwd launch");
     return FEWHA_OK;
 }
 
@@ -362,8 +383,9 @@ int launch_inv(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream
         record<T>(PUPD ? BK_INV_UPD : BK_INV).cl = a;
         return FEWHA_OK;
     }
-    k_cl_inv<T, PUPD><<<dim3(CL, d.n_layers), cblk<T>(), H->smem_inv, st>>>(d, a, H->lay_inv);
-    CK(cudaGetLastError(), "k_cl_inv launch");
+    CK(launch_k(H, k_cl_inv<T, PUPD>, dim3(CL, d.n_layers), dim3(cblk<T>()), H->smem_inv, st, d, a,
+                H->lay_inv),
+       "k_cl_inv launch");
     return FEWHA_OK;
 }
 
@@ -374,9 +396,9 @@ int launch_csensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaS
         record<T>(SRC == SSRC_PHI ? BK_SEN_PHI : BK_SEN_SLOPES).sa = a;
         return FEWHA_OK;
     }
-    k_cl_sensor<T, SRC><<<dim3(CL, d.n_wfs), cblk<T>(), H->smem_sen, st>>>(d, a, H->lay_sen,
-                                                                          pair_bufs<T>(H));
-    CK(cudaGetLastError(), "k_cl_sensor launch");
+    CK(launch_k(H, k_cl_sensor<T, SRC>, dim3(CL, d.n_wfs), dim3(cblk<T>()), H->smem_sen, st, d, a,
+                H->lay_sen, pair_bufs<T>(H)),
+       "k_cl_sensor launch");
     return FEWHA_OK;
 }
 
@@ -427,8 +449,7 @@ int launch_vec(fewha_handle* H, int n, const VecArgs<T>& v, cudaStream_t st) {
         record<T>(PHASE == V_INIT ? BK_VEC_INIT : PHASE == V_INIT_WARM ? BK_VEC_WARM : BK_VEC_UPDATE).va = v;
         return FEWHA_OK;
     }
-    k_vec<T, PHASE><<<vec_grid(H), PBLK, 0, st>>>(n, v);
-    CK(cudaGetLastError(), "k_vec launch");
+    CK(launch_k(H, k_vec<T, PHASE>, dim3(vec_grid(H)), dim3(PBLK), 0, st, n, v), "k_vec launch");
     return FEWHA_OK;
 }
 
@@ -438,8 +459,8 @@ int launch_fit(fewha_handle* H, const Desc<T>& d, const T* phi, T* a_prev, T* dm
         record<T>(BK_FIT).fa = FitArgs<T>{phi, a_prev, dm, gain};
         return FEWHA_OK;
     }
-    k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, a_prev, dm, gain);
-    CK(cudaGetLastError(), "k_fit launch");
+    CK(launch_k(H, k_fit<T>, dim3((d.n_act + PBLK - 1) / PBLK), dim3(PBLK), 0, st, d, phi, a_prev, dm, gain),
+       "k_fit launch");
     return FEWHA_OK;
 }
 
@@ -1238,6 +1259,7 @@ int batch_build(fewha_batch* B, const std::vector<Recorder<T>>& recs, const std:
             L.items = reinterpret_cast<const BItem*>(base + loff[li]);
             L.n_items = static_cast<int>(lists[li].size());
             L.smem = smem[g * BK_COUNT + kind];
+            L.pdl = (B->h[0]->params.flags & FEWHA_FLAG_PDL) != 0;
             le = batch_launch<T>(L, st);
         }
     }
@@ -1587,16 +1609,13 @@ int bench_stage(fewha_handle* H, int stage, int reps, cudaStream_t st) {
                 break;
             }
             case FEWHA_STAGE_VECTOR:
-                k_vec<T, V_UPDATE><<<vec_grid(H), PBLK, 0, st>>>(d.n_c, vec_args<T>(H, static_cast<T*>(H->c), 0));
-                CK(cudaGetLastError(), "k_vec launch");
+                rc = launch_vec<T, V_UPDATE>(H, d.n_c, vec_args<T>(H, static_cast<T*>(H->c), 0), st);
                 break;
             case FEWHA_STAGE_RHS:
                 rc = launch_csensor<T, SSRC_SLOPES>(H, d, static_cast<const T*>(H->s_tmp), u, st);
                 break;
             case FEWHA_STAGE_FIT:
-                k_fit<T><<<(d.n_act + PBLK - 1) / PBLK, PBLK, 0, st>>>(d, phi, static_cast<T*>(H->a_prev),
-                                                                       static_cast<T*>(H->dm_tmp), 1);
-                CK(cudaGetLastError(), "k_fit launch");
+                rc = launch_fit<T>(H, d, phi, static_cast<T*>(H->a_prev), static_cast<T*>(H->dm_tmp), 1, st);
                 break;
             case FEWHA_STAGE_PROJ:
                 rc = launch_proj<T>(H, d, phi, st);

@@ -2,6 +2,8 @@
 // of many instances in one launch.  A CTA first copies its instance's descriptor into
 // shared memory (the bodies then read it from there, as the single-instance kernels read
 // theirs from the constant bank), then runs the body on its unit.
+#include <utility>
+
 #include "fewha_batch.h"
 
 namespace fewha {
@@ -23,6 +25,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     kb_cl_inv(const BInst<T>* __restrict__ inst, const ClArgs<T>* __restrict__ args,
               const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
+    pdl_enter();
     const BItem it = items[blockIdx.y];
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
@@ -36,6 +39,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     kb_cl_fwd(const BInst<T>* __restrict__ inst, const ClArgs<T>* __restrict__ args,
               const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
+    pdl_enter();
     const BItem it = items[blockIdx.y];
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
@@ -50,6 +54,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     kb_cl_sensor(const BInst<T>* __restrict__ inst, const SensorArgs<T>* __restrict__ args,
                  const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
+    pdl_enter();
     const BItem it = items[blockIdx.y];
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
@@ -64,6 +69,7 @@ __global__ void __launch_bounds__(cblk<T>(), 1)
     kb_proj(const BInst<T>* __restrict__ inst, const T* const* __restrict__ args,
             const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
+    pdl_enter();
     const BItem it = items[blockIdx.x];
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
@@ -76,6 +82,7 @@ __global__ void __launch_bounds__(cblk<T>(), 1)
     kb_projT(const BInst<T>* __restrict__ inst, const T* const* __restrict__ args,
              const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
+    pdl_enter();
     const BItem it = items[blockIdx.x];
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
@@ -87,6 +94,7 @@ template <class T, int PHASE>
 __global__ void __launch_bounds__(PBLK)
     kb_vec(const BInst<T>* __restrict__ inst, const VecArgs<T>* __restrict__ args,
            const BItem* __restrict__ items) {
+    pdl_enter();
     const BItem it = items[blockIdx.x];
     const BInst<T>* I = inst + it.inst;
     const VecArgs<T> v = args[it.inst];
@@ -98,6 +106,7 @@ __global__ void __launch_bounds__(PBLK)
     kb_fit(const BInst<T>* __restrict__ inst, const FitArgs<T>* __restrict__ args,
            const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
+    pdl_enter();
     const BItem it = items[blockIdx.x];
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
@@ -156,57 +165,48 @@ cudaError_t batch_smem_limit(int kind, size_t* bytes) {
     return e;
 }
 
+template <typename... KArgs, typename... Args>
+cudaError_t launch_b(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <class T>
 cudaError_t batch_launch(const BLaunch& L, cudaStream_t st) {
     if (L.n_items <= 0) return cudaSuccess;
     const BInst<T>* I = static_cast<const BInst<T>*>(L.inst);
     const int n = L.n_items;
-    constexpr int NT = cblk<T>();
+    const dim3 cg(CL, n), pg(n), nt(cblk<T>()), vt(PBLK);
+    const ClArgs<T>* ca = static_cast<const ClArgs<T>*>(L.args);
+    const SensorArgs<T>* sa = static_cast<const SensorArgs<T>*>(L.args);
+    const T* const* pa = static_cast<const T* const*>(L.args);
+    const VecArgs<T>* va = static_cast<const VecArgs<T>*>(L.args);
+    const FitArgs<T>* fa = static_cast<const FitArgs<T>*>(L.args);
     switch (L.kind) {
-        case BK_INV:
-            kb_cl_inv<T, false><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args), L.items);
-            break;
-        case BK_INV_UPD:
-            kb_cl_inv<T, true><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args), L.items);
-            break;
-        case BK_FWD_APPLY:
-            kb_cl_fwd<T, LDST_APPLY><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args),
-                                                                     L.items);
-            break;
-        case BK_FWD_COEF:
-            kb_cl_fwd<T, LDST_COEF><<<dim3(CL, n), NT, L.smem, st>>>(I, static_cast<const ClArgs<T>*>(L.args),
-                                                                    L.items);
-            break;
-        case BK_SEN_PHI:
-            kb_cl_sensor<T, SSRC_PHI><<<dim3(CL, n), NT, L.smem, st>>>(
-                I, static_cast<const SensorArgs<T>*>(L.args), L.items);
-            break;
-        case BK_SEN_SLOPES:
-            kb_cl_sensor<T, SSRC_SLOPES><<<dim3(CL, n), NT, L.smem, st>>>(
-                I, static_cast<const SensorArgs<T>*>(L.args), L.items);
-            break;
-        case BK_PROJ:
-            kb_proj<T><<<n, NT, L.smem, st>>>(I, static_cast<const T* const*>(L.args), L.items);
-            break;
-        case BK_PROJT:
-            kb_projT<T><<<n, NT, L.smem, st>>>(I, static_cast<const T* const*>(L.args), L.items);
-            break;
-        case BK_VEC_INIT:
-            kb_vec<T, V_INIT><<<n, PBLK, 0, st>>>(I, static_cast<const VecArgs<T>*>(L.args), L.items);
-            break;
-        case BK_VEC_WARM:
-            kb_vec<T, V_INIT_WARM><<<n, PBLK, 0, st>>>(I, static_cast<const VecArgs<T>*>(L.args), L.items);
-            break;
-        case BK_VEC_UPDATE:
-            kb_vec<T, V_UPDATE><<<n, PBLK, 0, st>>>(I, static_cast<const VecArgs<T>*>(L.args), L.items);
-            break;
-        case BK_FIT:
-            kb_fit<T><<<n, PBLK, L.smem, st>>>(I, static_cast<const FitArgs<T>*>(L.args), L.items);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+        case BK_INV: return launch_b(L.pdl, kb_cl_inv<T, false>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_INV_UPD: return launch_b(L.pdl, kb_cl_inv<T, true>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_FWD_APPLY: return launch_b(L.pdl, kb_cl_fwd<T, LDST_APPLY>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_FWD_COEF: return launch_b(L.pdl, kb_cl_fwd<T, LDST_COEF>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_SEN_PHI: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_PHI>, cg, nt, L.smem, st, I, sa, L.items);
+        case BK_SEN_SLOPES: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_SLOPES>, cg, nt, L.smem, st, I, sa, L.items);
+        case BK_PROJ: return launch_b(L.pdl, kb_proj<T>, pg, nt, L.smem, st, I, pa, L.items);
+        case BK_PROJT: return launch_b(L.pdl, kb_projT<T>, pg, nt, L.smem, st, I, pa, L.items);
+        case BK_VEC_INIT: return launch_b(L.pdl, kb_vec<T, V_INIT>, pg, vt, 0, st, I, va, L.items);
+        case BK_VEC_WARM: return launch_b(L.pdl, kb_vec<T, V_INIT_WARM>, pg, vt, 0, st, I, va, L.items);
+        case BK_VEC_UPDATE: return launch_b(L.pdl, kb_vec<T, V_UPDATE>, pg, vt, 0, st, I, va, L.items);
+        case BK_FIT: return launch_b(L.pdl, kb_fit<T>, pg, vt, L.smem, st, I, fa, L.items);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template cudaError_t batch_launch<float>(const BLaunch&, cudaStream_t);

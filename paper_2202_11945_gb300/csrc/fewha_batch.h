@@ -76,6 +76,7 @@ struct BLaunch {
     const BItem* items;    // work list
     int n_items;
     size_t smem;           // dynamic shared memory (max over the instances present)
+    bool pdl;              // programmatic stream serialization (see FEWHA_FLAG_PDL)
 };
 
 // Launch one batched step (defined in fewha_batch.cu for float and double).

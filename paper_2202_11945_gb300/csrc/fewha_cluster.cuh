@@ -456,6 +456,7 @@ template <class T, int SRC, int DST>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_fwd(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay, __grid_constant__ const PairBufs<T> pb) {
+    pdl_enter();
     cl_fwd_body<T, SRC, DST>(d, a, lay, pb, blockIdx.y, gridDim.x * gridDim.y);
 }
 
@@ -620,6 +621,7 @@ template <class T, bool PUPD>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_inv(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay) {
+    pdl_enter();
     cl_inv_body<T, PUPD>(d, a, lay, blockIdx.y);
 }
 
@@ -867,6 +869,7 @@ template <class T, int SRC>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_sensor(__grid_constant__ const Desc<T> d, __grid_constant__ const SensorArgs<T> a,
                 __grid_constant__ const SensorLayout lay, __grid_constant__ const PairBufs<T> pb) {
+    pdl_enter();
     cl_sensor_body<T, SRC>(d, a, lay, pb, blockIdx.y);
 }
 

@@ -14,6 +14,15 @@ namespace fewha {
 constexpr int BLK = 1024;   // threads of the per-layer and per-sensor kernels
 constexpr int PQ_SLOTS = MAXL * 8;   // p.q partial slots per CG iteration (layer x cluster rank)
 constexpr int PBLK = 256;   // threads of the vector (PCG) kernels
+
+// Programmatic dependent launch: let the stream's next kernel start launching its CTAs,
+// then wait until the previous kernel has completed and its writes are visible.  Nothing
+// of this kernel's own work happens before the wait.  Both instructions are no-ops when the
+// kernel was launched without programmatic stream serialization.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 constexpr int NWARP = BLK / 32;
 
 __constant__ float c_h32[6];
@@ -735,6 +744,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
 
 template <class T, int PHASE>
 __global__ void __launch_bounds__(PBLK) k_vec(const int n, __grid_constant__ const VecArgs<T> v) {
+    pdl_enter();
     vec_body<T, PHASE>(n, v, blockIdx.x, gridDim.x);
 }
 
@@ -777,6 +787,7 @@ template <class T>
 __global__ void __launch_bounds__(PBLK) k_fit(__grid_constant__ const Desc<T> d, const T* __restrict__ phi,
                                               T* __restrict__ a_prev, T* __restrict__ out,
                                               int apply_gain) {
+    pdl_enter();
     fit_body<T>(d, phi, a_prev, out, apply_gain, blockIdx.x);
 }
 

@@ -59,6 +59,7 @@ template <class T>
 __global__ void __launch_bounds__(cblk<T>(), 1) k_proj(__grid_constant__ const Desc<T> d,
                                                        const T* __restrict__ phi,
                                                        __grid_constant__ const PairBufs<T> pb) {
+    pdl_enter();
     proj_body<T>(d, phi, pb, blockIdx.x, blockIdx.y);
 }
 
@@ -134,6 +135,7 @@ template <class T>
 __global__ void __launch_bounds__(cblk<T>(), 1) k_projT(__grid_constant__ const Desc<T> d,
                                                         const T* __restrict__ u,
                                                         __grid_constant__ const PairBufs<T> pb) {
+    pdl_enter();
     projT_body<T>(d, u, pb, blockIdx.x, blockIdx.y);
 }
 

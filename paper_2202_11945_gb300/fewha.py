@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfewha.so")
 
 FLAG_GRAPH = 1
 FLAG_WARM_RESIDUAL = 2
+FLAG_PDL = 4
 
 ERRORS = {
     -1: "invalid argument",
@@ -170,14 +171,15 @@ def _stream(stream):
 class Reconstructor:
     """One FEWHA instance on the current CUDA device (a handle of the C library)."""
 
-    def __init__(self, wl, precision=32, graph=True, warm_residual=False):
+    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False):
         if not torch.cuda.is_available():
             raise RuntimeError("FEWHA needs a CUDA device; there is no CPU path")
         torch.cuda.init()
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.precision = precision
         self.dtype = torch.float32 if precision == 32 else torch.float64
-        flags = (FLAG_GRAPH if graph else 0) | (FLAG_WARM_RESIDUAL if warm_residual else 0)
+        flags = ((FLAG_GRAPH if graph else 0) | (FLAG_WARM_RESIDUAL if warm_residual else 0) |
+                 (FLAG_PDL if pdl else 0))
         self._structs = structs_from_workload(wl, precision, flags)
         tel, wfs, layers, dms, params = self._structs
         self.L = lib()

@@ -141,3 +141,17 @@ def test_external_and_internal_warm_state_agree():
         a = to_np(A.reconstruct(s, x_warm=x))
         b = to_np(B.reconstruct(s))
         assert np.array_equal(a, b)
+
+
+def test_programmatic_dependent_launch_gives_identical_frames():
+    """FEWHA_FLAG_PDL changes only how the kernels are launched, not what they compute."""
+    from paper_2202_11945_gb300 import Reconstructor
+    for name, prec, graph in (("tiny_mcao", 32, True), ("maory", 32, True), ("tiny_scao", 64, False)):
+        wl = synth.workload_by_name(name)
+        A = Reconstructor(wl, precision=prec, graph=graph)
+        B = Reconstructor(wl, precision=prec, graph=graph, pdl=True)
+        for t in range(3):
+            s = to_dev(slopes(name, t), prec)
+            assert np.array_equal(to_np(A.reconstruct(s)), to_np(B.reconstruct(s))), (name, t)
+        A.close()
+        B.close()
