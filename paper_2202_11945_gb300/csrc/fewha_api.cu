@@ -728,6 +728,31 @@ int cluster_layouts(fewha_handle* H) {
         }
     }
     H->box_host = box;
+    // staged pair terms of the forward kernel's band: per layer and cluster rank, the
+    // band's rows of every sensor's term, each run rounded to a 16-byte chunk
+    bool aligned = true;
+    int ystg = 0;
+    for (size_t l = 0; l < s.L.size(); ++l) {
+        const int n = s.L[l].n, rb = n >= CL ? n / CL : 1;
+        for (int r = 0; r * rb < n && r < CL; ++r) {
+            int need = 0;
+            for (size_t g = 0; g < s.G.size(); ++g) {
+                const int* bx = &box[(g * MAXL + l) * 4];
+                aligned = aligned && (bx[3] % V) == 0;
+                const int lo = std::max(r * rb, bx[0]), hi = std::min(r * rb + rb, bx[0] + bx[1]);
+                if (hi > lo) need += ((hi - lo) * bx[3] + V - 1) & ~(V - 1);
+            }
+            ystg = std::max(ystg, need);
+        }
+    }
+    // the batched kernels also hold their instance's descriptor in static shared memory
+    const long long spare = 227LL * 1024 - static_cast<long long>(H->smem_fwd) -
+                            static_cast<long long>(sizeof(Desc<T>)) - 2048;
+    if (aligned && ystg > 0 && static_cast<long long>(round4(ystg)) * static_cast<long long>(sizeof(T)) <= spare) {
+        H->lay_fwd.ystg = H->lay_fwd.total;
+        H->lay_fwd.total += round4(ystg);
+        H->smem_fwd += static_cast<size_t>(round4(ystg)) * sizeof(T);
+    }
     H->smem_proj = proj * sizeof(T);
     H->smem_projT = projT * sizeof(T);
     H->pvs = round4(s.max_N + 1);

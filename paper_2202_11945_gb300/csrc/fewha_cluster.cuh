@@ -249,6 +249,7 @@ struct ClLayout {       // shared-memory offsets set by the host, in T units
     int ybuf, cbuf, lbuf, stage, stage2, tbuf, sbuf;
     int total;
     int umax;           // one staging buffer of the P^T pipeline
+    int ystg;           // staged pair terms of the band (forward kernel), 0 = not staged
 };
 
 constexpr int KMAX = 8;      // aperture rows / columns touching one layer row / column
@@ -303,6 +304,58 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 cp_async(ybuf + i * ys + j, a.in + off + (r0 + i) * n + j);
             }
             cp_async_wait();
+            __syncthreads();
+        } else if (lay.ystg > 0) {
+            // y = sum_g R_y,gl^T u_g R_x,gl over this band.  The band's rows of sensor g's
+            // term are one contiguous run of its pair slot (rows of box[g][l][3] columns):
+            // the runs' geometry goes to a shared table once, every run is staged with
+            // 16-byte copies, all in flight together, and the terms are added from shared
+            // memory in the fixed sensor order.
+            constexpr int V = vec16<T>();
+            constexpr int KB = (MAXN * (MAXN / CL) + NT - 1) / NT;   // band positions per thread
+            __shared__ int4 ygb[MAXG];        // per sensor: first and end band row, col0, cols
+            __shared__ int ygo[MAXG + 1];     // start of each sensor's run in the stage
+            __shared__ int ygs[MAXG];         // start of each run in the pair buffer
+            T* ystg = sm + lay.ystg;
+            if (threadIdx.x < d.n_wfs) {
+                const int g = threadIdx.x;
+                const int b0 = d.box[g][l][0], bc = d.box[g][l][3];
+                const int lo = max(r0, b0), hi = max(lo, min(r0 + rb, b0 + d.box[g][l][1]));
+                ygb[g] = make_int4(lo, hi, d.box[g][l][2], bc);
+                ygo[g + 1] = ((hi - lo) * bc + V - 1) & ~(V - 1);
+                ygs[g] = (g * d.n_layers + l) * pb.yslot + (lo - b0) * bc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                ygo[0] = 0;
+                for (int g = 0; g < d.n_wfs; ++g) ygo[g + 1] += ygo[g];
+            }
+            __syncthreads();
+            for (int g = 0; g < d.n_wfs; ++g) {
+                const int4 bx = ygb[g];
+                if (bx.y > bx.x) stage16(ystg + ygo[g], pb.Y + ygs[g], (bx.y - bx.x) * bx.w, threadIdx.x, NT);
+            }
+            cp_async_wait();
+            __syncthreads();
+            T acc[KB];
+#pragma unroll
+            for (int q = 0; q < KB; ++q) acc[q] = T(0);
+            for (int g = 0; g < d.n_wfs; ++g) {
+                const int4 bx = ygb[g];
+                const T* Yg = ystg + ygo[g];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) {
+                    const int k = threadIdx.x + q * NT;
+                    const int i = r0 + (k >> L.log2n), j = k & (n - 1);
+                    if (k < rb * n && i >= bx.x && i < bx.y && j >= bx.z && j < bx.z + bx.w)
+                        acc[q] += Yg[(i - bx.x) * bx.w + (j - bx.z)];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < KB; ++q) {
+                const int k = threadIdx.x + q * NT;
+                if (k < rb * n) ybuf[(k >> L.log2n) * ys + (k & (n - 1))] = acc[q];
+            }
             __syncthreads();
         } else {
             // y = sum_g R_y,gl^T u_g R_x,gl: add the pair terms (fixed sensor order) over
@@ -378,7 +431,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
     cluster.sync();                                                       // #3
-    double dot = 0.0;
+    DotAcc<T> dot;                 // p.q share of this CTA (double accuracy)
     if (coarse && r == 0) {
         constexpr int PL = (MAXN / 2) * (MAXN / 2) / NT;     // LL positions per thread
         T lp[PL], lD[PL];
@@ -411,7 +464,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 if (DST == LDST_APPLY) {
                     const T q = v + d.alpha * lD[s] * lp[s];
                     a.out[pos] = q;
-                    dot += double(lp[s]) * double(q);
+                    dot.add(lp[s], q);
                 } else {
                     a.out[pos] = v;
                 }
@@ -431,16 +484,16 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             if (DST == LDST_APPLY) {
                 const T q = v + d.alpha * pre_D[s] * pre_p[s];
                 a.out[pos] = q;
-                dot += double(pre_p[s]) * double(q);
+                dot.add(pre_p[s], q);
             } else {
                 a.out[pos] = v;
             }
         }
     }
     if (DST == LDST_APPLY) {
-        dot = cta_sum(dot, red);
+        const double cdot = cta_dot(dot, red);
         double* slots = a.pcg.pqpart + a.iter * PQ_SLOTS;
-        if (threadIdx.x == 0) slots[l * CL + r] = dot;
+        if (threadIdx.x == 0) slots[l * CL + r] = cdot;
         if (last_arrival(a.pcg.count + 1, ctas, &last) && threadIdx.x < 32) {
             // fixed order: layer-major, rank-minor over the slots of the layers present
             const double tot = warp_fixed_sum(slots, d.n_layers * CL);

@@ -43,6 +43,97 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// Inner products of the PCG (Sec. 3.3) to double accuracy.  In the FP32 form a thread's
+// share is accumulated in double-float (compensated FP32) arithmetic: the product of two
+// floats is exact as hi + lo (hi = fl(p q), lo = fma(p, q, -hi)), and the running sum is
+// an unevaluated s + c updated by a two-sum per term (relative error about 2^-48).  This
+// runs on the FP32 pipes; GB300's FP64 rate is about 1/64 of its FP32 rate, so converting
+// and accumulating every product in FP64 dominated the epilogues that form p.q and r.z.
+// The _rn intrinsics keep the compiler from fusing the two-sum steps.  A CTA's shares are
+// merged in the same arithmetic in a fixed order and leave the CTA as one double; totals
+// over CTAs, and alpha and beta, stay in FP64.  The FP64 form accumulates in double.
+// ---------------------------------------------------------------------------
+struct DFloat {
+    float s, c;    // value s + c, |c| small against |s|
+};
+
+__device__ __forceinline__ DFloat df_merge(DFloat a, DFloat b) {
+    const float t = __fadd_rn(a.s, b.s);                     // two-sum of the leading parts
+    const float bp = __fsub_rn(t, a.s);
+    const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(b.s, bp));
+    const float c = __fadd_rn(__fadd_rn(a.c, b.c), e);
+    const float s = __fadd_rn(t, c);                         // renormalise (fast two-sum)
+    return DFloat{s, __fsub_rn(c, __fsub_rn(s, t))};
+}
+
+template <class T>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double p, double q) { v += p * q; }
+};
+
+template <>
+struct DotAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float p, float q) {
+        const float h = __fmul_rn(p, q);
+        const float l = __fmaf_rn(p, q, -h);                 // p q = h + l exactly
+        const float t = __fadd_rn(s, h);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, l));
+    }
+};
+
+// Fixed-order CTA total of the threads' shares, returned to every thread.  `scratch`
+// holds blockDim.x doubles.
+__device__ __forceinline__ double cta_dot(const DotAcc<double>& a, double* scratch) {
+    const int nt = blockDim.x;
+    scratch[threadIdx.x] = a.v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double x = 0.0;
+        for (int i = threadIdx.x; i < nt; i += 32) x += scratch[i];
+        x = warp_sum(x);
+        if (threadIdx.x == 0) scratch[0] = x;
+    }
+    __syncthreads();
+    const double r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ DFloat warp_df_sum(DFloat v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const DFloat w{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+        v = df_merge(v, w);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double cta_dot(const DotAcc<float>& a, double* scratch) {
+    float2* sh = reinterpret_cast<float2*>(scratch);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const DFloat v = warp_df_sum(DFloat{a.s, a.c});
+    if (lane == 0) sh[warp] = make_float2(v.s, v.c);
+    __syncthreads();
+    if (warp == 0) {
+        const float2 x = lane < nw ? sh[lane] : make_float2(0.f, 0.f);
+        const DFloat t = warp_df_sum(DFloat{x.x, x.y});
+        if (lane == 0) scratch[0] = double(t.s) + double(t.c);
+    }
+    __syncthreads();
+    const double r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
 // Deterministic block sum of two doubles (fixed tree); red holds >= 2*(NWARP+1).
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
     a = warp_sum(a);
@@ -672,7 +763,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
         alpha = (rz != 0.0 && pq > 0.0) ? rz / pq : 0.0;
     }
     const T ta = T(alpha);
-    double dot = 0.0;
+    DotAcc<T> dot;
     for (int base = cta * PBLK * PVEC; base < n; base += nparts * PBLK * PVEC) {
         // issue every load of the batch before the arithmetic
         T b[PVEC], q[PVEC], r[PVEC], p[PVEC], c[PVEC], bp[PVEC], jv[PVEC];
@@ -715,24 +806,16 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
                 const T z = jv[k] * rr;
                 v.z[i] = z;
                 if (PHASE != V_UPDATE) v.p[i] = z;
-                dot += double(rr) * double(z);
+                dot.add(rr, z);
             }
         }
     }
-    // CTA partial of r.z (thread values summed by warp 0 in a fixed order: few FP64
-    // additions), then the last CTA forms the total in a fixed order
+    // CTA share of r.z (fixed order), then the last CTA forms the total in a fixed order
     __shared__ double part[PBLK];
-    part[threadIdx.x] = dot;
-    __syncthreads();
+    const double x = cta_dot(dot, part);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
-    if (w == 0) {
-        double x = 0.0;
-#pragma unroll
-        for (int i = 0; i < PBLK / 32; ++i) x += part[lane + 32 * i];
-        x = warp_sum(x);
-        if (lane == 0) v.pcg.rzpart[slot * v.pcg.npart + cta] = x;
-    }
+    if (threadIdx.x == 0) v.pcg.rzpart[slot * v.pcg.npart + cta] = x;
     if (last_arrival(v.pcg.count, nparts, &last) && w == 0) {
         const double tot = warp_fixed_sum(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart);
         if (lane == 0) {
