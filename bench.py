@@ -124,6 +124,23 @@ def make_inputs(wl):
     return [synth.simulate_slopes(wl, t, atm=atm) for t in range(N_FRAMES_INPUT)]
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum over the ranks of per-rank timed totals: the slowest replica
+    sets the job's time (every rank gets the result)."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch.distributed as dist
+    v = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return [float(x) for x in v.tolist()]
+
+
+def replica_throughput(world, steps, total_ms):
+    """Frames per second of the whole job: every rank runs `steps` frames of its own
+    replica in at most `total_ms` (the path does not shard; no data-path collective)."""
+    return world * steps / (total_ms * 1e-3)
+
+
 def time_frames(R, S, steps, warmup, flush, dm):
     """Per-frame device times (ms) of `steps` warm-started frames, L2 flushed between."""
     n = S.shape[0]
@@ -505,15 +522,9 @@ def main():
     batched = time_batched(args.batch_count, args.batch_steps, 3, flush) if args.batch_count > 0 else None
     backward = time_backward()
 
-    total32 = float(t32.sum())
-    total64 = float(t64.sum())
-    tot_e2e = float(te.sum())
-    if world > 1:
-        import torch.distributed as dist
-        v = torch.tensor([total32, total64, tot_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        total32, total64, tot_e2e = [float(x) for x in v.tolist()]
-    value = world * args.steps / (total32 * 1e-3)
+    total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
+                                               world, "cuda")
+    value = replica_throughput(world, args.steps, total32)
 
     base, parity = (None, None)
     if rank == 0 and world == 1:
@@ -534,12 +545,12 @@ def main():
                        "initial_residual": "explicit b - M c0", "form": "FP32 operators, FP64 "
                        "dots, CUDA graph", "l2": "512 MiB memset between timed frames",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "fp64_plain": {"value": world * args.steps / (total64 * 1e-3), "unit": UNIT,
+            "fp64_plain": {"value": replica_throughput(world, args.steps, total64), "unit": UNIT,
                            "ms_per_step": total64 / args.steps,
                            "p50_ms": float(np.percentile(t64, 50)),
                            "p99_ms": float(np.percentile(t64, 99)), "form": "FP64, stream launches"},
             "clocks": clk,
-            "e2e": {"value": world * e2e_steps / (tot_e2e * 1e-3), "unit": UNIT,
+            "e2e": {"value": replica_throughput(world, e2e_steps, tot_e2e), "unit": UNIT,
                     "p99_ms": float(np.percentile(te, 99)),
                     "h2d_bytes_per_step": R32.n_slopes * 4, "d2h_bytes_per_step": R32.n_act * 4 + 4,
                     "api": "fewha_reconstruct_host (pinned host buffers, wall clock)"},
