@@ -59,78 +59,80 @@ __device__ __forceinline__ void stage16(T* dst, const T* src, int count, int t, 
 // One periodic db3 analysis (INV = false) or synthesis (INV = true) step along an axis
 // of `lines` independent lines of length m, in place.  Element (line, pos) lives at
 // buf[line * ls + pos * ps].  A thread owns a run of R consecutive pairs of one line and
-// keeps a sliding window of the inputs in registers.
+// keeps a sliding window of the inputs in registers.  R is a compile-time constant of
+// the code that runs (1, 2, 4 or 8): the small coarse levels have R = 1, and code
+// unrolled for the largest R under run-time predicates made them instruction-bound.
+template <class T, bool INV, int R>
+__device__ __forceinline__ void dwt_run(T* Lp, int m, int h, int k0, int ps, bool act) {
+    T o0[R], o1[R];
+    if (act) {
+        if (!INV) {
+            T w[2 * R + 4];
+#pragma unroll
+            for (int s = 0; s < 2 * R + 4; ++s) w[s] = Lp[((2 * k0 + s) & (m - 1)) * ps];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                T a = T(0), d = T(0);
+#pragma unroll
+                for (int tt = 0; tt < 6; ++tt) {
+                    a += tap_h<T>(tt) * w[2 * q + tt];
+                    d += tap_g<T>(tt) * w[2 * q + tt];
+                }
+                o0[q] = a;
+                o1[q] = d;
+            }
+        } else {
+            T wa[R + 2], wd[R + 2];
+#pragma unroll
+            for (int s = 0; s < R + 2; ++s) {
+                const int idx = (k0 - 2 + s) & (h - 1);
+                wa[s] = Lp[idx * ps];
+                wd[s] = Lp[(h + idx) * ps];
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                o0[q] = tap_h<T>(0) * wa[q + 2] + tap_h<T>(2) * wa[q + 1] + tap_h<T>(4) * wa[q] +
+                        tap_g<T>(0) * wd[q + 2] + tap_g<T>(2) * wd[q + 1] + tap_g<T>(4) * wd[q];
+                o1[q] = tap_h<T>(1) * wa[q + 2] + tap_h<T>(3) * wa[q + 1] + tap_h<T>(5) * wa[q] +
+                        tap_g<T>(1) * wd[q + 2] + tap_g<T>(3) * wd[q + 1] + tap_g<T>(5) * wd[q];
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (!INV) {
+                Lp[(k0 + q) * ps] = o0[q];
+                Lp[(h + k0 + q) * ps] = o1[q];
+            } else {
+                Lp[(2 * (k0 + q)) * ps] = o0[q];
+                Lp[(2 * (k0 + q) + 1) * ps] = o1[q];
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <class T, bool INV>
 __device__ __forceinline__ void dwt_pass(T* buf, int lines, int m, int ls, int ps) {
     constexpr int NT = cblk<T>();
-    // lines, m and NT are powers of two
+    // lines, m and NT are powers of two; the callers keep R <= RMAX
     const int h = m >> 1;
     const int ll = __ffs(lines) - 1, lhh = __ffs(h) - 1;
     const int lnt = __ffs(NT) - 1;
     const int lruns = min(max(lnt - ll, 0), lhh);
-    const int runs = 1 << lruns;
     const int R = h >> lruns;
     const int t = threadIdx.x;
     const bool act = t < (lines << lruns);
     const int line = t & (lines - 1), k0 = (t >> ll) * R;
     T* Lp = buf + line * ls;
-    T o0[RMAX], o1[RMAX];
-    if (act) {
-        if (!INV) {
-            T w[2 * RMAX + 4];
-#pragma unroll
-            for (int s = 0; s < 2 * RMAX + 4; ++s)
-                if (s < 2 * R + 4) w[s] = Lp[((2 * k0 + s) & (m - 1)) * ps];
-#pragma unroll
-            for (int q = 0; q < RMAX; ++q) {
-                if (q < R) {
-                    T a = T(0), d = T(0);
-#pragma unroll
-                    for (int tt = 0; tt < 6; ++tt) {
-                        a += tap_h<T>(tt) * w[2 * q + tt];
-                        d += tap_g<T>(tt) * w[2 * q + tt];
-                    }
-                    o0[q] = a;
-                    o1[q] = d;
-                }
-            }
-        } else {
-            T wa[RMAX + 2], wd[RMAX + 2];
-#pragma unroll
-            for (int s = 0; s < RMAX + 2; ++s) {
-                if (s < R + 2) {
-                    const int idx = (k0 - 2 + s) & (h - 1);
-                    wa[s] = Lp[idx * ps];
-                    wd[s] = Lp[(h + idx) * ps];
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < RMAX; ++q) {
-                if (q < R) {
-                    o0[q] = tap_h<T>(0) * wa[q + 2] + tap_h<T>(2) * wa[q + 1] + tap_h<T>(4) * wa[q] +
-                            tap_g<T>(0) * wd[q + 2] + tap_g<T>(2) * wd[q + 1] + tap_g<T>(4) * wd[q];
-                    o1[q] = tap_h<T>(1) * wa[q + 2] + tap_h<T>(3) * wa[q + 1] + tap_h<T>(5) * wa[q] +
-                            tap_g<T>(1) * wd[q + 2] + tap_g<T>(3) * wd[q + 1] + tap_g<T>(5) * wd[q];
-                }
-            }
-        }
+    switch (R) {
+        case 1: dwt_run<T, INV, 1>(Lp, m, h, k0, ps, act); break;
+        case 2: dwt_run<T, INV, 2>(Lp, m, h, k0, ps, act); break;
+        case 4: dwt_run<T, INV, 4>(Lp, m, h, k0, ps, act); break;
+        default: dwt_run<T, INV, RMAX>(Lp, m, h, k0, ps, act); break;
     }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-        for (int q = 0; q < RMAX; ++q) {
-            if (q < R) {
-                if (!INV) {
-                    Lp[(k0 + q) * ps] = o0[q];
-                    Lp[(h + k0 + q) * ps] = o1[q];
-                } else {
-                    Lp[(2 * (k0 + q)) * ps] = o0[q];
-                    Lp[(2 * (k0 + q) + 1) * ps] = o1[q];
-                }
-            }
-        }
-    }
-    __syncthreads();
 }
 
 // Deterministic CTA sum of one double: every thread's value goes to shared memory and
