@@ -83,6 +83,7 @@ struct fewha_handle {
     size_t smem_fwd = 0, smem_inv = 0, smem_sen = 0, smem_proj = 0, smem_projT = 0;
     // (sensor, layer) pair terms of P and P^T
     int* box = nullptr;
+    int* ytab = nullptr;              // band-run table of the forward kernel (PairBufs::ytab)
     std::vector<int> box_host;
     void* pairV = nullptr;
     void* pairY = nullptr;
@@ -336,6 +337,7 @@ PairBufs<T> pair_bufs(fewha_handle* H) {
     pb.vslot = H->pvslot;
     pb.yslot = H->pyslot;
     pb.box = H->box;
+    pb.ytab = reinterpret_cast<const int4*>(H->ytab);
     return pb;
 }
 
@@ -748,10 +750,33 @@ int cluster_layouts(fewha_handle* H) {
     // the batched kernels also hold their instance's descriptor in static shared memory
     const long long spare = 227LL * 1024 - static_cast<long long>(H->smem_fwd) -
                             static_cast<long long>(sizeof(Desc<T>)) - 2048;
+    std::vector<int> ytab;
     if (aligned && ystg > 0 && static_cast<long long>(round4(ystg)) * static_cast<long long>(sizeof(T)) <= spare) {
         H->lay_fwd.ystg = H->lay_fwd.total;
         H->lay_fwd.total += round4(ystg);
         H->smem_fwd += static_cast<size_t>(round4(ystg)) * sizeof(T);
+        // the run table (see PairBufs::ytab)
+        const int nw = static_cast<int>(s.G.size());
+        ytab.assign(s.L.size() * CL * nw * 8, 0);
+        for (size_t l = 0; l < s.L.size(); ++l) {
+            const int n = s.L[l].n, rb = n >= CL ? n / CL : 1;
+            for (int r = 0; r < CL; ++r) {
+                int so = 0;
+                for (int g = 0; g < nw; ++g) {
+                    const int* bx = &box[(g * MAXL + l) * 4];
+                    const int lo = std::max(r * rb, bx[0]);
+                    const int hi = std::max(lo, std::min(r * rb + rb, bx[0] + bx[1]));
+                    int* e = &ytab[((l * CL + r) * nw + g) * 8];
+                    e[0] = lo;
+                    e[1] = hi;
+                    e[2] = bx[2];
+                    e[3] = bx[3];
+                    e[4] = so;
+                    e[5] = (g * static_cast<int>(s.L.size()) + static_cast<int>(l)) * yslot + (lo - bx[0]) * bx[3];
+                    so += ((hi - lo) * bx[3] + V - 1) & ~(V - 1);
+                }
+            }
+        }
     }
     H->smem_proj = proj * sizeof(T);
     H->smem_projT = projT * sizeof(T);
@@ -760,6 +785,7 @@ int cluster_layouts(fewha_handle* H) {
     H->pyslot = yslot;
     int rc;
     const size_t pairs = s.G.size() * s.L.size();
+    if (!ytab.empty() && ((rc = dalloc(H, &H->ytab, ytab.size())) || (rc = upload(H, H->ytab, ytab)))) return rc;
     if ((rc = dalloc(H, &H->box, box.size())) || (rc = upload(H, H->box, box)) ||
         (rc = talloc(H, &H->pairV, pairs * H->pvslot)) || (rc = talloc(H, &H->pairY, pairs * H->pyslot)))
         return rc;

@@ -223,6 +223,10 @@ struct PairBufs {
     int vslot;        // elements per V slot
     int yslot;        // elements per Y slot
     const int* box;   // per pair (g * MAXL + l): row0, rows, col0, cols
+    // staged band runs of the forward kernel, per (layer l, cluster rank r): for sensor g
+    // at ((l * CL + r) * n_wfs + g) * 2, {first row, end row, col0, cols} of the band's
+    // part of the term, then {offset in the stage, offset in Y, 0, 0}
+    const int4* ytab;
 };
 
 // ---------------------------------------------------------------------------
@@ -286,6 +290,10 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     const int row_start = (coarse && r0 < h) ? h : 0;
     const int ecnt = has_band ? (n - row_start) * rb : 0;
     T pre_p[PF], pre_D[PF];
+    // the band-run table of the staged sum, loaded now so that its latency overlaps
+    int4 ytv = make_int4(0, 0, 0, 0);
+    if (SRC == LSRC_NODES && lay.ystg > 0 && has_band && threadIdx.x < 2 * d.n_wfs)
+        ytv = pb.ytab[(l * CL + r) * 2 * d.n_wfs + threadIdx.x];
     if (DST == LDST_APPLY) {
 #pragma unroll
         for (int s = 0; s < PF; ++s) {
@@ -309,54 +317,47 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             __syncthreads();
         } else if (lay.ystg > 0) {
             // y = sum_g R_y,gl^T u_g R_x,gl over this band.  The band's rows of sensor g's
-            // term are one contiguous run of its pair slot (rows of box[g][l][3] columns):
-            // the runs' geometry goes to a shared table once, every run is staged with
-            // 16-byte copies, all in flight together, and the terms are added from shared
-            // memory in the fixed sensor order.
-            constexpr int V = vec16<T>();
+            // term are one contiguous run of its pair slot (rows of box[g][l][3] columns);
+            // the runs (host table) are staged with 16-byte copies, all in flight together,
+            // and added from shared memory in the fixed sensor order.  A thread owns one
+            // column j of the band (NT is a multiple of n) and the rows i0 + q * di.
             constexpr int KB = (MAXN * (MAXN / CL) + NT - 1) / NT;   // band positions per thread
             __shared__ int4 ygb[MAXG];        // per sensor: first and end band row, col0, cols
-            __shared__ int ygo[MAXG + 1];     // start of each sensor's run in the stage
-            __shared__ int ygs[MAXG];         // start of each run in the pair buffer
+            __shared__ int4 ygx[MAXG];        // per sensor: offset in the stage, offset in Y
             T* ystg = sm + lay.ystg;
-            if (threadIdx.x < d.n_wfs) {
-                const int g = threadIdx.x;
-                const int b0 = d.box[g][l][0], bc = d.box[g][l][3];
-                const int lo = max(r0, b0), hi = max(lo, min(r0 + rb, b0 + d.box[g][l][1]));
-                ygb[g] = make_int4(lo, hi, d.box[g][l][2], bc);
-                ygo[g + 1] = ((hi - lo) * bc + V - 1) & ~(V - 1);
-                ygs[g] = (g * d.n_layers + l) * pb.yslot + (lo - b0) * bc;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                ygo[0] = 0;
-                for (int g = 0; g < d.n_wfs; ++g) ygo[g + 1] += ygo[g];
+            if (threadIdx.x < 2 * d.n_wfs) {
+                if (threadIdx.x & 1)
+                    ygx[threadIdx.x >> 1] = ytv;
+                else
+                    ygb[threadIdx.x >> 1] = ytv;
             }
             __syncthreads();
             for (int g = 0; g < d.n_wfs; ++g) {
                 const int4 bx = ygb[g];
-                if (bx.y > bx.x) stage16(ystg + ygo[g], pb.Y + ygs[g], (bx.y - bx.x) * bx.w, threadIdx.x, NT);
+                if (bx.y > bx.x) stage16(ystg + ygx[g].x, pb.Y + ygx[g].y, (bx.y - bx.x) * bx.w, threadIdx.x, NT);
             }
-            cp_async_wait();
-            __syncthreads();
+            const int j = threadIdx.x & (n - 1);
+            const int i0 = threadIdx.x >> L.log2n, di = NT >> L.log2n;
             T acc[KB];
 #pragma unroll
             for (int q = 0; q < KB; ++q) acc[q] = T(0);
+            cp_async_wait();
+            __syncthreads();
             for (int g = 0; g < d.n_wfs; ++g) {
                 const int4 bx = ygb[g];
-                const T* Yg = ystg + ygo[g];
+                if (bx.y > bx.x && j >= bx.z && j < bx.z + bx.w) {
+                    const T* col = ystg + ygx[g].x + (j - bx.z);
 #pragma unroll
-                for (int q = 0; q < KB; ++q) {
-                    const int k = threadIdx.x + q * NT;
-                    const int i = r0 + (k >> L.log2n), j = k & (n - 1);
-                    if (k < rb * n && i >= bx.x && i < bx.y && j >= bx.z && j < bx.z + bx.w)
-                        acc[q] += Yg[(i - bx.x) * bx.w + (j - bx.z)];
+                    for (int q = 0; q < KB; ++q) {
+                        const int ii = i0 + q * di, i = r0 + ii;
+                        if (ii < rb && i >= bx.x && i < bx.y) acc[q] += col[(i - bx.x) * bx.w];
+                    }
                 }
             }
 #pragma unroll
             for (int q = 0; q < KB; ++q) {
-                const int k = threadIdx.x + q * NT;
-                if (k < rb * n) ybuf[(k >> L.log2n) * ys + (k & (n - 1))] = acc[q];
+                const int ii = i0 + q * di;
+                if (ii < rb) ybuf[ii * ys + j] = acc[q];
             }
             __syncthreads();
         } else {
@@ -541,10 +542,17 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     const int ys = n + 1, cs = rb + 1, lsd = h + 1;
     const bool coarse = L.levels >= 2;
 
+    // beta = rz_k / rz_(k-1), formed once (an FP64 division costs ~10 FP64 instructions,
+    // and GB300 issues a warp's FP64 instruction in ~64 cycles) and broadcast
+    __shared__ T sbeta;
     T beta = T(0);
     if (PUPD) {
-        const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
-        beta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
+        if (threadIdx.x == 0) {
+            const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
+            sbeta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
+        }
+        __syncthreads();
+        beta = sbeta;
     }
     const T* src = PUPD ? a.pupd : a.in;
     // ---- 1. stage this CTA's coefficients: its column band (without the LL quadrant
@@ -560,9 +568,10 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
     if (has_band) {
         if ((rb & (V - 1)) == 0) {
-            const int cpr = rb / V;             // chunks per row
+            const int cpr = rb / V;             // chunks per row (a power of two)
+            const int lcpr = __ffs(cpr) - 1;
             for (int k = threadIdx.x; k < nrow * cpr; k += NT) {
-                const int i = k / cpr, c = k - i * cpr;
+                const int i = k >> lcpr, c = k & (cpr - 1);
                 const int pos = off + (row_start + i) * n + r0 + c * V;
                 cp_async16(sp + i * rb + c * V, src + pos);
                 if (PUPD) cp_async16(sz + i * rb + c * V, a.zupd + pos);
@@ -781,9 +790,9 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
         }
         tx = cta_sum_t(tx, red);
         ty = cta_sum_t(ty, red);
-        if (threadIdx.x == 0) {
-            part[0] = double(tx);
-            part[1] = double(ty);
+        if (threadIdx.x == 0) {           // kept in T: no FP64 round trip on the slow pipe
+            reinterpret_cast<T*>(part)[0] = tx;
+            reinterpret_cast<T*>(part)[1] = ty;
         }
     }
     if (need_coarse) {
@@ -813,25 +822,25 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
         if (need_tt) {
             // warp 0 fetches the CL partials (one remote load per lane), fixed-order sum
             if (threadIdx.x < 32) {
-                double px = 0.0, py = 0.0;
+                T px = T(0), py = T(0);
                 if (lane < CL) {
-                    const double* pp = cluster.map_shared_rank(part, lane);
+                    const T* pp = cluster.map_shared_rank(reinterpret_cast<T*>(part), lane);
                     px = pp[0];
                     py = pp[1];
                 }
                 T tx = T(0), ty = T(0);
 #pragma unroll
                 for (int q = 0; q < CL; ++q) {
-                    tx += T(__shfl_sync(0xffffffffu, px, q));
-                    ty += T(__shfl_sync(0xffffffffu, py, q));
+                    tx += __shfl_sync(0xffffffffu, px, q);
+                    ty += __shfl_sync(0xffffffffu, py, q);
                 }
                 if (threadIdx.x == 0) {
-                    red[0] = double(tx);
-                    red[1] = double(ty);
+                    reinterpret_cast<T*>(red)[0] = tx;
+                    reinterpret_cast<T*>(red)[1] = ty;
                 }
             }
             __syncthreads();
-            const T tx = T(red[0]), ty = T(red[1]);
+            const T tx = reinterpret_cast<T*>(red)[0], ty = reinterpret_cast<T*>(red)[1];
             const T mx = tx / T(W.n_active), my = ty / T(W.n_active);
             // C_hat^-1 = (I - T) sigma^-2 (I - T) = sigma^-2 (I - T) for an LGS
             for (int k = threadIdx.x; k < rows * N; k += NT) {

@@ -756,13 +756,18 @@ template <class T, int PHASE>
 __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const int cta,
                                          const int nparts) {
     __shared__ bool last;
-    double alpha = 0.0;
+    __shared__ T salpha;
+    T ta = T(0);
     if (PHASE == V_UPDATE) {
-        // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final)
-        const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
-        alpha = (rz != 0.0 && pq > 0.0) ? rz / pq : 0.0;
+        // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final).  Formed
+        // once and broadcast: an FP64 division is ~10 instructions on GB300's slow FP64 pipe
+        if (threadIdx.x == 0) {
+            const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
+            salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
+        }
+        __syncthreads();
+        ta = salpha;
     }
-    const T ta = T(alpha);
     DotAcc<T> dot;
     for (int base = cta * PBLK * PVEC; base < n; base += nparts * PBLK * PVEC) {
         // issue every load of the batch before the arithmetic
