@@ -184,6 +184,34 @@ __device__ __forceinline__ float cta_sum_t(float v, double* scratch) {
 }
 __device__ __forceinline__ double cta_sum_t(double v, double* scratch) { return cta_sum(v, scratch); }
 
+// Two fixed-order CTA sums in one pass (each component in the order of cta_sum_t).
+template <class T>
+__device__ __forceinline__ void cta_sum2_t(T& x, T& y, double* scratch) {
+    const int nt = blockDim.x;
+    T* sx = reinterpret_cast<T*>(scratch);
+    T* sy = sx + nt;
+    sx[threadIdx.x] = x;
+    sy[threadIdx.x] = y;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T a = T(0), b = T(0);
+        for (int i = threadIdx.x; i < nt; i += 32) {
+            a += sx[i];
+            b += sy[i];
+        }
+        a = warp_sum_t(a);
+        b = warp_sum_t(b);
+        if (threadIdx.x == 0) {
+            sx[0] = a;
+            sy[0] = b;
+        }
+    }
+    __syncthreads();
+    x = sx[0];
+    y = sy[0];
+    __syncthreads();
+}
+
 constexpr int SMALL = 32;              // side of the spare scratch tile
 constexpr int SSTRIDE = SMALL + 1;
 
@@ -727,6 +755,11 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     T* cw = halo + 2 * N;       // 2 x MAXCOARSE: weighted coarse slopes / nb
     T* ph = sm + lay.phsub;
 
+    // peers' shared memory is written before the first full cluster barrier (the pushes
+    // below): arrive now, wait before the first push, so that every CTA has started
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+    __shared__ T ttp[2 * CL];                    // every rank's tip/tilt sums (pushed)
+    __shared__ T cps[CL * 2 * MAXCOARSE];        // every rank's coarse block sums (pushed)
     if (SRC == SSRC_PHI && rows > 0) {
         // ---- stage every layer's sub-block under this band's footprint and the tables --
         // ---- V = P_g phi = sum_l (pair term of layer l) on node rows [s0, s1] ---------
@@ -782,17 +815,18 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     // ---- cluster reductions (fixed order): LGS tip/tilt sums, coarse block sums -------
     const bool need_tt = W.lgs;
     const bool need_coarse = (SRC == SSRC_PHI) && W.nb > 1;
+    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
     if (need_tt) {
         T tx = T(0), ty = T(0);
         for (int k = threadIdx.x; k < rows * N; k += NT) {
             tx += SX[k];
             ty += SY[k];
         }
-        tx = cta_sum_t(tx, red);
-        ty = cta_sum_t(ty, red);
-        if (threadIdx.x == 0) {           // kept in T: no FP64 round trip on the slow pipe
-            reinterpret_cast<T*>(part)[0] = tx;
-            reinterpret_cast<T*>(part)[1] = ty;
+        cta_sum2_t(tx, ty, red);
+        if (threadIdx.x < CL) {           // push this rank's sums into every rank's table
+            T* dst = cluster.map_shared_rank(ttp, static_cast<unsigned>(threadIdx.x));
+            dst[2 * r] = tx;
+            dst[2 * r + 1] = ty;
         }
     }
     if (need_coarse) {
@@ -809,38 +843,27 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
                         sy += SY[(i - s0) * N + j];
                     }
             }
-            sx = warp_sum_t(sx);
+            sx = warp_sum_t(sx);          // complete in lane 0 only (shuffle-down tree)
             sy = warp_sum_t(sy);
-            if (lane == 0) {
-                part[2 + 2 * blk] = double(sx);
-                part[3 + 2 * blk] = double(sy);
+            sx = __shfl_sync(0xffffffffu, sx, 0);
+            sy = __shfl_sync(0xffffffffu, sy, 0);
+            if (lane < CL) {              // push this rank's block sums into every rank
+                T* dst = cluster.map_shared_rank(cps, static_cast<unsigned>(lane));
+                dst[r * 2 * MAXCOARSE + 2 * blk] = sx;
+                dst[r * 2 * MAXCOARSE + 2 * blk + 1] = sy;
             }
         }
     }
     if (need_tt || need_coarse) {
         cluster.sync();                                                   // partials ready
         if (need_tt) {
-            // warp 0 fetches the CL partials (one remote load per lane), fixed-order sum
-            if (threadIdx.x < 32) {
-                T px = T(0), py = T(0);
-                if (lane < CL) {
-                    const T* pp = cluster.map_shared_rank(reinterpret_cast<T*>(part), lane);
-                    px = pp[0];
-                    py = pp[1];
-                }
-                T tx = T(0), ty = T(0);
+            // the CL ranks' sums, local after the barrier, added in rank order
+            T tx = T(0), ty = T(0);
 #pragma unroll
-                for (int q = 0; q < CL; ++q) {
-                    tx += __shfl_sync(0xffffffffu, px, q);
-                    ty += __shfl_sync(0xffffffffu, py, q);
-                }
-                if (threadIdx.x == 0) {
-                    reinterpret_cast<T*>(red)[0] = tx;
-                    reinterpret_cast<T*>(red)[1] = ty;
-                }
+            for (int q = 0; q < CL; ++q) {
+                tx += ttp[2 * q];
+                ty += ttp[2 * q + 1];
             }
-            __syncthreads();
-            const T tx = reinterpret_cast<T*>(red)[0], ty = reinterpret_cast<T*>(red)[1];
             const T mx = tx / T(W.n_active), my = ty / T(W.n_active);
             // C_hat^-1 = (I - T) sigma^-2 (I - T) = sigma^-2 (I - T) for an LGS
             for (int k = threadIdx.x; k < rows * N; k += NT) {
@@ -855,9 +878,8 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
             for (int blk = threadIdx.x; blk < ns * ns; blk += NT) {
                 T sx = T(0), sy = T(0);
                 for (int q = 0; q < CL; ++q) {
-                    const double* pp = cluster.map_shared_rank(part, q);
-                    sx += T(pp[2 + 2 * blk]);
-                    sy += T(pp[3 + 2 * blk]);
+                    sx += cps[q * 2 * MAXCOARSE + 2 * blk];
+                    sy += cps[q * 2 * MAXCOARSE + 2 * blk + 1];
                 }
                 // coarse slope = sum / nb; Gamma_coarse^T spreads sigma^-2 slope / nb
                 cw[2 * blk] = sx * nbinv * inv * nbinv;
