@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-frames", type=int, default=20, help="oracle frames of the CPU baseline")
     ap.add_argument("--batch-count", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--batch-steps", type=int, default=50, help="timed batched frames")
+    ap.add_argument("--backward-frames", type=int, default=8,
+                    help="frames of the differentiable-reconstruction leg (0: leave it out)")
     ap.add_argument("--loop-frames", type=int, default=2000,
                     help="frames of the 1 kHz real-time loop (8 m single-conjugate geometry)")
     return ap.parse_args()
@@ -520,7 +522,7 @@ def main():
 
     loop, wl3, S3, dm3, dm3w = time_loop(args.loop_frames)
     batched = time_batched(args.batch_count, args.batch_steps, 3, flush) if args.batch_count > 0 else None
-    backward = time_backward()
+    backward = time_backward(args.backward_frames) if args.backward_frames > 0 else None
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")

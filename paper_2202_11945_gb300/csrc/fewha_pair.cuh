@@ -118,14 +118,28 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
     for (int ii = warp; ii < rows; ii += nwarp) {
         const int i = r0 + ii;
-        const int a0 = d.ry_lo[rbk + i], a1 = d.ry_hi[rbk + i];
-        for (int jj = lane; jj < cols; jj += 32) {
-            T acc = T(0);
-            for (int a = a0; a < a1; ++a) {
-                const T f = d.pfy[tp + a];
-                const T wv = d.pi0y[tp + a] == i ? T(1) - f : f;
-                acc += wv * Tx[a * cols + jj];
+        int a0 = 0, c = 0;
+        if (i < d.L[l].n) {
+            a0 = d.ry_lo[rbk + i];
+            c = d.ry_hi[rbk + i] - a0;
+        }
+        // the row's weights once, in registers (the stores to `out` would otherwise force
+        // the table loads to be repeated for every column)
+        T wv[KMAX];
+#pragma unroll
+        for (int q = 0; q < KMAX; ++q) {
+            wv[q] = T(0);
+            if (q < c) {
+                const T f = d.pfy[tp + a0 + q];
+                wv[q] = d.pi0y[tp + a0 + q] == i ? T(1) - f : f;
             }
+        }
+        for (int jj = lane; jj < cols; jj += 32) {
+            const T* tcol = Tx + a0 * cols + jj;
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < KMAX; ++q)
+                if (q < c) acc += wv[q] * tcol[q * cols];
             out[ii * cols + jj] = acc;
         }
     }
