@@ -522,12 +522,11 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
     if (DST == LDST_APPLY) {
-        const double cdot = cta_dot(dot, red);
         double* slots = a.pcg.pqpart + a.iter * PQ_SLOTS;
-        if (threadIdx.x == 0) slots[l * CL + r] = cdot;
+        cta_dot_store(dot, red, slots + l * CL + r);
         if (last_arrival(a.pcg.count + 1, ctas, &last) && threadIdx.x < 32) {
             // fixed order: layer-major, rank-minor over the slots of the layers present
-            const double tot = warp_fixed_sum(slots, d.n_layers * CL);
+            const double tot = warp_total(slots, d.n_layers * CL, &dot);
             if (threadIdx.x == 0) {
                 a.pcg.pqtot[a.iter] = tot;
                 a.pcg.count[1] = 0;
@@ -574,14 +573,6 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     // and GB300 issues a warp's FP64 instruction in ~64 cycles) and broadcast
     __shared__ T sbeta;
     T beta = T(0);
-    if (PUPD) {
-        if (threadIdx.x == 0) {
-            const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
-            sbeta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
-        }
-        __syncthreads();
-        beta = sbeta;
-    }
     const T* src = PUPD ? a.pupd : a.in;
     // ---- 1. stage this CTA's coefficients: its column band (without the LL quadrant
     // when coarse) and, for the leader, the LL quadrant.  Rows go through unpadded
@@ -629,8 +620,14 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
             }
         }
     }
+    // beta is formed while the copies are in flight; the staging barrier publishes it
+    if (PUPD && threadIdx.x == 0) {
+        const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
+        sbeta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
+    }
     cp_async_wait();
     __syncthreads();
+    if (PUPD) beta = sbeta;
     // p = z + beta p (PUPD) into the padded tiles and back to global
     if (has_band) {
         for (int k = threadIdx.x; k < nrow * rb; k += NT) {

@@ -134,6 +134,58 @@ __device__ __forceinline__ double cta_dot(const DotAcc<float>& a, double* scratc
     return r;
 }
 
+// A CTA's share of an inner product into its 8-byte slot, for the last-arriving CTA to
+// total (fixed order).  The FP64 form stores the double; the FP32 form stores the
+// double-float pair (s, c) itself, so that the total is also formed on the FP32 pipes.
+// The slot is written by thread 0 (last_arrival orders it before the arrival count).
+__device__ __forceinline__ void cta_dot_store(const DotAcc<double>& a, double* scratch, double* slot) {
+    const double x = cta_dot(a, scratch);
+    if (threadIdx.x == 0) *slot = x;
+}
+
+__device__ __forceinline__ void cta_dot_store(const DotAcc<float>& a, double* scratch, double* slot) {
+    float2* sh = reinterpret_cast<float2*>(scratch);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const DFloat v = warp_df_sum(DFloat{a.s, a.c});
+    if (lane == 0) sh[warp] = make_float2(v.s, v.c);
+    __syncthreads();
+    if (warp == 0) {
+        const float2 x = lane < nw ? sh[lane] : make_float2(0.f, 0.f);
+        const DFloat t = warp_df_sum(DFloat{x.x, x.y});
+        if (lane == 0) *reinterpret_cast<float2*>(slot) = make_float2(t.s, t.c);
+    }
+}
+
+// Total of `cnt` <= 512 slots written by other CTAs, by one warp in a fixed order: every
+// lane issues its loads at once (L2, bypassing L1), then a fixed tree.  Valid in lane 0.
+__device__ __forceinline__ double warp_total(const double* p, int cnt, const DotAcc<double>*) {
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = (threadIdx.x & 31) + 32 * k;
+        v[k] = i < cnt ? __ldcg(p + i) : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s += v[k];
+    return warp_sum(s);
+}
+
+__device__ __forceinline__ double warp_total(const double* p, int cnt, const DotAcc<float>*) {
+    float2 v[16];
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = (threadIdx.x & 31) + 32 * k;
+        v[k] = i < cnt ? __ldcg(q + i) : make_float2(0.f, 0.f);
+    }
+    DFloat s{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s = df_merge(s, DFloat{v[k].x, v[k].y});
+    s = warp_df_sum(s);
+    return double(s.s) + double(s.c);
+}
+
 // Deterministic block sum of two doubles (fixed tree); red holds >= 2*(NWARP+1).
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
     a = warp_sum(a);
@@ -348,21 +400,6 @@ struct PcgSlots {
     unsigned* count;    // [2]: arrival counters of the reducing grids, reset by the last CTA
     int npart;
 };
-
-// Fixed-order sum of cnt <= 512 doubles written by other CTAs of this grid, by one warp:
-// every lane issues its loads at once (L2, bypassing L1), then a fixed shuffle tree.
-__device__ __forceinline__ double warp_fixed_sum(const double* p, int cnt) {
-    double v[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int i = (threadIdx.x & 31) + 32 * k;
-        v[k] = i < cnt ? __ldcg(p + i) : 0.0;
-    }
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) s += v[k];
-    return warp_sum(s);
-}
 
 // Arrival of one CTA of a reducing grid; true in the CTA that arrives last.  Its
 // partial must already be stored; the fence orders it before the count.
@@ -758,15 +795,13 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     __shared__ bool last;
     __shared__ T salpha;
     T ta = T(0);
-    if (PHASE == V_UPDATE) {
+    bool have_alpha = PHASE != V_UPDATE;
+    if (!have_alpha && threadIdx.x == 0) {
         // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final).  Formed
-        // once and broadcast: an FP64 division is ~10 instructions on GB300's slow FP64 pipe
-        if (threadIdx.x == 0) {
-            const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
-            salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
-        }
-        __syncthreads();
-        ta = salpha;
+        // once and broadcast (an FP64 division is ~10 instructions on GB300's slow FP64
+        // pipe), while the first batch of vector loads is in flight
+        const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
+        salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
     }
     DotAcc<T> dot;
     for (int base = cta * PBLK * PVEC; base < n; base += nparts * PBLK * PVEC) {
@@ -791,6 +826,11 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
                     q[k] = v.q[i];
                 }
             }
+        }
+        if (!have_alpha) {               // uniform over the CTA (base does not depend on the thread)
+            __syncthreads();
+            ta = salpha;
+            have_alpha = true;
         }
 #pragma unroll
         for (int k = 0; k < PVEC; ++k) {
@@ -817,12 +857,11 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     }
     // CTA share of r.z (fixed order), then the last CTA forms the total in a fixed order
     __shared__ double part[PBLK];
-    const double x = cta_dot(dot, part);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
-    if (threadIdx.x == 0) v.pcg.rzpart[slot * v.pcg.npart + cta] = x;
+    cta_dot_store(dot, part, v.pcg.rzpart + slot * v.pcg.npart + cta);
     if (last_arrival(v.pcg.count, nparts, &last) && w == 0) {
-        const double tot = warp_fixed_sum(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart);
+        const double tot = warp_total(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart, &dot);
         if (lane == 0) {
             v.pcg.rztot[slot] = tot;
             v.pcg.count[0] = 0;
