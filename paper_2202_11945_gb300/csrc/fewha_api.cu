@@ -84,6 +84,8 @@ struct fewha_handle {
     // (sensor, layer) pair terms of P and P^T
     int* box = nullptr;
     int* ytab = nullptr;              // band-run table of the forward kernel (PairBufs::ytab)
+    void* ptw = nullptr;              // adjoint-projection weights (PairBufs::tw), T
+    int* pti = nullptr;               // their first index and count (PairBufs::ti)
     std::vector<int> box_host;
     void* pairV = nullptr;
     void* pairY = nullptr;
@@ -338,6 +340,8 @@ PairBufs<T> pair_bufs(fewha_handle* H) {
     pb.yslot = H->pyslot;
     pb.box = H->box;
     pb.ytab = reinterpret_cast<const int4*>(H->ytab);
+    pb.tw = static_cast<const T*>(H->ptw);
+    pb.ti = reinterpret_cast<const int2*>(H->pti);
     return pb;
 }
 
@@ -725,11 +729,51 @@ int cluster_layouts(fewha_handle* H) {
             bx[2] = c0;
             bx[3] = c1 - c0;
             yslot = std::max(yslot, round4(rows * (c1 - c0)));
-            proj = std::max(proj, static_cast<size_t>(round4(rows * (c1 - c0)) + rows * NP));
-            projT = std::max(projT, static_cast<size_t>(round4(V + NP * NP) + NP * (c1 - c0)));
+            proj = std::max(proj, static_cast<size_t>(round4(rows * (c1 - c0)) + rows * NP + 4 * NP + 4));
+            projT = std::max(projT, static_cast<size_t>(round4(2 * V + NP * NP) + round4(NP * (c1 - c0)) +
+                                                        (c1 - c0 + rows + 2) * (KMAX + 2) + 8));
         }
     }
     H->box_host = box;
+    // adjoint-projection weights of every pair (see PairBufs::tw / ti), in T arithmetic
+    {
+        const int nl = static_cast<int>(s.L.size()), ng = static_cast<int>(s.G.size());
+        std::vector<T> tw(static_cast<size_t>(ng) * nl * 2 * MAXN * KMAX, T(0));
+        std::vector<int> ti(static_cast<size_t>(ng) * nl * 2 * MAXN * 2 + 16, 0);
+        for (int g = 0; g < ng; ++g)
+            for (int l = 0; l < nl; ++l) {
+                const int pr = g * nl + l, n = s.L[l].n;
+                const int tp = (g * MAXL + l) * TAB, rbk = (g * MAXL + l) * MAXN;
+                const int* bx = &box[(g * MAXL + l) * 4];
+                for (int q = 0; q < 2; ++q) {
+                    const int cnt = q == 0 ? bx[3] : bx[1], base = q == 0 ? bx[2] : bx[0];
+                    const std::vector<int>& lo = q == 0 ? s.rx_lo : s.ry_lo;
+                    const std::vector<int>& hi = q == 0 ? s.rx_hi : s.ry_hi;
+                    const std::vector<int>& i0 = q == 0 ? s.pi0x : s.pi0y;
+                    const std::vector<double>& fw = q == 0 ? s.pfx : s.pfy;
+                    for (int k = 0; k < cnt && k < MAXN; ++k) {
+                        const int j = base + k;
+                        int b0 = 0, c = 0;
+                        if (j < n) {
+                            b0 = lo[rbk + j];
+                            c = hi[rbk + j] - b0;
+                        }
+                        int* e = &ti[((static_cast<size_t>(pr) * 2 + q) * MAXN + k) * 2];
+                        e[0] = b0;
+                        e[1] = c;
+                        T* w = &tw[((static_cast<size_t>(pr) * 2 + q) * MAXN + k) * KMAX];
+                        for (int m = 0; m < c && m < KMAX; ++m) {
+                            const T f = static_cast<T>(fw[tp + b0 + m]);
+                            w[m] = i0[tp + b0 + m] == j ? T(1) - f : f;
+                        }
+                    }
+                }
+            }
+        int rc0;
+        if ((rc0 = talloc(H, &H->ptw, tw.size())) || (rc0 = dalloc(H, &H->pti, ti.size()))) return rc0;
+        CK(cudaMemcpy(H->ptw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice), "projection weights");
+        if ((rc0 = upload(H, H->pti, ti))) return rc0;
+    }
     // staged pair terms of the forward kernel's band: per layer and cluster rank, the
     // band's rows of every sensor's term, each run rounded to a 16-byte chunk
     bool aligned = true;

@@ -251,6 +251,11 @@ struct PairBufs {
     int vslot;        // elements per V slot
     int yslot;        // elements per Y slot
     const int* box;   // per pair (g * MAXL + l): row0, rows, col0, cols
+    // adjoint-projection weights per pair p = g * n_layers + l, host-built: for box column
+    // (q = 0) or box row (q = 1) k, tw[((p * 2 + q) * MAXN + k) * KMAX ...] are the weights of
+    // the aperture columns (rows) starting at ti[(p * 2 + q) * MAXN + k].x, .y of them
+    const T* tw;
+    const int2* ti;
     // staged band runs of the forward kernel, per (layer l, cluster rank r): for sensor g
     // at ((l * CL + r) * n_wfs + g) * 2, {first row, end row, col0, cols} of the band's
     // part of the term, then {offset in the stage, offset in Y, 0, 0}

@@ -22,7 +22,19 @@ __device__ __forceinline__ void proj_body(const Desc<T>& d, const T* __restrict_
     const int r0 = d.box[g][l][0], rows = d.box[g][l][1], c0 = d.box[g][l][2], cols = d.box[g][l][3];
     const int n = d.L[l].n;
     T* Tm = F + rows * cols;                      // pass X result: rows x NP
+    T* tfx = Tm + rows * NP;                      // the pair's interpolation tables (NP each)
+    T* tfy = tfx + NP;
+    int* tj0 = reinterpret_cast<int*>(tfy + NP);
+    int* ti0 = tj0 + NP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
+    // the tables travel with the footprint (async copies, all in flight together), so
+    // that no pass waits on a table load from global memory
+    for (int k = threadIdx.x; k < NP; k += NT) {
+        cp_async(tfx + k, d.pfx + tp + k);
+        cp_async(tfy + k, d.pfy + tp + k);
+        cp_async(tj0 + k, d.pi0x + tp + k);
+        cp_async(ti0 + k, d.pi0y + tp + k);
+    }
     const T* src = phi + d.L[l].off + r0 * n + c0;
     if ((n & (V - 1)) == 0) {
         const int cpr = cols / V;
@@ -38,8 +50,8 @@ __device__ __forceinline__ void proj_body(const Desc<T>& d, const T* __restrict_
     {
         const int b = threadIdx.x % NP, rg = threadIdx.x / NP, groups = NT / NP;
         if (rg < groups) {
-            const int j0 = d.pi0x[tp + b] - c0;
-            const T fx = d.pfx[tp + b];
+            const int j0 = tj0[b] - c0;
+            const T fx = tfx[b];
             for (int i = rg; i < rows; i += groups)
                 Tm[i * NP + b] = (T(1) - fx) * F[i * cols + j0] + fx * F[i * cols + j0 + 1];
         }
@@ -48,8 +60,8 @@ __device__ __forceinline__ void proj_body(const Desc<T>& d, const T* __restrict_
     // pass Y: V(a, b) = (1 - fy_a) Tm(i0_a, b) + fy_a Tm(i0_a + 1, b)
     T* out = pb.V + static_cast<size_t>(g * d.n_layers + l) * pb.vslot;
     for (int a = warp; a < NP; a += nwarp) {
-        const int i0 = d.pi0y[tp + a] - r0;
-        const T fy = d.pfy[tp + a];
+        const int i0 = ti0[a] - r0;
+        const T fy = tfy[a];
         for (int b = lane; b < NP; b += 32)
             out[a * pb.vs + b] = (T(1) - fy) * Tm[i0 * NP + b] + fy * Tm[(i0 + 1) * NP + b];
     }
@@ -72,12 +84,25 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = reinterpret_cast<T*>(smem_raw);       // u_g, (N+1)^2 (+ alignment shift)
     const int N = d.G[g].N, NP = N + 1;
-    const int tp = (g * MAXL + l) * TAB, rbk = (g * MAXL + l) * MAXN;
-    const int r0 = d.box[g][l][0], rows = d.box[g][l][1], c0 = d.box[g][l][2], cols = d.box[g][l][3];
+    const int r0 = d.box[g][l][0], rows = d.box[g][l][1], cols = d.box[g][l][3];
     const int start = d.G[g].node_off, s0a = start & ~(V - 1);
     const int ushift = start - s0a;
-    T* Tx = U + ((ushift + NP * NP + V - 1) & ~(V - 1));   // pass X result: NP x cols
+    const int pr = g * d.n_layers + l;
+    auto up16 = [](int x) { return (x + V - 1) & ~(V - 1); };
+    T* Tx = U + up16(ushift + NP * NP);           // pass X result: NP x cols
+    T* cw = Tx + up16(NP * cols);                // column weights: cols x KMAX
+    T* rw = cw + cols * KMAX;                     // row weights: rows x KMAX
+    int2* cinf = reinterpret_cast<int2*>(rw + rows * KMAX);   // first aperture column, count
+    int2* rinf = cinf + ((cols + 1) & ~1);        // 16-byte aligned
+    constexpr int I2 = sizeof(int2) / sizeof(T);  // T elements per int2
+    // u_g and the pair's weight tables, 16-byte copies all in flight together
     stage16(U, u + s0a, ushift + NP * NP, threadIdx.x, NT);
+    stage16(cw, pb.tw + static_cast<size_t>(pr * 2) * MAXN * KMAX, cols * KMAX, threadIdx.x, NT);
+    stage16(rw, pb.tw + static_cast<size_t>(pr * 2 + 1) * MAXN * KMAX, rows * KMAX, threadIdx.x, NT);
+    stage16(reinterpret_cast<T*>(cinf), reinterpret_cast<const T*>(pb.ti + static_cast<size_t>(pr * 2) * MAXN),
+            cols * I2, threadIdx.x, NT);
+    stage16(reinterpret_cast<T*>(rinf), reinterpret_cast<const T*>(pb.ti + static_cast<size_t>(pr * 2 + 1) * MAXN),
+            rows * I2, threadIdx.x, NT);
     cp_async_wait();
     __syncthreads();
     const T* Us = U + ushift;
@@ -86,28 +111,16 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
         const int groups = NT / cols;
         const int jj = threadIdx.x % cols, rg = threadIdx.x / cols;
         if (rg < groups) {
-            const int j = c0 + jj;
-            const int n = d.L[l].n;
-            int b0 = 0, c = 0;
-            if (j < n) {
-                b0 = d.rx_lo[rbk + j];
-                c = d.rx_hi[rbk + j] - b0;
-            }
+            const int2 ci = cinf[jj];
             T w[KMAX];
 #pragma unroll
-            for (int q = 0; q < KMAX; ++q) {
-                w[q] = T(0);
-                if (q < c) {
-                    const T f = d.pfx[tp + b0 + q];
-                    w[q] = d.pi0x[tp + b0 + q] == j ? T(1) - f : f;
-                }
-            }
+            for (int q = 0; q < KMAX; ++q) w[q] = cw[jj * KMAX + q];
             for (int a = rg; a < NP; a += groups) {
-                const T* urow = Us + a * NP + b0;
+                const T* urow = Us + a * NP + ci.x;
                 T acc = T(0);
 #pragma unroll
                 for (int q = 0; q < KMAX; ++q)
-                    if (q < c) acc += w[q] * urow[q];
+                    if (q < ci.y) acc += w[q] * urow[q];
                 Tx[a * cols + jj] = acc;
             }
         }
@@ -116,30 +129,18 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
     // pass Y: Y(i, j) = sum_{a touching i} wy(a, i) Tx(a, j); warp per box row i
     T* out = pb.Y + static_cast<size_t>(g * d.n_layers + l) * pb.yslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
+    (void)r0;
     for (int ii = warp; ii < rows; ii += nwarp) {
-        const int i = r0 + ii;
-        int a0 = 0, c = 0;
-        if (i < d.L[l].n) {
-            a0 = d.ry_lo[rbk + i];
-            c = d.ry_hi[rbk + i] - a0;
-        }
-        // the row's weights once, in registers (the stores to `out` would otherwise force
-        // the table loads to be repeated for every column)
+        const int2 ri = rinf[ii];
         T wv[KMAX];
 #pragma unroll
-        for (int q = 0; q < KMAX; ++q) {
-            wv[q] = T(0);
-            if (q < c) {
-                const T f = d.pfy[tp + a0 + q];
-                wv[q] = d.pi0y[tp + a0 + q] == i ? T(1) - f : f;
-            }
-        }
+        for (int q = 0; q < KMAX; ++q) wv[q] = rw[ii * KMAX + q];
         for (int jj = lane; jj < cols; jj += 32) {
-            const T* tcol = Tx + a0 * cols + jj;
+            const T* tcol = Tx + ri.x * cols + jj;
             T acc = T(0);
 #pragma unroll
             for (int q = 0; q < KMAX; ++q)
-                if (q < c) acc += wv[q] * tcol[q * cols];
+                if (q < ri.y) acc += wv[q] * tcol[q * cols];
             out[ii * cols + jj] = acc;
         }
     }
