@@ -707,6 +707,8 @@ int cluster_layouts(fewha_handle* H) {
     q.SY = q.SX + round4(SXn);
     q.halo = q.SY + round4(SXn);
     q.total = q.halo + round4(halo);
+    q.msk = q.total;                               // rows x N ints
+    q.total += round4(SXn);
     H->lay_sen = q;
     const size_t hdr_s = (RED_DBL + 2 + 2 * MAXCOARSE) * sizeof(double) + (4 * MAXL + 4) * sizeof(int);
     H->smem_sen = hdr_s + static_cast<size_t>(q.total) * sizeof(T);

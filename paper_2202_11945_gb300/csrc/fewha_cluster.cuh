@@ -726,6 +726,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
 // ---------------------------------------------------------------------------
 struct SensorLayout {
     int phsub, V, SX, SY, halo, total;         // T units
+    int msk;            // the band's rows of the active-subaperture index table (ints)
 };
 
 template <class T, int SRC>
@@ -762,28 +763,38 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
     __shared__ T ttp[2 * CL];                    // every rank's tip/tilt sums (pushed)
     __shared__ T cps[CL * 2 * MAXCOARSE];        // every rank's coarse block sums (pushed)
+    // the band's rows of the active-subaperture table, copied while the terms are summed
+    int* msk = reinterpret_cast<int*>(sm + lay.msk);
+    for (int k = threadIdx.x; k < rows * N; k += NT) cp_async(msk + k, sidx + s0 * N + k);
     if (SRC == SSRC_PHI && rows > 0) {
-        // ---- stage every layer's sub-block under this band's footprint and the tables --
         // ---- V = P_g phi = sum_l (pair term of layer l) on node rows [s0, s1] ---------
+        // a warp per node row; every lane's columns accumulate in the fixed layer order,
+        // with the loads of several layers in flight
+        constexpr int LB = (MAXNF + 1 + 31) / 32;
         const T* Vb = pb.V + static_cast<size_t>(g * d.n_layers) * pb.vslot;
-        for (int ia = warp; ia < rows + 1; ia += nwarp)
-        for (int b = lane; b < NP; b += 32) {
-            T t[MAXL];
+        for (int ia = warp; ia < rows + 1; ia += nwarp) {
+            const T* row = Vb + (s0 + ia) * pb.vs + lane;
+            T acc[LB];
 #pragma unroll
-            for (int l = 0; l < MAXL; ++l)
-                t[l] = l < d.n_layers ? Vb[l * pb.vslot + (s0 + ia) * pb.vs + b] : T(0);
-            T v = T(0);
+            for (int u = 0; u < LB; ++u) acc[u] = T(0);
+#pragma unroll 3
+            for (int l = 0; l < d.n_layers; ++l) {
 #pragma unroll
-            for (int l = 0; l < MAXL; ++l) v += t[l];
-            V[ia * NP + b] = v;
+                for (int u = 0; u < LB; ++u)
+                    if (lane + 32 * u < NP) acc[u] += row[static_cast<size_t>(l) * pb.vslot + 32 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < LB; ++u)
+                if (lane + 32 * u < NP) V[ia * NP + lane + 32 * u] = acc[u];
         }
+        cp_async_wait();
         __syncthreads();
         // ---- Gamma_g on the band's active subapertures -----------------------------------
         for (int ii = warp; ii < rows; ii += nwarp)
         for (int j = lane; j < N; j += 32) {
             const int k = ii * N + j;
             T sx = T(0), sy = T(0);
-            if (sidx[(s0 + ii) * N + j] >= 0) {
+            if (msk[ii * N + j] >= 0) {
                 const T v00 = V[ii * NP + j], v01 = V[ii * NP + j + 1];
                 const T v10 = V[(ii + 1) * NP + j], v11 = V[(ii + 1) * NP + j + 1];
                 sx = T(0.5) * ((v01 - v00) + (v11 - v10));
@@ -795,8 +806,10 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     } else if (SRC == SSRC_SLOPES && rows > 0) {
         const T* s = a.in + W.soff;
         bool bad = false;
+        cp_async_wait();
+        __syncthreads();
         for (int k = threadIdx.x; k < rows * N; k += NT) {
-            const int id = sidx[s0 * N + k];
+            const int id = msk[k];
             T sx = T(0), sy = T(0);
             if (id >= 0) {
                 sx = s[id];
@@ -812,6 +825,7 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
         }
         if (bad && a.status) atomicOr(a.status, 1u);
     }
+    cp_async_wait();
     __syncthreads();
 
     // ---- cluster reductions (fixed order): LGS tip/tilt sums, coarse block sums -------
@@ -869,7 +883,7 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
             const T mx = tx / T(W.n_active), my = ty / T(W.n_active);
             // C_hat^-1 = (I - T) sigma^-2 (I - T) = sigma^-2 (I - T) for an LGS
             for (int k = threadIdx.x; k < rows * N; k += NT) {
-                if (sidx[s0 * N + k] >= 0) {
+                if (msk[k] >= 0) {
                     SX[k] = inv * (SX[k] - mx);
                     SY[k] = inv * (SY[k] - my);
                 }
@@ -893,7 +907,7 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
                 const int k = ii * N + j;
                 const int i = s0 + ii;
                 T sx = T(0), sy = T(0);
-                if (sidx[i * N + j] >= 0) {
+                if (msk[ii * N + j] >= 0) {
                     const int blk = (i / W.nb) * W.n_sub + j / W.nb;
                     sx = cw[2 * blk];
                     sy = cw[2 * blk + 1];

@@ -889,17 +889,40 @@ __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__
     while (m + 1 < d.n_dms && idx >= d.Mi[m + 1].off) ++m;
     const int na = d.Mi[m].n_act, loc = idx - d.Mi[m].off;
     const int p = loc / na, q = loc - p * na;
+    // layers four at a time: their table loads, then their samples, all in flight
+    // together; the terms are added in layer order
     T acc = T(0);
-    for (int l = 0; l < d.n_layers; ++l) {
-        const T w = d.fitw[m][l];
-        if (w == T(0)) continue;
-        const int tb = (m * MAXL + l) * MAXNACT;
-        const int i0 = d.di0[tb + p], j0 = d.di0[tb + q];
-        const T fy = d.dfw[tb + p], fx = d.dfw[tb + q];
-        const int n = d.L[l].n;
-        const T* P = phi + d.L[l].off + i0 * n + j0;
-        acc += w * ((T(1) - fy) * ((T(1) - fx) * P[0] + fx * P[1]) +
-                    fy * ((T(1) - fx) * P[n] + fx * P[n + 1]));
+    for (int l0 = 0; l0 < d.n_layers; l0 += 4) {
+        T w[4], fy[4], fx[4], v[4][4];
+        int i0[4], j0[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int l = l0 + u;
+            w[u] = l < d.n_layers ? d.fitw[m][l] : T(0);
+            if (w[u] != T(0)) {
+                const int tb = (m * MAXL + l) * MAXNACT;
+                i0[u] = d.di0[tb + p];
+                j0[u] = d.di0[tb + q];
+                fy[u] = d.dfw[tb + p];
+                fx[u] = d.dfw[tb + q];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (w[u] != T(0)) {
+                const int l = l0 + u, n = d.L[l].n;
+                const T* P = phi + d.L[l].off + i0[u] * n + j0[u];
+                v[u][0] = P[0];
+                v[u][1] = P[1];
+                v[u][2] = P[n];
+                v[u][3] = P[n + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (w[u] != T(0))
+                acc += w[u] * ((T(1) - fy[u]) * ((T(1) - fx[u]) * v[u][0] + fx[u] * v[u][1]) +
+                               fy[u] * ((T(1) - fx[u]) * v[u][2] + fx[u] * v[u][3]));
     }
     if (apply_gain) {
         const T a = (T(1) - d.gain) * a_prev[idx] + d.gain * acc;
