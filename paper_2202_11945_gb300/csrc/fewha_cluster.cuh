@@ -777,12 +777,18 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
             T acc[LB];
 #pragma unroll
             for (int u = 0; u < LB; ++u) acc[u] = T(0);
-#pragma unroll 3
-            for (int l = 0; l < d.n_layers; ++l) {
+            T t[MAXL][LB];
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l)
 #pragma unroll
                 for (int u = 0; u < LB; ++u)
-                    if (lane + 32 * u < NP) acc[u] += row[static_cast<size_t>(l) * pb.vslot + 32 * u];
-            }
+                    t[l][u] = (l < d.n_layers && lane + 32 * u < NP) ? row[static_cast<size_t>(l) * pb.vslot + 32 * u]
+                                                                     : T(0);
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l)
+#pragma unroll
+                for (int u = 0; u < LB; ++u)
+                    if (l < d.n_layers) acc[u] += t[l][u];
 #pragma unroll
             for (int u = 0; u < LB; ++u)
                 if (lane + 32 * u < NP) V[ia * NP + lane + 32 * u] = acc[u];
@@ -846,28 +852,41 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
         }
     }
     if (need_coarse) {
-        // per coarse block: the band's share of the fine-slope sums (one warp per block)
-        const int ns = W.n_sub, nb = W.nb;
-        for (int blk = warp; blk < ns * ns; blk += nwarp) {
+        // per coarse block: the band's share of the fine-slope sums.  The warps split over
+        // blocks and, within a block, over its rows (subset sw of SUB); the subsets' sums are
+        // merged in subset order and pushed into every rank's table.
+        constexpr int SUB = 4;
+        __shared__ T csub[MAXCOARSE][SUB][2];
+        const int ns = W.n_sub, nb = W.nb, nblk = ns * ns;
+        for (int wk = warp; wk < nblk * SUB; wk += nwarp) {
+            const int blk = wk % nblk, sw = wk / nblk;
             const int I = blk / ns, J = blk - I * ns;
             const int i0 = max(I * nb, s0), i1 = min((I + 1) * nb, s1);
             T sx = T(0), sy = T(0);
-            if (i0 < i1) {
-                for (int i = i0; i < i1; ++i)
-                    for (int j = J * nb + lane; j < (J + 1) * nb; j += 32) {
-                        sx += SX[(i - s0) * N + j];
-                        sy += SY[(i - s0) * N + j];
-                    }
-            }
-            sx = warp_sum_t(sx);          // complete in lane 0 only (shuffle-down tree)
+            for (int i = i0 + sw; i < i1; i += SUB)
+                for (int j = J * nb + lane; j < (J + 1) * nb; j += 32) {
+                    sx += SX[(i - s0) * N + j];
+                    sy += SY[(i - s0) * N + j];
+                }
+            sx = warp_sum_t(sx);          // complete in lane 0 (shuffle-down tree)
             sy = warp_sum_t(sy);
-            sx = __shfl_sync(0xffffffffu, sx, 0);
-            sy = __shfl_sync(0xffffffffu, sy, 0);
-            if (lane < CL) {              // push this rank's block sums into every rank
-                T* dst = cluster.map_shared_rank(cps, static_cast<unsigned>(lane));
-                dst[r * 2 * MAXCOARSE + 2 * blk] = sx;
-                dst[r * 2 * MAXCOARSE + 2 * blk + 1] = sy;
+            if (lane == 0) {
+                csub[blk][sw][0] = sx;
+                csub[blk][sw][1] = sy;
             }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nblk * CL; k += NT) {
+            const int blk = k / CL, q = k - blk * CL;
+            T sx = T(0), sy = T(0);
+#pragma unroll
+            for (int sw = 0; sw < SUB; ++sw) {
+                sx += csub[blk][sw][0];
+                sy += csub[blk][sw][1];
+            }
+            T* dst = cluster.map_shared_rank(cps, static_cast<unsigned>(q));   // push to rank q
+            dst[r * 2 * MAXCOARSE + 2 * blk] = sx;
+            dst[r * 2 * MAXCOARSE + 2 * blk + 1] = sy;
         }
     }
     if (need_tt || need_coarse) {
