@@ -318,6 +318,9 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     T* lbuf = sm + lay.lbuf;          // h x (h + 1)
     const int ys = n + 1, cs = rb + 1, lsd = h + 1;
 
+    // the exchanges below push into peers' shared memory before the first full cluster
+    // barrier: arrive now, wait before the first push, so that every CTA has started
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
     // ---- 0. prefetch the epilogue operands of the column band (independent of u) ----
     constexpr int PF = MAXN * (MAXN / CL) / NT;     // column-band positions per thread
     const int row_start = (coarse && r0 < h) ? h : 0;
@@ -424,49 +427,29 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         // ---- 2. level-0 analysis along the rows of the band --------------------
         dwt_pass<T, false>(ybuf, rb, n, ys, 1);
     }
-    cluster.sync();                                                       // #1
-    // ---- 3. column band: gather the band's columns from every row band -------------
+    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+    // ---- 3. the band's rows go to every column band's owner (pushed), column analysis ---
     if (has_band) {
-        constexpr int G = MAXN * (MAXN / CL) / NT;
-        T v[G];
-#pragma unroll
-        for (int s = 0; s < G; ++s) {           // every remote load in flight before any store
-            const int k = threadIdx.x + s * NT;
-            if (k < n * rb) {
-                const int i = (k >> lrb), jj = k - i * rb;
-                const int q = (i >> lrb), ii = i - q * rb;
-                v[s] = cluster.map_shared_rank(ybuf, q)[ii * ys + r0 + jj];
-            }
+        for (int k = threadIdx.x; k < rb * n; k += NT) {
+            const int ii = k >> L.log2n, j = k & (n - 1);
+            cluster.map_shared_rank(cbuf, static_cast<unsigned>(j >> lrb))[(r0 + ii) * cs + (j & (rb - 1))] =
+                ybuf[ii * ys + j];
         }
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int k = threadIdx.x + s * NT;
-            if (k < n * rb) cbuf[((k >> lrb)) * cs + (k & (rb - 1))] = v[s];
-        }
-        __syncthreads();
+    }
+    cluster.sync();                                                       // #1: column tiles complete
+    if (has_band) {
         dwt_pass<T, false>(cbuf, rb, n, 1, cs);
-    }
-    cluster.sync();                                                       // #2
-    // ---- 4. the leader gathers the LL quadrant and finishes the coarse levels --------
-    if (coarse && r == 0) {
-        constexpr int G = (MAXN / 2) * (MAXN / 2) / NT;
-        T v[G];
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int k = threadIdx.x + s * NT;
-            if (k < h * h) {
-                const int i = (k >> lh), j = k - i * h;
-                const int q = (j >> lrb), jj = j - q * rb;
-                v[s] = cluster.map_shared_rank(cbuf, q)[i * cs + jj];
+        // ---- 4. the LL quadrant's part of this column band goes to the leader (pushed) ---
+        if (coarse && r0 < h) {
+            T* lead = cluster.map_shared_rank(lbuf, 0);
+            for (int k = threadIdx.x; k < h * rb; k += NT) {
+                const int i = k >> lrb, jj = k & (rb - 1);
+                lead[i * lsd + r0 + jj] = cbuf[i * cs + jj];
             }
         }
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int k = threadIdx.x + s * NT;
-            if (k < h * h) lbuf[((k >> lh)) * lsd + (k & (h - 1))] = v[s];
-        }
     }
-    cluster.sync();                                                       // #3
+    cluster.sync();                                                       // #2: the leader holds LL;
+                                                                          // no remote access after this
     DotAcc<T> dot;                 // p.q share of this CTA (double accuracy)
     if (coarse && r == 0) {
         constexpr int PL = (MAXN / 2) * (MAXN / 2) / NT;     // LL positions per thread
@@ -579,6 +562,9 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     __shared__ T sbeta;
     T beta = T(0);
     const T* src = PUPD ? a.pupd : a.in;
+    // the exchanges below push into peers' shared memory before the first full cluster
+    // barrier: arrive now, wait before the first push, so that every CTA has started
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
     // ---- 1. stage this CTA's coefficients: its column band (without the LL quadrant
     // when coarse) and, for the leader, the LL quadrant.  Rows go through unpadded
     // staging tiles in 16-byte chunks when aligned, then into the padded tiles.
@@ -657,58 +643,35 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
     __syncthreads();
-    // ---- 2. the leader synthesises the coarse levels into the LL quadrant ------------
+    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+    // ---- 2. the leader synthesises the coarse levels into the LL quadrant and pushes its
+    // columns into the column bands' tiles ---------------------------------------------
     if (coarse && r == 0) {
         coarse_inverse<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+        for (int k = threadIdx.x; k < h * h; k += NT) {
+            const int i = k >> lh, j = k & (h - 1);
+            cluster.map_shared_rank(cbuf, static_cast<unsigned>(j >> lrb))[i * cs + (j & (rb - 1))] = lbuf[i * lsd + j];
+        }
     }
     cluster.sync();                                                       // #1
-    // ---- 3. column synthesis of level 0 on the column band ------------------------------
+    // ---- 3. column synthesis of level 0 on the column band; its rows go to every row
+    // band's owner (pushed) -----------------------------------------------------------------
     if (has_band) {
-        if (coarse && r0 < h) {
-            const T* lead = cluster.map_shared_rank(lbuf, 0);
-            constexpr int G = (MAXN / 2) * (MAXN / CL) / NT + 1;
-            T v[G];
-#pragma unroll
-            for (int s = 0; s < G; ++s) {
-                const int k = threadIdx.x + s * NT;
-                if (k < h * rb) v[s] = lead[((k >> lrb)) * lsd + r0 + (k & (rb - 1))];
-            }
-#pragma unroll
-            for (int s = 0; s < G; ++s) {
-                const int k = threadIdx.x + s * NT;
-                if (k < h * rb) cbuf[((k >> lrb)) * cs + (k & (rb - 1))] = v[s];
-            }
-            __syncthreads();
-        }
         dwt_pass<T, true>(cbuf, rb, n, 1, cs);
+        for (int k = threadIdx.x; k < n * rb; k += NT) {
+            const int i = k >> lrb, jj = k & (rb - 1), q = i >> lrb;
+            cluster.map_shared_rank(ybuf, static_cast<unsigned>(q))[(i - q * rb) * ys + r0 + jj] = cbuf[i * cs + jj];
+        }
     }
-    cluster.sync();                                                       // #2
-    // ---- 4. row band: gather from every column band, row synthesis, store phi ---------
+    cluster.sync();                                                       // #2: no remote access after this
+    // ---- 4. row synthesis of the row band, store phi --------------------------------------
     if (has_band) {
-        constexpr int G = MAXN * (MAXN / CL) / NT;
-        T v[G];
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int k = threadIdx.x + s * NT;
-            if (k < rb * n) {
-                const int ii = (k >> L.log2n), j = k - ii * n;
-                const int q = (j >> lrb), jj = j - q * rb;
-                v[s] = cluster.map_shared_rank(cbuf, q)[(r0 + ii) * cs + jj];
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int k = threadIdx.x + s * NT;
-            if (k < rb * n) ybuf[(k >> L.log2n) * ys + (k & (n - 1))] = v[s];
-        }
-        __syncthreads();
         dwt_pass<T, true>(ybuf, rb, n, ys, 1);
         for (int k = threadIdx.x; k < rb * n; k += NT) {
             const int ii = (k >> L.log2n), j = k - ii * n;
             a.out[off + (r0 + ii) * n + j] = ybuf[ii * ys + j];
         }
     }
-    cluster.sync();                                                       // #3: peers done reading
 }
 
 template <class T, bool PUPD>
