@@ -42,6 +42,12 @@ Readings where the paper is silent or garbled (each also listed in the design doc):
       DM (or below the lowest) it goes wholly to that DM.  The shape is sampled
       bilinearly at the actuator positions, lateral coordinates unchanged.
   R14 open-loop control a = (1 - gain) a_prev + gain a_tilde (Algorithm 1)
+  R26 augmented PCG (Sec. 3.4, Algorithm 1): the previous frame's directions P and
+      Q = M P augment the Krylov space.  The start is corrected over span(P),
+      c0 += P y, r0 -= Q y, y_k = p_k.r0 / p_k.q_k, and every new direction is made
+      M-conjugate to P, p = z + beta p_old - P mu, mu_k = q_k.z / p_k.q_k (P^T Q is
+      diagonal for the M-conjugate directions of one CG run).  At most 8 directions
+      (iter <= 8); none on the first frame.
 """
 
 import math
@@ -601,6 +607,57 @@ def pcg(geo, b, c0, Jinv, iters, D=None, r0=None):
     return c, r
 
 
+def augmented_pcg(geo, b, c0, Jinv, iters, D=None, r0=None, prev=None):
+    """Augmented PCG of Algorithm 1 (Sec. 3.4, reading R26).
+
+    `prev` = (P, Q, pq): the search directions p_k of the previous frame's PCG, their
+    images q_k = M p_k and the inner products p_k . q_k.  The start is corrected over
+    span(P), all coefficients from the same residual:
+        y_k = (p_k . r0) / (p_k . q_k),   c0 <- c0 + sum_k y_k p_k,   r0 <- r0 - sum_k y_k q_k,
+    and every direction of this frame is made M-conjugate to P:
+        p = z + beta p_old - sum_k mu_k p_k,   mu_k = (q_k . z) / (p_k . q_k)
+    (a previous direction with p_k . q_k <= 0 is left out).  Otherwise standard PCG for
+    `iters` iterations; its directions, images and inner products are returned.
+
+    Returns (c, r, (P, Q, pq)).
+    """
+    c = np.array(c0, float, copy=True)
+    r = b - apply_M(geo, c, D) if r0 is None else np.array(r0, float, copy=True)
+    P, Q, pq = prev if prev is not None else ([], [], [])
+    use = [k for k in range(len(pq)) if pq[k] > 0.0]
+    y = {k: float(P[k] @ r) / pq[k] for k in use}
+    for k in use:
+        c = c + y[k] * P[k]
+        r = r - y[k] * Q[k]
+
+    def conjugate_to_prev(v):
+        mu = {k: float(Q[k] @ v) / pq[k] for k in use}
+        for k in use:
+            v = v - mu[k] * P[k]
+        return v
+
+    z = Jinv * r
+    p = conjugate_to_prev(z)
+    rz = float(r @ z)
+    Ps, Qs, pqs = [], [], []
+    for _ in range(iters):
+        if rz == 0.0:
+            break
+        q = apply_M(geo, p, D)
+        pq_k = float(p @ q)
+        Ps.append(p.copy())
+        Qs.append(q)
+        pqs.append(pq_k)
+        a = rz / pq_k
+        c = c + a * p
+        r = r - a * q
+        z = Jinv * r
+        rz_new = float(r @ z)
+        p = conjugate_to_prev(z) + (rz_new / rz) * p
+        rz = rz_new
+    return c, r, (Ps, Qs, pqs)
+
+
 def fit(geo, c):
     """a_tilde = F W^-1 c: layers back to the FE domain, then the DM fit (R13)."""
     phis = W_inv(geo, c)
@@ -626,7 +683,7 @@ def fit_adj(geo, a):
 
 
 class Reconstructor:
-    """One FEWHA instance across frames (Algorithm 1, open loop, no augmentation)."""
+    """One FEWHA instance across frames (Algorithm 1, open loop; augmented PCG on request)."""
 
     def __init__(self, wl):
         self.geo = Geometry(wl)
@@ -637,14 +694,19 @@ class Reconstructor:
         self.a = np.zeros(self.geo.n_a)
         self.b_prev = None
         self.r_prev = None
+        self.dirs = None         # (P, Q, pq) of the previous augmented frame
 
-    def frame(self, s, warm_residual=False):
+    def frame(self, s, warm_residual=False, augmented=False):
         geo = self.geo
         b = rhs(geo, s)
         r0 = None
         if warm_residual and self.b_prev is not None:
             r0 = (b - self.b_prev) + self.r_prev
-        self.c, r = pcg(geo, b, self.c, self.Jinv, geo.iters, self.D, r0)
+        if augmented:
+            self.c, r, self.dirs = augmented_pcg(geo, b, self.c, self.Jinv, geo.iters, self.D, r0,
+                                                 self.dirs)
+        else:
+            self.c, r = pcg(geo, b, self.c, self.Jinv, geo.iters, self.D, r0)
         self.b_prev, self.r_prev = b, r
         a_tilde = fit(geo, self.c)
         self.a = (1.0 - geo.gain) * self.a + geo.gain * a_tilde
