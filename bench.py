@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=50, help="timed batched frames")
     ap.add_argument("--backward-frames", type=int, default=8,
                     help="frames of the differentiable-reconstruction leg (0: leave it out)")
+    ap.add_argument("--aug-steps", type=int, default=500,
+                    help="timed frames per configuration of the augmented-PCG comparison")
     ap.add_argument("--loop-frames", type=int, default=2000,
                     help="frames of the 1 kHz real-time loop (8 m single-conjugate geometry)")
     return ap.parse_args()
@@ -399,6 +401,45 @@ def time_backward(frames=8):
     return out
 
 
+def time_augmented(wl, S32, S_np, flush, steps, parity=True):
+    """Augmented PCG (Sec. 3.4) on the MAORY workload against the plain warm start, at 4
+    and 2 iterations: frames/s of the graph-replayed frame, and the mean relative
+    residual ||r|| / ||b|| that the fixed iteration count leaves (frames 2..7 of the
+    frozen-flow sequence, each configuration from a cold start)."""
+    from paper_2202_11945_gb300 import Reconstructor
+    out = {"workload": wl["name"], "form": "FP32 operators, FP64 dots, CUDA graph"}
+    for it in (4, 2):
+        for aug in (False, True):
+            R = Reconstructor(wl, precision=32, graph=True, augmented=aug)
+            if it != wl["params"]["iters"]:
+                R.update_params(iters=it)
+            rel = []
+            for k in range(S32.shape[0]):
+                R.reconstruct(S32[k])
+                r, b = R.residual()
+                rel.append(float(torch.linalg.norm(r.double()) / torch.linalg.norm(b.double())))
+            dm = torch.empty(R.n_act, dtype=torch.float32, device="cuda")
+            t = time_frames(R, S32, steps, 20, flush, dm)
+            out["%s_iters%d" % ("augmented" if aug else "plain", it)] = {
+                "frames_per_s": 1e3 / float(t.mean()), "p99_ms": float(np.percentile(t, 99)),
+                "mean_rel_residual": float(np.mean(rel[2:])), "launches_per_frame": R.frame_launches()}
+            R.close()
+    out["steps"] = steps
+    if parity:
+        # the first frames against the oracle's augmented frames
+        import oracle as O
+        R = Reconstructor(wl, precision=32, graph=True, augmented=True)
+        ref = O.Reconstructor(wl)
+        err = []
+        for k in range(3):
+            a = R.reconstruct(S32[k]).double().cpu().numpy()
+            a_ref = ref.frame(S_np[k], augmented=True)
+            err.append(float(np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)))
+        R.close()
+        out["parity_max_rel_l2_dm"] = max(err)
+    return out
+
+
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
     the same sequence (explicit initial residual), and the oracle's own frame rate."""
@@ -523,6 +564,8 @@ def main():
     loop, wl3, S3, dm3, dm3w = time_loop(args.loop_frames)
     batched = time_batched(args.batch_count, args.batch_steps, 3, flush) if args.batch_count > 0 else None
     backward = time_backward(args.backward_frames) if args.backward_frames > 0 else None
+    augmented = (time_augmented(wl, S32, S_np, flush, args.aug_steps, parity=(rank == 0 and world == 1))
+                 if args.aug_steps > 0 else None)
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")
@@ -569,6 +612,7 @@ def main():
             "realtime_loop": loop,
             "batched": batched,
             "backward": backward,
+            "augmented": augmented,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

@@ -79,6 +79,16 @@ extern "C" {
                                        the next one launch its CTAs early, which wait on
                                        the device for it to finish (off by default: on
                                        GB300 it slows the graph-replayed frame)        */
+#define FEWHA_FLAG_AUGMENTED 8u     /* augmented PCG (Sec. 3.4, the augPCG step of
+                                       Algorithm 1): the previous frame's search
+                                       directions P and their images Q = M P are kept;
+                                       the start is corrected over span(P) and every new
+                                       direction is made M-conjugate to P.  Needs
+                                       iters <= FEWHA_AUG_MAX_ITERS.  The directions are
+                                       dropped by update_params, reset and set_state (the
+                                       next frame runs unaugmented).  Not available in
+                                       batched frames (FEWHA_ERR_INVALID_ARG).         */
+#define FEWHA_AUG_MAX_ITERS 8
 
 /* Telescope aperture: diameter D [m], central obstruction as a diameter ratio. */
 typedef struct fewha_telescope {
@@ -189,6 +199,12 @@ int fewha_reconstruct_host_f64(fewha_handle* h, const double* h_slopes, double* 
 int fewha_get_state(fewha_handle* h, void* d_c, void* d_a_prev, void* stream);
 int fewha_set_state(fewha_handle* h, const void* d_c, const void* d_a_prev, void* stream);
 
+/* The residual r and right-hand side b of the last frame's PCG (the recurrence residual;
+ * Sec. 3.3), n_coeffs each, copied into device buffers of the handle's element type
+ * (either pointer may be NULL).  Inspection only: ||r|| / ||b|| measures how far the
+ * fixed iteration count left the frame from M c = b.  Stream-ordered. */
+int fewha_get_residual(fewha_handle* h, void* d_r, void* d_b, void* stream);
+
 /* Real-time frame loop (Algorithm 1 run frame after frame, open loop): frame k reads
  * the host slopes h_slopes + k * n_slopes, is warm-started from frame k - 1 (the
  * handle's internal state, so frame 0 continues from whatever the handle holds), and
@@ -263,7 +279,8 @@ int fewha_get_diagonals(fewha_handle* h, void* d_D, void* d_J, void* stream);
  * the handle's warm-start state: use a handle dedicated to measurement, or call
  * fewha_reset afterwards.  Asynchronous. */
 int fewha_bench_stage(fewha_handle* h, int stage, int reps, void* stream);
-/* Kernel launches one frame enqueues (for the launch count of a timed region). */
+/* Kernel launches one frame enqueues (for the launch count of a timed region; for
+ * FEWHA_FLAG_AUGMENTED, a frame that has the previous frame's directions). */
 int fewha_frame_launches(const fewha_handle* h, int* launches);
 
 /* ---- differentiable reconstruction (a build addition: the paper has no gradients) --

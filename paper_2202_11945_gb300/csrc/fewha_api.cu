@@ -36,6 +36,7 @@ struct DeviceGuard {
 
 constexpr int NPART_MAX = 512;
 constexpr int PQ_SCRATCH_SLOT = FEWHA_MAX_ITERS;   // p.q slot of the explicit r0 apply
+static_assert(AUG_MAX == FEWHA_AUG_MAX_ITERS, "augmented PCG direction count");
 
 }  // namespace
 
@@ -68,9 +69,17 @@ struct fewha_handle {
     double grad_tol = 0.0;
     int grad_max_iters = 0;
     bool have_prev = false;
+    // augmented PCG (FEWHA_FLAG_AUGMENTED): two sets of AUG_MAX directions and images
+    // (stride aug_ld), a frame writes set aug_set and reads the other (aug_m directions)
+    void *Pd[2] = {nullptr, nullptr}, *Qd[2] = {nullptr, nullptr};
+    double* pqd[2] = {nullptr, nullptr};
+    double *augpart = nullptr, *augtot = nullptr;
+    size_t aug_ld = 0;
+    int aug_set = 0, aug_m = 0;
     // frame-graph cache
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gaug[4] = {};     // augmented frames: [2 * set + (directions present)]
     const void* g_s = nullptr;
     void* g_x = nullptr;
     void* g_dm = nullptr;
@@ -488,6 +497,80 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
     return FEWHA_OK;
 }
 
+template <class T, int PHASE>
+int launch_aug(fewha_handle* H, int n, const VecArgs<T>& v, const AugArgs<T>& a, cudaStream_t st) {
+    if (recorder<T>()) return fail(H, FEWHA_ERR_INVALID_ARG, "augmented PCG frames are not batched");
+    CK(launch_k(H, k_aug<T, PHASE>, dim3(vec_grid(H)), dim3(PBLK), 0, st, n, v, a), "k_aug launch");
+    return FEWHA_OK;
+}
+
+// Device arrays of the augmented PCG, allocated on first use (never inside a capture).
+int ensure_aug(fewha_handle* H) {
+    if (H->Pd[0]) return FEWHA_OK;
+    const size_t ld = (static_cast<size_t>(H->setup.n_c) + 63) & ~static_cast<size_t>(63);
+    int rc;
+    for (int s = 0; s < 2; ++s)
+        if ((rc = talloc(H, &H->Pd[s], AUG_MAX * ld)) || (rc = talloc(H, &H->Qd[s], AUG_MAX * ld)) ||
+            (rc = dalloc(H, &H->pqd[s], AUG_MAX)))
+            return rc;
+    if ((rc = dalloc(H, &H->augpart, static_cast<size_t>(AUG_MAX) * NPART_MAX)) ||
+        (rc = dalloc(H, &H->augtot, 2 * AUG_MAX)))
+        return rc;
+    H->aug_ld = ld;
+    return FEWHA_OK;
+}
+
+// Augmented PCG of Algorithm 1 (Sec. 3.4): `iters` iterations on M c = b whose directions
+// and images go to set `set`, augmented by the `m` directions of the other set (the
+// previous frame's; m = 0 on the first frame).  Each direction is formed by a vector
+// kernel and the apply runs on it without the fused update.
+template <class T>
+int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, int set, int m,
+                    cudaStream_t st) {
+    const size_t ld = H->aug_ld;
+    T* Pn = static_cast<T*>(H->Pd[set]);
+    T* Qn = static_cast<T*>(H->Qd[set]);
+    AugArgs<T> a;
+    a.P = static_cast<const T*>(H->Pd[1 - set]);
+    a.Q = static_cast<const T*>(H->Qd[1 - set]);
+    a.pq = H->pqd[1 - set];
+    a.pnew = nullptr;
+    a.pold = nullptr;
+    a.pqnew = H->pqd[set];
+    a.part = H->augpart;
+    a.tot = H->augtot;
+    a.ld = static_cast<long long>(ld);
+    a.m = m;
+    a.mu_next = 0;
+    int rc;
+    if (!warm && (rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
+    VecArgs<T> v = vec_args<T>(H, c, 0);
+    if (m > 0) {
+        rc = warm ? launch_aug<T, V_AUG_R0_WARM>(H, d.n_c, v, a, st) : launch_aug<T, V_AUG_R0>(H, d.n_c, v, a, st);
+        if (rc || (rc = launch_aug<T, V_AUG_INIT>(H, d.n_c, v, a, st))) return rc;
+    } else {
+        v.p = Pn;                                // p_0 = z_0
+        rc = warm ? launch_vec<T, V_INIT_WARM>(H, d.n_c, v, st) : launch_vec<T, V_INIT>(H, d.n_c, v, st);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < iters; ++k) {
+        T* pk = Pn + k * ld;
+        T* qk = Qn + k * ld;
+        v = vec_args<T>(H, c, k);
+        if (k > 0 || m > 0) {
+            a.pnew = pk;
+            a.pold = k > 0 ? Pn + (k - 1) * ld : nullptr;
+            if ((rc = launch_aug<T, V_PROJ>(H, d.n_c, v, a, st))) return rc;
+        }
+        if ((rc = enqueue_apply<T>(H, d, pk, qk, k, false, st))) return rc;
+        v.p = pk;
+        v.q = qk;
+        a.mu_next = (m > 0 && k + 1 < iters) ? 1 : 0;
+        if ((rc = launch_aug<T, V_UPDATE_AUG>(H, d.n_c, v, a, st))) return rc;
+    }
+    return FEWHA_OK;
+}
+
 template <class T>
 int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain, cudaStream_t st) {
     T* phi = static_cast<T*>(H->phi);
@@ -497,25 +580,44 @@ int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain,
 }
 
 // One frame of Algorithm 1 (open loop).
+// (With FEWHA_FLAG_AUGMENTED the PCG is the augmented one; its directions go to set
+// H->aug_set, augmented by the H->aug_m directions of the other set.)
 template <class T>
 int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStream_t st) {
     const Desc<T> d = make_desc<T>(H);
     int rc;
     if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
-    if ((rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st))) return rc;
+    if (H->params.flags & FEWHA_FLAG_AUGMENTED)
+        rc = enqueue_pcg_aug<T>(H, d, c, H->params.iters, warm, H->aug_set, H->aug_m, st);
+    else
+        rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st);
+    if (rc) return rc;
     return enqueue_fit<T>(H, d, c, dm, true, st);
+}
+
+void drop_graph(fewha_handle* H) {
+    if (H->gexec) cudaGraphExecDestroy(H->gexec);
+    H->gexec = nullptr;
+    for (auto& g : H->gaug) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    H->g_s = nullptr;
+    H->g_x = nullptr;
+    H->g_dm = nullptr;
 }
 
 template <class T>
 int run_frame(fewha_handle* H, const T* s, T* c, T* dm, cudaStream_t st) {
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) && H->have_prev;
+    const bool aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) != 0;
     int rc;
+    if (aug && (rc = ensure_aug(H))) return rc;
     if (H->params.flags & FEWHA_FLAG_GRAPH) {
-        if (!H->gexec || H->g_s != s || H->g_x != c || H->g_dm != dm || H->g_warm != warm) {
-            if (H->gexec) {
-                cudaGraphExecDestroy(H->gexec);
-                H->gexec = nullptr;
-            }
+        if (H->g_s != s || H->g_x != c || H->g_dm != dm || H->g_warm != warm) drop_graph(H);
+        // one graph per form: plain, or augmented per (direction set, directions present)
+        cudaGraphExec_t* gx = aug ? &H->gaug[2 * H->aug_set + (H->aug_m > 0 ? 1 : 0)] : &H->gexec;
+        if (!*gx) {
             CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             rc = enqueue_frame<T>(H, s, c, dm, warm, H->cap_stream);
             cudaGraph_t graph = nullptr;
@@ -525,10 +627,10 @@ int run_frame(fewha_handle* H, const T* s, T* c, T* dm, cudaStream_t st) {
                 return rc;
             }
             if (e != cudaSuccess) return cuda_fail(H, e, "end capture");
-            e = cudaGraphInstantiate(&H->gexec, graph, 0);
+            e = cudaGraphInstantiate(gx, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) {
-                H->gexec = nullptr;
+                *gx = nullptr;
                 return cuda_fail(H, e, "graph instantiate");
             }
             H->g_s = s;
@@ -536,20 +638,16 @@ int run_frame(fewha_handle* H, const T* s, T* c, T* dm, cudaStream_t st) {
             H->g_dm = dm;
             H->g_warm = warm;
         }
-        CK(cudaGraphLaunch(H->gexec, st), "graph launch");
+        CK(cudaGraphLaunch(*gx, st), "graph launch");
     } else {
         if ((rc = enqueue_frame<T>(H, s, c, dm, warm, st))) return rc;
     }
     H->have_prev = true;
+    if (aug) {
+        H->aug_m = H->params.iters;
+        H->aug_set = 1 - H->aug_set;
+    }
     return FEWHA_OK;
-}
-
-void drop_graph(fewha_handle* H) {
-    if (H->gexec) cudaGraphExecDestroy(H->gexec);
-    H->gexec = nullptr;
-    H->g_s = nullptr;
-    H->g_x = nullptr;
-    H->g_dm = nullptr;
 }
 
 // D, the exact data diagonal (GPU) and J^-1 for the current parameters.
@@ -857,6 +955,10 @@ int check_params(const fewha_params* p, std::string& err) {
     }
     if (p->iters < 0 || p->iters > FEWHA_MAX_ITERS) {
         err = "iters out of range";
+        return FEWHA_ERR_LIMIT;
+    }
+    if ((p->flags & FEWHA_FLAG_AUGMENTED) && p->iters > FEWHA_AUG_MAX_ITERS) {
+        err = "augmented PCG keeps at most FEWHA_AUG_MAX_ITERS directions";
         return FEWHA_ERR_LIMIT;
     }
     if (!(p->alpha >= 0) || !(p->tau >= 0) || !(p->r0 > 0) || !(p->L0 > 0) || !(p->gain >= 0) ||
@@ -1196,6 +1298,8 @@ int batch_record(fewha_batch* B, const T* const* s, T* const* dm, bool warm, std
     for (size_t i = 0; i < n; ++i) {
         fewha_handle* H = B->h[i];
         if (!s[i] || !dm[i]) return bfail(B, FEWHA_ERR_INVALID_ARG, "null slope or DM pointer of instance " + std::to_string(i));
+        if (H->params.flags & FEWHA_FLAG_AUGMENTED)
+            return bfail(B, FEWHA_ERR_INVALID_ARG, "augmented PCG frames are not batched (instance " + std::to_string(i) + ")");
         g_recorder = &recs[i];
         const int rc = enqueue_frame<T>(H, s[i], static_cast<T*>(H->c), dm[i], warm, nullptr);
         g_recorder = nullptr;
@@ -1890,6 +1994,7 @@ int fewha_update_params(fewha_handle* H, const fewha_params* params, const doubl
     H->params = *params;
     drop_graph(H);
     H->have_prev = false;
+    H->aug_m = 0;                     // M changed: the stored directions no longer apply
     ++H->version;
     H->grad_ready = false;
     return H->precision == 32 ? compute_diagonals<float>(H) : compute_diagonals<double>(H);
@@ -1904,6 +2009,7 @@ int fewha_reset(fewha_handle* H, void* stream) {
     CK(cudaMemsetAsync(H->r, 0, H->setup.n_c * H->esz, st), "reset");
     CK(cudaMemsetAsync(H->b_prev, 0, H->setup.n_c * H->esz, st), "reset");
     H->have_prev = false;
+    H->aug_m = 0;
     return FEWHA_OK;
 }
 
@@ -1990,6 +2096,16 @@ int fewha_set_state(fewha_handle* H, const void* c, const void* a_prev, void* st
     if (a_prev)
         CK(cudaMemcpyAsync(H->a_prev, a_prev, H->setup.n_act * H->esz, cudaMemcpyDeviceToDevice, st), "set state");
     H->have_prev = false;
+    H->aug_m = 0;
+    return FEWHA_OK;
+}
+
+int fewha_get_residual(fewha_handle* H, void* r, void* b, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (r) CK(cudaMemcpyAsync(r, H->r, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
+    if (b) CK(cudaMemcpyAsync(b, H->b, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
     return FEWHA_OK;
 }
 
@@ -2073,8 +2189,10 @@ int fewha_bench_stage(fewha_handle* H, int stage, int reps, void* stream) {
 int fewha_frame_launches(const fewha_handle* H, int* launches) {
     if (!H || !launches) return FEWHA_ERR_INVALID_ARG;
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
-    // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2
-    *launches = 3 + (warm ? 1 : 6) + 6 * H->params.iters + 2;
+    // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2; the
+    // augmented frame (with directions) adds one start kernel and one per iteration
+    const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
+    *launches = 3 + (warm ? 1 : 6) + aug + (6 + aug) * H->params.iters + 2;
     return FEWHA_OK;
 }
 

@@ -876,6 +876,232 @@ __global__ void __launch_bounds__(PBLK) k_vec(const int n, __grid_constant__ con
 }
 
 // ---------------------------------------------------------------------------
+// Augmented PCG (Sec. 3.4, the augPCG step of Algorithm 1).  The previous frame's search
+// directions P = [p_j] and their images Q = M P (with p_j.q_j) augment this frame's
+// Krylov space: the start is corrected over span(P),
+//     y_j = p_j.r0 / p_j.q_j,   c0 += sum_j y_j p_j,   r0 -= sum_j y_j q_j,
+// and every new direction is made M-conjugate to P,
+//     p = z + beta p_old - sum_j mu_j p_j,   mu_j = q_j.z / p_j.q_j.
+// Directions of one CG run are M-conjugate, so P^T Q is diagonal.  A direction with
+// p_j.q_j <= 0 is skipped.  Vectors in T, inner products and coefficients in double.
+// ---------------------------------------------------------------------------
+constexpr int AUG_MAX = 8;      // directions kept: the iterations of an augmented frame
+
+enum {
+    V_AUG_R0 = 3,        // r0 = b - q (q = M c0), b_prev = b, and p_j.r0
+    V_AUG_R0_WARM = 4,   // r0 = (b - b_prev) + r_prev, b_prev = b, and p_j.r0
+    V_AUG_INIT = 5,      // c0 += P y, r0 -= Q y, z0 = J^-1 r0, r.z, and q_j.z0
+    V_PROJ = 6,          // p_k = z_k + beta_k p_(k-1) - P mu (no reduction)
+    V_UPDATE_AUG = 7     // the CG update of V_UPDATE; keeps p.q; q_j.z for the next direction
+};
+
+template <class T>
+struct AugArgs {
+    const T* P;          // previous frame's directions, [j * ld + i], j < m
+    const T* Q;          // their images M p_j
+    const double* pq;    // p_j . q_j
+    T* pnew;             // V_PROJ: the direction formed
+    const T* pold;       // V_PROJ: this frame's previous direction (iteration > 0)
+    double* pqnew;       // V_UPDATE_AUG: p.q of this frame's direction `iter`
+    double* part;        // [t * npart + cta]: CTA shares of the dots
+    double* tot;         // [j]: p_j.r0;  [AUG_MAX + j]: q_j.z
+    long long ld;
+    int m;               // directions in P, 0 .. AUG_MAX
+    int mu_next;         // V_UPDATE_AUG: form q_j.z for the next direction
+};
+
+// Warp share of a dot into *dst (lane 0), and the fixed-order total of `nw` warp shares.
+__device__ __forceinline__ void warp_share(const DotAcc<double>& a, double* dst) {
+    const double x = warp_sum(a.v);
+    if ((threadIdx.x & 31) == 0) *dst = x;
+}
+__device__ __forceinline__ void warp_share(const DotAcc<float>& a, double* dst) {
+    const DFloat x = warp_df_sum(DFloat{a.s, a.c});
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(dst) = make_float2(x.s, x.c);
+}
+__device__ __forceinline__ void shares_store(const double* src, int nw, double* slot, const DotAcc<double>*) {
+    const int lane = threadIdx.x & 31;
+    const double x = warp_sum(lane < nw ? src[lane] : 0.0);
+    if (lane == 0) {
+        *slot = x;
+        __threadfence();
+    }
+}
+__device__ __forceinline__ void shares_store(const double* src, int nw, double* slot, const DotAcc<float>*) {
+    const int lane = threadIdx.x & 31;
+    const float2 v = lane < nw ? *reinterpret_cast<const float2*>(src + lane) : make_float2(0.f, 0.f);
+    const DFloat t = warp_df_sum(DFloat{v.x, v.y});
+    if (lane == 0) {
+        *reinterpret_cast<float2*>(slot) = make_float2(t.s, t.c);
+        __threadfence();
+    }
+}
+
+template <class T, int PHASE>
+__device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const AugArgs<T>& a,
+                                         const int cta, const int nparts) {
+    constexpr bool R0 = PHASE == V_AUG_R0 || PHASE == V_AUG_R0_WARM;
+    __shared__ bool last;
+    __shared__ T scoef[AUG_MAX + 1];                 // y_j or mu_j; [AUG_MAX]: alpha or beta
+    __shared__ double shares[AUG_MAX + 1][32];       // per-warp shares: [0] r.z, [1 + j] dot j
+    const int m = a.m;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = PBLK >> 5;
+    // the scalars, one FP64 division per thread (GB300's FP64 pipe is slow)
+    if ((PHASE == V_AUG_INIT || PHASE == V_PROJ) && threadIdx.x < m) {
+        const double num = PHASE == V_AUG_INIT ? a.tot[threadIdx.x] : a.tot[AUG_MAX + threadIdx.x];
+        const double den = a.pq[threadIdx.x];
+        scoef[threadIdx.x] = T(den > 0.0 ? num / den : 0.0);
+    }
+    if (threadIdx.x == 32) {
+        if (PHASE == V_UPDATE_AUG) {
+            const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
+            scoef[AUG_MAX] = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
+            if (cta == 0) a.pqnew[v.iter] = pq;
+        } else if (PHASE == V_PROJ) {
+            double beta = 0.0;
+            if (v.iter > 0) {
+                const double rn = v.pcg.rztot[v.iter], ro = v.pcg.rztot[v.iter - 1];
+                beta = ro != 0.0 ? rn / ro : 0.0;
+            }
+            scoef[AUG_MAX] = T(beta);
+        }
+    }
+    __syncthreads();
+    const bool dots = R0 || PHASE == V_AUG_INIT || (PHASE == V_UPDATE_AUG && a.mu_next && m > 0);
+    // elements per thread and pass: fewer where a pass holds both P and Q
+    constexpr int PV = (PHASE == V_AUG_INIT || sizeof(T) == 8) ? 2 : PVEC;
+    DotAcc<T> dj[AUG_MAX];
+    DotAcc<T> dot;
+    for (int base = cta * PBLK * PV; base < n; base += nparts * PBLK * PV) {
+        // every load of the batch before the arithmetic
+        T x0[PV], x1[PV], x2[PV], x3[PV], x4[PV];
+        T pj[AUG_MAX][PV], qj[AUG_MAX][PV];
+#pragma unroll
+        for (int k = 0; k < PV; ++k) {
+            const int i = base + k * PBLK + threadIdx.x;
+            if (i < n) {
+                if (PHASE == V_AUG_R0) {
+                    x0[k] = v.b[i];
+                    x1[k] = v.q[i];
+                } else if (PHASE == V_AUG_R0_WARM) {
+                    x0[k] = v.b[i];
+                    x1[k] = v.b_prev[i];
+                    x2[k] = v.r[i];
+                } else if (PHASE == V_AUG_INIT) {
+                    x0[k] = v.c[i];
+                    x1[k] = v.r[i];
+                    x2[k] = v.Jinv[i];
+                } else if (PHASE == V_PROJ) {
+                    x0[k] = v.z[i];
+                    if (v.iter > 0) x1[k] = a.pold[i];
+                } else {
+                    x0[k] = v.c[i];
+                    x1[k] = v.p[i];
+                    x2[k] = v.r[i];
+                    x3[k] = v.q[i];
+                    x4[k] = v.Jinv[i];
+                }
+#pragma unroll
+                for (int j = 0; j < AUG_MAX; ++j) {
+                    if (j < m) {
+                        if (R0 || PHASE == V_AUG_INIT || PHASE == V_PROJ) pj[j][k] = a.P[j * a.ld + i];
+                        if (PHASE == V_AUG_INIT || (PHASE == V_UPDATE_AUG && dots)) qj[j][k] = a.Q[j * a.ld + i];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PV; ++k) {
+            const int i = base + k * PBLK + threadIdx.x;
+            if (i < n) {
+                if (R0) {
+                    const T rr = PHASE == V_AUG_R0 ? x0[k] - x1[k] : (x0[k] - x1[k]) + x2[k];
+                    v.r[i] = rr;
+                    v.b_prev[i] = x0[k];
+#pragma unroll
+                    for (int j = 0; j < AUG_MAX; ++j)
+                        if (j < m) dj[j].add(pj[j][k], rr);
+                } else if (PHASE == V_AUG_INIT) {
+                    T c = x0[k], rr = x1[k];
+#pragma unroll
+                    for (int j = 0; j < AUG_MAX; ++j) {
+                        if (j < m) {
+                            c += scoef[j] * pj[j][k];
+                            rr -= scoef[j] * qj[j][k];
+                        }
+                    }
+                    const T z = x2[k] * rr;
+                    v.c[i] = c;
+                    v.r[i] = rr;
+                    v.z[i] = z;
+                    dot.add(rr, z);
+#pragma unroll
+                    for (int j = 0; j < AUG_MAX; ++j)
+                        if (j < m) dj[j].add(qj[j][k], z);
+                } else if (PHASE == V_PROJ) {
+                    T p = x0[k];
+                    if (v.iter > 0) p = x0[k] + scoef[AUG_MAX] * x1[k];
+#pragma unroll
+                    for (int j = 0; j < AUG_MAX; ++j)
+                        if (j < m) p -= scoef[j] * pj[j][k];
+                    a.pnew[i] = p;
+                } else {
+                    const T al = scoef[AUG_MAX];
+                    v.c[i] = x0[k] + al * x1[k];
+                    const T rr = x2[k] - al * x3[k];
+                    const T z = x4[k] * rr;
+                    v.r[i] = rr;
+                    v.z[i] = z;
+                    dot.add(rr, z);
+                    if (dots) {
+#pragma unroll
+                        for (int j = 0; j < AUG_MAX; ++j)
+                            if (j < m) dj[j].add(qj[j][k], z);
+                    }
+                }
+            }
+        }
+    }
+    if (PHASE == V_PROJ) return;
+    // CTA shares (fixed order): t = 0 is r.z (not in the R0 phases), t = 1 + j dot j
+    const bool has_rz = !R0;
+    const int nd = dots ? m : 0;
+    if (has_rz) warp_share(dot, &shares[0][w]);
+#pragma unroll
+    for (int j = 0; j < AUG_MAX; ++j)
+        if (j < nd) warp_share(dj[j], &shares[1 + j][w]);
+    __syncthreads();
+    const int slot = PHASE == V_UPDATE_AUG ? v.iter + 1 : 0;
+    for (int t = w; t <= nd; t += nw) {
+        if (t == 0 && !has_rz) continue;
+        double* dst = t == 0 ? v.pcg.rzpart + slot * v.pcg.npart + cta : a.part + (t - 1) * v.pcg.npart + cta;
+        shares_store(shares[t], nw, dst, &dot);
+    }
+    if (last_arrival(v.pcg.count, nparts, &last)) {
+        // the totals, one warp each, in a fixed order over the CTAs
+        for (int t = w; t <= nd; t += nw) {
+            if (t == 0 && !has_rz) continue;
+            const double* src = t == 0 ? v.pcg.rzpart + slot * v.pcg.npart : a.part + (t - 1) * v.pcg.npart;
+            const double tot = warp_total(src, v.pcg.npart, &dot);
+            if (lane == 0) {
+                if (t == 0)
+                    v.pcg.rztot[slot] = tot;
+                else
+                    a.tot[(R0 ? 0 : AUG_MAX) + t - 1] = tot;
+            }
+        }
+        if (threadIdx.x == 0) v.pcg.count[0] = 0;
+    }
+}
+
+template <class T, int PHASE>
+__global__ void __launch_bounds__(PBLK) k_aug(const int n, __grid_constant__ const VecArgs<T> v,
+                                              __grid_constant__ const AugArgs<T> a) {
+    pdl_enter();
+    aug_body<T, PHASE>(n, v, a, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
 // DM fitting (Algorithm 1 fitting step, Table 3): a~_m(p, q) = sum_l w_lm phi_l
 // sampled bilinearly at the actuator, then open-loop gain a = (1-g) a_prev + g a~.
 // ---------------------------------------------------------------------------

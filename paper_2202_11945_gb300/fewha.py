@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(HERE, "libfewha.so")
 FLAG_GRAPH = 1
 FLAG_WARM_RESIDUAL = 2
 FLAG_PDL = 4
+FLAG_AUGMENTED = 8
+AUG_MAX_ITERS = 8
 
 ERRORS = {
     -1: "invalid argument",
@@ -76,7 +78,7 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_batch_last_error", "fewha_batch_set_config", "fewha_batch_get_config",
            "fewha_batch_reconstruct", "fewha_batch_autotune", "fewha_reconstruct_batched",
            "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state", "fewha_solve",
-           "fewha_reconstruct_converged", "fewha_backward"] + _OPS
+           "fewha_reconstruct_converged", "fewha_backward", "fewha_get_residual"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -121,6 +123,7 @@ def lib():
     L.fewha_backward.argtypes = [_VP, _VP, _VP, dp, dp, _VP]
     L.fewha_get_state.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_set_state.argtypes = [_VP, _VP, _VP, _VP]
+    L.fewha_get_residual.argtypes = [_VP, _VP, _VP, _VP]
     for name in ["fewha_run_loop", "fewha_run_loop_f64"]:
         getattr(L, name).argtypes = [_VP, _VP, ctypes.c_int, _VP, ctypes.c_double, _VP, _VP,
                                      ctypes.POINTER(ctypes.c_int), _VP]
@@ -171,7 +174,7 @@ def _stream(stream):
 class Reconstructor:
     """One FEWHA instance on the current CUDA device (a handle of the C library)."""
 
-    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False):
+    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False, augmented=False):
         if not torch.cuda.is_available():
             raise RuntimeError("FEWHA needs a CUDA device; there is no CPU path")
         torch.cuda.init()
@@ -179,7 +182,7 @@ class Reconstructor:
         self.precision = precision
         self.dtype = torch.float32 if precision == 32 else torch.float64
         flags = ((FLAG_GRAPH if graph else 0) | (FLAG_WARM_RESIDUAL if warm_residual else 0) |
-                 (FLAG_PDL if pdl else 0))
+                 (FLAG_PDL if pdl else 0) | (FLAG_AUGMENTED if augmented else 0))
         self._structs = structs_from_workload(wl, precision, flags)
         tel, wfs, layers, dms, params = self._structs
         self.L = lib()
@@ -285,6 +288,13 @@ class Reconstructor:
         ap = self._dev(a_prev, self.n_act, "a_prev") if a_prev is not None else None
         self._check(self.L.fewha_set_state(self.h, cp, ap, _stream(stream)))
 
+    def residual(self, stream=None):
+        """(r, b): the last frame's PCG residual and right-hand side (copies)."""
+        r, b = self._new(self.n_coeffs), self._new(self.n_coeffs)
+        self._check(self.L.fewha_get_residual(self.h, self._dev(r, self.n_coeffs, "r"),
+                                              self._dev(b, self.n_coeffs, "b"), _stream(stream)))
+        return r, b
+
     def check_input(self, stream=None):
         flag = ctypes.c_int(0)
         self._check(self.L.fewha_check_input(self.h, ctypes.byref(flag), _stream(stream)))
@@ -294,7 +304,7 @@ class Reconstructor:
         self._check(self.L.fewha_reset(self.h, _stream(stream)))
 
     def update_params(self, alpha=None, tau=None, gain=None, r0=None, L0=None, iters=None,
-                      cn2_weights=None, sigmas=None, graph=None, warm_residual=None):
+                      cn2_weights=None, sigmas=None, graph=None, warm_residual=None, augmented=None):
         tel, wfs, layers, dms, p = self._structs
         if alpha is not None:
             p.alpha = alpha
@@ -312,6 +322,8 @@ class Reconstructor:
             p.flags = (p.flags & ~FLAG_GRAPH) | (FLAG_GRAPH if graph else 0)
         if warm_residual is not None:
             p.flags = (p.flags & ~FLAG_WARM_RESIDUAL) | (FLAG_WARM_RESIDUAL if warm_residual else 0)
+        if augmented is not None:
+            p.flags = (p.flags & ~FLAG_AUGMENTED) | (FLAG_AUGMENTED if augmented else 0)
         w = s = None
         if cn2_weights is not None:
             w = (ctypes.c_double * len(layers))(*cn2_weights)
