@@ -48,6 +48,14 @@ Readings where the paper is silent or garbled (each also listed in the design doc):
       M-conjugate to P, p = z + beta p_old - P mu, mu_k = q_k.z / p_k.q_k (P^T Q is
       diagonal for the M-conjugate directions of one CG run).  At most 8 directions
       (iter <= 8); none on the first frame.
+  R27 closed loop (Algorithm 1): the DM shape is bilinear between actuators (Sec. 4.1),
+      i.e. sum_k a_k times the bilinear hat of actuator k, so it is zero beyond the
+      outer actuators' hats; actuator (p, q) of a DM with n_act per side sits at
+      ((q - (n_act-1)/2) spacing, (p - (n_act-1)/2) spacing).  Sensor g sees DM m like a
+      layer, at s x + theta h_m (s = 1 - h_m/H for an LGS).  The pseudo-open-loop slopes
+      are s + Gamma P_DM a^(i-1) (the residual slopes s measure phase minus DM shape)
+      and the control law is a^(i+1) = a^(i) + gain (a_tilde - a^(i-1)), both as printed;
+      a^(0) = a^(-1) = 0.
 """
 
 import math
@@ -179,6 +187,20 @@ def _interp_matrix(coord, n):
     return R
 
 
+def _hat_matrix(coord, n):
+    """Bilinear hat-function sampling on a lattice of n nodes (R27): like the layer
+    interpolation, but a stencil point outside [0, n-1] contributes nothing."""
+    R = np.zeros((coord.size, n))
+    for a, u in enumerate(coord):
+        i0 = int(np.floor(u))
+        f = u - i0
+        if 0 <= i0 < n:
+            R[a, i0] += 1.0 - f
+        if 0 <= i0 + 1 < n:
+            R[a, i0 + 1] += f
+    return R
+
+
 def active_mask(n, D, obs):
     """Active subapertures of an n x n lenslet array (R4)."""
     c = -D / 2 + (np.arange(n) + 0.5) * (D / n)
@@ -253,9 +275,17 @@ class Geometry:
                 tx, ty = W["theta"]
                 Rx.append(_interp_matrix((s * xs + tx * L["h"]) / L["delta"] + L["n"] / 2, L["n"]))
                 Ry.append(_interp_matrix((s * xs + ty * L["h"]) / L["delta"] + L["n"] / 2, L["n"]))
+            # the DMs seen by this sensor (R27), the same propagation as the layers
+            Qx, Qy = [], []
+            for m in wl["dms"]:
+                hm, na = float(m["h"]), int(m["n_act"])
+                s = 1.0 - hm / float(W["H"]) if lgs else 1.0
+                tx, ty = W["theta"]
+                Qx.append(_hat_matrix((s * xs + tx * hm) / float(m["spacing"]) + (na - 1) / 2.0, na))
+                Qy.append(_hat_matrix((s * xs + ty * hm) / float(m["spacing"]) + (na - 1) / 2.0, na))
             self.wfs.append(dict(N=N, n_sub=n_sub, nb=nb, d=d, lgs=lgs, sigma=float(W["sigma"]),
                                  mask=fine, cmask=coarse, n_active=n_act, soff=soff,
-                                 ns=2 * n_act, Rx=Rx, Ry=Ry))
+                                 ns=2 * n_act, Rx=Rx, Ry=Ry, Qx=Qx, Qy=Qy))
             soff += 2 * n_act
         self.n_s = soff
         # deformable mirrors and the fitting split (R13)
@@ -300,6 +330,23 @@ def project(geo, g, phis):
     for l, phi in enumerate(phis):
         out += W["Ry"][l] @ phi @ W["Rx"][l].T
     return out
+
+
+def dm_project(geo, g, a):
+    """The DM shapes seen by sensor g on its aperture nodes: sum over DMs of the
+    bilinear mirror surface (Sec. 4.1) at s x + theta h_m (R27)."""
+    W = geo.wfs[g]
+    out = np.zeros((W["N"] + 1, W["N"] + 1))
+    for mi, m in enumerate(geo.dms):
+        A = np.asarray(a[m["off"]:m["off"] + m["n_act"] ** 2]).reshape(m["n_act"], m["n_act"])
+        out += W["Qy"][mi] @ A @ W["Qx"][mi].T
+    return out
+
+
+def dm_slopes(geo, a):
+    """Gamma P_DM a: the slopes every sensor would measure of the DM shapes a (the term
+    of the pseudo-open-loop slopes of Algorithm 1)."""
+    return np.concatenate([sh_slopes(geo, g, dm_project(geo, g, a)) for g in range(len(geo.wfs))])
 
 
 def project_adj(geo, g, v):
@@ -695,9 +742,14 @@ class Reconstructor:
         self.b_prev = None
         self.r_prev = None
         self.dirs = None         # (P, Q, pq) of the previous augmented frame
+        self.a_old = np.zeros(self.geo.n_a)   # a^(i-1) of the closed loop
 
-    def frame(self, s, warm_residual=False, augmented=False):
+    def frame(self, s, warm_residual=False, augmented=False, closed_loop=False):
+        """One frame; with closed_loop, s are residual slopes and the pseudo-open-loop
+        slopes and the closed-loop control law of Algorithm 1 apply (R27)."""
         geo = self.geo
+        if closed_loop:
+            s = np.asarray(s, float) + dm_slopes(geo, self.a_old)
         b = rhs(geo, s)
         r0 = None
         if warm_residual and self.b_prev is not None:
@@ -709,5 +761,10 @@ class Reconstructor:
             self.c, r = pcg(geo, b, self.c, self.Jinv, geo.iters, self.D, r0)
         self.b_prev, self.r_prev = b, r
         a_tilde = fit(geo, self.c)
-        self.a = (1.0 - geo.gain) * self.a + geo.gain * a_tilde
+        if closed_loop:
+            a_new = self.a + geo.gain * (a_tilde - self.a_old)
+            self.a_old = self.a
+            self.a = a_new
+        else:
+            self.a = (1.0 - geo.gain) * self.a + geo.gain * a_tilde
         return self.a.copy()
