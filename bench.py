@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--backward-frames", type=int, default=8,
                     help="frames of the differentiable-reconstruction leg (0: leave it out)")
     ap.add_argument("--aug-steps", type=int, default=500,
-                    help="timed frames per configuration of the augmented-PCG comparison")
+                    help="timed frames per configuration of the augmented-PCG and closed-loop runs")
     ap.add_argument("--loop-frames", type=int, default=2000,
                     help="frames of the 1 kHz real-time loop (8 m single-conjugate geometry)")
     return ap.parse_args()
@@ -440,6 +440,37 @@ def time_augmented(wl, S32, S_np, flush, steps, parity=True):
     return out
 
 
+def time_closed_loop(wl, S32, S_np, flush, steps, parity=True):
+    """Closed-loop frames (Algorithm 1: pseudo-open-loop slopes from the commands of two
+    frames back, delayed control law) on the MAORY workload, FP32 graph form; the timed
+    inputs are the benchmark's slope frames taken as residual slopes."""
+    from paper_2202_11945_gb300 import Reconstructor
+    R = Reconstructor(wl, precision=32, graph=True, closed_loop=True)
+    dm = torch.empty(R.n_act, dtype=torch.float32, device="cuda")
+    t = time_frames(R, S32, steps, 20, flush, dm)
+    out = {"workload": wl["name"], "form": "FP32 operators, FP64 dots, CUDA graph",
+           "frames_per_s": 1e3 / float(t.mean()), "p50_ms": float(np.percentile(t, 50)),
+           "p99_ms": float(np.percentile(t, 99)), "launches_per_frame": R.frame_launches(),
+           "steps": steps}
+    R.close()
+    if parity:
+        # residual slopes synthesised from the oracle's own commands (the sensors saw the
+        # DM shape of two frames back), the same slopes to both sides
+        import oracle as O
+        ref = O.Reconstructor(wl)
+        R = Reconstructor(wl, precision=32, graph=True, closed_loop=True)
+        A = [np.zeros(ref.geo.n_a), np.zeros(ref.geo.n_a)]
+        err = []
+        for k in range(3):
+            s_cl = S_np[k] - O.dm_slopes(ref.geo, A[-2])
+            A.append(ref.frame(s_cl, closed_loop=True))
+            a = R.reconstruct(torch.as_tensor(s_cl, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+            err.append(float(np.linalg.norm(a - A[-1]) / np.linalg.norm(A[-1])))
+        R.close()
+        out["parity_max_rel_l2_dm"] = max(err)
+    return out
+
+
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
     the same sequence (explicit initial residual), and the oracle's own frame rate."""
@@ -566,6 +597,8 @@ def main():
     backward = time_backward(args.backward_frames) if args.backward_frames > 0 else None
     augmented = (time_augmented(wl, S32, S_np, flush, args.aug_steps, parity=(rank == 0 and world == 1))
                  if args.aug_steps > 0 else None)
+    closed = (time_closed_loop(wl, S32, S_np, flush, args.aug_steps, parity=(rank == 0 and world == 1))
+              if args.aug_steps > 0 else None)
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")
@@ -613,6 +646,7 @@ def main():
             "batched": batched,
             "backward": backward,
             "augmented": augmented,
+            "closed_loop": closed,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

@@ -89,6 +89,16 @@ extern "C" {
                                        next frame runs unaugmented).  Not available in
                                        batched frames (FEWHA_ERR_INVALID_ARG).         */
 #define FEWHA_AUG_MAX_ITERS 8
+#define FEWHA_FLAG_CLOSED_LOOP 16u  /* closed-loop control (Algorithm 1): the slopes passed
+                                       in are residual slopes; the frame first forms the
+                                       pseudo-open-loop slopes s + Gamma P_DM a^(i-1)
+                                       (the DM shapes of two frames back, bilinear between
+                                       actuators, seen by each sensor like a layer) and
+                                       ends with a^(i+1) = a^(i) + gain (a~ - a^(i-1)).
+                                       fewha_reset zeroes a^(i) and a^(i-1); set_state
+                                       sets a^(i) only.  Every DM must sit below every
+                                       LGS (FEWHA_ERR_GEOMETRY).  Not available in
+                                       batched frames (FEWHA_ERR_INVALID_ARG).         */
 
 /* Telescope aperture: diameter D [m], central obstruction as a diameter ratio. */
 typedef struct fewha_telescope {

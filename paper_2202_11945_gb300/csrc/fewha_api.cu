@@ -63,6 +63,10 @@ struct fewha_handle {
          *q = nullptr, *phi = nullptr, *u = nullptr, *a_prev = nullptr, *dm_tmp = nullptr,
          *s_tmp = nullptr, *c_tmp = nullptr, *cgrad = nullptr, *lam = nullptr;
     double* gdot = nullptr;           // per-layer sums of the backward pass
+    // closed loop (FEWHA_FLAG_CLOSED_LOOP): DM projection tables, pseudo-open-loop slopes
+    // and the commands of the frame before (a^(i-1))
+    int *qi0y = nullptr, *qi0x = nullptr;
+    void *qfy = nullptr, *qfx = nullptr, *s_pol = nullptr, *a_old = nullptr;
     bool grad_ready = false;          // a converged reconstruction is held in cgrad
     bool have_cgrad = false;          // cgrad / lam hold earlier solutions (warm starts)
     bool have_lam = false;
@@ -469,13 +473,29 @@ int launch_vec(fewha_handle* H, int n, const VecArgs<T>& v, cudaStream_t st) {
 }
 
 template <class T>
-int launch_fit(fewha_handle* H, const Desc<T>& d, const T* phi, T* a_prev, T* dm, int gain, cudaStream_t st) {
+int launch_fit(fewha_handle* H, const Desc<T>& d, const T* phi, T* a_prev, T* dm, int gain, cudaStream_t st,
+               T* a_old = nullptr) {
     if (recorder<T>()) {
+        if (gain == 2) return fail(H, FEWHA_ERR_INVALID_ARG, "closed-loop frames are not batched");
         record<T>(BK_FIT).fa = FitArgs<T>{phi, a_prev, dm, gain};
         return FEWHA_OK;
     }
-    CK(launch_k(H, k_fit<T>, dim3((d.n_act + PBLK - 1) / PBLK), dim3(PBLK), 0, st, d, phi, a_prev, dm, gain),
+    CK(launch_k(H, k_fit<T>, dim3((d.n_act + PBLK - 1) / PBLK), dim3(PBLK), 0, st, d, phi, a_prev, dm, gain,
+                a_old),
        "k_fit launch");
+    return FEWHA_OK;
+}
+
+// Pseudo-open-loop slopes s_pol = s + Gamma P_DM a^(i-1) (Algorithm 1, closed loop).
+template <class T>
+int launch_pol(fewha_handle* H, const Desc<T>& d, const T* s, T* out, cudaStream_t st) {
+    if (recorder<T>()) return fail(H, FEWHA_ERR_INVALID_ARG, "closed-loop frames are not batched");
+    PolArgs<T> p{s, static_cast<const T*>(H->a_old), out, H->qi0y, H->qi0x,
+                 static_cast<const T*>(H->qfy), static_cast<const T*>(H->qfx)};
+    int gx = 1;
+    for (const WfsInfo& W : H->setup.G)
+        gx = std::max(gx, W.nb == 1 ? (W.N * W.N + PBLK - 1) / PBLK : W.n_sub * W.n_sub);
+    CK(launch_k(H, k_pol<T>, dim3(gx, d.n_wfs), dim3(PBLK), 0, st, d, p), "k_pol launch");
     return FEWHA_OK;
 }
 
@@ -576,7 +596,9 @@ int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain,
     T* phi = static_cast<T*>(H->phi);
     int rc;
     if ((rc = launch_inv<T, false>(H, d, cl_args<T>(H, c, phi), st))) return rc;
-    return launch_fit<T>(H, d, phi, static_cast<T*>(H->a_prev), dm, gain ? 1 : 0, st);
+    const bool closed = gain && (H->params.flags & FEWHA_FLAG_CLOSED_LOOP);
+    return launch_fit<T>(H, d, phi, static_cast<T*>(H->a_prev), dm, closed ? 2 : (gain ? 1 : 0), st,
+                         static_cast<T*>(H->a_old));
 }
 
 // One frame of Algorithm 1 (open loop).
@@ -586,6 +608,12 @@ template <class T>
 int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStream_t st) {
     const Desc<T> d = make_desc<T>(H);
     int rc;
+    if (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) {
+        // closed loop: the slopes are residual slopes; form the pseudo-open-loop slopes
+        T* sp = static_cast<T*>(H->s_pol);
+        if ((rc = launch_pol<T>(H, d, s, sp, st))) return rc;
+        s = sp;
+    }
     if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
     if (H->params.flags & FEWHA_FLAG_AUGMENTED)
         rc = enqueue_pcg_aug<T>(H, d, c, H->params.iters, warm, H->aug_set, H->aug_m, st);
@@ -990,7 +1018,8 @@ int typed_create(fewha_handle* H) {
         (rc = dalloc(H, &H->pqpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * PQ_SLOTS)) ||
         (rc = dalloc(H, &H->rztot, static_cast<size_t>(FEWHA_MAX_ITERS + 2))) ||
         (rc = dalloc(H, &H->pqtot, static_cast<size_t>(FEWHA_MAX_ITERS + 2))) ||
-        (rc = dalloc(H, &H->count, 2)) || (rc = dalloc(H, &H->status, 1)))
+        (rc = dalloc(H, &H->count, 2)) || (rc = dalloc(H, &H->status, 1)) ||
+        (rc = dalloc(H, &H->qi0y, s.qi0y.size())) || (rc = dalloc(H, &H->qi0x, s.qi0x.size())))
         return rc;
     if ((rc = talloc(H, &H->pfy, tab)) || (rc = talloc(H, &H->pfx, tab)) ||
         (rc = talloc(H, &H->dfw, dtab)) || (rc = talloc(H, &H->D, s.n_c)) ||
@@ -1002,7 +1031,9 @@ int typed_create(fewha_handle* H) {
         (rc = talloc(H, &H->u, s.n_nodes)) || (rc = talloc(H, &H->a_prev, s.n_act)) ||
         (rc = talloc(H, &H->dm_tmp, s.n_act)) || (rc = talloc(H, &H->s_tmp, s.n_s)) ||
         (rc = talloc(H, &H->cgrad, s.n_c)) || (rc = talloc(H, &H->lam, s.n_c)) ||
-        (rc = dalloc(H, &H->gdot, MAXL + 1)))
+        (rc = dalloc(H, &H->gdot, MAXL + 1)) || (rc = talloc(H, &H->qfy, s.qfy.size())) ||
+        (rc = talloc(H, &H->qfx, s.qfx.size())) || (rc = talloc(H, &H->s_pol, s.n_s)) ||
+        (rc = talloc(H, &H->a_old, s.n_act)))
         return rc;
     if ((rc = upload(H, H->pi0y, s.pi0y)) || (rc = upload(H, H->pi0x, s.pi0x)) ||
         (rc = upload(H, H->pfy64, s.pfy)) || (rc = upload(H, H->pfx64, s.pfx)) ||
@@ -1011,7 +1042,10 @@ int typed_create(fewha_handle* H) {
         (rc = upload(H, H->sidx, s.sidx)) || (rc = upload(H, H->cidx, s.cidx)) ||
         (rc = upload(H, H->di0, s.di0)) || (rc = upload(H, H->dr_lo, s.dr_lo)) ||
         (rc = upload(H, H->dr_hi, s.dr_hi)) || (rc = upload(H, H->basis_off, s.basis_off)) ||
-        (rc = upload(H, H->basis, s.basis)))
+        (rc = upload(H, H->basis, s.basis)) || (rc = upload(H, H->qi0y, s.qi0y)) ||
+        (rc = upload(H, H->qi0x, s.qi0x)) ||
+        (rc = upload(H, static_cast<T*>(H->qfy), std::vector<T>(s.qfy.begin(), s.qfy.end()))) ||
+        (rc = upload(H, static_cast<T*>(H->qfx), std::vector<T>(s.qfx.begin(), s.qfx.end()))))
         return rc;
     H->smem_layer = (2 * NWARP + 4) * sizeof(double) + static_cast<size_t>(s.max_n) * s.max_n * sizeof(T);
     H->smem_sensor = (2 * NWARP + 4 + 2 * MAXCOARSE) * sizeof(double) +
@@ -1300,6 +1334,8 @@ int batch_record(fewha_batch* B, const T* const* s, T* const* dm, bool warm, std
         if (!s[i] || !dm[i]) return bfail(B, FEWHA_ERR_INVALID_ARG, "null slope or DM pointer of instance " + std::to_string(i));
         if (H->params.flags & FEWHA_FLAG_AUGMENTED)
             return bfail(B, FEWHA_ERR_INVALID_ARG, "augmented PCG frames are not batched (instance " + std::to_string(i) + ")");
+        if (H->params.flags & FEWHA_FLAG_CLOSED_LOOP)
+            return bfail(B, FEWHA_ERR_INVALID_ARG, "closed-loop frames are not batched (instance " + std::to_string(i) + ")");
         g_recorder = &recs[i];
         const int rc = enqueue_frame<T>(H, s[i], static_cast<T*>(H->c), dm[i], warm, nullptr);
         g_recorder = nullptr;
@@ -1926,6 +1962,10 @@ int fewha_create(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, co
     H->precision = params->precision;
     H->esz = params->precision == 32 ? sizeof(float) : sizeof(double);
     rc = build_setup(*tel, wfs, n_wfs, layers, n_layers, dms, n_dms, H->setup, g_create_error);
+    if (!rc && (params->flags & FEWHA_FLAG_CLOSED_LOOP) && !H->setup.dm_proj_ok) {
+        g_create_error = "closed loop needs every DM below every LGS";
+        rc = FEWHA_ERR_GEOMETRY;
+    }
     if (rc) {
         delete H;
         return rc;
@@ -1976,6 +2016,8 @@ int fewha_update_params(fewha_handle* H, const fewha_params* params, const doubl
     int rc = check_params(params, e);
     if (rc) return fail(H, rc, e);
     if (params->precision != H->precision) return fail(H, FEWHA_ERR_INVALID_ARG, "precision cannot change");
+    if ((params->flags & FEWHA_FLAG_CLOSED_LOOP) && !H->setup.dm_proj_ok)
+        return fail(H, FEWHA_ERR_GEOMETRY, "closed loop needs every DM below every LGS");
     DeviceGuard g(H->device);
     CK(cudaDeviceSynchronize(), "update sync");
     if (cn2_weights) {
@@ -2008,6 +2050,7 @@ int fewha_reset(fewha_handle* H, void* stream) {
     CK(cudaMemsetAsync(H->a_prev, 0, H->setup.n_act * H->esz, st), "reset");
     CK(cudaMemsetAsync(H->r, 0, H->setup.n_c * H->esz, st), "reset");
     CK(cudaMemsetAsync(H->b_prev, 0, H->setup.n_c * H->esz, st), "reset");
+    CK(cudaMemsetAsync(H->a_old, 0, H->setup.n_act * H->esz, st), "reset");
     H->have_prev = false;
     H->aug_m = 0;
     return FEWHA_OK;
@@ -2192,7 +2235,8 @@ int fewha_frame_launches(const fewha_handle* H, int* launches) {
     // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2; the
     // augmented frame (with directions) adds one start kernel and one per iteration
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
-    *launches = 3 + (warm ? 1 : 6) + aug + (6 + aug) * H->params.iters + 2;
+    const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 1 : 0;
+    *launches = closed + 3 + (warm ? 1 : 6) + aug + (6 + aug) * H->params.iters + 2;
     return FEWHA_OK;
 }
 

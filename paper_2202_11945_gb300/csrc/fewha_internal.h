@@ -99,6 +99,11 @@ struct HostSetup {
     std::vector<int> di0;               // MAXM*MAXL*MAXNACT
     std::vector<double> dfw;
     std::vector<int> dr_lo, dr_hi;      // MAXM*MAXL*MAXN
+    // DM m seen by sensor g (closed loop), pair (g, m) at (g * MAXM + m) * TAB: actuator
+    // row/col index of node a (the stencil {i0, i0 + 1} may leave the lattice) and weight
+    std::vector<int> qi0y, qi0x;
+    std::vector<double> qfy, qfx;
+    bool dm_proj_ok = true;             // every DM below every LGS
     // 1-D wavelet basis functions at shift 0: layer l, level j (1..levels), kind 0/1
     std::vector<double> basis;
     std::vector<int> basis_off;         // MAXL * (MAXN_LEVELS + 1) * 2

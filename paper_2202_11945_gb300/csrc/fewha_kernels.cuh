@@ -1103,12 +1103,15 @@ __global__ void __launch_bounds__(PBLK) k_aug(const int n, __grid_constant__ con
 
 // ---------------------------------------------------------------------------
 // DM fitting (Algorithm 1 fitting step, Table 3): a~_m(p, q) = sum_l w_lm phi_l
-// sampled bilinearly at the actuator, then open-loop gain a = (1-g) a_prev + g a~.
+// sampled bilinearly at the actuator, then the control law of Algorithm 1: open loop
+// (apply_gain 1) a = (1-g) a_prev + g a~; closed loop (apply_gain 2)
+// a = a_prev + g (a~ - a_old), after which a_old = a_prev (the commands of the frame
+// before) and a_prev = a.
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__ phi,
                                          T* __restrict__ a_prev, T* __restrict__ out, int apply_gain,
-                                         const int blk) {
+                                         const int blk, T* __restrict__ a_old = nullptr) {
     const int idx = blk * PBLK + threadIdx.x;
     if (idx >= d.n_act) return;
     int m = 0;
@@ -1150,7 +1153,13 @@ __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__
                 acc += w[u] * ((T(1) - fy[u]) * ((T(1) - fx[u]) * v[u][0] + fx[u] * v[u][1]) +
                                fy[u] * ((T(1) - fx[u]) * v[u][2] + fx[u] * v[u][3]));
     }
-    if (apply_gain) {
+    if (apply_gain == 2) {
+        const T cur = a_prev[idx];
+        const T a = cur + d.gain * (acc - a_old[idx]);
+        a_old[idx] = cur;
+        a_prev[idx] = a;
+        out[idx] = a;
+    } else if (apply_gain) {
         const T a = (T(1) - d.gain) * a_prev[idx] + d.gain * acc;
         a_prev[idx] = a;
         out[idx] = a;
@@ -1162,9 +1171,117 @@ __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__
 template <class T>
 __global__ void __launch_bounds__(PBLK) k_fit(__grid_constant__ const Desc<T> d, const T* __restrict__ phi,
                                               T* __restrict__ a_prev, T* __restrict__ out,
-                                              int apply_gain) {
+                                              int apply_gain, T* __restrict__ a_old) {
     pdl_enter();
-    fit_body<T>(d, phi, a_prev, out, apply_gain, blockIdx.x);
+    fit_body<T>(d, phi, a_prev, out, apply_gain, blockIdx.x, a_old);
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo-open-loop slopes of the closed loop (Algorithm 1): s_pol = s + Gamma P_DM a with
+// a the commands of two frames back (the two-step delay).  The DM shape is bilinear
+// between actuators (Sec. 4.1), i.e. zero beyond the outer actuators' hats; sensor g sees
+// DM m at s x + theta h_m, like a layer.  Block (x, g) of sensor g: PBLK of its fine
+// subapertures, or, on a coarse sensor, coarse subaperture x ((1/nb) x the sum of its
+// active fine slopes, R9).
+// ---------------------------------------------------------------------------
+template <class T>
+struct PolArgs {
+    const T* s;          // measured (residual) slopes
+    const T* a;          // the commands a^(i-1)
+    T* out;              // pseudo-open-loop slopes
+    const int* qi0y;     // DM tables, pair (g, m) at (g * MAXM + m) * TAB
+    const int* qi0x;
+    const T* qfy;
+    const T* qfx;
+};
+
+// The DM shapes seen by sensor g at aperture node (row ra, column cb).
+template <class T>
+__device__ __forceinline__ T dm_node(const Desc<T>& d, const PolArgs<T>& p, int g, int ra, int cb) {
+    T v = T(0);
+    for (int m = 0; m < d.n_dms; ++m) {
+        const int base = (g * MAXM + m) * TAB;
+        const int iy = p.qi0y[base + ra], ix = p.qi0x[base + cb];
+        const T fy = p.qfy[base + ra], fx = p.qfx[base + cb];
+        const int na = d.Mi[m].n_act;
+        const T* A = p.a + d.Mi[m].off;
+        const bool y0 = iy >= 0 && iy < na, y1 = iy + 1 >= 0 && iy + 1 < na;
+        const bool x0 = ix >= 0 && ix < na, x1 = ix + 1 >= 0 && ix + 1 < na;
+        const T a00 = (y0 && x0) ? A[iy * na + ix] : T(0);
+        const T a01 = (y0 && x1) ? A[iy * na + ix + 1] : T(0);
+        const T a10 = (y1 && x0) ? A[(iy + 1) * na + ix] : T(0);
+        const T a11 = (y1 && x1) ? A[(iy + 1) * na + ix + 1] : T(0);
+        v += (T(1) - fy) * ((T(1) - fx) * a00 + fx * a01) + fy * ((T(1) - fx) * a10 + fx * a11);
+    }
+    return v;
+}
+
+// Gamma of the DM shapes on fine subaperture (i, j) (Sec. 2, reading R1 for s^y).
+template <class T>
+__device__ __forceinline__ void dm_fine_slope(const Desc<T>& d, const PolArgs<T>& p, int g, int i, int j,
+                                              T& sx, T& sy) {
+    const T v00 = dm_node(d, p, g, i, j), v01 = dm_node(d, p, g, i, j + 1);
+    const T v10 = dm_node(d, p, g, i + 1, j), v11 = dm_node(d, p, g, i + 1, j + 1);
+    sx = T(0.5) * ((v01 - v00) + (v11 - v10));
+    sy = T(0.5) * ((v10 - v00) + (v11 - v01));
+}
+
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_pol(__grid_constant__ const Desc<T> d,
+                                              __grid_constant__ const PolArgs<T> p) {
+    const int g = blockIdx.y;
+    const WfsInfo& W = d.G[g];
+    const int N = W.N;
+    if (W.nb == 1) {
+        const int k = blockIdx.x * PBLK + threadIdx.x;
+        if (k >= N * N) return;
+        const int id = d.sidx[W.mask_off + k];
+        if (id < 0) return;
+        const int i = k / N, j = k - i * N;
+        T sx, sy;
+        dm_fine_slope(d, p, g, i, j, sx, sy);
+        p.out[W.soff + id] = p.s[W.soff + id] + sx;
+        p.out[W.soff + W.n_active + id] = p.s[W.soff + W.n_active + id] + sy;
+        return;
+    }
+    const int K = blockIdx.x;
+    if (K >= W.n_sub * W.n_sub) return;
+    const int cid = d.cidx[W.cmask_off + K];
+    if (cid < 0) return;                                  // uniform over the block
+    const int I = K / W.n_sub, J = K - I * W.n_sub, nb = W.nb;
+    T ax = T(0), ay = T(0);
+    for (int t = threadIdx.x; t < nb * nb; t += PBLK) {
+        const int u = t / nb, v = t - u * nb;
+        const int i = I * nb + u, j = J * nb + v;
+        if (d.sidx[W.mask_off + i * N + j] == cid) {
+            T sx, sy;
+            dm_fine_slope(d, p, g, i, j, sx, sy);
+            ax += sx;
+            ay += sy;
+        }
+    }
+    // fixed-order block sum
+    __shared__ T sh[2][PBLK / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        ax += __shfl_down_sync(0xffffffffu, ax, o);
+        ay += __shfl_down_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+        sh[0][w] = ax;
+        sh[1][w] = ay;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T tx = T(0), ty = T(0);
+        for (int k = 0; k < PBLK / 32; ++k) {
+            tx += sh[0][k];
+            ty += sh[1][k];
+        }
+        p.out[W.soff + cid] = p.s[W.soff + cid] + tx / T(nb);
+        p.out[W.soff + W.n_active + cid] = p.s[W.soff + W.n_active + cid] + ty / T(nb);
+    }
 }
 
 // ---------------------------------------------------------------------------

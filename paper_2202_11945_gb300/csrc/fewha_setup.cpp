@@ -262,6 +262,34 @@ int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
         }
     }
     s.n_act = aoff;
+    // DM shapes seen by the sensors (closed loop, Algorithm 1): the mirror surface is
+    // bilinear between actuators (Sec. 4.1); actuator k of DM m sits at
+    // (k - (n_act - 1)/2) spacing; sensor g sees it at s x + theta h_m like a layer
+    s.qi0y.assign(MAXG * MAXM * TAB, 0);
+    s.qi0x.assign(MAXG * MAXM * TAB, 0);
+    s.qfy.assign(MAXG * MAXM * TAB, 0.0);
+    s.qfx.assign(MAXG * MAXM * TAB, 0.0);
+    for (int g = 0; g < n_wfs; ++g) {
+        const fewha_wfs& W = wfs[g];
+        const int N = W.n_sub * W.nb;
+        const double d = D / N;
+        for (int m = 0; m < n_dms; ++m) {
+            const double h = dms[m].h, sp = dms[m].spacing, c = (dms[m].n_act - 1) / 2.0;
+            const double sc = W.is_lgs ? 1.0 - h / W.H : 1.0;
+            if (!(sc > 0)) s.dm_proj_ok = false;
+            const int base = (g * MAXM + m) * TAB;
+            for (int a = 0; a <= N; ++a) {
+                const double xa = -D / 2 + a * d;
+                const double uy = (sc * xa + W.theta_y * h) / sp + c, ux = (sc * xa + W.theta_x * h) / sp + c;
+                const double fy = std::floor(uy), fx = std::floor(ux);
+                // far outside the lattice both stencil points are outside: clamp the index
+                s.qi0y[base + a] = static_cast<int>(std::max(-2.0, std::min(fy, double(MAXNACT + 1))));
+                s.qfy[base + a] = uy - fy;
+                s.qi0x[base + a] = static_cast<int>(std::max(-2.0, std::min(fx, double(MAXNACT + 1))));
+                s.qfx[base + a] = ux - fx;
+            }
+        }
+    }
     // 1-D basis functions: synthesis of a unit coefficient of level j through j steps
     s.basis_off.assign(MAXL * (MAXLEV + 1) * 2, -1);
     for (int l = 0; l < n_layers; ++l) {

@@ -18,6 +18,7 @@ FLAG_GRAPH = 1
 FLAG_WARM_RESIDUAL = 2
 FLAG_PDL = 4
 FLAG_AUGMENTED = 8
+FLAG_CLOSED_LOOP = 16
 AUG_MAX_ITERS = 8
 
 ERRORS = {
@@ -174,7 +175,8 @@ def _stream(stream):
 class Reconstructor:
     """One FEWHA instance on the current CUDA device (a handle of the C library)."""
 
-    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False, augmented=False):
+    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False, augmented=False,
+                 closed_loop=False):
         if not torch.cuda.is_available():
             raise RuntimeError("FEWHA needs a CUDA device; there is no CPU path")
         torch.cuda.init()
@@ -182,7 +184,8 @@ class Reconstructor:
         self.precision = precision
         self.dtype = torch.float32 if precision == 32 else torch.float64
         flags = ((FLAG_GRAPH if graph else 0) | (FLAG_WARM_RESIDUAL if warm_residual else 0) |
-                 (FLAG_PDL if pdl else 0) | (FLAG_AUGMENTED if augmented else 0))
+                 (FLAG_PDL if pdl else 0) | (FLAG_AUGMENTED if augmented else 0) |
+                 (FLAG_CLOSED_LOOP if closed_loop else 0))
         self._structs = structs_from_workload(wl, precision, flags)
         tel, wfs, layers, dms, params = self._structs
         self.L = lib()
@@ -304,7 +307,8 @@ class Reconstructor:
         self._check(self.L.fewha_reset(self.h, _stream(stream)))
 
     def update_params(self, alpha=None, tau=None, gain=None, r0=None, L0=None, iters=None,
-                      cn2_weights=None, sigmas=None, graph=None, warm_residual=None, augmented=None):
+                      cn2_weights=None, sigmas=None, graph=None, warm_residual=None, augmented=None,
+                      closed_loop=None):
         tel, wfs, layers, dms, p = self._structs
         if alpha is not None:
             p.alpha = alpha
@@ -324,6 +328,8 @@ class Reconstructor:
             p.flags = (p.flags & ~FLAG_WARM_RESIDUAL) | (FLAG_WARM_RESIDUAL if warm_residual else 0)
         if augmented is not None:
             p.flags = (p.flags & ~FLAG_AUGMENTED) | (FLAG_AUGMENTED if augmented else 0)
+        if closed_loop is not None:
+            p.flags = (p.flags & ~FLAG_CLOSED_LOOP) | (FLAG_CLOSED_LOOP if closed_loop else 0)
         w = s = None
         if cn2_weights is not None:
             w = (ctypes.c_double * len(layers))(*cn2_weights)

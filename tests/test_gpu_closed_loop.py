@@ -1,0 +1,102 @@
+"""Closed-loop control (Algorithm 1) on the CUDA path against the FP64 oracle: residual
+slopes in, pseudo-open-loop slopes s + Gamma P_DM a^(i-1) formed on the device, and the
+delayed control law a^(i+1) = a^(i) + gain (a~ - a^(i-1)).
+
+The residual slopes of frame k are synthesised from the ORACLE's own commands (the
+sensor saw the DM shape of two frames back); the same slopes go to both sides."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests.gpu_common import TOL_FRAME, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+_seq = {}
+
+
+def closed_loop_sequence(name, frames, gain, augmented=False, warm=False):
+    """Residual slopes and the oracle's closed-loop commands of a frozen-flow run."""
+    key = (name, frames, gain, augmented, warm)
+    if key not in _seq:
+        wl = synth.workload_by_name(name)
+        wl["params"]["gain"] = gain
+        atm = synth.TruthAtmosphere(wl["truth"])
+        ref = O.Reconstructor(wl)
+        A = [np.zeros(ref.geo.n_a), np.zeros(ref.geo.n_a)]
+        S, out = [], []
+        for t in range(frames):
+            s_cl = synth.simulate_slopes(wl, t, atm=atm) - O.dm_slopes(ref.geo, A[-2])
+            S.append(s_cl)
+            A.append(ref.frame(s_cl, warm_residual=warm, augmented=augmented, closed_loop=True))
+            out.append(A[-1])
+        _seq[key] = (wl, S, out, ref.geo)
+    return _seq[key]
+
+
+def recon(wl, prec, **kw):
+    from paper_2202_11945_gb300 import Reconstructor
+    return Reconstructor(wl, precision=prec, closed_loop=True, **kw)
+
+
+def check(a, a_ref, geo, tol, what):
+    """Each DM's commands without their mean within tol (the layers' piston is unseen by
+    the slopes and set by the prior alone), the full commands within 10 tol."""
+    assert rel_l2(a, a_ref) <= 10 * tol, (what, rel_l2(a, a_ref))
+    for m in geo.dms:
+        sl = slice(m["off"], m["off"] + m["n_act"] ** 2)
+        x, y = a[sl] - a[sl].mean(), a_ref[sl] - a_ref[sl].mean()
+        assert np.linalg.norm(x - y) <= tol * np.linalg.norm(a_ref), (what, m["off"])
+
+
+CASES = [("tiny_scao", 64, 1.0, 8), ("tiny_scao", 32, 0.5, 8), ("tiny_mcao", 64, 0.5, 8),
+         ("tiny_mcao", 32, 1.0, 8), ("maory", 32, 0.5, 4), ("maory", 64, 1.0, 3)]
+
+
+@pytest.mark.parametrize("name,prec,gain,frames", CASES, ids=lambda x: str(x))
+def test_closed_loop_sequence_matches_oracle(name, prec, gain, frames):
+    wl, S, A_ref, geo = closed_loop_sequence(name, frames, gain)
+    R = recon(wl, prec)
+    for t in range(frames):
+        a = to_np(R.reconstruct(to_dev(S[t], prec)))
+        check(a, A_ref[t], geo, TOL_FRAME[prec], t)
+    R.close()
+
+
+def test_closed_loop_with_augmented_pcg_and_warm_residual():
+    wl, S, A_ref, geo = closed_loop_sequence("tiny_mcao", 6, 0.5, augmented=True, warm=True)
+    R = recon(wl, 64, augmented=True, warm_residual=True)
+    for t in range(6):
+        check(to_np(R.reconstruct(to_dev(S[t], 64))), A_ref[t], geo, TOL_FRAME[64], t)
+    R.close()
+
+
+def test_graph_stream_and_reset():
+    """Graph and stream forms are bit-identical; after fewha_reset the handle repeats a
+    fresh handle's frames bit for bit (a^(i), a^(i-1) and the warm state zeroed)."""
+    wl, S, _, _ = closed_loop_sequence("tiny_mcao", 8, 1.0)
+    A, B = recon(wl, 32, graph=True), recon(wl, 32, graph=False)
+    first = []
+    for t in range(4):
+        s = to_dev(S[t], 32)
+        a, b = to_np(A.reconstruct(s)), to_np(B.reconstruct(s))
+        assert np.array_equal(a, b), t
+        first.append(a)
+    A.reset()
+    for t in range(4):
+        assert np.array_equal(to_np(A.reconstruct(to_dev(S[t], 32))), first[t]), t
+    A.close()
+    B.close()
+
+
+def test_closed_loop_is_not_batched():
+    from paper_2202_11945_gb300 import Batch, FewhaError
+    wl, S, _, _ = closed_loop_sequence("tiny_scao", 2, 1.0)
+    A, B = recon(wl, 32), recon(synth.tiny_mcao(), 32, graph=False)
+    bt = Batch([A, B])
+    with pytest.raises(FewhaError):
+        bt.reconstruct([to_dev(S[0], 32), to_dev(np.zeros(B.n_slopes), 32)])
+    bt.close()
+    A.close()
+    B.close()
