@@ -66,7 +66,7 @@ struct fewha_handle {
     // closed loop (FEWHA_FLAG_CLOSED_LOOP): DM projection tables, pseudo-open-loop slopes
     // and the commands of the frame before (a^(i-1))
     int *qi0y = nullptr, *qi0x = nullptr;
-    void *qfy = nullptr, *qfx = nullptr, *s_pol = nullptr, *a_old = nullptr;
+    void *qfy = nullptr, *qfx = nullptr, *s_pol = nullptr, *a_old = nullptr, *dm_nodes = nullptr;
     bool grad_ready = false;          // a converged reconstruction is held in cgrad
     bool have_cgrad = false;          // cgrad / lam hold earlier solutions (warm starts)
     bool have_lam = false;
@@ -490,12 +490,14 @@ int launch_fit(fewha_handle* H, const Desc<T>& d, const T* phi, T* a_prev, T* dm
 template <class T>
 int launch_pol(fewha_handle* H, const Desc<T>& d, const T* s, T* out, cudaStream_t st) {
     if (recorder<T>()) return fail(H, FEWHA_ERR_INVALID_ARG, "closed-loop frames are not batched");
-    PolArgs<T> p{s, static_cast<const T*>(H->a_old), out, H->qi0y, H->qi0x,
+    PolArgs<T> p{s, static_cast<const T*>(H->a_old), out, static_cast<T*>(H->dm_nodes), H->qi0y, H->qi0x,
                  static_cast<const T*>(H->qfy), static_cast<const T*>(H->qfx)};
+    CK(launch_k(H, k_dmnodes<T>, dim3((d.n_nodes + PBLK - 1) / PBLK), dim3(PBLK), 0, st, d, p),
+       "k_dmnodes launch");
     int gx = 1;
     for (const WfsInfo& W : H->setup.G)
-        gx = std::max(gx, W.nb == 1 ? (W.N * W.N + PBLK - 1) / PBLK : W.n_sub * W.n_sub);
-    CK(launch_k(H, k_pol<T>, dim3(gx, d.n_wfs), dim3(PBLK), 0, st, d, p), "k_pol launch");
+        gx = std::max(gx, W.nb == 1 ? (W.N * W.N + POLBLK - 1) / POLBLK : W.n_sub * W.n_sub);
+    CK(launch_k(H, k_pol<T>, dim3(gx, d.n_wfs), dim3(POLBLK), 0, st, d, p), "k_pol launch");
     return FEWHA_OK;
 }
 
@@ -1033,7 +1035,7 @@ int typed_create(fewha_handle* H) {
         (rc = talloc(H, &H->cgrad, s.n_c)) || (rc = talloc(H, &H->lam, s.n_c)) ||
         (rc = dalloc(H, &H->gdot, MAXL + 1)) || (rc = talloc(H, &H->qfy, s.qfy.size())) ||
         (rc = talloc(H, &H->qfx, s.qfx.size())) || (rc = talloc(H, &H->s_pol, s.n_s)) ||
-        (rc = talloc(H, &H->a_old, s.n_act)))
+        (rc = talloc(H, &H->a_old, s.n_act)) || (rc = talloc(H, &H->dm_nodes, s.n_nodes)))
         return rc;
     if ((rc = upload(H, H->pi0y, s.pi0y)) || (rc = upload(H, H->pi0x, s.pi0x)) ||
         (rc = upload(H, H->pfy64, s.pfy)) || (rc = upload(H, H->pfx64, s.pfx)) ||
@@ -2235,7 +2237,7 @@ int fewha_frame_launches(const fewha_handle* H, int* launches) {
     // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2; the
     // augmented frame (with directions) adds one start kernel and one per iteration
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
-    const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 1 : 0;
+    const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
     *launches = closed + 3 + (warm ? 1 : 6) + aug + (6 + aug) * H->params.iters + 2;
     return FEWHA_OK;
 }

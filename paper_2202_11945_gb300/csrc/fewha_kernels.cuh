@@ -1180,7 +1180,8 @@ __global__ void __launch_bounds__(PBLK) k_fit(__grid_constant__ const Desc<T> d,
 // Pseudo-open-loop slopes of the closed loop (Algorithm 1): s_pol = s + Gamma P_DM a with
 // a the commands of two frames back (the two-step delay).  The DM shape is bilinear
 // between actuators (Sec. 4.1), i.e. zero beyond the outer actuators' hats; sensor g sees
-// DM m at s x + theta h_m, like a layer.  Block (x, g) of sensor g: PBLK of its fine
+// DM m at s x + theta h_m, like a layer.  Two kernels: the DM shapes on every aperture
+// node, then the slopes; block (x, g) of the second takes PBLK of sensor g's fine
 // subapertures, or, on a coarse sensor, coarse subaperture x ((1/nb) x the sum of its
 // active fine slopes, R9).
 // ---------------------------------------------------------------------------
@@ -1189,6 +1190,7 @@ struct PolArgs {
     const T* s;          // measured (residual) slopes
     const T* a;          // the commands a^(i-1)
     T* out;              // pseudo-open-loop slopes
+    T* nodes;            // the DM shapes on the aperture nodes (n_nodes)
     const int* qi0y;     // DM tables, pair (g, m) at (g * MAXM + m) * TAB
     const int* qi0x;
     const T* qfy;
@@ -1199,7 +1201,9 @@ struct PolArgs {
 template <class T>
 __device__ __forceinline__ T dm_node(const Desc<T>& d, const PolArgs<T>& p, int g, int ra, int cb) {
     T v = T(0);
-    for (int m = 0; m < d.n_dms; ++m) {
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+        if (m >= d.n_dms) break;
         const int base = (g * MAXM + m) * TAB;
         const int iy = p.qi0y[base + ra], ix = p.qi0x[base + cb];
         const T fy = p.qfy[base + ra], fx = p.qfx[base + cb];
@@ -1216,30 +1220,46 @@ __device__ __forceinline__ T dm_node(const Desc<T>& d, const PolArgs<T>& p, int 
     return v;
 }
 
-// Gamma of the DM shapes on fine subaperture (i, j) (Sec. 2, reading R1 for s^y).
+// The DM shapes on every aperture node of every sensor, one thread per node.
 template <class T>
-__device__ __forceinline__ void dm_fine_slope(const Desc<T>& d, const PolArgs<T>& p, int g, int i, int j,
-                                              T& sx, T& sy) {
-    const T v00 = dm_node(d, p, g, i, j), v01 = dm_node(d, p, g, i, j + 1);
-    const T v10 = dm_node(d, p, g, i + 1, j), v11 = dm_node(d, p, g, i + 1, j + 1);
+__global__ void __launch_bounds__(PBLK) k_dmnodes(__grid_constant__ const Desc<T> d,
+                                                  __grid_constant__ const PolArgs<T> p) {
+    const int k = blockIdx.x * PBLK + threadIdx.x;
+    if (k >= d.n_nodes) return;
+    int g = 0;
+    while (g + 1 < d.n_wfs && k >= d.G[g + 1].node_off) ++g;
+    const int np = d.G[g].N + 1, loc = k - d.G[g].node_off;
+    const int ra = loc / np, cb = loc - ra * np;
+    p.nodes[k] = dm_node(d, p, g, ra, cb);
+}
+
+// Gamma of node values v (row stride np) on fine subaperture (i, j) (Sec. 2, reading R1
+// for s^y).
+template <class T>
+__device__ __forceinline__ void node_slope(const T* v, int np, int i, int j, T& sx, T& sy) {
+    const T v00 = v[i * np + j], v01 = v[i * np + j + 1];
+    const T v10 = v[(i + 1) * np + j], v11 = v[(i + 1) * np + j + 1];
     sx = T(0.5) * ((v01 - v00) + (v11 - v10));
     sy = T(0.5) * ((v10 - v00) + (v11 - v01));
 }
 
+constexpr int POLBLK = 1024;   // threads of the slope kernel: a coarse block in 2 passes
+
 template <class T>
-__global__ void __launch_bounds__(PBLK) k_pol(__grid_constant__ const Desc<T> d,
-                                              __grid_constant__ const PolArgs<T> p) {
+__global__ void __launch_bounds__(POLBLK) k_pol(__grid_constant__ const Desc<T> d,
+                                                __grid_constant__ const PolArgs<T> p) {
     const int g = blockIdx.y;
     const WfsInfo& W = d.G[g];
-    const int N = W.N;
+    const int N = W.N, np = N + 1;
+    const T* v = p.nodes + W.node_off;
     if (W.nb == 1) {
-        const int k = blockIdx.x * PBLK + threadIdx.x;
+        const int k = blockIdx.x * POLBLK + threadIdx.x;
         if (k >= N * N) return;
         const int id = d.sidx[W.mask_off + k];
         if (id < 0) return;
         const int i = k / N, j = k - i * N;
         T sx, sy;
-        dm_fine_slope(d, p, g, i, j, sx, sy);
+        node_slope(v, np, i, j, sx, sy);
         p.out[W.soff + id] = p.s[W.soff + id] + sx;
         p.out[W.soff + W.n_active + id] = p.s[W.soff + W.n_active + id] + sy;
         return;
@@ -1250,18 +1270,19 @@ __global__ void __launch_bounds__(PBLK) k_pol(__grid_constant__ const Desc<T> d,
     if (cid < 0) return;                                  // uniform over the block
     const int I = K / W.n_sub, J = K - I * W.n_sub, nb = W.nb;
     T ax = T(0), ay = T(0);
-    for (int t = threadIdx.x; t < nb * nb; t += PBLK) {
-        const int u = t / nb, v = t - u * nb;
-        const int i = I * nb + u, j = J * nb + v;
+    for (int t = threadIdx.x; t < nb * nb; t += POLBLK) {
+        const int u = t / nb, w = t - u * nb;
+        const int i = I * nb + u, j = J * nb + w;
+        // the node loads do not wait for the mask (every (i, j) of the block is inside)
+        T sx, sy;
+        node_slope(v, np, i, j, sx, sy);
         if (d.sidx[W.mask_off + i * N + j] == cid) {
-            T sx, sy;
-            dm_fine_slope(d, p, g, i, j, sx, sy);
             ax += sx;
             ay += sy;
         }
     }
     // fixed-order block sum
-    __shared__ T sh[2][PBLK / 32];
+    __shared__ T sh[2][POLBLK / 32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -1275,7 +1296,7 @@ __global__ void __launch_bounds__(PBLK) k_pol(__grid_constant__ const Desc<T> d,
     __syncthreads();
     if (threadIdx.x == 0) {
         T tx = T(0), ty = T(0);
-        for (int k = 0; k < PBLK / 32; ++k) {
+        for (int k = 0; k < POLBLK / 32; ++k) {
             tx += sh[0][k];
             ty += sh[1][k];
         }
