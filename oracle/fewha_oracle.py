@@ -32,7 +32,8 @@ Readings where the paper is silent or garbled (each also listed in the design doc):
   R9  coarse NGS sensors (nb > 1 fine subapertures per coarse one and side) live
       on the fine aperture grid; a coarse slope is (1/nb) * the sum of the fine
       slopes of the active fine subapertures in its block
-  R10 C_g = sigma_g^2 I for every sensor (alpha_eta = 0), T applies to LGS only
+  R10 C_g = sigma_g^2 I for every NGS and, with alpha_eta = 0, every LGS; T applies to
+      LGS only
   R11 J uses the exact diagonal of W (sum_g P_g^T Gamma_g^T C_hat_g^-1 Gamma_g P_g)
       W^T; tau defaults to 0
   R12 PCG: left-preconditioned, Fletcher-Reeves beta, fixed iteration count, no
@@ -56,6 +57,13 @@ Readings where the paper is silent or garbled (each also listed in the design doc):
       are s + Gamma P_DM a^(i-1) (the residual slopes s measure phase minus DM shape)
       and the control law is a^(i+1) = a^(i) + gain (a_tilde - a^(i-1)), both as printed;
       a^(0) = a^(-1) = 0.
+  R28 LGS spot elongation (Eq. 3): in subaperture (i, j) with midpoint (x, y) (R3),
+      beta = (FWHM / H^2) ((x, y) - (x_LL, y_LL)), FWHM the sodium profile's, (x_LL, y_LL)
+      the sensor's laser launch position; C_ij = sigma^2 (I + (alpha_eta^2 / f^2) beta
+      beta^T), f the FWHM of the non-elongated spot [rad].  Its inverse (Sherman-Morrison)
+      is sigma^-2 (I - gamma beta beta^T), gamma = c / (1 + c |beta|^2), c = alpha_eta^2
+      / f^2, and C_hat^-1 = (I - T) C^-1 (I - T) no longer collapses to sigma^-2 (I - T).
+      Elongation is on for an LGS when alpha_eta, FWHM and f are all > 0.
 """
 
 import math
@@ -285,7 +293,10 @@ class Geometry:
                 Qy.append(_hat_matrix((s * xs + ty * hm) / float(m["spacing"]) + (na - 1) / 2.0, na))
             self.wfs.append(dict(N=N, n_sub=n_sub, nb=nb, d=d, lgs=lgs, sigma=float(W["sigma"]),
                                  mask=fine, cmask=coarse, n_active=n_act, soff=soff,
-                                 ns=2 * n_act, Rx=Rx, Ry=Ry, Qx=Qx, Qy=Qy))
+                                 ns=2 * n_act, Rx=Rx, Ry=Ry, Qx=Qx, Qy=Qy,
+                                 H=float(W["H"]), launch=tuple(W.get("launch", (0.0, 0.0))),
+                                 na_fwhm=float(W.get("na_fwhm", 0.0)),
+                                 spot_fwhm=float(W.get("spot_fwhm", 0.0))))
             soff += 2 * n_act
         self.n_s = soff
         # deformable mirrors and the fitting split (R13)
@@ -304,6 +315,7 @@ class Geometry:
             self.dms.append(dict(n_act=na, off=aoff, R=Rs, w=fw[:, mi], spacing=float(m["spacing"])))
             aoff += na * na
         self.n_a = aoff
+        set_elongation(self, float(p.get("alpha_eta", 0.0)))
 
     # -- vector layout helpers ------------------------------------------------
     def split(self, c):
@@ -312,6 +324,25 @@ class Geometry:
 
     def join(self, blocks):
         return np.concatenate([np.asarray(b, float).ravel() for b in blocks])
+
+
+def set_elongation(geo, alpha_eta):
+    """The spot-elongation weights of every LGS (Eq. 3, reading R28) on its fine
+    subaperture grid: beta_1, beta_2 and gamma = c / (1 + c |beta|^2), c = alpha_eta^2 /
+    f^2, so that C_ij^-1 = sigma^-2 (I - gamma beta beta^T).  None where it is off."""
+    geo.alpha_eta = alpha_eta
+    for W in geo.wfs:
+        W["el"] = None
+        if not (W["lgs"] and alpha_eta > 0 and W["na_fwhm"] > 0 and W["spot_fwhm"] > 0):
+            continue
+        N, d = W["N"], W["d"]
+        mid = -geo.D / 2 + (np.arange(N) + 0.5) * d
+        k = W["na_fwhm"] / W["H"] ** 2
+        b1 = k * (mid[None, :] - W["launch"][0]) * np.ones((N, 1))
+        b2 = k * (mid[:, None] - W["launch"][1]) * np.ones((1, N))
+        c = (alpha_eta / W["spot_fwhm"]) ** 2
+        gam = c / (1.0 + c * (b1 ** 2 + b2 ** 2))
+        W["el"] = dict(b1=b1, b2=b2, gamma=gam)
 
 
 # ----------------------------------------------------------------------------
@@ -429,8 +460,9 @@ def tiptilt_projector(k):
 def noise_weight(geo, g, s):
     """C_hat_g^-1 s: (I - T) C_g^-1 (I - T) s for an LGS, C_g^-1 s for an NGS.
 
-    C_g = sigma_g^2 I (Eq. 2, R10); T from Sec. 3.2, applied through its rank-2 form
-    T s = (1/|M|)(t^x (t^x . s) + t^y (t^y . s)).
+    C_g = sigma_g^2 I (Eq. 2, R10), or for an elongated LGS the 2x2 blocks of Eq. 3,
+    inverted per subaperture as sigma^-2 (I - gamma beta beta^T) (R28); T from Sec. 3.2,
+    applied through its rank-2 form T s = (1/|M|)(t^x (t^x . s) + t^y (t^y . s)).
     """
     W = geo.wfs[g]
     inv = 1.0 / W["sigma"] ** 2
@@ -444,7 +476,15 @@ def noise_weight(geo, g, s):
         out[k:] -= v[k:].sum() / k
         return out
 
-    return i_minus_t(inv * i_minus_t(s))
+    def c_inv(v):
+        if W["el"] is None:
+            return inv * v
+        m = W["mask"]
+        b1, b2, gam = W["el"]["b1"][m], W["el"]["b2"][m], W["el"]["gamma"][m]
+        bu = b1 * v[:k] + b2 * v[k:]
+        return inv * np.concatenate([v[:k] - gam * b1 * bu, v[k:] - gam * b2 * bu])
+
+    return i_minus_t(c_inv(i_minus_t(s)))
 
 
 def forward_model(geo, phis):
@@ -596,6 +636,22 @@ def data_diag(geo):
                         tx = ya.T @ m @ xd
                         ty = yd.T @ m @ xa
                         val = val - (tx ** 2 + ty ** 2) / W["n_active"]
+                        if W["el"] is not None:
+                            # minus sum over the mask of gamma (beta . u)^2, u the slopes
+                            # without their means mu = (tx, ty) / |M| (R28):
+                            #   E - 2 mu . e + mu^T K mu
+                            e = W["el"]
+                            G11 = m * e["gamma"] * e["b1"] ** 2
+                            G12 = m * e["gamma"] * e["b1"] * e["b2"]
+                            G22 = m * e["gamma"] * e["b2"] ** 2
+                            E = ((ya ** 2).T @ G11 @ (xd ** 2) + 2.0 * (ya * yd).T @ G12 @ (xd * xa)
+                                 + (yd ** 2).T @ G22 @ (xa ** 2))
+                            e1 = ya.T @ G11 @ xd + yd.T @ G12 @ xa
+                            e2 = ya.T @ G12 @ xd + yd.T @ G22 @ xa
+                            mx, my = tx / W["n_active"], ty / W["n_active"]
+                            K11, K12, K22 = G11.sum(), G12.sum(), G22.sum()
+                            val = val - (E - 2.0 * (mx * e1 + my * e2)
+                                         + K11 * mx ** 2 + 2.0 * K12 * mx * my + K22 * my ** 2)
                 else:
                     nb, ns = W["nb"], W["n_sub"]
                     val = 0.0

@@ -13,7 +13,7 @@ wind -> 3000, batched instance i -> 4000 + i.
 
 from .configs import (  # noqa: F401
     tiny_scao, tiny_mcao, maory, realtime_loop, batched_instances, differentiable,
-    workload_by_name, arcsec,
+    workload_by_name, arcsec, with_elongation, paper_mcao, tiny_mcao_elongated,
 )
 from .atmosphere import TruthAtmosphere  # noqa: F401
 from .sensor import simulate_slopes, slope_counts, slope_sequence, true_phase_at  # noqa: F401

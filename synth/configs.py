@@ -122,6 +122,67 @@ def maory():
     )
 
 
+NA_FWHM = 11.4e3                 # sodium profile FWHM [m] (Table 1)
+SPOT_FWHM = arcsec(1.1)          # non-elongated LGS spot FWHM [rad]: not in the paper; a
+                                 # value typical of an ELT LGS spot, stated as a choice
+
+
+def with_elongation(wl, alpha_eta=0.2, na_fwhm=NA_FWHM, spot_fwhm=SPOT_FWHM):
+    """Turn on the LGS spot-elongation noise model (Eq. 3; alpha_eta = 0.2 as in Table 5).
+
+    Launch positions are not given in the paper: each laser is side-launched from the
+    pupil edge at its guide star's azimuth, (D/2)(cos az, sin az)."""
+    wl = dict(wl)
+    wl["name"] = wl["name"] + "_elongated"
+    wl["params"] = dict(wl["params"], alpha_eta=alpha_eta)
+    wfs = []
+    for W in wl["wfs"]:
+        W = dict(W)
+        if W["lgs"]:
+            az = math.atan2(W["theta"][1], W["theta"][0])
+            W.update(launch=(0.5 * wl["D"] * math.cos(az), 0.5 * wl["D"] * math.sin(az)),
+                     na_fwhm=na_fwhm, spot_fwhm=spot_fwhm)
+        wfs.append(W)
+    wl["wfs"] = wfs
+    return wl
+
+
+def paper_mcao():
+    """The paper's own MAORY simulation geometry (Sec. 4.1, Tables 1-5): 37 m, 11 % of the
+    pupil area obstructed, 6 LGS 74x74 on a 90 arcsec diameter circle with spot
+    elongation (alpha_eta = 0.2), 3 NGS 2x2 on a 110 arcsec circle, and 3 layers at the DM
+    altitudes (128^2 @ 0.5 m, 64^2 @ 1 m, 64^2 @ 1 m) so that the fit F is the identity on
+    the DM actuators (75^2 @ 0.5 m, 47^2 @ 1 m, 37^2 @ 1 m)."""
+    D, nsub = 37.0, 74
+    lgs = [dict(n_sub=nsub, nb=1, lgs=True, theta=t, H=NA_HEIGHT, sigma=0.1)
+           for t in _ring(arcsec(45.0), [0, 60, 120, 180, 240, 300])]
+    ngs = [dict(n_sub=2, nb=37, lgs=False, theta=t, H=0.0, sigma=0.02)
+           for t in _ring(arcsec(55.0), [60, 180, 300])]
+    layers = [dict(h=0.0, w=0.75, delta=0.5, n=128, levels=7),
+              dict(h=4000.0, w=0.15, delta=1.0, n=64, levels=6),
+              dict(h=12700.0, w=0.10, delta=1.0, n=64, levels=6)]
+    dms = [dict(h=0.0, spacing=0.5, n_act=75), dict(h=4000.0, spacing=1.0, n_act=47),
+           dict(h=12700.0, spacing=1.0, n_act=37)]
+    th, tw = maory_truth_profile()
+    wl = dict(
+        name="paper_37m_6lgs74_3ngs2_3L_3dm", D=D, obs=math.sqrt(0.11), wfs=lgs + ngs,
+        layers=layers, dms=dms,
+        params=dict(alpha=1.0, tau=0.0, gain=1.0, iters=4, r0=0.157, L0=25.0),
+        truth=dict(h=th, w=tw, r0=0.157, L0=25.0, screen_n=512, screen_dx=D / nsub / 2,
+                   wind=_wind(len(th)), frame_rate=1000.0),
+    )
+    wl = with_elongation(wl)
+    wl["name"] = "paper_37m_6lgs74_3ngs2_3L_3dm"
+    return wl
+
+
+def tiny_mcao_elongated():
+    """The 4 m MCAO test geometry with the LGS spot-elongation noise model.  On a 4 m
+    pupil the elongation is small; a 0.1 arcsec spot makes its term (alpha_eta |beta| /
+    f)^2 of order one, so that the tests exercise it."""
+    return with_elongation(tiny_mcao(), spot_fwhm=arcsec(0.1))
+
+
 def realtime_loop():
     """Config 3: the config-1 geometry run as a 1 kHz frame loop with frozen flow."""
     wl = tiny_scao()
@@ -207,5 +268,6 @@ def tiny_mcao():
 
 def workload_by_name(name):
     table = {"tiny_scao": tiny_scao, "maory": maory, "realtime": realtime_loop,
-             "differentiable": differentiable, "tiny_mcao": tiny_mcao}
+             "differentiable": differentiable, "tiny_mcao": tiny_mcao,
+             "tiny_mcao_elongated": tiny_mcao_elongated, "paper_mcao": paper_mcao}
     return table[name]()
