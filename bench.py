@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--backward-frames", type=int, default=8,
                     help="frames of the differentiable-reconstruction leg (0: leave it out)")
     ap.add_argument("--aug-steps", type=int, default=500,
-                    help="timed frames per configuration of the augmented-PCG and closed-loop runs")
+                    help="timed frames per configuration of the augmented-PCG, closed-loop and "
+                         "paper-geometry runs")
     ap.add_argument("--loop-frames", type=int, default=2000,
                     help="frames of the 1 kHz real-time loop (8 m single-conjugate geometry)")
     return ap.parse_args()
@@ -471,6 +472,39 @@ def time_closed_loop(wl, S32, S_np, flush, steps, parity=True):
     return out
 
 
+def time_paper_geometry(flush, steps, parity=True):
+    """The paper's own MAORY simulation geometry (37 m, 6 LGS 74x74 with spot elongation,
+    3 NGS 2x2, 3 layers at the DM altitudes, F the identity) at 2 and 4 iterations, FP32
+    graph form: context for the paper's 1.48 ms per frame (2 iterations, 9 threads)."""
+    from paper_2202_11945_gb300 import Reconstructor
+    wl = synth.paper_mcao()
+    S_np = make_inputs(wl)
+    S = torch.as_tensor(np.stack(S_np), dtype=torch.float32, device="cuda").contiguous()
+    out = {"workload": wl["name"], "form": "FP32 operators, FP64 dots, CUDA graph",
+           "alpha_eta": wl["params"]["alpha_eta"], "steps": steps}
+    for it in (2, 4):
+        R = Reconstructor(wl, precision=32, graph=True)
+        if it != wl["params"]["iters"]:
+            R.update_params(iters=it)
+        dm = torch.empty(R.n_act, dtype=torch.float32, device="cuda")
+        t = time_frames(R, S, steps, 20, flush, dm)
+        out["iters%d" % it] = {"frames_per_s": 1e3 / float(t.mean()), "p50_ms": float(np.percentile(t, 50)),
+                               "p99_ms": float(np.percentile(t, 99))}
+        R.close()
+    if parity:
+        import oracle as O
+        ref = O.Reconstructor(wl)
+        R = Reconstructor(wl, precision=32, graph=True)
+        err = []
+        for k in range(3):
+            a = R.reconstruct(S[k]).double().cpu().numpy()
+            a_ref = ref.frame(S_np[k])
+            err.append(float(np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)))
+        R.close()
+        out["parity_max_rel_l2_dm"] = max(err)
+    return out
+
+
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
     the same sequence (explicit initial residual), and the oracle's own frame rate."""
@@ -599,6 +633,8 @@ def main():
                  if args.aug_steps > 0 else None)
     closed = (time_closed_loop(wl, S32, S_np, flush, args.aug_steps, parity=(rank == 0 and world == 1))
               if args.aug_steps > 0 else None)
+    paper = (time_paper_geometry(flush, args.aug_steps, parity=(rank == 0 and world == 1))
+             if args.aug_steps > 0 else None)
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")
@@ -647,6 +683,7 @@ def main():
             "backward": backward,
             "augmented": augmented,
             "closed_loop": closed,
+            "paper_geometry": paper,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

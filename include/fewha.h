@@ -119,6 +119,15 @@ typedef struct fewha_wfs {
     double theta_x, theta_y;
     double H;
     double sigma;
+    /* LGS spot elongation (Eq. 3), used when fewha_params.alpha_eta, na_fwhm and
+     * spot_fwhm are all > 0: laser launch position (launch_x, launch_y) [m] in the pupil
+     * plane, FWHM of the sodium profile na_fwhm [m], FWHM of the non-elongated spot
+     * spot_fwhm [rad].  Subaperture (i, j) with midpoint (x, y) then has the 2 x 2 noise
+     * covariance sigma^2 (I + (alpha_eta / spot_fwhm)^2 beta beta^T), beta =
+     * (na_fwhm / H^2) ((x, y) - (launch_x, launch_y)).  Zero for an NGS. */
+    double launch_x, launch_y;
+    double na_fwhm;
+    double spot_fwhm;
 } fewha_wfs;
 
 /* One reconstruction layer (Sec. 3.1; Table 2): altitude h [m], Cn2 weight, grid
@@ -151,6 +160,7 @@ typedef struct fewha_params {
     int iters;
     int precision;
     unsigned flags;
+    double alpha_eta;   /* spot-elongation tuning of Eq. 3 (Table 5); 0 = C_g = sigma^2 I */
 } fewha_params;
 
 typedef struct fewha_handle fewha_handle;

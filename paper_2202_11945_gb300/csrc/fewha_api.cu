@@ -992,8 +992,8 @@ int check_params(const fewha_params* p, std::string& err) {
         return FEWHA_ERR_LIMIT;
     }
     if (!(p->alpha >= 0) || !(p->tau >= 0) || !(p->r0 > 0) || !(p->L0 > 0) || !(p->gain >= 0) ||
-        !(p->gain <= 1)) {
-        err = "alpha, tau >= 0, r0, L0 > 0 and gain in [0, 1] required";
+        !(p->gain <= 1) || !(p->alpha_eta >= 0) || !std::isfinite(p->alpha_eta)) {
+        err = "alpha, tau, alpha_eta >= 0, r0, L0 > 0 and gain in [0, 1] required";
         return FEWHA_ERR_INVALID_ARG;
     }
     return FEWHA_OK;
@@ -1964,6 +1964,7 @@ int fewha_create(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, co
     H->precision = params->precision;
     H->esz = params->precision == 32 ? sizeof(float) : sizeof(double);
     rc = build_setup(*tel, wfs, n_wfs, layers, n_layers, dms, n_dms, H->setup, g_create_error);
+    if (!rc) set_elongation(H->setup, params->alpha_eta);
     if (!rc && (params->flags & FEWHA_FLAG_CLOSED_LOOP) && !H->setup.dm_proj_ok) {
         g_create_error = "closed loop needs every DM below every LGS";
         rc = FEWHA_ERR_GEOMETRY;
@@ -2036,6 +2037,7 @@ int fewha_update_params(fewha_handle* H, const fewha_params* params, const doubl
         }
     }
     H->params = *params;
+    set_elongation(H->setup, params->alpha_eta);
     drop_graph(H);
     H->have_prev = false;
     H->aug_m = 0;                     // M changed: the stored directions no longer apply

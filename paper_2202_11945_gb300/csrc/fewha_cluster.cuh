@@ -724,7 +724,7 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     // peers' shared memory is written before the first full cluster barrier (the pushes
     // below): arrive now, wait before the first push, so that every CTA has started
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
-    __shared__ T ttp[2 * CL];                    // every rank's tip/tilt sums (pushed)
+    __shared__ T ttp[4 * CL];                    // every rank's tip/tilt (and elongation) sums
     __shared__ T cps[CL * 2 * MAXCOARSE];        // every rank's coarse block sums (pushed)
     // the band's rows of the active-subaperture table, copied while the terms are summed
     int* msk = reinterpret_cast<int*>(sm + lay.msk);
@@ -802,16 +802,32 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     const bool need_coarse = (SRC == SSRC_PHI) && W.nb > 1;
     asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
     if (need_tt) {
-        T tx = T(0), ty = T(0);
+        T tx = T(0), ty = T(0), ex = T(0), ey = T(0);
         for (int k = threadIdx.x; k < rows * N; k += NT) {
             tx += SX[k];
             ty += SY[k];
         }
         cta_sum2_t(tx, ty, red);
+        if (W.el) {
+            // spot elongation (Eq. 3): the sums of gamma beta (beta . s) as well
+            for (int k = threadIdx.x; k < rows * N; k += NT) {
+                if (msk[k] >= 0) {
+                    const int ii = k / N;
+                    T b1, b2, gam;
+                    elong(W, s0 + ii, k - ii * N, b1, b2, gam);
+                    const T bs = b1 * SX[k] + b2 * SY[k];
+                    ex += gam * b1 * bs;
+                    ey += gam * b2 * bs;
+                }
+            }
+            cta_sum2_t(ex, ey, red);
+        }
         if (threadIdx.x < CL) {           // push this rank's sums into every rank's table
             T* dst = cluster.map_shared_rank(ttp, static_cast<unsigned>(threadIdx.x));
-            dst[2 * r] = tx;
-            dst[2 * r + 1] = ty;
+            dst[4 * r] = tx;
+            dst[4 * r + 1] = ty;
+            dst[4 * r + 2] = ex;
+            dst[4 * r + 3] = ey;
         }
     }
     if (need_coarse) {
@@ -859,15 +875,39 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
             T tx = T(0), ty = T(0);
 #pragma unroll
             for (int q = 0; q < CL; ++q) {
-                tx += ttp[2 * q];
-                ty += ttp[2 * q + 1];
+                tx += ttp[4 * q];
+                ty += ttp[4 * q + 1];
             }
             const T mx = tx / T(W.n_active), my = ty / T(W.n_active);
-            // C_hat^-1 = (I - T) sigma^-2 (I - T) = sigma^-2 (I - T) for an LGS
-            for (int k = threadIdx.x; k < rows * N; k += NT) {
-                if (msk[k] >= 0) {
-                    SX[k] = inv * (SX[k] - mx);
-                    SY[k] = inv * (SY[k] - my);
+            if (!W.el) {
+                // C_hat^-1 = (I - T) sigma^-2 (I - T) = sigma^-2 (I - T) for an LGS
+                for (int k = threadIdx.x; k < rows * N; k += NT) {
+                    if (msk[k] >= 0) {
+                        SX[k] = inv * (SX[k] - mx);
+                        SY[k] = inv * (SY[k] - my);
+                    }
+                }
+            } else {
+                // elongated: C_hat^-1 s = sigma^-2 (u - gamma beta (beta . u) + g), u = s
+                // minus its means m, g = (e - K m) / |M| the mean of gamma beta (beta . u)
+                T ex = T(0), ey = T(0);
+#pragma unroll
+                for (int q = 0; q < CL; ++q) {
+                    ex += ttp[4 * q + 2];
+                    ey += ttp[4 * q + 3];
+                }
+                const T g1 = (ex - (el_K(W, 0, T()) * mx + el_K(W, 1, T()) * my)) / T(W.n_active);
+                const T g2 = (ey - (el_K(W, 1, T()) * mx + el_K(W, 2, T()) * my)) / T(W.n_active);
+                for (int k = threadIdx.x; k < rows * N; k += NT) {
+                    if (msk[k] >= 0) {
+                        const int ii = k / N;
+                        T b1, b2, gam;
+                        elong(W, s0 + ii, k - ii * N, b1, b2, gam);
+                        const T ux = SX[k] - mx, uy = SY[k] - my;
+                        const T bu = b1 * ux + b2 * uy;
+                        SX[k] = inv * ((ux - gam * b1 * bu) + g1);
+                        SY[k] = inv * ((uy - gam * b2 * bu) + g2);
+                    }
                 }
             }
         }

@@ -37,6 +37,17 @@ struct WfsInfo {
     int mask_off;   // offset of its N*N slope-index table
     int cmask_off;  // offset of its n_sub^2 coarse-index table (nb > 1)
     double sig2inv; // 1 / sigma^2
+    // LGS spot elongation (Eq. 3): subaperture (i, j) has beta = el_k ((el_x0 + j el_d,
+    // el_x0 + i el_d) - (el_lx, el_ly)) and C_ij^-1 = sigma^-2 (I - gamma beta beta^T),
+    // gamma = el_c / (1 + el_c |beta|^2); el_K = sum of gamma beta beta^T over the
+    // active subapertures
+    int el;
+    double el_k, el_c, el_lx, el_ly, el_x0, el_d;
+    double el_K11, el_K12, el_K22;
+    // the same nine constants in single precision (k, c, lx, ly, x0, d, K11, K12, K22), so
+    // that the FP32 kernels convert nothing (GB300's FP64 pipe, conversions included,
+    // runs at ~1/64 of the FP32 rate)
+    float el_f[9];
 };
 
 struct DmInfo {
@@ -104,6 +115,9 @@ struct HostSetup {
     std::vector<int> qi0y, qi0x;
     std::vector<double> qfy, qfx;
     bool dm_proj_ok = true;             // every DM below every LGS
+    // per sensor: launch position, sodium FWHM, spot FWHM, LGS height (spot elongation)
+    std::vector<double> wfs_lx, wfs_ly, wfs_na_fwhm, wfs_spot_fwhm, wfs_H;
+    double D = 0.0;
     // 1-D wavelet basis functions at shift 0: layer l, level j (1..levels), kind 0/1
     std::vector<double> basis;
     std::vector<int> basis_off;         // MAXL * (MAXN_LEVELS + 1) * 2
@@ -121,6 +135,8 @@ int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
                 const fewha_layer* layers, int n_layers, const fewha_dm* dms, int n_dms,
                 HostSetup& out, std::string& err);
 void db3_taps(double h[6], double g[6]);
+// Spot-elongation constants of every LGS for alpha_eta (Eq. 3); 0 turns them off.
+void set_elongation(HostSetup& s, double alpha_eta);
 // Prior D (Sec. 3.1), one value per coefficient.
 void prior_diag(const HostSetup& s, const std::vector<double>& weights, double r0, double L0,
                 std::vector<double>& D);

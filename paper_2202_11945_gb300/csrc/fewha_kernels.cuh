@@ -186,6 +186,24 @@ __device__ __forceinline__ double warp_total(const double* p, int cnt, const Dot
     return double(s.s) + double(s.c);
 }
 
+// LGS spot elongation of subaperture (i, j) (Eq. 3): beta and gamma, so that
+// C_ij^-1 = sigma^-2 (I - gamma beta beta^T) (Sherman-Morrison).
+__device__ __forceinline__ void elong(const WfsInfo& W, int i, int j, double& b1, double& b2, double& gam) {
+    b1 = W.el_k * ((W.el_x0 + j * W.el_d) - W.el_lx);
+    b2 = W.el_k * ((W.el_x0 + i * W.el_d) - W.el_ly);
+    gam = W.el_c / (1.0 + W.el_c * (b1 * b1 + b2 * b2));
+}
+__device__ __forceinline__ void elong(const WfsInfo& W, int i, int j, float& b1, float& b2, float& gam) {
+    b1 = W.el_f[0] * ((W.el_f[4] + float(j) * W.el_f[5]) - W.el_f[2]);
+    b2 = W.el_f[0] * ((W.el_f[4] + float(i) * W.el_f[5]) - W.el_f[3]);
+    gam = W.el_f[1] / (1.f + W.el_f[1] * (b1 * b1 + b2 * b2));
+}
+// K11, K12, K22 (q = 0, 1, 2) of the sensor in the kernel's precision.
+__device__ __forceinline__ double el_K(const WfsInfo& W, int q, double) {
+    return q == 0 ? W.el_K11 : (q == 1 ? W.el_K12 : W.el_K22);
+}
+__device__ __forceinline__ float el_K(const WfsInfo& W, int q, float) { return W.el_f[6 + q]; }
+
 // Deterministic block sum of two doubles (fixed tree); red holds >= 2*(NWARP+1).
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
     a = warp_sum(a);
@@ -702,17 +720,38 @@ __global__ void __launch_bounds__(BLK) k_sensor(const Desc<T> d, const SensorArg
     // T removing the mean x- and y-slope over the active set (Sec. 3.2); NGS sigma^-2.
     if (WEIGHT && W.nb == 1) {
         if (W.lgs) {
-            double tx = 0.0, ty = 0.0;
+            double tx = 0.0, ty = 0.0, ex = 0.0, ey = 0.0;
             for (int k = threadIdx.x; k < NN; k += BLK) {
                 tx += double(SX[k]);
                 ty += double(SY[k]);
+                if (W.el && sidx[k] >= 0) {
+                    T b1, b2, gam;
+                    elong(W, k / N, k % N, b1, b2, gam);
+                    const T bs = b1 * SX[k] + b2 * SY[k];
+                    ex += double(gam * b1 * bs);
+                    ey += double(gam * b2 * bs);
+                }
             }
             block_sum2(tx, ty, red);
+            if (W.el) block_sum2(ex, ey, red);
             const T mx = T(tx / W.n_active), my = T(ty / W.n_active);
+            // elongated: C_hat^-1 s = sigma^-2 (u - gamma beta (beta . u) + g), u = s minus
+            // its means, g = (e - K m) / |M| the mean of gamma beta (beta . u)
+            const T g1 = T((ex - (W.el_K11 * double(mx) + W.el_K12 * double(my))) / W.n_active);
+            const T g2 = T((ey - (W.el_K12 * double(mx) + W.el_K22 * double(my))) / W.n_active);
             for (int k = threadIdx.x; k < NN; k += BLK) {
                 if (sidx[k] >= 0) {
-                    SX[k] = inv * (SX[k] - mx);
-                    SY[k] = inv * (SY[k] - my);
+                    const T ux = SX[k] - mx, uy = SY[k] - my;
+                    if (W.el) {
+                        T b1, b2, gam;
+                        elong(W, k / N, k % N, b1, b2, gam);
+                        const T bu = b1 * ux + b2 * uy;
+                        SX[k] = inv * ((ux - gam * b1 * bu) + g1);
+                        SY[k] = inv * ((uy - gam * b2 * bu) + g2);
+                    } else {
+                        SX[k] = inv * ux;
+                        SY[k] = inv * uy;
+                    }
                 }
             }
         } else {
@@ -1440,7 +1479,7 @@ __global__ void __launch_bounds__(128) k_jdiag(const Desc<T> d, const DiagArgs a
         const int* sidx = d.sidx + W.mask_off;
         double contrib = 0.0;
         if (W.nb == 1) {
-            double s2 = 0.0, tx = 0.0, ty = 0.0;
+            double s2 = 0.0, tx = 0.0, ty = 0.0, E = 0.0, e1 = 0.0, e2 = 0.0;
             if (wi > 0 && wj > 0) {
                 for (int t = lane; t < wi * wj; t += 32) {
                     const int i = i0 + t / wj, jj = j0 + t % wj;
@@ -1451,6 +1490,14 @@ __global__ void __launch_bounds__(128) k_jdiag(const Desc<T> d, const DiagArgs a
                     s2 += vx * vx + vy * vy;
                     tx += vx;
                     ty += vy;
+                    if (W.el) {
+                        double b1, b2, gam;
+                        elong(W, i, jj, b1, b2, gam);
+                        const double bv = b1 * vx + b2 * vy;
+                        E += gam * bv * bv;
+                        e1 += gam * b1 * bv;
+                        e2 += gam * b2 * bv;
+                    }
                 }
             }
             s2 = warp_sum(s2);
@@ -1458,6 +1505,16 @@ __global__ void __launch_bounds__(128) k_jdiag(const Desc<T> d, const DiagArgs a
             ty = warp_sum(ty);
             contrib = s2;
             if (W.lgs) contrib -= (tx * tx + ty * ty) / W.n_active;
+            if (W.el) {
+                // minus the elongation term: sum of gamma (beta . u)^2 over the mask, u the
+                // slopes without their means m = (tx, ty) / |M|: E - 2 m . e + m^T K m
+                E = warp_sum(E);
+                e1 = warp_sum(e1);
+                e2 = warp_sum(e2);
+                const double mx = tx / W.n_active, my = ty / W.n_active;
+                contrib -= E - 2.0 * (mx * e1 + my * e2) +
+                           (W.el_K11 * mx * mx + 2.0 * W.el_K12 * mx * my + W.el_K22 * my * my);
+            }
         } else {
             const int ns = W.n_sub, nb = W.nb;
             for (int blk = 0; blk < ns * ns; ++blk) {

@@ -15,6 +15,37 @@
 
 namespace fewha {
 
+void set_elongation(HostSetup& s, double alpha_eta) {
+    for (size_t g = 0; g < s.G.size(); ++g) {
+        WfsInfo& W = s.G[g];
+        W.el = 0;
+        W.el_k = W.el_c = W.el_lx = W.el_ly = W.el_x0 = W.el_d = 0.0;
+        W.el_K11 = W.el_K12 = W.el_K22 = 0.0;
+        for (float& f : W.el_f) f = 0.f;
+        if (!W.lgs || W.nb != 1 || !(alpha_eta > 0) || !(s.wfs_na_fwhm[g] > 0) || !(s.wfs_spot_fwhm[g] > 0))
+            continue;
+        W.el = 1;
+        W.el_k = s.wfs_na_fwhm[g] / (s.wfs_H[g] * s.wfs_H[g]);
+        W.el_c = (alpha_eta / s.wfs_spot_fwhm[g]) * (alpha_eta / s.wfs_spot_fwhm[g]);
+        W.el_lx = s.wfs_lx[g];
+        W.el_ly = s.wfs_ly[g];
+        W.el_d = s.D / W.N;
+        W.el_x0 = -s.D / 2 + 0.5 * W.el_d;
+        for (int i = 0; i < W.N; ++i)
+            for (int j = 0; j < W.N; ++j) {
+                if (s.sidx[W.mask_off + i * W.N + j] < 0) continue;
+                const double b1 = W.el_k * (W.el_x0 + j * W.el_d - W.el_lx);
+                const double b2 = W.el_k * (W.el_x0 + i * W.el_d - W.el_ly);
+                const double gam = W.el_c / (1.0 + W.el_c * (b1 * b1 + b2 * b2));
+                W.el_K11 += gam * b1 * b1;
+                W.el_K12 += gam * b1 * b2;
+                W.el_K22 += gam * b2 * b2;
+            }
+        const double c9[9] = {W.el_k, W.el_c, W.el_lx, W.el_ly, W.el_x0, W.el_d, W.el_K11, W.el_K12, W.el_K22};
+        for (int q = 0; q < 9; ++q) W.el_f[q] = static_cast<float>(c9[q]);
+    }
+}
+
 void db3_taps(double h[6], double g[6]) {
     // Daubechies' N = 3 scaling filter in closed form (sum h = sqrt 2), Sec. 3.1.
     const double s10 = std::sqrt(10.0);
@@ -117,6 +148,7 @@ int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
     }
     db3_taps(s.taps_h, s.taps_g);
     const double D = tel.D;
+    s.D = D;
     // layers
     int off = 0;
     s.max_n = 0;
@@ -222,6 +254,11 @@ int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
         }
         s.G.push_back(wi);
         s.wfs_sigma.push_back(W.sigma);
+        s.wfs_lx.push_back(W.launch_x);
+        s.wfs_ly.push_back(W.launch_y);
+        s.wfs_na_fwhm.push_back(W.is_lgs ? W.na_fwhm : 0.0);
+        s.wfs_spot_fwhm.push_back(W.is_lgs ? W.spot_fwhm : 0.0);
+        s.wfs_H.push_back(W.H);
     }
     s.n_s = soff;
     s.n_nodes = noff;

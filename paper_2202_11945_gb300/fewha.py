@@ -44,7 +44,9 @@ class Telescope(ctypes.Structure):
 class Wfs(ctypes.Structure):
     _fields_ = [("n_sub", ctypes.c_int), ("nb", ctypes.c_int), ("is_lgs", ctypes.c_int),
                 ("theta_x", ctypes.c_double), ("theta_y", ctypes.c_double),
-                ("H", ctypes.c_double), ("sigma", ctypes.c_double)]
+                ("H", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("launch_x", ctypes.c_double), ("launch_y", ctypes.c_double),
+                ("na_fwhm", ctypes.c_double), ("spot_fwhm", ctypes.c_double)]
 
 
 class Layer(ctypes.Structure):
@@ -59,7 +61,8 @@ class Dm(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("gain", ctypes.c_double),
                 ("r0", ctypes.c_double), ("L0", ctypes.c_double), ("iters", ctypes.c_int),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("alpha_eta", ctypes.c_double)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -156,13 +159,14 @@ def structs_from_workload(wl, precision=32, flags=FLAG_GRAPH):
     tel = Telescope(wl["D"], wl["obs"])
     wfs = (Wfs * len(wl["wfs"]))(*[
         Wfs(w["n_sub"], w["nb"], 1 if w["lgs"] else 0, w["theta"][0], w["theta"][1],
-            w["H"] if w["lgs"] else 0.0, w["sigma"]) for w in wl["wfs"]])
+            w["H"] if w["lgs"] else 0.0, w["sigma"], *w.get("launch", (0.0, 0.0)),
+            w.get("na_fwhm", 0.0), w.get("spot_fwhm", 0.0)) for w in wl["wfs"]])
     layers = (Layer * len(wl["layers"]))(*[
         Layer(L["h"], L["w"], L["delta"], L["n"], L["levels"]) for L in wl["layers"]])
     dms = (Dm * len(wl["dms"]))(*[Dm(m["h"], m["spacing"], m["n_act"]) for m in wl["dms"]])
     p = wl["params"]
     params = Params(p["alpha"], p.get("tau", 0.0), p.get("gain", 1.0), p["r0"], p["L0"],
-                    p["iters"], precision, flags)
+                    p["iters"], precision, flags, p.get("alpha_eta", 0.0))
     return tel, wfs, layers, dms, params
 
 
@@ -306,7 +310,7 @@ class Reconstructor:
     def reset(self, stream=None):
         self._check(self.L.fewha_reset(self.h, _stream(stream)))
 
-    def update_params(self, alpha=None, tau=None, gain=None, r0=None, L0=None, iters=None,
+    def update_params(self, alpha=None, tau=None, gain=None, r0=None, L0=None, iters=None, alpha_eta=None,
                       cn2_weights=None, sigmas=None, graph=None, warm_residual=None, augmented=None,
                       closed_loop=None):
         tel, wfs, layers, dms, p = self._structs
@@ -322,6 +326,8 @@ class Reconstructor:
             p.L0 = L0
         if iters is not None:
             p.iters = iters
+        if alpha_eta is not None:
+            p.alpha_eta = alpha_eta
         if graph is not None:
             p.flags = (p.flags & ~FLAG_GRAPH) | (FLAG_GRAPH if graph else 0)
         if warm_residual is not None:

@@ -10,7 +10,8 @@ from tests.gpu_common import TOL_FRAME, recon, rel_l2, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 SEQ = [("tiny_scao", 64, 20), ("tiny_scao", 32, 20), ("tiny_mcao", 64, 10), ("tiny_mcao", 32, 10),
-       ("maory", 32, 10), ("maory", 64, 3)]
+       ("maory", 32, 10), ("maory", 64, 3), ("tiny_mcao_elongated", 64, 8),
+       ("tiny_mcao_elongated", 32, 8), ("paper_mcao", 32, 4), ("paper_mcao", 64, 2)]
 
 _slopes = {}
 

@@ -9,7 +9,8 @@ from tests.gpu_common import TOL_OP, assert_close, geometry, recon, to_dev, to_n
 pytestmark = pytest.mark.gpu
 
 CASES = [("tiny_scao", 64), ("tiny_scao", 32), ("tiny_mcao", 64), ("tiny_mcao", 32),
-         ("maory", 32), ("maory", 64)]
+         ("maory", 32), ("maory", 64), ("tiny_mcao_elongated", 64), ("tiny_mcao_elongated", 32),
+         ("paper_mcao", 32)]
 
 
 @pytest.fixture(scope="module", params=CASES, ids=lambda c: "%s-fp%d" % c)
