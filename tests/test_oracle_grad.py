@@ -137,3 +137,54 @@ def test_prior_scales_inversely_with_the_weight():
     rest = np.ones(geo.n_c, bool)
     rest[sl] = False
     assert np.array_equal(D2[rest], D1[rest])
+
+
+# -- reverse mode through the fixed-iteration frame -----------------------------------
+
+
+@pytest.mark.parametrize("name,k", [("tiny_scao", 1), ("tiny_scao", 4), ("tiny_mcao", 4)])
+def test_unrolled_vjp_matches_central_differences(name, k):
+    """The reverse pass against central differences of the forward map (h = 1e-4 of the
+    slopes' scale) in seeded random directions, warm start c0 != 0."""
+    wl = synth.workload_by_name(name)
+    geo = O.Geometry(wl)
+    D = O.prior_diag(geo)
+    s = synth.simulate_slopes(wl, 1)
+    rng = np.random.default_rng(11)
+    c0 = 0.1 * rng.standard_normal(geo.n_c)
+    g_a = rng.standard_normal(geo.n_a)
+    a, _, tape = G.unrolled_frame(geo, s, c0, k, D)
+    gs = G.unrolled_frame_vjp(geo, tape, g_a)
+
+    def J(x):
+        return float(g_a @ G.unrolled_frame(geo, x, c0, k, D)[0])
+
+    h = 1e-4 * np.abs(s).max()
+    for _ in range(3):
+        v = rng.standard_normal(geo.n_s)
+        fd = (J(s + h * v) - J(s - h * v)) / (2 * h)
+        assert abs(fd - gs @ v) <= 1e-6 * (abs(fd) + np.linalg.norm(gs) * np.linalg.norm(v) * 1e-3), (fd, gs @ v)
+
+
+def test_unrolled_vjp_euler_identity():
+    """From c0 = 0 every PCG iterate is homogeneous of degree one in b (alpha, beta are
+    ratios of quadratic forms), so s . dJ/ds = J(s) exactly."""
+    wl = synth.tiny_mcao()
+    geo = O.Geometry(wl)
+    s = synth.simulate_slopes(wl, 2)
+    g_a = np.random.default_rng(4).standard_normal(geo.n_a)
+    a, _, tape = G.unrolled_frame(geo, s, np.zeros(geo.n_c), 4)
+    gs = G.unrolled_frame_vjp(geo, tape, g_a)
+    assert abs(gs @ s - g_a @ a) <= 1e-7 * abs(g_a @ a)
+
+
+def test_unrolled_frame_is_the_oracle_frame():
+    """The differentiated map is the frame of Algorithm 1 (explicit r0, gain 1)."""
+    wl = synth.tiny_mcao()
+    ref = O.Reconstructor(wl)
+    s0, s1 = synth.simulate_slopes(wl, 0), synth.simulate_slopes(wl, 1)
+    ref.frame(s0)
+    c0 = ref.c.copy()
+    a = ref.frame(s1)
+    a2, c2, _ = G.unrolled_frame(ref.geo, s1, c0, wl["params"]["iters"])
+    np.testing.assert_allclose(a2, a, rtol=0, atol=1e-12 * np.abs(a).max())
