@@ -505,6 +505,38 @@ def time_paper_geometry(flush, steps, parity=True):
     return out
 
 
+def time_unrolled(wl, S_np, reps=10, parity=True):
+    """Reverse mode through the fixed-iteration MAORY frame (fewha_frame_vjp): wall time of
+    forward + reverse per call (synchronous), FP32 and FP64, and the FP32 gradient against
+    the oracle's reverse pass on one frame."""
+    from paper_2202_11945_gb300 import Reconstructor
+    rng = np.random.default_rng(21)
+    out = {"workload": wl["name"], "iters": wl["params"]["iters"]}
+    for prec, dt in ((32, torch.float32), (64, torch.float64)):
+        R = Reconstructor(wl, precision=prec, graph=False)
+        s = torch.as_tensor(S_np[1], dtype=dt, device="cuda")
+        c0 = torch.zeros(R.n_coeffs, dtype=dt, device="cuda")
+        g = torch.as_tensor(rng.standard_normal(R.n_act), dtype=dt, device="cuda")
+        R.frame_vjp(s, c0, g)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            R.frame_vjp(s, c0, g)
+        torch.cuda.synchronize()
+        out["fp%d_ms" % prec] = 1e3 * (time.perf_counter() - t0) / reps
+        if parity and prec == 32:
+            from oracle import fewha_grad as G
+            import oracle as O
+            geo = O.Geometry(wl)
+            a_ref, _, tape = G.unrolled_frame(geo, S_np[1], np.zeros(geo.n_c), wl["params"]["iters"])
+            gs_ref = G.unrolled_frame_vjp(geo, tape, g.double().cpu().numpy())
+            _, gs = R.frame_vjp(s, c0, g)
+            gs = gs.double().cpu().numpy()
+            out["fp32_grad_rel_l2_vs_oracle"] = float(np.linalg.norm(gs - gs_ref) / np.linalg.norm(gs_ref))
+        R.close()
+    return out
+
+
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
     the same sequence (explicit initial residual), and the oracle's own frame rate."""
@@ -635,6 +667,7 @@ def main():
               if args.aug_steps > 0 else None)
     paper = (time_paper_geometry(flush, args.aug_steps, parity=(rank == 0 and world == 1))
              if args.aug_steps > 0 else None)
+    unrolled = time_unrolled(wl, S_np, parity=(rank == 0 and world == 1)) if args.backward_frames > 0 else None
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")
@@ -684,6 +717,7 @@ def main():
             "augmented": augmented,
             "closed_loop": closed,
             "paper_geometry": paper,
+            "unrolled_backward": unrolled,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

@@ -225,6 +225,19 @@ int fewha_set_state(fewha_handle* h, const void* d_c, const void* d_a_prev, void
  * fixed iteration count left the frame from M c = b.  Stream-ordered. */
 int fewha_get_residual(fewha_handle* h, void* d_r, void* d_b, void* stream);
 
+/* Reverse mode through the fixed-iteration frame (a build addition; the paper has no
+ * gradients).  The map is the frame of Algorithm 1 started from the warm start d_c0
+ * (n_coeffs) with the explicit initial residual r0 = b(s) - M c0, params.iters PCG
+ * iterations (Sec. 3.3) and the fit, without the control law: a~ = F W^T c_k(s), written
+ * to d_dm_out (n_act, nullable).  With d_grad_dm = dJ/da~ (n_act; NULL: forward only) it
+ * writes dJ/ds (n_slopes) to d_grad_slopes by running the recurrence backwards, the
+ * adjoint of every statement in reverse order.  Device pointers of the handle's element
+ * type.  The handle's warm state is untouched; the warm-residual, augmented and
+ * closed-loop flags do not apply.  FEWHA_ERR_NONFINITE if the recurrence stopped
+ * (r.z or p.q vanished).  Synchronous on `stream`. */
+int fewha_frame_vjp(fewha_handle* h, const void* d_slopes, const void* d_c0, const void* d_grad_dm,
+                    void* d_dm_out, void* d_grad_slopes, void* stream);
+
 /* Real-time frame loop (Algorithm 1 run frame after frame, open loop): frame k reads
  * the host slopes h_slopes + k * n_slopes, is warm-started from frame k - 1 (the
  * handle's internal state, so frame 0 continues from whatever the handle holds), and

@@ -4,7 +4,9 @@ Both run the library's CUDA kernels in forward and backward (no PyTorch arithmet
 path): the forward model s = Gamma P phi with its adjoint kernels, and the converged
 reconstruction a~ = F W^T M^-1 b(s) whose backward is a second PCG on the symmetric M
 (fewha_backward), giving gradients with respect to the slopes, alpha and the layer Cn2
-weights.
+weights; and the fixed-iteration frame a~ = F W^T c_k(s) from a warm start, whose backward
+runs the PCG recurrence in reverse (fewha_frame_vjp), giving the gradient with respect to
+the slopes of the map the real-time loop runs.
 """
 
 import torch
@@ -61,3 +63,29 @@ def reconstruct(recon, slopes, alpha, cn2, tol=None, max_iters=20000):
 def forward_model(recon, phi):
     """Differentiable s = Gamma P phi (see ForwardModel)."""
     return ForwardModel.apply(phi, recon)
+
+
+class UnrolledFrame(torch.autograd.Function):
+    """a~ = F W^T c_k(s): the frame's `iters` PCG iterations from the warm start c0 with the
+    explicit initial residual (no control law); backward by reverse mode through the
+    recurrence.  Gradients flow to the slopes (c0 is a constant)."""
+
+    @staticmethod
+    def forward(ctx, slopes, c0, recon):
+        s = slopes.detach().contiguous()
+        c = c0.detach().contiguous()
+        a, _ = recon.frame_vjp(s, c)
+        ctx.recon = recon
+        ctx.save_for_backward(s, c)
+        return a
+
+    @staticmethod
+    def backward(ctx, g):
+        s, c = ctx.saved_tensors
+        _, gs = ctx.recon.frame_vjp(s, c, g.detach().contiguous())
+        return gs, None, None
+
+
+def frame(recon, slopes, c0):
+    """Differentiable fixed-iteration frame (see UnrolledFrame)."""
+    return UnrolledFrame.apply(slopes, c0, recon)

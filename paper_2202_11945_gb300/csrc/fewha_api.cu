@@ -84,6 +84,9 @@ struct fewha_handle {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t gaug[4] = {};     // augmented frames: [2 * set + (directions present)]
+    // reverse pass through the fixed-iteration frame: its recorded vectors (allocated on use)
+    void* vjp = nullptr;
+    size_t vjp_cap = 0;
     const void* g_s = nullptr;
     void* g_x = nullptr;
     void* g_dm = nullptr;
@@ -1278,6 +1281,151 @@ int backward(fewha_handle* H, const T* g_a, T* g_s, double* g_alpha, double* g_w
     return FEWHA_OK;
 }
 
+// Reverse mode through the fixed-iteration frame: the forward recurrence from c0 with
+// every vector kept, then each statement's adjoint in reverse order (M and J^-1 are
+// symmetric).  Scalars (rho, sigma, alpha, beta and their adjoints) live on the host in
+// double; each reverse iteration reads three inner products back.  Synchronous.
+template <class T>
+int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* g_s, cudaStream_t st) {
+    const Desc<T> d = make_desc<T>(H);
+    const int k = H->params.iters, n = d.n_c;
+    const size_t ld = (static_cast<size_t>(n) + 63) & ~static_cast<size_t>(63);
+    const size_t need = (4 * static_cast<size_t>(k + 1) + 8) * ld;
+    if (H->vjp_cap < need) {
+        if (H->vjp) {
+            cudaFree(H->vjp);
+            H->allocs.erase(std::remove(H->allocs.begin(), H->allocs.end(), H->vjp), H->allocs.end());
+            H->vjp = nullptr;
+        }
+        int rc0;
+        if ((rc0 = talloc(H, &H->vjp, need))) return rc0;
+        H->vjp_cap = need;
+    }
+    T* base = static_cast<T*>(H->vjp);
+    T* R = base;                                   // r_0 .. r_k
+    T* Z = R + (k + 1) * ld;                       // z_0 .. z_k
+    T* P = Z + (k + 1) * ld;                       // p_0 .. p_(k-1) (p_k unused)
+    T* Q = P + (k + 1) * ld;                       // q_0 .. q_(k-1)
+    T* c = Q + (k + 1) * ld;
+    T* scratch = c + ld;
+    T* cbar = scratch + ld;
+    T* rbar = cbar + ld;
+    T* zbar = rbar + ld;
+    T* pbar = zbar + ld;
+    T* pbi = pbar + ld;
+    T* qbar = pbi + ld;
+    const T* Jinv = static_cast<const T*>(H->Jinv);
+    const int gl = std::min(4 * 152, static_cast<int>((n + PBLK - 1) / PBLK));
+    auto lin = [&](double a, const T* x, double b, const T* y, double cc, const T* u, const T* v, T* out) {
+        k_lin<T><<<gl, PBLK, 0, st>>>(n, a, x, b, y, cc, u, v, out);
+        return cudaGetLastError();
+    };
+    int rc;
+    // ---- forward: b, r0 = b - M c0, then the iterations, every vector kept -------------
+    if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
+    CK(cudaMemcpyAsync(c, c0, n * sizeof(T), cudaMemcpyDeviceToDevice, st), "vjp c0");
+    if ((rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
+    VecArgs<T> v = vec_args<T>(H, c, 0);
+    v.r = R;
+    v.z = Z;
+    v.p = P;
+    v.b_prev = scratch;                            // the handle's b_prev stays untouched
+    if ((rc = launch_vec<T, V_INIT>(H, n, v, st))) return rc;
+    AugArgs<T> a{};
+    a.m = 0;
+    for (int i = 0; i < k; ++i) {
+        if (i > 0) {
+            VecArgs<T> w = vec_args<T>(H, c, i);
+            w.z = Z + i * ld;
+            a.pnew = P + i * ld;
+            a.pold = P + (i - 1) * ld;
+            if ((rc = launch_aug<T, V_PROJ>(H, n, w, a, st))) return rc;
+        }
+        if ((rc = enqueue_apply<T>(H, d, P + i * ld, Q + i * ld, i, false, st))) return rc;
+        CK(cudaMemcpyAsync(R + (i + 1) * ld, R + i * ld, n * sizeof(T), cudaMemcpyDeviceToDevice, st), "vjp r");
+        VecArgs<T> w = vec_args<T>(H, c, i);
+        w.p = P + i * ld;
+        w.q = Q + i * ld;
+        w.r = R + (i + 1) * ld;
+        w.z = Z + (i + 1) * ld;
+        if ((rc = launch_vec<T, V_UPDATE>(H, n, w, st))) return rc;
+    }
+    if (dm && (rc = enqueue_fit<T>(H, d, c, dm, false, st))) return rc;
+    if (!g_a) {
+        CK(cudaStreamSynchronize(st), "vjp forward");
+        return FEWHA_OK;
+    }
+    std::vector<double> rho(k + 1), sigma(k + 1);
+    CK(cudaMemcpyAsync(rho.data(), H->rztot, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st), "vjp rho");
+    if (k > 0)
+        CK(cudaMemcpyAsync(sigma.data(), H->pqtot, k * sizeof(double), cudaMemcpyDeviceToHost, st), "vjp sigma");
+    CK(cudaStreamSynchronize(st), "vjp scalars");
+    for (int i = 0; i < k; ++i)
+        if (!(sigma[i] > 0.0) || rho[i] == 0.0)
+            return fail(H, FEWHA_ERR_NONFINITE, "the frame's recurrence stopped (r.z or p.q vanished)");
+    // ---- reverse ------------------------------------------------------------------------
+    double* dots = H->gdot;                        // MAXL + 1 doubles of device scratch
+    double hd[2];
+    if ((rc = launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, g_a, cbar), st))) return rc;
+    CK(cudaMemsetAsync(rbar, 0, n * sizeof(T), st), "vjp zero");
+    CK(cudaMemsetAsync(zbar, 0, n * sizeof(T), st), "vjp zero");
+    CK(cudaMemsetAsync(pbar, 0, n * sizeof(T), st), "vjp zero");
+    double rhobar = 0.0;
+    for (int i = k - 1; i >= 0; --i) {
+        const T* p = P + i * ld;
+        const T* q = Q + i * ld;
+        const T* r1 = R + (i + 1) * ld;
+        const T* z1 = Z + (i + 1) * ld;
+        const double alpha = rho[i] / sigma[i], beta = rho[i + 1] / rho[i];
+        // p_(i+1) = z_(i+1) + beta_i p_i
+        CK(lin(1.0, zbar, 1.0, pbar, 0.0, nullptr, nullptr, zbar), "vjp lin");
+        k_vdot<T><<<1, PBLK, 0, st>>>(n, pbar, p, dots);
+        CK(cudaGetLastError(), "vjp dot");
+        CK(cudaMemcpyAsync(hd, dots, sizeof(double), cudaMemcpyDeviceToHost, st), "vjp dot");
+        CK(cudaStreamSynchronize(st), "vjp dot");
+        const double betabar = hd[0];
+        CK(lin(beta, pbar, 0.0, nullptr, 0.0, nullptr, nullptr, pbi), "vjp lin");
+        // beta_i = rho_(i+1) / rho_i
+        rhobar += betabar / rho[i];
+        double rhobar_i = -betabar * rho[i + 1] / (rho[i] * rho[i]);
+        // rho_(i+1) = r_(i+1) . z_(i+1);  z_(i+1) = J^-1 r_(i+1)
+        CK(lin(1.0, rbar, rhobar, z1, 0.0, nullptr, nullptr, rbar), "vjp lin");
+        CK(lin(1.0, zbar, rhobar, r1, 0.0, nullptr, nullptr, zbar), "vjp lin");
+        CK(lin(1.0, rbar, 0.0, nullptr, 1.0, Jinv, zbar, rbar), "vjp lin");
+        // r_(i+1) = r_i - alpha_i q_i;  c_(i+1) = c_i + alpha_i p_i
+        k_vdot<T><<<1, PBLK, 0, st>>>(n, rbar, q, dots);
+        k_vdot<T><<<1, PBLK, 0, st>>>(n, cbar, p, dots + 1);
+        CK(cudaGetLastError(), "vjp dot");
+        CK(cudaMemcpyAsync(hd, dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "vjp dot");
+        CK(cudaStreamSynchronize(st), "vjp dot");
+        const double abar = -hd[0] + hd[1];
+        // alpha_i = rho_i / sigma_i;  sigma_i = p_i . q_i
+        rhobar_i += abar / sigma[i];
+        const double sigmabar = -abar * rho[i] / (sigma[i] * sigma[i]);
+        CK(lin(-alpha, rbar, sigmabar, p, 0.0, nullptr, nullptr, qbar), "vjp lin");
+        CK(lin(1.0, pbi, alpha, cbar, 0.0, nullptr, nullptr, pbi), "vjp lin");
+        CK(lin(1.0, pbi, sigmabar, q, 0.0, nullptr, nullptr, pbi), "vjp lin");
+        // q_i = M p_i
+        if ((rc = enqueue_apply<T>(H, d, qbar, scratch, PQ_SCRATCH_SLOT, false, st))) return rc;
+        CK(lin(1.0, pbi, 1.0, scratch, 0.0, nullptr, nullptr, pbar), "vjp lin");
+        rhobar = rhobar_i;
+        CK(cudaMemsetAsync(zbar, 0, n * sizeof(T), st), "vjp zero");
+    }
+    // p_0 = z_0, rho_0 = r_0 . z_0, z_0 = J^-1 r_0, r_0 = b - M c0: b_bar = r_bar_0
+    CK(lin(1.0, zbar, 1.0, pbar, 0.0, nullptr, nullptr, zbar), "vjp lin");
+    CK(lin(1.0, rbar, rhobar, Z, 0.0, nullptr, nullptr, rbar), "vjp lin");
+    CK(lin(1.0, zbar, rhobar, R, 0.0, nullptr, nullptr, zbar), "vjp lin");
+    CK(lin(1.0, rbar, 0.0, nullptr, 1.0, Jinv, zbar, rbar), "vjp lin");
+    // dJ/ds = C_hat^-1 Gamma P W^T b_bar
+    T* phi = static_cast<T*>(H->phi);
+    T* st_s = static_cast<T*>(H->s_tmp);
+    if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, rbar, phi), st))) return rc;
+    if ((rc = launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, phi, st_s, st))) return rc;
+    if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, st_s, g_s, st))) return rc;
+    CK(cudaStreamSynchronize(st), "vjp");
+    return FEWHA_OK;
+}
+
 // ---------------------------------------------------------------- batched frames
 int bfail(fewha_batch* B, int code, const std::string& msg) {
     if (B) B->err = msg;
@@ -2191,6 +2339,20 @@ int fewha_backward(fewha_handle* H, const void* g_dm, void* g_s, double* g_alpha
                ? backward<float>(H, static_cast<const float*>(g_dm), static_cast<float*>(g_s), g_alpha, g_cn2, st)
                : backward<double>(H, static_cast<const double*>(g_dm), static_cast<double*>(g_s), g_alpha, g_cn2,
                                   st);
+}
+
+int fewha_frame_vjp(fewha_handle* H, const void* s, const void* c0, const void* g_dm, void* dm, void* g_s,
+                    void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!s || !c0 || (g_dm && !g_s)) return fail(H, FEWHA_ERR_INVALID_ARG, "null slopes, warm start or gradient output");
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32
+               ? frame_vjp<float>(H, static_cast<const float*>(s), static_cast<const float*>(c0),
+                                  static_cast<const float*>(g_dm), static_cast<float*>(dm), static_cast<float*>(g_s), st)
+               : frame_vjp<double>(H, static_cast<const double*>(s), static_cast<const double*>(c0),
+                                   static_cast<const double*>(g_dm), static_cast<double*>(dm),
+                                   static_cast<double*>(g_s), st);
 }
 
 int fewha_check_input(fewha_handle* H, int* nonfinite, void* stream) {

@@ -1369,6 +1369,38 @@ __global__ void __launch_bounds__(PBLK) k_layer_dots(__grid_constant__ const Des
     }
 }
 
+// Vector kernels of the reverse pass through the fixed-iteration frame (a build addition):
+// out = a x + b y + c (u o v) elementwise, a null pointer dropping its term (out may be x
+// or y); and x . y in double, one CTA, fixed order.
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_lin(const int n, const double a, const T* x, const double b, const T* y,
+                                              const double c, const T* u, const T* v, T* out) {
+    const T ta = T(a), tb = T(b), tc = T(c);
+    for (int i = blockIdx.x * PBLK + threadIdx.x; i < n; i += gridDim.x * PBLK) {
+        T acc = T(0);
+        if (x) acc = ta * x[i];
+        if (y) acc += tb * y[i];
+        if (u) acc += tc * (u[i] * v[i]);
+        out[i] = acc;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_vdot(const int n, const T* __restrict__ x, const T* __restrict__ y,
+                                               double* __restrict__ out) {
+    __shared__ double part[PBLK];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += PBLK) acc += double(x[i]) * double(y[i]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < PBLK; k += 32) s += part[k];
+        s = warp_sum(s);
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+
 // b^T J^-1 b in double, one CTA, fixed order (the reference of a warm-started solve's
 // relative residual).
 template <class T>

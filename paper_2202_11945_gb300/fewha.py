@@ -82,7 +82,7 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_batch_last_error", "fewha_batch_set_config", "fewha_batch_get_config",
            "fewha_batch_reconstruct", "fewha_batch_autotune", "fewha_reconstruct_batched",
            "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state", "fewha_solve",
-           "fewha_reconstruct_converged", "fewha_backward", "fewha_get_residual"] + _OPS
+           "fewha_reconstruct_converged", "fewha_backward", "fewha_get_residual", "fewha_frame_vjp"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -128,6 +128,7 @@ def lib():
     L.fewha_get_state.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_set_state.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_get_residual.argtypes = [_VP, _VP, _VP, _VP]
+    L.fewha_frame_vjp.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
     for name in ["fewha_run_loop", "fewha_run_loop_f64"]:
         getattr(L, name).argtypes = [_VP, _VP, ctypes.c_int, _VP, ctypes.c_double, _VP, _VP,
                                      ctypes.POINTER(ctypes.c_int), _VP]
@@ -301,6 +302,20 @@ class Reconstructor:
         self._check(self.L.fewha_get_residual(self.h, self._dev(r, self.n_coeffs, "r"),
                                               self._dev(b, self.n_coeffs, "b"), _stream(stream)))
         return r, b
+
+    def frame_vjp(self, slopes, c0, grad_dm=None, stream=None):
+        """The fixed-iteration frame from the warm start c0 (explicit initial residual, no
+        control law) and, with grad_dm = dJ/da~, dJ/dslopes by reverse mode through the
+        recurrence.  Returns (a~, dJ/dslopes or None)."""
+        a = self._new(self.n_act)
+        g = self._new(self.n_slopes) if grad_dm is not None else None
+        gp = self._dev(grad_dm, self.n_act, "grad_dm") if grad_dm is not None else None
+        self._check(self.L.fewha_frame_vjp(self.h, self._dev(slopes, self.n_slopes, "slopes"),
+                                           self._dev(c0, self.n_coeffs, "c0"), gp,
+                                           self._dev(a, self.n_act, "dm"),
+                                           self._dev(g, self.n_slopes, "grad") if g is not None else None,
+                                           _stream(stream)))
+        return a, g
 
     def check_input(self, stream=None):
         flag = ctypes.c_int(0)
