@@ -15,7 +15,7 @@ Paper passages followed
   Sec. 3.4      Algorithm 1 (RHS, initial residual, PCG, fitting, control law)
   Sec. 4.1      Tables 2 and 3 (layer grids, DM actuators, bilinear mirror shape)
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
   R1  the printed y-slope formula is garbled; the y-slope is the x-slope's mirror:
       s^y_ij = ((phi_{i+1,j} - phi_{i,j}) + (phi_{i+1,j+1} - phi_{i,j+1})) / 2
   R2  slopes are phase differences across a subaperture (rad), no 1/d factor

@@ -5,7 +5,7 @@ import torch
 import oracle as O
 import synth
 
-# Tolerances, from the arithmetic:
+# Tolerances, derived from the arithmetic:
 #  FP64 operators: a handful of roundings per output, no cancellation amplification -> 1e-12
 #  FP32 operators: up to ~100 roundings of 6e-8 per output (7 wavelet levels x 12 terms,
 #                  9 layers x 4-point stencils) -> 1e-5 of the largest reference entry
