@@ -560,8 +560,8 @@ def run_reference(args, world, rank):
     wl = synth.maory()
     S_np = make_inputs(wl)
     ref = O.Reconstructor(wl)
-    # a bounded sample: at most 2 warm-up and 60 timed frames (~0.3-0.5 s each)
-    warm = min(args.warmup, 2)
+    # a bounded sample: at most 10 warm-up and 60 timed frames (~0.3-0.5 s each)
+    warm = min(args.warmup, 10)
     steps = min(args.steps, 60)
     for k in range(warm):
         ref.frame(S_np[k % len(S_np)])
