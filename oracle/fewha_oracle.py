@@ -64,6 +64,12 @@ Readings where the paper is silent or garbled:
       is sigma^-2 (I - gamma beta beta^T), gamma = c / (1 + c |beta|^2), c = alpha_eta^2
       / f^2, and C_hat^-1 = (I - T) C^-1 (I - T) no longer collapses to sigma^-2 (I - T).
       Elongation is on for an LGS when alpha_eta, FWHM and f are all > 0.
+  R30 least-squares DM fitting (the "additional minimization problem" of Sec. 4.1): the
+      commands minimise sum_k w_k ||Pi (A_k a - L_k phi)||^2 + eps ||a||^2, where along
+      fitting direction theta_k the pupil nodes x (spacing D / n_fit, inside the annulus)
+      see the layers at x + theta_k h_l (bilinear, R5) and the DMs at x + theta_k h_m
+      (bilinear hats, R27), and Pi removes the mean over the pupil (piston is not fitted).
+      Directions, weights, n_fit and eps are inputs.
 """
 
 import math
@@ -312,7 +318,8 @@ class Geometry:
                     Rs.append(_interp_matrix(xa / L["delta"] + L["n"] / 2, L["n"]))
                 else:
                     Rs.append(None)
-            self.dms.append(dict(n_act=na, off=aoff, R=Rs, w=fw[:, mi], spacing=float(m["spacing"])))
+            self.dms.append(dict(n_act=na, off=aoff, R=Rs, w=fw[:, mi], spacing=float(m["spacing"]),
+                                 h=float(m["h"])))
             aoff += na * na
         self.n_a = aoff
         set_elongation(self, float(p.get("alpha_eta", 0.0)))
@@ -772,6 +779,82 @@ def fit(geo, c):
                 a += m["w"][l] * (m["R"][l] @ phi @ m["R"][l].T)
         out.append(a.ravel())
     return np.concatenate(out)
+
+
+def fitting_geometry(geo, directions, n_fit):
+    """Pupil nodes and, per fitting direction, the layer and DM sampling matrices (R30)."""
+    D = geo.D
+    xs = -D / 2 + np.arange(n_fit + 1) * (D / n_fit)
+    r = np.hypot(xs[None, :], xs[:, None])
+    mask = (r >= geo.obs * D / 2) & (r <= D / 2)
+    dirs = []
+    for tx, ty in directions:
+        L = [(_interp_matrix((xs + ty * Ly["h"]) / Ly["delta"] + Ly["n"] / 2, Ly["n"]),
+              _interp_matrix((xs + tx * Ly["h"]) / Ly["delta"] + Ly["n"] / 2, Ly["n"]))
+             for Ly in geo.layers]
+        M = [(_hat_matrix((xs + ty * m["h"]) / m["spacing"] + (m["n_act"] - 1) / 2.0, m["n_act"]),
+              _hat_matrix((xs + tx * m["h"]) / m["spacing"] + (m["n_act"] - 1) / 2.0, m["n_act"]))
+             for m in geo.dms]
+        dirs.append(dict(L=L, M=M))
+    return dict(mask=mask, dirs=dirs)
+
+
+def pupil_centre(fg, v):
+    """Pi v: the pupil nodes' values without their mean, zero outside the pupil."""
+    m = fg["mask"]
+    out = np.where(m, v, 0.0)
+    out[m] -= out[m].mean()
+    return out
+
+
+def dm_along(geo, fg, k, a):
+    out = 0.0
+    for mi, m in enumerate(geo.dms):
+        A = np.asarray(a[m["off"]:m["off"] + m["n_act"] ** 2]).reshape(m["n_act"], m["n_act"])
+        Qy, Qx = fg["dirs"][k]["M"][mi]
+        out = out + Qy @ A @ Qx.T
+    return out
+
+
+def dm_along_adj(geo, fg, k, v):
+    out = []
+    for mi, m in enumerate(geo.dms):
+        Qy, Qx = fg["dirs"][k]["M"][mi]
+        out.append((Qy.T @ v @ Qx).ravel())
+    return np.concatenate(out)
+
+
+def ls_fit(geo, phis, fg, weights, eps, tol=1e-13, max_iters=100000):
+    """Least-squares DM fit (R30) by CG on the normal equations
+    (sum_k w_k A_k^T Pi A_k + eps I) a = sum_k w_k A_k^T Pi L_k phi."""
+    K = len(fg["dirs"])
+
+    def normal(a):
+        out = eps * a
+        for k in range(K):
+            out = out + weights[k] * dm_along_adj(geo, fg, k, pupil_centre(fg, dm_along(geo, fg, k, a)))
+        return out
+
+    rhs_ = np.zeros(geo.n_a)
+    for k in range(K):
+        v = sum(Ly @ phi @ Lx.T for (Ly, Lx), phi in zip(fg["dirs"][k]["L"], phis))
+        rhs_ = rhs_ + weights[k] * dm_along_adj(geo, fg, k, pupil_centre(fg, v))
+    a = np.zeros(geo.n_a)
+    r = rhs_.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    r0 = np.sqrt(rr)
+    for _ in range(max_iters):
+        if np.sqrt(rr) <= tol * r0 or rr == 0.0:
+            break
+        q = normal(p)
+        al = rr / float(p @ q)
+        a = a + al * p
+        r = r - al * q
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return a
 
 
 def fit_adj(geo, a):
