@@ -10,7 +10,11 @@
  *
  * with a fixed number of Jacobi-preconditioned CG iterations (Eq. 7, Sec. 3.3),
  * warm-started from the previous frame, then fits the DMs, a~ = F W^T c, and applies
- * the open-loop gain (Algorithm 1).
+ * the control law (Algorithm 1: open loop, or closed loop with FEWHA_FLAG_CLOSED_LOOP).
+ * Options: the augmented PCG of Sec. 3.4 (FEWHA_FLAG_AUGMENTED), the LGS spot-elongation
+ * noise model of Eq. 3 (fewha_params.alpha_eta); batches of uneven instances; gradients
+ * of the converged map (fewha_backward) and of the fixed-iteration frame
+ * (fewha_frame_vjp).
  *
  * Conventions shared by every entry point
  *   - All functions return FEWHA_OK (0) or a negative FEWHA_ERR_* code; the text of
@@ -62,7 +66,8 @@ extern "C" {
 #define FEWHA_ERR_GEOMETRY (-2)    /* footprint outside a layer grid, n not 2^k ... */
 #define FEWHA_ERR_OOM (-3)         /* device allocation failed                      */
 #define FEWHA_ERR_CUDA (-4)        /* a CUDA runtime call failed                    */
-#define FEWHA_ERR_NONFINITE (-5)   /* a NaN/Inf was found in the input slopes       */
+#define FEWHA_ERR_NONFINITE (-5)   /* a NaN/Inf was found in the input slopes, or a
+                                      recurrence being differentiated stopped          */
 #define FEWHA_ERR_LIMIT (-6)       /* a size exceeds a compiled-in maximum          */
 
 #define FEWHA_MAX_LAYERS 16
