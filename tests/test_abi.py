@@ -87,3 +87,32 @@ def test_maory_geometry_passes_validation(L):
         L.fewha_destroy(h)
     else:
         assert rc == -4 and "device" in msg
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the C header's sizes and field offsets
+    (compiled here with the host C compiler from include/fewha.h)."""
+    import shutil
+    import subprocess
+    from paper_2202_11945_gb300 import fewha
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"fewha_telescope": fewha.Telescope, "fewha_wfs": fewha.Wfs, "fewha_layer": fewha.Layer,
+               "fewha_dm": fewha.Dm, "fewha_params": fewha.Params, "fewha_batch_config": fewha.BatchConfig}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fewha.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
