@@ -171,7 +171,7 @@ def stage_bytes(R, b):
         "proj": (nc + nn) * b,            # read phi; write P phi on the aperture nodes
         "sensor": 2 * nn * b,             # read P phi; write the aperture-node adjoint u
         "projT": (nn + nc) * b,           # read u; write P^T u on the layers
-        "layer": 4 * nc * b,              # read P^T u, p, D; write q
+        "layer": 3 * nc * b,              # read P^T u and p; write q (D: one value per level)
         "vector": 8 * nc * b,             # read c, p, r, q, J^-1; write c, r, z
         "rhs": (ns + nn) * b,             # read slopes; write u
         "fit": (nc + 3 * na) * b,         # read phi, a_prev; write a_prev, dm

@@ -331,13 +331,21 @@ int fewha_frame_launches(const fewha_handle* h, int* launches);
  * frame forms r0 = b - M c explicitly) but keep the frame's warm start c.  Synchronous. */
 
 /* x = M^-1 b by PCG from x = 0 (one recurrence, no restarts), until
- * sqrt(r^T J^-1 r / b^T J^-1 b) <= tol (r the recursively updated residual) or max_iters
- * iterations; the test is made every FEWHA_MAX_ITERS - 1 iterations.  *iters_done and *rel_residual (nullable) report the outcome; reaching
- * max_iters is not an error.  Device pointers of the handle's element type. */
+ * sqrt(r^T J^-1 r / b^T J^-1 b) <= tol or max_iters iterations; the test is made every
+ * FEWHA_MAX_ITERS - 1 iterations.  Precision 64: r is the recursively updated residual.
+ * Precision 32 (mixed precision): the recurrence runs in float on a residual scaled to
+ * unit norm, its iterate is accumulated in double, and whenever the float residual has
+ * dropped tenfold the TRUE residual r = b - M x is formed in double (by an internal
+ * double-precision copy of the instance, created on the first such call) and replaces it
+ * (reliable updates); the test uses that true residual, so both precisions reach the same
+ * tolerance.  *iters_done (nullable) counts the recurrence's iterations, *rel_residual
+ * (nullable) the final relative residual; reaching max_iters is not an error.  Device
+ * pointers of the handle's element type. */
 int fewha_solve(fewha_handle* h, const void* d_b, void* d_x, double tol, int max_iters,
                 int* iters_done, double* rel_residual, void* stream);
 
-/* a~ = F W^T M^-1 b(s) with the solve above; the handle keeps c* for fewha_backward.
+/* a~ = F W^T M^-1 b(s) with the solve above; the handle keeps c* for fewha_backward (in
+ * double for precision 32, where b(s) and the fit are formed in double as well).
  * The solve (and the adjoint solve of fewha_backward) starts from the handle's previous
  * solution, if any: a nearby b or M (parameter sweeps, consecutive frames) converges in
  * fewer iterations. */
@@ -347,7 +355,8 @@ int fewha_reconstruct_converged(fewha_handle* h, const void* d_slopes, void* d_d
 /* Given d_grad_dm = dJ/da~ (n_act), the gradients of J at the last converged
  * reconstruction: d_grad_slopes (n_slopes, nullable), *grad_alpha (nullable) and
  * grad_cn2[n_layers] (nullable), the adjoint solve using the same tolerance and
- * iteration limit.  FEWHA_ERR_INVALID_ARG if no converged reconstruction is held (none
+ * iteration limit (precision 32: the adjoint solve as above, F^T, the slope map and the
+ * per-layer sums in double, the slope gradient rounded to float at the end).  FEWHA_ERR_INVALID_ARG if no converged reconstruction is held (none
  * yet, or fewha_update_params since). */
 int fewha_backward(fewha_handle* h, const void* d_grad_dm, void* d_grad_slopes, double* grad_alpha,
                    double* grad_cn2, void* stream);
@@ -420,11 +429,14 @@ int fewha_reconstruct_batched_f64(fewha_handle* const* handles, int count,
  * static device block of FEWHA_NOALLOC_SCRATCH_BYTES inside the library (held by every
  * GPU that loads the library until the process exits), not in the handle.  It calls
  * no cudaMalloc, cudaFree or allocating routine.  It returns FEWHA_ERR_LIMIT, doing
- * nothing, when the instance needs more scratch than the block holds: about
- * (n_coeffs + n_nodes) elements plus 512 bytes (the MAORY-size instance needs 1.46 MB in
- * double precision).  The first call on each device looks up the block's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  All calls share the one block and leave their intermediates in it:
+ * nothing, when the instance needs more scratch than the block holds.  The need is
+ * round256(n_coeffs * e) + round256(n_nodes * e) + 256 bytes, e the element size (4 or
+ * 8) and round256 rounding up to a multiple of 256 (the MAORY-size instance needs
+ * 1 455 872 bytes in double precision).  The first call on each device looks up the
+ * block's device address (cudaGetSymbolAddress) with that device current and keeps it
+ * for the life of the process: make that first call before any stream capture, and do
+ * not tear the device's primary context down (cudaDeviceReset) while the library is in
+ * use, since the kept address would then be stale.  All calls share the one block and leave their intermediates in it:
  * calls whose device work overlaps (different streams, or different handles on one
  * device) race on it and must be serialised by the caller.  Asynchronous on `stream`;
  * d_c and d_q are device pointers of the handle's element type. */

@@ -110,6 +110,13 @@ struct fewha_handle {
     // rebuilds its copy of the descriptor when it changes)
     std::vector<fewha_batch*> batches;
     unsigned version = 0;
+    // creation inputs, and the double-precision twin of a single-precision handle that
+    // forms the true residuals of its converged solves (created on first use)
+    fewha_telescope tel_in{};
+    std::vector<fewha_wfs> wfs_in;
+    std::vector<fewha_layer> layers_in;
+    std::vector<fewha_dm> dms_in;
+    fewha_handle* twin = nullptr;
 };
 
 struct fewha_batch {
@@ -224,6 +231,8 @@ Desc<T> make_desc(const fewha_handle* H) {
     d.dr_hi = H->dr_hi;
     d.D = static_cast<const T*>(H->D);
     d.Jinv = static_cast<const T*>(H->Jinv);
+    for (int l = 0; l < d.n_layers && !s.dlev.empty(); ++l)
+        for (int k = 0; k <= MAXLEV; ++k) d.Dlev[l][k] = T(s.dlev[l * (MAXLEV + 1) + k]);
     for (int g = 0; g < d.n_wfs; ++g)
         for (int l = 0; l < d.n_layers; ++l)
             for (int k = 0; k < 4; ++k) d.box[g][l][k] = H->box_host[(g * MAXL + l) * 4 + k];
@@ -399,7 +408,7 @@ int launch_fwd(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream
     return FEWHA_OK;
 }
 
-template <class T, bool PUPD>
+template <class T, int PUPD>
 int launch_inv(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream_t st) {
     if (recorder<T>()) {
         record<T>(PUPD ? BK_INV_UPD : BK_INV).cl = a;
@@ -433,13 +442,14 @@ int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int sl
     T* u = static_cast<T*>(H->u);
     int rc;
     ClArgs<T> a = cl_args<T>(H, x, phi);
+    a.zero_piston = 1;                 // the data path's input leaves the piston out
     if (pupdate) {
         a.pupd = static_cast<T*>(H->p);
         a.zupd = static_cast<const T*>(H->z);
         a.iter = slot;
-        rc = launch_inv<T, true>(H, d, a, st);
+        rc = launch_inv<T, 1>(H, d, a, st);
     } else {
-        rc = launch_inv<T, false>(H, d, a, st);
+        rc = launch_inv<T, 0>(H, d, a, st);
     }
     if (rc) return rc;
     if ((rc = launch_proj<T>(H, d, phi, st))) return rc;
@@ -447,6 +457,37 @@ int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int sl
     if ((rc = launch_projT<T>(H, d, u, st))) return rc;
     ClArgs<T> b = cl_args<T>(H, u, qout);
     b.pin = x;
+    b.iter = slot;
+    b.zero_piston = 1;
+    return launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, b, st);
+}
+
+// q = M p_new with the direction update of the augmented PCG (Sec. 3.4) fused into the
+// inverse kernel: p_new = z + beta p_old - sum_j mu_j P_j (beta from rz slots `slot` and
+// `slot - 1`; no p_old, and beta = 0, when pold is null; the m directions of `aug`).
+template <class T>
+int enqueue_apply_aug(fewha_handle* H, const Desc<T>& d, const T* pold, T* pnew, const T* z, T* qout, int slot,
+                      const AugArgs<T>& aug, cudaStream_t st) {
+    T* phi = static_cast<T*>(H->phi);
+    T* u = static_cast<T*>(H->u);
+    int rc;
+    ClArgs<T> a = cl_args<T>(H, nullptr, phi);
+    a.zero_piston = 1;
+    a.pupd = const_cast<T*>(pold);       // read only by the augmented update
+    a.zupd = z;
+    a.pout = pnew;
+    a.iter = slot;
+    a.augP = aug.P;
+    a.aug_tot = aug.tot;
+    a.aug_pq = aug.pq;
+    a.aug_ld = aug.ld;
+    a.aug_m = aug.m;
+    if ((rc = launch_inv<T, 2>(H, d, a, st))) return rc;
+    if ((rc = launch_proj<T>(H, d, phi, st))) return rc;
+    if ((rc = launch_csensor<T, SSRC_PHI>(H, d, phi, u, st))) return rc;
+    if ((rc = launch_projT<T>(H, d, u, st))) return rc;
+    ClArgs<T> b = cl_args<T>(H, u, qout);
+    b.pin = pnew;
     b.iter = slot;
     b.zero_piston = 1;
     return launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, b, st);
@@ -559,8 +600,6 @@ int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool war
     a.P = static_cast<const T*>(H->Pd[1 - set]);
     a.Q = static_cast<const T*>(H->Qd[1 - set]);
     a.pq = H->pqd[1 - set];
-    a.pnew = nullptr;
-    a.pold = nullptr;
     a.pqnew = H->pqd[set];
     a.part = H->augpart;
     a.tot = H->augtot;
@@ -583,11 +622,13 @@ int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool war
         T* qk = Qn + k * ld;
         v = vec_args<T>(H, c, k);
         if (k > 0 || m > 0) {
-            a.pnew = pk;
-            a.pold = k > 0 ? Pn + (k - 1) * ld : nullptr;
-            if ((rc = launch_aug<T, V_PROJ>(H, d.n_c, v, a, st))) return rc;
+            // p_k = z_k + beta p_(k-1) - P mu, fused into the apply's inverse kernel
+            rc = enqueue_apply_aug<T>(H, d, k > 0 ? Pn + (k - 1) * ld : nullptr, pk, static_cast<const T*>(H->z), qk,
+                                      k, a, st);
+        } else {
+            rc = enqueue_apply<T>(H, d, pk, qk, k, false, st);       // p_0 = z_0 (no directions)
         }
-        if ((rc = enqueue_apply<T>(H, d, pk, qk, k, false, st))) return rc;
+        if (rc) return rc;
         v.p = pk;
         v.q = qk;
         a.mu_next = (m > 0 && k + 1 < iters) ? 1 : 0;
@@ -600,7 +641,7 @@ template <class T>
 int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain, cudaStream_t st) {
     T* phi = static_cast<T*>(H->phi);
     int rc;
-    if ((rc = launch_inv<T, false>(H, d, cl_args<T>(H, c, phi), st))) return rc;
+    if ((rc = launch_inv<T, 0>(H, d, cl_args<T>(H, c, phi), st))) return rc;
     const bool closed = gain && (H->params.flags & FEWHA_FLAG_CLOSED_LOOP);
     return launch_fit<T>(H, d, phi, static_cast<T*>(H->a_prev), dm, closed ? 2 : (gain ? 1 : 0), st,
                          static_cast<T*>(H->a_old));
@@ -689,6 +730,15 @@ int compute_diagonals(fewha_handle* H) {
     std::vector<double> D;
     prior_diag(H->setup, H->weights, H->params.r0, H->params.L0, D);
     if (upload(H, H->D64, D)) return FEWHA_ERR_CUDA;
+    // D is constant per (layer, level): one value per level for the forward kernel, read at
+    // row 0, column n / 2^k (detail level k) and at (0, 0) (the LL band)
+    HostSetup& su = H->setup;
+    su.dlev.assign(static_cast<size_t>(MAXL) * (MAXLEV + 1), 0.0);
+    for (size_t l = 0; l < su.L.size(); ++l) {
+        const LayerInfo& L = su.L[l];
+        for (int k = 1; k <= L.levels; ++k) su.dlev[l * (MAXLEV + 1) + k] = D[L.off + (L.n >> k)];
+        su.dlev[l * (MAXLEV + 1) + L.levels + 1] = D[L.off];
+    }
     const Desc<T> d = make_desc<T>(H);
     DiagArgs a{H->basis, H->basis_off, H->pfy64, H->pfx64, H->Jdata};
     k_jdiag<T><<<(d.n_c + 3) / 4, 128>>>(d, a);
@@ -769,8 +819,9 @@ int set_smem_limits(fewha_handle* H) {
     int rc = 0;
     if ((rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_APPLY>, H->smem_fwd)) ||
         (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_COEF>, H->smem_fwd)) ||
-        (rc = allow_smem(H, k_cl_inv<T, false>, H->smem_inv)) ||
-        (rc = allow_smem(H, k_cl_inv<T, true>, H->smem_inv)) ||
+        (rc = allow_smem(H, k_cl_inv<T, 0>, H->smem_inv)) ||
+        (rc = allow_smem(H, k_cl_inv<T, 1>, H->smem_inv)) ||
+        (rc = allow_smem(H, k_cl_inv<T, 2>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_sensor<T, SSRC_PHI>, H->smem_sen)) ||
         (rc = allow_smem(H, k_cl_sensor<T, SSRC_SLOPES>, H->smem_sen)) ||
         (rc = allow_smem(H, k_proj<T>, H->smem_proj)) || (rc = allow_smem(H, k_projT<T>, H->smem_projT)))
@@ -1227,19 +1278,182 @@ int solve_converged(fewha_handle* H, const T* b, T* x, bool warm, double tol, in
     return FEWHA_OK;
 }
 
+// Zero the piston coefficient (the constant function) of every full-depth layer of a
+// coefficient vector.  Used before the slope map Gamma P W^T of a gradient: Gamma
+// annihilates constants, so this changes nothing mathematically, but the adjoint vectors
+// carry a large piston component (J^-1 of that coefficient is ~1 / (alpha D_LL)) whose
+// rounding in phi would otherwise leak through the differences of Gamma.
+template <class T>
+int zero_pistons(fewha_handle* H, T* v, cudaStream_t st) {
+    for (const LayerInfo& L : H->setup.L)
+        if (L.full) CK(cudaMemsetAsync(v + L.off, 0, sizeof(T), st), "zero piston");
+    return FEWHA_OK;
+}
+
+// The double-precision twin of a single-precision handle: the same geometry and
+// parameters, no flags.  It computes the true residuals b - M x of the single-precision
+// form's converged solves and holds their double iterates.
+int twin_params(fewha_handle* H) {
+    fewha_params p = H->params;
+    p.precision = 64;
+    p.flags = 0;
+    const int rc = fewha_update_params(H->twin, &p, H->weights.data(), H->setup.wfs_sigma.data());
+    if (rc) return fail(H, rc, std::string("double-precision twin: ") + fewha_last_error(H->twin));
+    return FEWHA_OK;
+}
+
+int ensure_twin(fewha_handle* H) {
+    if (H->twin) return FEWHA_OK;
+    fewha_params p = H->params;
+    p.precision = 64;
+    p.flags = 0;
+    std::vector<fewha_layer> layers = H->layers_in;
+    for (size_t l = 0; l < layers.size(); ++l) layers[l].cn2_weight = H->weights[l];
+    std::vector<fewha_wfs> wfs = H->wfs_in;
+    for (size_t g = 0; g < wfs.size(); ++g) wfs[g].sigma = H->setup.wfs_sigma[g];
+    fewha_handle* X = nullptr;
+    const int rc = fewha_create(&H->tel_in, wfs.data(), static_cast<int>(wfs.size()), layers.data(),
+                                static_cast<int>(layers.size()), H->dms_in.empty() ? nullptr : H->dms_in.data(),
+                                static_cast<int>(H->dms_in.size()), &p, &X);
+    if (rc) return fail(H, rc, std::string("double-precision twin: ") + fewha_create_error());
+    H->twin = X;
+    return FEWHA_OK;
+}
+
+// b^T J^-1 b of a double vector of the twin, on the host (synchronises).
+int twin_wnorm(fewha_handle* H, fewha_handle* X, const double* v, double* out, cudaStream_t st) {
+    k_wnorm<double><<<1, PBLK, 0, st>>>(X->setup.n_c, v, static_cast<const double*>(X->Jinv), X->gdot + MAXL);
+    CK(cudaGetLastError(), "k_wnorm launch");
+    CK(cudaMemcpyAsync(out, X->gdot + MAXL, sizeof(double), cudaMemcpyDeviceToHost, st), "norm");
+    CK(cudaStreamSynchronize(st), "norm");
+    return FEWHA_OK;
+}
+
+// Mixed-precision converged solve of the single-precision form: M x64 = b64 (double
+// vectors of the twin X) to sqrt(r^T J^-1 r / b^T J^-1 b) <= tol with r = b - M x64 the
+// TRUE residual in double.  One CG recurrence runs in float on H (its operators, its
+// vector kernels) on a residual scaled to unit J^-1-norm; its iterate is an increment
+// that is folded into x64 whenever the recurrence's residual has dropped tenfold (or the
+// chunk ends at max_iters, or the recurrence's estimate says tol is met).  The true
+// residual then replaces the recurrence's (reliable updates, k_refresh), and the search
+// direction continues, rescaled.  The float operator is accurate to ~1e-7 relative, far
+// inside the tenfold reduction, so the recurrence converges like the double one (about
+// 1.5 times its iterations were measured on the 8 m geometry) while every step is a
+// float step.  *iters_out counts float iterations.  Synchronous.
+int reliable_solve(fewha_handle* H, fewha_handle* X, const double* b64, double* x64, bool warm, double tol,
+                   int max_iters, cudaStream_t st, int* iters_out, double* rel_out) {
+    constexpr double DELTA = 0.1;
+    const Desc<float> d = make_desc<float>(H);
+    const Desc<double> dx = make_desc<double>(X);
+    const int n = d.n_c;
+    double* r64 = static_cast<double*>(X->r);
+    double* q64 = static_cast<double*>(X->q);
+    float* x32 = static_cast<float*>(H->c_tmp);
+    float* p = static_cast<float*>(H->p);
+    float* q = static_cast<float*>(H->q);
+    int rc;
+    double bn2 = 0.0, rr2 = 0.0;
+    if ((rc = twin_wnorm(H, X, b64, &bn2, st))) return rc;
+    if (!warm) CK(cudaMemsetAsync(x64, 0, n * sizeof(double), st), "solve start");
+    const int gl = std::min(4 * 152, (n + PBLK - 1) / PBLK);
+    auto true_residual = [&]() -> int {
+        int r2 = 0;
+        if ((r2 = enqueue_apply<double>(X, dx, x64, q64, PQ_SCRATCH_SLOT, false, st))) return fail(H, r2, X->err);
+        k_lin<double><<<gl, PBLK, 0, st>>>(n, 1.0, b64, -1.0, q64, 0.0, nullptr, nullptr, r64);
+        CK(cudaGetLastError(), "k_lin launch");
+        return twin_wnorm(H, X, r64, &rr2, st);
+    };
+    if ((rc = true_residual())) return rc;
+    double rel = bn2 > 0.0 ? std::sqrt(std::max(rr2, 0.0) / bn2) : 0.0;
+    int done = 0;
+    if (bn2 > 0.0 && rr2 > 0.0 && rel > tol && max_iters > 0) {
+        double sc = std::sqrt(rr2);
+        VecArgs<float> v = vec_args<float>(H, x32, 0);
+        CK(cudaMemsetAsync(x32, 0, n * sizeof(float), st), "solve increment");
+        k_refresh<float><<<H->npart, PBLK, 0, st>>>(n, r64, 1.0 / sc, 0.0, 1, 0.0, v);
+        CK(cudaGetLastError(), "k_refresh launch");
+        double rz[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(rz, H->rztot, sizeof(double), cudaMemcpyDeviceToHost, st), "solve rz");
+        CK(cudaStreamSynchronize(st), "solve rz");
+        double rz_upd = rz[0];
+        int j0 = 0;
+        for (;;) {
+            const int k = std::min(FEWHA_MAX_ITERS - j0, max_iters - done);
+            for (int j = j0; j < j0 + k; ++j) {
+                if ((rc = enqueue_apply<float>(H, d, p, q, j, j > 0, st))) return rc;
+                if ((rc = launch_vec<float, V_UPDATE>(H, n, vec_args<float>(H, x32, j), st))) return rc;
+            }
+            done += k;
+            const int last = j0 + k;
+            CK(cudaMemcpyAsync(rz, H->rztot + last - 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st),
+               "solve rz");
+            CK(cudaStreamSynchronize(st), "solve rz");
+            const bool stopped = !(rz[1] > 0.0) || !std::isfinite(rz[1]);
+            const bool fold = stopped || done >= max_iters || rz[1] < DELTA * DELTA * rz_upd ||
+                              sc * std::sqrt(rz[1]) <= tol * std::sqrt(bn2);
+            if (!fold) {
+                // continue the recurrence: slots (last - 1, last) -> (0, 1)
+                CK(cudaMemcpyAsync(H->rztot, H->rztot + last - 1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                   "solve resume");
+                j0 = 1;
+                continue;
+            }
+            k_accum<float><<<gl, PBLK, 0, st>>>(n, sc, x32, x64);
+            CK(cudaGetLastError(), "k_accum launch");
+            if ((rc = true_residual())) return rc;
+            rel = std::sqrt(std::max(rr2, 0.0) / bn2);
+            if (!std::isfinite(rr2)) break;
+            if (rel <= tol || done >= max_iters || !(rr2 > 0.0) || stopped) break;
+            const double scn = std::sqrt(rr2), ratio = sc / scn;
+            k_refresh<float><<<H->npart, PBLK, 0, st>>>(n, r64, 1.0 / scn, ratio, 0, rz[0] * ratio * ratio, v);
+            CK(cudaGetLastError(), "k_refresh launch");
+            CK(cudaMemcpyAsync(&rz_upd, H->rztot + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "solve rz");
+            CK(cudaStreamSynchronize(st), "solve rz");
+            sc = scn;
+            j0 = 1;
+        }
+    }
+    H->have_prev = false;
+    if (iters_out) *iters_out = done;
+    if (rel_out) *rel_out = rel;
+    if (!std::isfinite(rr2)) return fail(H, FEWHA_ERR_NONFINITE, "non-finite residual in the converged solve");
+    return FEWHA_OK;
+}
+
 template <class T>
 int reconstruct_converged(fewha_handle* H, const T* s, T* dm, double tol, int max_iters, int* iters,
                           double* rel, cudaStream_t st) {
     const Desc<T> d = make_desc<T>(H);
     int rc;
     H->grad_ready = false;
-    if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
-    // warm start from the previous converged solution (a nearby M or b)
-    if ((rc = solve_converged<T>(H, static_cast<const T*>(H->b), static_cast<T*>(H->cgrad), H->have_cgrad, tol,
-                                 max_iters, st, iters, rel)))
-        return rc;
-    H->have_cgrad = true;
-    if ((rc = enqueue_fit<T>(H, d, static_cast<const T*>(H->cgrad), dm, false, st))) return rc;
+    if constexpr (sizeof(T) == 4) {
+        // single precision: the rhs, the iterate c* and the fit in double on the twin, the
+        // solve's iterations in float (reliable_solve)
+        if ((rc = ensure_twin(H))) return rc;
+        fewha_handle* X = H->twin;
+        const Desc<double> dx = make_desc<double>(X);
+        double* s64 = static_cast<double*>(X->s_tmp);
+        k_convert<double, float><<<(d.n_s + 255) / 256, 256, 0, st>>>(d.n_s, s, s64);
+        CK(cudaGetLastError(), "k_convert launch");
+        if ((rc = enqueue_rhs<double>(X, dx, s64, static_cast<double*>(X->b), st))) return fail(H, rc, X->err);
+        if ((rc = reliable_solve(H, X, static_cast<const double*>(X->b), static_cast<double*>(X->cgrad),
+                                 X->have_cgrad, tol, max_iters, st, iters, rel)))
+            return rc;
+        X->have_cgrad = true;
+        double* dm64 = static_cast<double*>(X->dm_tmp);
+        if ((rc = enqueue_fit<double>(X, dx, static_cast<const double*>(X->cgrad), dm64, false, st)))
+            return fail(H, rc, X->err);
+        k_convert<float, double><<<(d.n_act + 255) / 256, 256, 0, st>>>(d.n_act, dm64, dm);
+        CK(cudaGetLastError(), "k_convert launch");
+    } else {
+        if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
+        // warm start from the previous converged solution (a nearby M or b)
+        if ((rc = solve_converged<T>(H, static_cast<const T*>(H->b), static_cast<T*>(H->cgrad), H->have_cgrad, tol,
+                                     max_iters, st, iters, rel)))
+            return rc;
+        H->have_cgrad = true;
+        if ((rc = enqueue_fit<T>(H, d, static_cast<const T*>(H->cgrad), dm, false, st))) return rc;
+    }
     H->grad_ready = true;
     H->grad_tol = tol;
     H->grad_max_iters = max_iters;
@@ -1249,29 +1463,67 @@ int reconstruct_converged(fewha_handle* H, const T* s, T* dm, double tol, int ma
 // Gradients of J(a~) at the last converged reconstruction, given g_a = dJ/da~:
 //   lambda = M^-1 (F W^T)^T g_a,  dJ/ds = C_hat^-1 Gamma P W^T lambda,
 //   dJ/dalpha = -lambda^T D c*,   dJ/dw_l = alpha lambda_l^T D_l c*_l / w_l.
+// The single-precision form solves for lambda with reliable_solve and forms every other
+// step (F^T, the slope map, the per-layer sums) in double on the twin.
 template <class T>
 int backward(fewha_handle* H, const T* g_a, T* g_s, double* g_alpha, double* g_w, cudaStream_t st) {
     if (!H->grad_ready) return fail(H, FEWHA_ERR_INVALID_ARG, "no converged reconstruction to differentiate");
     const Desc<T> d = make_desc<T>(H);
     int rc;
-    T* b = static_cast<T*>(H->b);
-    T* lam = static_cast<T*>(H->lam);
-    T* phi = static_cast<T*>(H->phi);
-    T* st_s = static_cast<T*>(H->s_tmp);
-    if ((rc = launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, g_a, b), st))) return rc;
     int it = 0;
     double rel = 0.0;
-    if ((rc = solve_converged<T>(H, b, lam, H->have_lam, H->grad_tol, H->grad_max_iters, st, &it, &rel))) return rc;
-    H->have_lam = true;
-    if (g_s) {
-        if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, lam, phi), st))) return rc;
-        if ((rc = launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, phi, st_s, st))) return rc;
-        if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, st_s, g_s, st))) return rc;
-    }
-    k_layer_dots<T><<<d.n_layers, PBLK, 0, st>>>(d, lam, static_cast<const T*>(H->cgrad), H->gdot);
-    CK(cudaGetLastError(), "k_layer_dots launch");
     double S[MAXL];
-    CK(cudaMemcpyAsync(S, H->gdot, d.n_layers * sizeof(double), cudaMemcpyDeviceToHost, st), "layer sums");
+    if constexpr (sizeof(T) == 4) {
+        fewha_handle* X = H->twin;
+        const Desc<double> dx = make_desc<double>(X);
+        double* ga64 = static_cast<double*>(X->dm_tmp);
+        double* b64 = static_cast<double*>(X->b);
+        double* lam = static_cast<double*>(X->lam);
+        k_convert<double, float><<<(d.n_act + 255) / 256, 256, 0, st>>>(d.n_act, g_a, ga64);
+        CK(cudaGetLastError(), "k_convert launch");
+        if ((rc = launch_layer<double, LSRC_DM, LDST_COEF, false>(X, dx, layer_args<double>(X, ga64, b64), st)))
+            return fail(H, rc, X->err);
+        if ((rc = reliable_solve(H, X, b64, lam, X->have_lam, H->grad_tol, H->grad_max_iters, st, &it, &rel)))
+            return rc;
+        X->have_lam = true;
+        if (g_s) {
+            double* lz = static_cast<double*>(X->c_tmp);
+            double* phi = static_cast<double*>(X->phi);
+            double* t1 = static_cast<double*>(X->s_tmp);
+            double* t2 = static_cast<double*>(X->s_pol);
+            CK(cudaMemcpyAsync(lz, lam, d.n_c * sizeof(double), cudaMemcpyDeviceToDevice, st), "lambda copy");
+            if ((rc = zero_pistons<double>(H, lz, st))) return rc;
+            if ((rc = launch_layer<double, LSRC_COEF, LDST_PHI, false>(X, dx, layer_args<double>(X, lz, phi), st)) ||
+                (rc = launch_sensor<double, SSRC_PHI, false, SDST_SLOPES>(X, dx, phi, t1, st)) ||
+                (rc = launch_sensor<double, SSRC_SLOPES, true, SDST_SLOPES>(X, dx, t1, t2, st)))
+                return fail(H, rc, X->err);
+            k_convert<float, double><<<(d.n_s + 255) / 256, 256, 0, st>>>(d.n_s, t2, g_s);
+            CK(cudaGetLastError(), "k_convert launch");
+        }
+        k_layer_dots<double><<<d.n_layers, PBLK, 0, st>>>(dx, lam, static_cast<const double*>(X->cgrad), X->gdot);
+        CK(cudaGetLastError(), "k_layer_dots launch");
+        CK(cudaMemcpyAsync(S, X->gdot, d.n_layers * sizeof(double), cudaMemcpyDeviceToHost, st), "layer sums");
+    } else {
+        T* b = static_cast<T*>(H->b);
+        T* lam = static_cast<T*>(H->lam);
+        T* phi = static_cast<T*>(H->phi);
+        T* st_s = static_cast<T*>(H->s_tmp);
+        if ((rc = launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, g_a, b), st))) return rc;
+        if ((rc = solve_converged<T>(H, b, lam, H->have_lam, H->grad_tol, H->grad_max_iters, st, &it, &rel)))
+            return rc;
+        H->have_lam = true;
+        if (g_s) {
+            T* lz = static_cast<T*>(H->c_tmp);
+            CK(cudaMemcpyAsync(lz, lam, d.n_c * sizeof(T), cudaMemcpyDeviceToDevice, st), "lambda copy");
+            if ((rc = zero_pistons<T>(H, lz, st))) return rc;
+            if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, lz, phi), st))) return rc;
+            if ((rc = launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, phi, st_s, st))) return rc;
+            if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, st_s, g_s, st))) return rc;
+        }
+        k_layer_dots<T><<<d.n_layers, PBLK, 0, st>>>(d, lam, static_cast<const T*>(H->cgrad), H->gdot);
+        CK(cudaGetLastError(), "k_layer_dots launch");
+        CK(cudaMemcpyAsync(S, H->gdot, d.n_layers * sizeof(double), cudaMemcpyDeviceToHost, st), "layer sums");
+    }
     CK(cudaStreamSynchronize(st), "backward");
     double tot = 0.0;
     for (int l = 0; l < d.n_layers; ++l) tot += S[l];
@@ -1279,6 +1531,30 @@ int backward(fewha_handle* H, const T* g_a, T* g_s, double* g_alpha, double* g_w
     if (g_w)
         for (int l = 0; l < d.n_layers; ++l) g_w[l] = H->params.alpha * S[l] / H->weights[l];
     return FEWHA_OK;
+}
+
+// x = M^-1 b from x = 0 (fewha_solve): the double-precision form by solve_converged, the
+// single-precision form by reliable_solve with b and x converted at the ends.
+template <class T>
+int solve_entry(fewha_handle* H, const T* b, T* x, double tol, int max_iters, cudaStream_t st, int* iters,
+                double* rel) {
+    if constexpr (sizeof(T) == 4) {
+        int rc;
+        if ((rc = ensure_twin(H))) return rc;
+        fewha_handle* X = H->twin;
+        const int n = H->setup.n_c;
+        double* b64 = static_cast<double*>(X->b);
+        double* x64 = static_cast<double*>(X->c_tmp);
+        k_convert<double, float><<<(n + 255) / 256, 256, 0, st>>>(n, b, b64);
+        CK(cudaGetLastError(), "k_convert launch");
+        if ((rc = reliable_solve(H, X, b64, x64, false, tol, max_iters, st, iters, rel))) return rc;
+        k_convert<float, double><<<(n + 255) / 256, 256, 0, st>>>(n, x64, x);
+        CK(cudaGetLastError(), "k_convert launch");
+        CK(cudaStreamSynchronize(st), "solve");
+        return FEWHA_OK;
+    } else {
+        return solve_converged<T>(H, b, x, false, tol, max_iters, st, iters, rel);
+    }
 }
 
 // Reverse mode through the fixed-iteration frame: the forward recurrence from c0 with
@@ -1334,14 +1610,12 @@ int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* 
     AugArgs<T> a{};
     a.m = 0;
     for (int i = 0; i < k; ++i) {
-        if (i > 0) {
-            VecArgs<T> w = vec_args<T>(H, c, i);
-            w.z = Z + i * ld;
-            a.pnew = P + i * ld;
-            a.pold = P + (i - 1) * ld;
-            if ((rc = launch_aug<T, V_PROJ>(H, n, w, a, st))) return rc;
-        }
-        if ((rc = enqueue_apply<T>(H, d, P + i * ld, Q + i * ld, i, false, st))) return rc;
+        // p_i = z_i + beta p_(i-1) into its own slot, fused into the apply's inverse kernel
+        if (i > 0)
+            rc = enqueue_apply_aug<T>(H, d, P + (i - 1) * ld, P + i * ld, Z + i * ld, Q + i * ld, i, a, st);
+        else
+            rc = enqueue_apply<T>(H, d, P, Q, 0, false, st);
+        if (rc) return rc;
         CK(cudaMemcpyAsync(R + (i + 1) * ld, R + i * ld, n * sizeof(T), cudaMemcpyDeviceToDevice, st), "vjp r");
         VecArgs<T> w = vec_args<T>(H, c, i);
         w.p = P + i * ld;
@@ -1416,9 +1690,11 @@ int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* 
     CK(lin(1.0, rbar, rhobar, Z, 0.0, nullptr, nullptr, rbar), "vjp lin");
     CK(lin(1.0, zbar, rhobar, R, 0.0, nullptr, nullptr, zbar), "vjp lin");
     CK(lin(1.0, rbar, 0.0, nullptr, 1.0, Jinv, zbar, rbar), "vjp lin");
-    // dJ/ds = C_hat^-1 Gamma P W^T b_bar
+    // dJ/ds = C_hat^-1 Gamma P W^T b_bar (b_bar's pistons, large and annihilated by Gamma,
+    // left out first)
     T* phi = static_cast<T*>(H->phi);
     T* st_s = static_cast<T*>(H->s_tmp);
+    if ((rc = zero_pistons<T>(H, rbar, st))) return rc;
     if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, rbar, phi), st))) return rc;
     if ((rc = launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, phi, st_s, st))) return rc;
     if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, st_s, g_s, st))) return rc;
@@ -1981,7 +2257,8 @@ int bench_stage(fewha_handle* H, int stage, int reps, cudaStream_t st) {
                 a.pupd = p;
                 a.zupd = static_cast<const T*>(H->z);
                 a.iter = 1;
-                rc = launch_inv<T, true>(H, d, a, st);
+                a.zero_piston = 1;
+                rc = launch_inv<T, 1>(H, d, a, st);
                 break;
             }
             case FEWHA_STAGE_SENSOR:
@@ -2068,10 +2345,9 @@ int apply_M_noalloc(fewha_handle* H, const T* x, T* qout, cudaStream_t st) {
     if (rc) return rc;
     T* phi = reinterpret_cast<T*>(base);
     T* u = reinterpret_cast<T*>(base + b_phi);
+    // the layer kernel also writes each layer's p.q partial; nothing reads them in this
+    // entry point, so these slots are write-only and need no clearing
     double* pq = reinterpret_cast<double*>(base + b_phi + b_u);
-    // the block keeps the previous call's contents; the layer kernel writes only the
-    // p.q slots of the layers present, so clear all slots before use
-    CK(cudaMemsetAsync(pq, 0, b_pq, st), "fewha_apply_M_noalloc: clear partials");
     const Desc<T> d = make_desc<T>(H);
     if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, x, phi), st))) return rc;
     if ((rc = launch_sensor<T, SSRC_PHI, true, SDST_ADJ>(H, d, phi, u, st))) return rc;
@@ -2122,6 +2398,10 @@ int fewha_create(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, co
         return rc;
     }
     for (int l = 0; l < n_layers; ++l) H->weights.push_back(layers[l].cn2_weight);
+    H->tel_in = *tel;
+    H->wfs_in.assign(wfs, wfs + n_wfs);
+    H->layers_in.assign(layers, layers + n_layers);
+    if (n_dms > 0) H->dms_in.assign(dms, dms + n_dms);
     H->npart = (H->setup.n_c + PBLK * 4 - 1) / (PBLK * 4);
     if (H->npart > NPART_MAX) H->npart = NPART_MAX;
     if (H->npart < 1) H->npart = 1;
@@ -2191,7 +2471,9 @@ int fewha_update_params(fewha_handle* H, const fewha_params* params, const doubl
     H->aug_m = 0;                     // M changed: the stored directions no longer apply
     ++H->version;
     H->grad_ready = false;
-    return H->precision == 32 ? compute_diagonals<float>(H) : compute_diagonals<double>(H);
+    rc = H->precision == 32 ? compute_diagonals<float>(H) : compute_diagonals<double>(H);
+    if (rc || !H->twin) return rc;
+    return twin_params(H);
 }
 
 int fewha_reset(fewha_handle* H, void* stream) {
@@ -2311,10 +2593,10 @@ int fewha_solve(fewha_handle* H, const void* b, void* x, double tol, int max_ite
     DeviceGuard g(H->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return H->precision == 32
-               ? solve_converged<float>(H, static_cast<const float*>(b), static_cast<float*>(x), false, tol,
-                                        max_iters, st, iters, rel)
-               : solve_converged<double>(H, static_cast<const double*>(b), static_cast<double*>(x), false, tol,
-                                         max_iters, st, iters, rel);
+               ? solve_entry<float>(H, static_cast<const float*>(b), static_cast<float*>(x), tol, max_iters, st,
+                                    iters, rel)
+               : solve_entry<double>(H, static_cast<const double*>(b), static_cast<double*>(x), tol, max_iters, st,
+                                     iters, rel);
 }
 
 int fewha_reconstruct_converged(fewha_handle* H, const void* s, void* dm, double tol, int max_iters,
@@ -2399,10 +2681,11 @@ int fewha_frame_launches(const fewha_handle* H, int* launches) {
     if (!H || !launches) return FEWHA_ERR_INVALID_ARG;
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
     // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2; the
-    // augmented frame (with directions) adds one start kernel and one per iteration
+    // augmented frame (with directions) adds one start kernel (its direction update is
+    // fused into the inverse kernel of each apply)
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
     const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
-    *launches = closed + 3 + (warm ? 1 : 6) + aug + (6 + aug) * H->params.iters + 2;
+    *launches = closed + 3 + (warm ? 1 : 6) + aug + 6 * H->params.iters + 2;
     return FEWHA_OK;
 }
 

@@ -20,7 +20,7 @@ __device__ __forceinline__ void load_desc(Desc<T>& sd, const BInst<T>* __restric
     __syncthreads();
 }
 
-template <class T, bool PUPD>
+template <class T, int PUPD>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     kb_cl_inv(const BInst<T>* __restrict__ inst, const ClArgs<T>* __restrict__ args,
               const BItem* __restrict__ items) {
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(PBLK)
 template <class T>
 const void* kernel_of(int kind) {
     switch (kind) {
-        case BK_INV: return reinterpret_cast<const void*>(kb_cl_inv<T, false>);
-        case BK_INV_UPD: return reinterpret_cast<const void*>(kb_cl_inv<T, true>);
+        case BK_INV: return reinterpret_cast<const void*>(kb_cl_inv<T, 0>);
+        case BK_INV_UPD: return reinterpret_cast<const void*>(kb_cl_inv<T, 1>);
         case BK_PROJ: return reinterpret_cast<const void*>(kb_proj<T>);
         case BK_SEN_PHI: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_PHI>);
         case BK_SEN_SLOPES: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_SLOPES>);
@@ -193,8 +193,8 @@ cudaError_t batch_launch(const BLaunch& L, cudaStream_t st) {
     const VecArgs<T>* va = static_cast<const VecArgs<T>*>(L.args);
     const FitArgs<T>* fa = static_cast<const FitArgs<T>*>(L.args);
     switch (L.kind) {
-        case BK_INV: return launch_b(L.pdl, kb_cl_inv<T, false>, cg, nt, L.smem, st, I, ca, L.items);
-        case BK_INV_UPD: return launch_b(L.pdl, kb_cl_inv<T, true>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_INV: return launch_b(L.pdl, kb_cl_inv<T, 0>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_INV_UPD: return launch_b(L.pdl, kb_cl_inv<T, 1>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_FWD_APPLY: return launch_b(L.pdl, kb_cl_fwd<T, LDST_APPLY>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_FWD_COEF: return launch_b(L.pdl, kb_cl_fwd<T, LDST_COEF>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_SEN_PHI: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_PHI>, cg, nt, L.smem, st, I, sa, L.items);

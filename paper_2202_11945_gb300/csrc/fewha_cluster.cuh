@@ -281,7 +281,17 @@ struct ClArgs {
     const T* zupd;
     PcgSlots pcg;
     int iter;           // p.q slot of the apply / CG iteration of the update
-    int zero_piston;
+    int zero_piston;    // data term of M: forward kernel, the full-depth LL output is exactly
+                        // 0; inverse kernel, the full-depth LL input is left out
+    // augmented direction update (inverse kernel, PUPD = 2): output p_new, the previous
+    // frame's directions P_j (stride aug_ld, aug_m of them), q_j.z at aug_tot[AUG_MAX + j]
+    // and p_j.q_j at aug_pq[j]
+    T* pout;
+    const T* augP;
+    const double* aug_tot;
+    const double* aug_pq;
+    long long aug_ld;
+    int aug_m;
 };
 
 struct ClLayout {       // shared-memory offsets set by the host, in T units
@@ -325,7 +335,11 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     constexpr int PF = MAXN * (MAXN / CL) / NT;     // column-band positions per thread
     const int row_start = (coarse && r0 < h) ? h : 0;
     const int ecnt = has_band ? (n - row_start) * rb : 0;
-    T pre_p[PF], pre_D[PF];
+    T pre_p[PF];
+    // D is one value per (layer, level) (Sec. 3.1): the layer's row of the table, in shared
+    // memory, indexed by the level of each position
+    __shared__ T sD[MAXLEV + 1];
+    if (threadIdx.x <= MAXLEV) sD[threadIdx.x] = d.Dlev[l][threadIdx.x];
     // the band-run table of the staged sum, loaded now so that its latency overlaps
     int4 ytv = make_int4(0, 0, 0, 0);
     if (SRC == LSRC_NODES && lay.ystg > 0 && has_band && threadIdx.x < 2 * d.n_wfs)
@@ -337,7 +351,6 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             if (k < ecnt) {
                 const int pos = off + (row_start + (k >> lrb)) * n + r0 + (k & (rb - 1));
                 pre_p[s] = a.pin[pos];
-                pre_D[s] = d.D[pos];
             }
         }
     }
@@ -453,7 +466,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     DotAcc<T> dot;                 // p.q share of this CTA (double accuracy)
     if (coarse && r == 0) {
         constexpr int PL = (MAXN / 2) * (MAXN / 2) / NT;     // LL positions per thread
-        T lp[PL], lD[PL];
+        T lp[PL];
         if (DST == LDST_APPLY) {
 #pragma unroll
             for (int s = 0; s < PL; ++s) {
@@ -461,7 +474,6 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 if (k < h * h) {
                     const int pos = off + ((k >> lh)) * n + (k & (h - 1));
                     lp[s] = a.pin[pos];
-                    lD[s] = d.D[pos];
                 }
             }
         }
@@ -481,7 +493,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 const int pos = off + i * n + j;
                 const T v = lbuf[i * lsd + j];
                 if (DST == LDST_APPLY) {
-                    const T q = v + d.alpha * lD[s] * lp[s];
+                    const T q = v + d.alpha * sD[level_of(i, j, L)] * lp[s];
                     a.out[pos] = q;
                     dot.add(lp[s], q);
                 } else {
@@ -501,7 +513,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             const int pos = off + i * n + r0 + jj;
             const T v = cbuf[i * cs + jj];
             if (DST == LDST_APPLY) {
-                const T q = v + d.alpha * pre_D[s] * pre_p[s];
+                const T q = v + d.alpha * sD[level_of(i, r0 + jj, L)] * pre_p[s];
                 a.out[pos] = q;
                 dot.add(pre_p[s], q);
             } else {
@@ -533,12 +545,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
 
 // ---------------------------------------------------------------------------
 // Inverse layer kernel (cluster per layer): phi = W^T c, optionally advancing the CG
-// direction first (p = z + beta p, beta = rz_k / rz_(k-1), Sec. 3.3).
+// direction first (Sec. 3.3).  PUPD = 0: phi = W^T a.in.  PUPD = 1: p = z + beta p in place
+// (a.pupd), beta = rz_k / rz_(k-1), then phi = W^T p.  PUPD = 2, the augmented PCG of
+// Sec. 3.4: p_new = z + beta p_old - sum_j mu_j P_j into a.pout, mu_j = q_j.z / p_j.q_j of
+// the previous frame's directions P_j (p_old = a.pupd; none, and beta = 0, for a frame's
+// first direction), then phi = W^T p_new.  The direction update is spread over the
+// cluster: every CTA updates its column band (below the LL quadrant when coarse) and a
+// share of the LL quadrant's rows, which it pushes to the leader for the coarse levels.
 // ---------------------------------------------------------------------------
-template <class T, bool PUPD>
+template <class T, int PUPD>
 __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a, const ClLayout& lay,
                                             const int l) {
     constexpr int NT = cblk<T>();
+    constexpr int PF = MAXN * (MAXN / CL) / NT;                      // band positions per thread
+    constexpr int PL = ((MAXN / 2) * (MAXN / 2) / CL + NT - 1) / NT; // LL-share positions per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);
     T* sm = reinterpret_cast<T*>(red + RED_DBL);
@@ -556,25 +576,31 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     T* lbuf = sm + lay.lbuf;
     const int ys = n + 1, cs = rb + 1, lsd = h + 1;
     const bool coarse = L.levels >= 2;
+    // this CTA's rows of the LL quadrant (coarse layers): [lr0, lr1)
+    const int hb = max(h >> 3, 1);                     // h / CL
+    const int lr0 = coarse ? min(r * hb, h) : 0, lr1 = coarse ? min(lr0 + hb, h) : 0;
+    const int lcnt = (lr1 - lr0) * h;
 
-    // beta = rz_k / rz_(k-1), formed once (an FP64 division costs ~10 FP64 instructions,
-    // and GB300 issues a warp's FP64 instruction in ~64 cycles) and broadcast
+    // beta = rz_k / rz_(k-1) and the mu_j, formed once (an FP64 division costs ~10 FP64
+    // instructions, and GB300 issues a warp's FP64 instruction in ~64 cycles) and broadcast
     __shared__ T sbeta;
-    T beta = T(0);
+    __shared__ T smu[AUG_MAX];
+    const bool has_old = PUPD == 1 || (PUPD == 2 && a.pupd != nullptr);
+    const bool stage_src = PUPD == 0 || has_old;
     const T* src = PUPD ? a.pupd : a.in;
+    T* pdst = PUPD == 2 ? a.pout : a.pupd;
     // the exchanges below push into peers' shared memory before the first full cluster
     // barrier: arrive now, wait before the first push, so that every CTA has started
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
-    // ---- 1. stage this CTA's coefficients: its column band (without the LL quadrant
-    // when coarse) and, for the leader, the LL quadrant.  Rows go through unpadded
-    // staging tiles in 16-byte chunks when aligned, then into the padded tiles.
+    // ---- 1. stage this CTA's coefficients: its column band and its LL rows.  Rows go
+    // through unpadded staging tiles in 16-byte chunks when aligned.
     constexpr int V = vec16<T>();
     const int row_start = (coarse && r0 < h) ? h : 0;
     const int nrow = n - row_start;
     T* sp = sm + lay.stage;                     // column band, stride rb: p (or c)
     T* sz = sp + MAXN * (MAXN / CL);            // column band: z (PUPD)
-    T* lp = sm + lay.stage2;                    // LL quadrant, stride h: p (or c)
-    T* lz = lp + (MAXN / 2) * (MAXN / 2);       // LL quadrant: z (PUPD)
+    T* lp = sm + lay.stage2;                    // LL rows, stride h: p (or c)
+    T* lz = lp + (MAXN / 2) * (MAXN / 2);       // LL rows: z (PUPD)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
     if (has_band) {
         if ((rb & (V - 1)) == 0) {
@@ -583,74 +609,127 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
             for (int k = threadIdx.x; k < nrow * cpr; k += NT) {
                 const int i = k >> lcpr, c = k & (cpr - 1);
                 const int pos = off + (row_start + i) * n + r0 + c * V;
-                cp_async16(sp + i * rb + c * V, src + pos);
+                if (stage_src) cp_async16(sp + i * rb + c * V, src + pos);
                 if (PUPD) cp_async16(sz + i * rb + c * V, a.zupd + pos);
             }
         } else {
             for (int k = threadIdx.x; k < nrow * rb; k += NT) {
                 const int i = k >> lrb, jj = k & (rb - 1);
                 const int pos = off + (row_start + i) * n + r0 + jj;
-                cp_async(sp + k, src + pos);
+                if (stage_src) cp_async(sp + k, src + pos);
                 if (PUPD) cp_async(sz + k, a.zupd + pos);
             }
         }
     }
-    if (coarse && r == 0) {
-        for (int i = warp; i < h; i += nwarp) {
-            const int pos = off + i * n;
-            if ((h & (V - 1)) == 0) {
-                for (int c = lane; c < h / V; c += 32) {
-                    cp_async16(lp + i * h + c * V, src + pos + c * V);
-                    if (PUPD) cp_async16(lz + i * h + c * V, a.zupd + pos + c * V);
-                }
-            } else {
-                for (int j = lane; j < h; j += 32) {
-                    cp_async(lp + i * h + j, src + pos + j);
-                    if (PUPD) cp_async(lz + i * h + j, a.zupd + pos + j);
-                }
+    for (int i = lr0 + warp; i < lr1; i += nwarp) {
+        const int pos = off + i * n;
+        T* dp = lp + (i - lr0) * h;
+        T* dz = lz + (i - lr0) * h;
+        if ((h & (V - 1)) == 0) {
+            for (int c = lane; c < h / V; c += 32) {
+                if (stage_src) cp_async16(dp + c * V, src + pos + c * V);
+                if (PUPD) cp_async16(dz + c * V, a.zupd + pos + c * V);
+            }
+        } else {
+            for (int j = lane; j < h; j += 32) {
+                if (stage_src) cp_async(dp + j, src + pos + j);
+                if (PUPD) cp_async(dz + j, a.zupd + pos + j);
             }
         }
     }
-    // beta is formed while the copies are in flight; the staging barrier publishes it
+    // beta and mu are formed while the copies are in flight
     if (PUPD && threadIdx.x == 0) {
-        const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
-        sbeta = rz_old != 0.0 ? T(rz_new / rz_old) : T(0);
+        double b = 0.0;
+        if (has_old) {
+            const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
+            b = rz_old != 0.0 ? rz_new / rz_old : 0.0;
+        }
+        sbeta = T(b);
+    }
+    if (PUPD == 2 && threadIdx.x >= 32 && threadIdx.x < 32 + a.aug_m) {
+        const int j = threadIdx.x - 32;
+        const double num = a.aug_tot[AUG_MAX + j], den = a.aug_pq[j];
+        smu[j] = T(den > 0.0 ? num / den : 0.0);
+    }
+    // the augmented update's sum_j mu_j P_j at this thread's positions, its loads in flight
+    // beside the staging copies
+    T cb[PF], cl[PL];
+#pragma unroll
+    for (int s2 = 0; s2 < PF; ++s2) cb[s2] = T(0);
+#pragma unroll
+    for (int s2 = 0; s2 < PL; ++s2) cl[s2] = T(0);
+    if (PUPD == 2) {
+        __syncthreads();                                             // smu
+        for (int j = 0; j < a.aug_m; ++j) {
+            const T mu = smu[j];
+            const T* Pj = a.augP + static_cast<long long>(j) * a.aug_ld + off;
+#pragma unroll
+            for (int s2 = 0; s2 < PF; ++s2) {
+                const int k = threadIdx.x + s2 * NT;
+                if (has_band && k < nrow * rb)
+                    cb[s2] += mu * __ldg(Pj + (row_start + (k >> lrb)) * n + r0 + (k & (rb - 1)));
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < PL; ++s2) {
+                const int k = threadIdx.x + s2 * NT;
+                if (k < lcnt) cl[s2] += mu * __ldg(Pj + (lr0 + (k >> lh)) * n + (k & (h - 1)));
+            }
+        }
     }
     cp_async_wait();
     __syncthreads();
-    if (PUPD) beta = sbeta;
-    // p = z + beta p (PUPD) into the padded tiles and back to global
-    if (has_band) {
-        for (int k = threadIdx.x; k < nrow * rb; k += NT) {
+    const T beta = PUPD ? sbeta : T(0);
+    // the direction update into the padded tiles and back to global
+#pragma unroll
+    for (int s2 = 0; s2 < PF; ++s2) {
+        const int k = threadIdx.x + s2 * NT;
+        if (has_band && k < nrow * rb) {
             const int i = k >> lrb, jj = k & (rb - 1);
-            T p = sp[k];
-            if (PUPD) {
-                p = sz[k] + beta * p;
-                a.pupd[off + (row_start + i) * n + r0 + jj] = p;
-            }
+            T p = stage_src ? sp[k] : T(0);
+            if (PUPD == 1) p = sz[k] + beta * p;
+            if (PUPD == 2) p = (has_old ? sz[k] + beta * p : sz[k]) - cb[s2];
+            if (PUPD) pdst[off + (row_start + i) * n + r0 + jj] = p;
             cbuf[(row_start + i) * cs + jj] = p;
         }
     }
-    if (coarse && r == 0) {
-        for (int k = threadIdx.x; k < h * h; k += NT) {
-            const int i = k >> lh, j = k & (h - 1);
-            T p = lp[k];
-            if (PUPD) {
-                p = lz[k] + beta * p;
-                a.pupd[off + i * n + j] = p;
-            }
-            lbuf[i * lsd + j] = p;
+#pragma unroll
+    for (int s2 = 0; s2 < PL; ++s2) {
+        const int k = threadIdx.x + s2 * NT;
+        if (k < lcnt) {
+            T p = stage_src ? lp[k] : T(0);
+            if (PUPD == 1) p = lz[k] + beta * p;
+            if (PUPD == 2) p = (has_old ? lz[k] + beta * p : lz[k]) - cl[s2];
+            if (PUPD) pdst[off + (lr0 + (k >> lh)) * n + (k & (h - 1))] = p;
+            lp[k] = p;
         }
+    }
+    // Input of the data path of M (a.zero_piston): Gamma annihilates constants and bilinear
+    // weights sum to one, so a full-depth layer's piston coefficient (its constant function)
+    // contributes nothing to P, Gamma and back, and is left out.  Exact; without it a large
+    // piston component (the adjoint vectors of the gradient passes carry one, J^-1 of that
+    // coefficient being ~1e5) rounds into phi and leaks through the differences of Gamma.
+    // Element (0, 0) was filled by thread 0 of rank 0; p itself is stored unchanged.
+    if (a.zero_piston && L.full && r == 0 && threadIdx.x == 0) {
+        if (coarse)
+            lp[0] = T(0);
+        else
+            cbuf[0] = T(0);
     }
     __syncthreads();
     asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
-    // ---- 2. the leader synthesises the coarse levels into the LL quadrant and pushes its
-    // columns into the column bands' tiles ---------------------------------------------
-    if (coarse && r == 0) {
-        coarse_inverse<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
-        for (int k = threadIdx.x; k < h * h; k += NT) {
-            const int i = k >> lh, j = k & (h - 1);
-            cluster.map_shared_rank(cbuf, static_cast<unsigned>(j >> lrb))[i * cs + (j & (rb - 1))] = lbuf[i * lsd + j];
+    // ---- 2. the LL rows go to the leader (pushed); the leader synthesises the coarse
+    // levels and pushes the quadrant's columns into the column bands' tiles --------------
+    if (coarse) {
+        T* lead = cluster.map_shared_rank(lbuf, 0);
+        for (int k = threadIdx.x; k < lcnt; k += NT) lead[(lr0 + (k >> lh)) * lsd + (k & (h - 1))] = lp[k];
+        cluster.sync();                                                   // #0: the leader holds LL
+        if (r == 0) {
+            coarse_inverse<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+            for (int k = threadIdx.x; k < h * h; k += NT) {
+                const int i = k >> lh, j = k & (h - 1);
+                cluster.map_shared_rank(cbuf, static_cast<unsigned>(j >> lrb))[i * cs + (j & (rb - 1))] =
+                    lbuf[i * lsd + j];
+            }
         }
     }
     cluster.sync();                                                       // #1
@@ -674,7 +753,7 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     }
 }
 
-template <class T, bool PUPD>
+template <class T, int PUPD>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_inv(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay) {

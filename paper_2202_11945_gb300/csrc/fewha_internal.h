@@ -89,6 +89,8 @@ struct alignas(16) Desc {   // 16-byte multiple: batched kernels copy it in 16-b
     // per-coefficient diagonals
     const T* D;
     const T* Jinv;
+    // D per (layer, level): detail level k = 1 .. levels (1 the finest), levels + 1 the LL band
+    T Dlev[MAXL][9];
     // footprint box of each (sensor, layer) pair: row0, rows, col0, cols (16-byte aligned
     // column superset); kept in the descriptor so that warps read it from the constant bank
     int box[MAXG][MAXL][4];
@@ -100,6 +102,7 @@ struct HostSetup {
     std::vector<WfsInfo> G;
     std::vector<DmInfo> Mi;
     std::vector<double> layer_h, layer_w, layer_delta;
+    std::vector<double> dlev;           // D per (layer, level), MAXL * (MAXLEV + 1) (see Desc::Dlev)
     std::vector<double> wfs_sigma;
     double fitw[MAXM][MAXL];
     int n_c = 0, n_s = 0, n_nodes = 0, n_act = 0, max_n = 0, max_N = 0;
@@ -125,6 +128,7 @@ struct HostSetup {
 };
 
 constexpr int MAXLEV = 8;   // log2(MAXN) + 1
+static_assert(MAXLEV + 1 == 9, "Desc::Dlev holds levels 0 .. MAXLEV");
 #ifdef __CUDACC__
 __host__ __device__
 #endif

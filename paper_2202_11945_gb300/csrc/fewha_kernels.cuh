@@ -405,6 +405,13 @@ __device__ __forceinline__ void dwt_inverse(T* S, const LayerInfo& L) {
     }
 }
 
+// Level of position (i, j) of a layer in Mallat layout: detail level k (1 = finest) where
+// n / 2^k <= max(i, j) < n / 2^(k-1), and levels + 1 for the LL band.
+__device__ __forceinline__ int level_of(int i, int j, const LayerInfo& L) {
+    const int m = max(i, j);
+    return m < (L.n >> L.levels) ? L.levels + 1 : L.log2n - (31 - __clz(m));
+}
+
 // ---------------------------------------------------------------------------
 // PCG bookkeeping: per-iteration partial inner products in fixed slots.
 // rz of iteration k = sum of rzpart[k * npart + 0 .. npart); p.q of iteration k =
@@ -827,8 +834,9 @@ enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2 };
 
 constexpr int PVEC = 4;     // elements per thread and pass of the vector kernels
 
-// Body of the vector kernel: CTA `cta` of the `nparts` sharing the instance's vectors.
-template <class T, int PHASE>
+// Body of the vector kernel: CTA `cta` of the `nparts` sharing the instance's vectors, NTV
+// threads per CTA.
+template <class T, int PHASE, int NTV = PBLK>
 __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const int cta,
                                          const int nparts) {
     __shared__ bool last;
@@ -843,12 +851,12 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
         salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
     }
     DotAcc<T> dot;
-    for (int base = cta * PBLK * PVEC; base < n; base += nparts * PBLK * PVEC) {
+    for (int base = cta * NTV * PVEC; base < n; base += nparts * NTV * PVEC) {
         // issue every load of the batch before the arithmetic
         T b[PVEC], q[PVEC], r[PVEC], p[PVEC], c[PVEC], bp[PVEC], jv[PVEC];
 #pragma unroll
         for (int k = 0; k < PVEC; ++k) {
-            const int i = base + k * PBLK + threadIdx.x;
+            const int i = base + k * NTV + threadIdx.x;
             if (i < n) {
                 jv[k] = v.Jinv[i];
                 if (PHASE == V_INIT) {
@@ -873,7 +881,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
         }
 #pragma unroll
         for (int k = 0; k < PVEC; ++k) {
-            const int i = base + k * PBLK + threadIdx.x;
+            const int i = base + k * NTV + threadIdx.x;
             if (i < n) {
                 T rr;
                 if (PHASE == V_INIT) {
@@ -895,7 +903,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
         }
     }
     // CTA share of r.z (fixed order), then the last CTA forms the total in a fixed order
-    __shared__ double part[PBLK];
+    __shared__ double part[NTV];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
     cta_dot_store(dot, part, v.pcg.rzpart + slot * v.pcg.npart + cta);
@@ -930,8 +938,9 @@ enum {
     V_AUG_R0 = 3,        // r0 = b - q (q = M c0), b_prev = b, and p_j.r0
     V_AUG_R0_WARM = 4,   // r0 = (b - b_prev) + r_prev, b_prev = b, and p_j.r0
     V_AUG_INIT = 5,      // c0 += P y, r0 -= Q y, z0 = J^-1 r0, r.z, and q_j.z0
-    V_PROJ = 6,          // p_k = z_k + beta_k p_(k-1) - P mu (no reduction)
     V_UPDATE_AUG = 7     // the CG update of V_UPDATE; keeps p.q; q_j.z for the next direction
+                         // (the direction update p = z + beta p_old - P mu runs fused into the
+                         // inverse wavelet kernel, k_cl_inv with PUPD = 2)
 };
 
 template <class T>
@@ -939,8 +948,6 @@ struct AugArgs {
     const T* P;          // previous frame's directions, [j * ld + i], j < m
     const T* Q;          // their images M p_j
     const double* pq;    // p_j . q_j
-    T* pnew;             // V_PROJ: the direction formed
-    const T* pold;       // V_PROJ: this frame's previous direction (iteration > 0)
     double* pqnew;       // V_UPDATE_AUG: p.q of this frame's direction `iter`
     double* part;        // [t * npart + cta]: CTA shares of the dots
     double* tot;         // [j]: p_j.r0;  [AUG_MAX + j]: q_j.z
@@ -986,8 +993,8 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
     const int m = a.m;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = PBLK >> 5;
     // the scalars, one FP64 division per thread (GB300's FP64 pipe is slow)
-    if ((PHASE == V_AUG_INIT || PHASE == V_PROJ) && threadIdx.x < m) {
-        const double num = PHASE == V_AUG_INIT ? a.tot[threadIdx.x] : a.tot[AUG_MAX + threadIdx.x];
+    if (PHASE == V_AUG_INIT && threadIdx.x < m) {
+        const double num = a.tot[threadIdx.x];
         const double den = a.pq[threadIdx.x];
         scoef[threadIdx.x] = T(den > 0.0 ? num / den : 0.0);
     }
@@ -996,13 +1003,6 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
             const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
             scoef[AUG_MAX] = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
             if (cta == 0) a.pqnew[v.iter] = pq;
-        } else if (PHASE == V_PROJ) {
-            double beta = 0.0;
-            if (v.iter > 0) {
-                const double rn = v.pcg.rztot[v.iter], ro = v.pcg.rztot[v.iter - 1];
-                beta = ro != 0.0 ? rn / ro : 0.0;
-            }
-            scoef[AUG_MAX] = T(beta);
         }
     }
     __syncthreads();
@@ -1030,9 +1030,6 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
                     x0[k] = v.c[i];
                     x1[k] = v.r[i];
                     x2[k] = v.Jinv[i];
-                } else if (PHASE == V_PROJ) {
-                    x0[k] = v.z[i];
-                    if (v.iter > 0) x1[k] = a.pold[i];
                 } else {
                     x0[k] = v.c[i];
                     x1[k] = v.p[i];
@@ -1043,7 +1040,7 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
 #pragma unroll
                 for (int j = 0; j < AUG_MAX; ++j) {
                     if (j < m) {
-                        if (R0 || PHASE == V_AUG_INIT || PHASE == V_PROJ) pj[j][k] = a.P[j * a.ld + i];
+                        if (R0 || PHASE == V_AUG_INIT) pj[j][k] = a.P[j * a.ld + i];
                         if (PHASE == V_AUG_INIT || (PHASE == V_UPDATE_AUG && dots)) qj[j][k] = a.Q[j * a.ld + i];
                     }
                 }
@@ -1077,13 +1074,7 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
 #pragma unroll
                     for (int j = 0; j < AUG_MAX; ++j)
                         if (j < m) dj[j].add(qj[j][k], z);
-                } else if (PHASE == V_PROJ) {
-                    T p = x0[k];
-                    if (v.iter > 0) p = x0[k] + scoef[AUG_MAX] * x1[k];
-#pragma unroll
-                    for (int j = 0; j < AUG_MAX; ++j)
-                        if (j < m) p -= scoef[j] * pj[j][k];
-                    a.pnew[i] = p;
+
                 } else {
                     const T al = scoef[AUG_MAX];
                     v.c[i] = x0[k] + al * x1[k];
@@ -1101,7 +1092,6 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
             }
         }
     }
-    if (PHASE == V_PROJ) return;
     // CTA shares (fixed order): t = 0 is r.z (not in the R0 phases), t = 1 + j dot j
     const bool has_rz = !R0;
     const int nd = dots ? m : 0;
@@ -1147,11 +1137,11 @@ __global__ void __launch_bounds__(PBLK) k_aug(const int n, __grid_constant__ con
 // a = a_prev + g (a~ - a_old), after which a_old = a_prev (the commands of the frame
 // before) and a_prev = a.
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, int NTF = PBLK>
 __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__ phi,
                                          T* __restrict__ a_prev, T* __restrict__ out, int apply_gain,
                                          const int blk, T* __restrict__ a_old = nullptr) {
-    const int idx = blk * PBLK + threadIdx.x;
+    const int idx = blk * NTF + threadIdx.x;
     if (idx >= d.n_act) return;
     int m = 0;
     while (m + 1 < d.n_dms && idx >= d.Mi[m + 1].off) ++m;
@@ -1416,6 +1406,55 @@ __global__ void __launch_bounds__(PBLK) k_wnorm(const int n, const T* __restrict
         for (int k = threadIdx.x; k < PBLK; k += 32) x += part[k];
         x = warp_sum(x);
         if (threadIdx.x == 0) *out = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reliable updates of a mixed-precision CG (a build addition for the converged solves of
+// the single-precision form): the recurrence runs in T on a residual scaled to unit
+// J^-1-norm, its iterate is an increment x that is folded into the double iterate x64
+// (x64 += sc x, x = 0) whenever the recurrence's residual has dropped tenfold; the true
+// residual b - M x64 is then formed in double and replaces the recurrence's residual
+// (r = T(r64 / sc_new), z = J^-1 r, p scaled by sc_old / sc_new so that the search
+// direction continues).  r.z of the refreshed residual goes to rz slot `slot` (0 on a
+// restart, where also p = z; 1 otherwise, with slot 0 set to rz0, the previous r.z in
+// the new scale, so that the next direction update forms beta = slot 1 / slot 0).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_accum(const int n, const double sc, T* __restrict__ x,
+                                                double* __restrict__ x64) {
+    for (int i = blockIdx.x * PBLK + threadIdx.x; i < n; i += gridDim.x * PBLK) {
+        x64[i] += sc * double(x[i]);
+        x[i] = T(0);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(PBLK) k_refresh(const int n, const double* __restrict__ r64, const double scale,
+                                                  const double ratio, const int restart, const double rz0,
+                                                  __grid_constant__ const VecArgs<T> v) {
+    __shared__ bool last;
+    __shared__ double part[PBLK];
+    const int cta = blockIdx.x, nparts = gridDim.x;
+    const T tr = T(ratio);
+    DotAcc<T> dot;
+    for (int i = cta * PBLK + threadIdx.x; i < n; i += nparts * PBLK) {
+        const T r = T(scale * r64[i]);
+        const T z = v.Jinv[i] * r;
+        v.r[i] = r;
+        v.z[i] = z;
+        v.p[i] = restart ? z : tr * v.p[i];
+        dot.add(r, z);
+    }
+    const int slot = restart ? 0 : 1;
+    cta_dot_store(dot, part, v.pcg.rzpart + slot * v.pcg.npart + cta);
+    if (last_arrival(v.pcg.count, nparts, &last) && threadIdx.x < 32) {
+        const double tot = warp_total(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart, &dot);
+        if (threadIdx.x == 0) {
+            v.pcg.rztot[slot] = tot;
+            if (!restart) v.pcg.rztot[0] = rz0;
+            v.pcg.count[0] = 0;
+        }
     }
 }
 

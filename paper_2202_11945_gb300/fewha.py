@@ -417,9 +417,10 @@ class Reconstructor:
 
     # -- converged solve and gradients ------------------------------------------------
     def default_tol(self):
-        """Relative residual of the converged solves: 1e-10 in FP64, 1e-6 in FP32 (FP32
-        operators cannot resolve M's weakly determined modes much further)."""
-        return 1e-10 if self.precision == 64 else 1e-6
+        """Relative residual of the converged solves, 1e-10: the single-precision form
+        refreshes its float recurrence with the true residual formed in double, so both
+        forms reach the same tolerance."""
+        return 1e-10
 
     def solve(self, b, tol=None, max_iters=20000, stream=None):
         """x = M^-1 b (PCG to a relative preconditioned residual); returns (x, iters, rel)."""

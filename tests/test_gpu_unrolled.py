@@ -14,15 +14,12 @@ pytestmark = pytest.mark.gpu
 
 # The reverse pass keeps the forward vectors in the operator precision and forms its
 # scalars in double on the host: FP64 follows the oracle to rounding.  The adjoint
-# recurrence adds terms such as rho_bar z and J^-1 z_bar that cancel to a far smaller
-# result; FP32 vectors resolve that on the single-sensor geometry (1e-3) but not on the
-# MCAO geometries (16 % measured on the 4 m case), where only the direction of the
-# gradient is checked (cosine >= 0.9) and the FP64 form is the differentiable path.
-TOL_GRAD = {64: 1e-8, 32: 1e-3}
-
-
-def cosine(a, b):
-    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+# vectors carry a large piston component (J^-1 of a full-depth layer's piston coefficient
+# is ~1 / (alpha D_LL) ~ 1e5), which the data path of every M apply and the final slope
+# map leave out (Gamma annihilates constants), so float rounding of it cannot leak into
+# the other components: the FP32 gradient then follows the oracle to ~1e-6 (CPU
+# emulation with float rounding at every operator stage), checked at 1e-4.
+TOL_GRAD = {64: 1e-8, 32: 1e-4}
 
 
 def case(name):
@@ -47,10 +44,7 @@ def test_frame_vjp_matches_oracle(name, prec):
     a, gs = R.frame_vjp(to_dev(s, prec), to_dev(c0, prec), to_dev(g_a, prec))
     assert rel_l2(to_np(a), a_ref) <= TOL_FRAME[prec], rel_l2(to_np(a), a_ref)
     g = to_np(gs)
-    if prec == 32 and name != "tiny_scao":
-        assert np.all(np.isfinite(g)) and cosine(g, gs_ref) >= 0.9, (rel_l2(g, gs_ref), cosine(g, gs_ref))
-    else:
-        assert rel_l2(g, gs_ref) <= TOL_GRAD[prec], rel_l2(g, gs_ref)
+    assert rel_l2(g, gs_ref) <= TOL_GRAD[prec], rel_l2(g, gs_ref)
     a2, none = R.frame_vjp(to_dev(s, prec), to_dev(c0, prec))        # forward only
     assert none is None and np.array_equal(to_np(a2), to_np(a))
     R.close()

@@ -24,8 +24,12 @@ def _noalloc(R, c, q):
     return rc
 
 
+# the elongated geometries exercise the LGS spot-elongation weighting (Eq. 3) of the
+# single-CTA sensor kernel this entry point runs, against the cluster kernels of apply_M
 @pytest.mark.parametrize("name,prec", [("tiny_mcao", 64), ("tiny_mcao", 32), ("maory", 32),
-                                       ("maory", 64)])
+                                       ("maory", 64), ("tiny_mcao_elongated", 64),
+                                       ("tiny_mcao_elongated", 32), ("paper_mcao", 32),
+                                       ("paper_mcao", 64)])
 def test_matches_apply_M_on_consecutive_calls(name, prec):
     R = recon(name, prec)
     rng = np.random.default_rng(77)
