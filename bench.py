@@ -267,8 +267,11 @@ def time_loop(frames, warmup=100, period_us=1000.0):
     dm, wall, dev, late = R.run_loop(S, period_us=period_us)
     Rw = Reconstructor(wl, precision=32, graph=True, warm_residual=True)
     dmw, _, _, _ = Rw.run_loop(S, period_us=0.0)
+    Rr = Reconstructor(wl, precision=32, graph=True, warm_residual=True, warm_refresh=50)
+    dmr, _, _, _ = Rr.run_loop(S, period_us=0.0)
     R.close()
     Rw.close()
+    Rr.close()
     wall, dev = wall.numpy().astype(float), dev.numpy().astype(float)
     out = {"workload": wl["name"], "frames": frames, "period_us": period_us,
            "form": "FP32 operators, FP64 dots, CUDA graph; host slopes in, host commands out",
@@ -276,7 +279,7 @@ def time_loop(frames, warmup=100, period_us=1000.0):
                           "max": float(wall.max())},
            "device_us": {"p50": float(np.percentile(dev, 50)), "p99": float(np.percentile(dev, 99))},
            "late_frames": late}
-    return out, wl, S, dm.double().numpy(), dmw.double().numpy()
+    return out, wl, S, dm.double().numpy(), (dmw.double().numpy(), dmr.double().numpy())
 
 
 def frame_bytes(R, b=4):
@@ -441,6 +444,65 @@ def time_augmented(wl, S32, S_np, flush, steps, parity=True):
     return out
 
 
+def time_persistent(wl, S32, S_np, flush, steps, parity=True):
+    """The persistent frame (one cooperative launch per frame, grid-wide waits between the
+    stages) on the MAORY workload, FP32 and graph-captured, against the graph of separate
+    launches; parity of its first frames against the oracle."""
+    from paper_2202_11945_gb300 import Reconstructor
+    out = {"workload": wl["name"], "steps": steps}
+    for name, kw in (("launches", {}), ("persistent", {"persistent": True})):
+        R = Reconstructor(wl, precision=32, graph=True, **kw)
+        dm = torch.empty(R.n_act, dtype=torch.float32, device="cuda")
+        t = time_frames(R, S32, steps, 20, flush, dm)
+        out[name] = {"frames_per_s": 1e3 / float(t.mean()), "p50_ms": float(np.percentile(t, 50)),
+                     "p99_ms": float(np.percentile(t, 99)), "launches_per_frame": R.frame_launches()}
+        R.close()
+    if parity:
+        import oracle as O
+        ref = O.Reconstructor(wl)
+        R = Reconstructor(wl, precision=32, graph=True, persistent=True)
+        err = []
+        for k in range(3):
+            a = R.reconstruct(S32[k]).double().cpu().numpy()
+            a_ref = ref.frame(S_np[k])
+            err.append(float(np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)))
+        R.close()
+        out["parity_max_rel_l2_dm"] = max(err)
+    return out
+
+
+def footprint(wl, S32, S_np):
+    """Device memory of the MAORY instance (Sec. 4.3 compares 16 MB for FEWHA with 53 GB for
+    a matrix-vector method): the instance's own accounting (fewha_device_bytes) and the drop
+    of the device's free memory, at creation and after the options' first use."""
+    from paper_2202_11945_gb300 import Reconstructor
+
+    def free():
+        torch.cuda.synchronize()
+        return torch.cuda.mem_get_info()[0]
+    out = {"workload": wl["name"], "unit": "MB"}
+    for prec in (32, 64):
+        dt = torch.float32 if prec == 32 else torch.float64
+        f0 = free()
+        R = Reconstructor(wl, precision=prec, graph=True)
+        rec = {"created": R.device_bytes() / 1e6, "created_free_drop": (f0 - free()) / 1e6}
+        R.close()
+        R = Reconstructor(wl, precision=prec, graph=True, augmented=True)
+        R.reconstruct(S32[0].to(dt))
+        rec["augmented"] = R.device_bytes() / 1e6
+        R.close()
+        R = Reconstructor(wl, precision=prec, graph=False)
+        s = S32[1].to(dt)
+        c0 = torch.zeros(R.n_coeffs, dtype=dt, device="cuda")
+        R.frame_vjp(s, c0, torch.ones(R.n_act, dtype=dt, device="cuda"))
+        rec["with_reverse_record"] = R.device_bytes() / 1e6
+        R.reconstruct_converged(s, tol=1e-3, max_iters=200)
+        rec["with_reverse_record_and_converged"] = R.device_bytes() / 1e6
+        R.close()
+        out["fp%d" % prec] = rec
+    return out
+
+
 def time_closed_loop(wl, S32, S_np, flush, steps, parity=True):
     """Closed-loop frames (Algorithm 1: pseudo-open-loop slopes from the commands of two
     frames back, delayed control law) on the MAORY workload, FP32 graph form; the timed
@@ -539,7 +601,10 @@ def time_unrolled(wl, S_np, reps=10, parity=True):
 
 def loop_parity(wl, S, dm, dmw):
     """Per-frame relative L2 error of the loop's commands against the FP64 oracle run on
-    the same sequence (explicit initial residual), and the oracle's own frame rate."""
+    the same sequence (explicit initial residual), of the warm-residual recurrence's
+    commands without and with an explicit refresh every 50th frame, and the oracle's own
+    frame rate."""
+    dmw, dmr = dmw
     import oracle as O
     ref = O.Reconstructor(wl)
     t0 = time.perf_counter()
@@ -550,7 +615,17 @@ def loop_parity(wl, S, dm, dmw):
     return {"max_rel_l2_dm": float(e.max()), "p99_rel_l2_dm": float(np.percentile(e, 99)),
             "warm_residual_max_rel_l2_dm": float(ew.max()),
             "warm_residual_last_rel_l2_dm": float(ew[-1]),
+            "warm_residual_refresh50_max_rel_l2_dm": float(max(np.linalg.norm(x - y) / np.linalg.norm(y)
+                                                               for x, y in zip(dmr, a))),
             "oracle_frames_per_s": len(S) / t}
+
+
+def bench_config(wl, n_coeffs, n_slopes, n_act, world):
+    """The workload of the JSON line, the same for the native and the reference arm."""
+    return {"workload": wl["name"], "n_coeffs": n_coeffs, "n_slopes": n_slopes, "n_act": n_act,
+            "iters": wl["params"]["iters"], "warm_start": True, "initial_residual": "explicit b - M c0",
+            "l2": "512 MiB memset between timed frames (native arm)",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def run_reference(args, world, rank):
@@ -577,7 +652,7 @@ def run_reference(args, world, rank):
         "steps": steps, "warmup": warm, "ms_per_step": float(ts.mean()),
         "p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wl["name"], "iters": wl["params"]["iters"]},
+        "data": "synthetic", "config": bench_config(wl, ref.geo.n_c, ref.geo.n_s, ref.geo.n_a, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d warm-started MAORY frames after %d warm-up (requested "
                                    "%d/%d), numpy FP64, 1 thread" % (steps, warm, args.steps,
@@ -665,6 +740,9 @@ def main():
                  if args.aug_steps > 0 else None)
     closed = (time_closed_loop(wl, S32, S_np, flush, args.aug_steps, parity=(rank == 0 and world == 1))
               if args.aug_steps > 0 else None)
+    pers = (time_persistent(wl, S32, S_np, flush, args.aug_steps, parity=(rank == 0 and world == 1))
+            if args.aug_steps > 0 else None)
+    foot = footprint(wl, S32, S_np)
     paper = (time_paper_geometry(flush, args.aug_steps, parity=(rank == 0 and world == 1))
              if args.aug_steps > 0 else None)
     unrolled = time_unrolled(wl, S_np, parity=(rank == 0 and world == 1)) if args.backward_frames > 0 else None
@@ -685,13 +763,10 @@ def main():
             "p50_ms": float(np.percentile(t32, 50)), "p99_ms": float(np.percentile(t32, 99)),
             "max_ms": float(t32.max()),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "form": "FP32 operators, FP64 dots, CUDA graph",
             "data": "synthetic: seeded 35-layer von Karman atmosphere with frozen flow, "
                     "simulated SH slopes + noise; %d distinct frames cycled" % N_FRAMES_INPUT,
-            "config": {"workload": wl["name"], "n_coeffs": R32.n_coeffs, "n_slopes": R32.n_slopes,
-                       "n_act": R32.n_act, "iters": wl["params"]["iters"], "warm_start": True,
-                       "initial_residual": "explicit b - M c0", "form": "FP32 operators, FP64 "
-                       "dots, CUDA graph", "l2": "512 MiB memset between timed frames",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": bench_config(wl, R32.n_coeffs, R32.n_slopes, R32.n_act, world),
             "fp64_plain": {"value": replica_throughput(world, args.steps, total64), "unit": UNIT,
                            "ms_per_step": total64 / args.steps,
                            "p50_ms": float(np.percentile(t64, 50)),
@@ -716,6 +791,8 @@ def main():
             "backward": backward,
             "augmented": augmented,
             "closed_loop": closed,
+            "persistent": pers,
+            "footprint": foot,
             "paper_geometry": paper,
             "unrolled_backward": unrolled,
         }

@@ -69,6 +69,8 @@ extern "C" {
 #define FEWHA_ERR_NONFINITE (-5)   /* a NaN/Inf was found in the input slopes, or a
                                       recurrence being differentiated stopped          */
 #define FEWHA_ERR_LIMIT (-6)       /* a size exceeds a compiled-in maximum          */
+#define FEWHA_ERR_TIMEOUT (-7)     /* a grid-wide wait of the persistent frame ran out
+                                      of polls (FEWHA_FLAG_PERSISTENT)                 */
 
 #define FEWHA_MAX_LAYERS 16
 #define FEWHA_MAX_WFS 16
@@ -104,6 +106,18 @@ extern "C" {
                                        sets a^(i) only.  Every DM must sit below every
                                        LGS (FEWHA_ERR_GEOMETRY).  Not available in
                                        batched frames (FEWHA_ERR_INVALID_ARG).         */
+
+#define FEWHA_FLAG_PERSISTENT 32u  /* run each frame (right-hand side, initial residual,
+                                       PCG iterations, fit: Algorithm 1) as ONE cooperative
+                                       launch of thread-block clusters whose stages are
+                                       separated by grid-wide waits instead of kernel
+                                       boundaries.  Every wait gives up after a bounded
+                                       number of polls (fewha_set_wait_limit); the frame
+                                       then stops and FEWHA_ERR_TIMEOUT is reported by the
+                                       host-buffer entry points, fewha_run_loop and
+                                       fewha_check_input.  Not with FEWHA_FLAG_AUGMENTED or
+                                       FEWHA_FLAG_CLOSED_LOOP (FEWHA_ERR_INVALID_ARG);
+                                       batched frames ignore it.                          */
 
 /* Telescope aperture: diameter D [m], central obstruction as a diameter ratio. */
 typedef struct fewha_telescope {
@@ -166,6 +180,10 @@ typedef struct fewha_params {
     int precision;
     unsigned flags;
     double alpha_eta;   /* spot-elongation tuning of Eq. 3 (Table 5); 0 = C_g = sigma^2 I */
+    int warm_refresh;   /* with FEWHA_FLAG_WARM_RESIDUAL: after this many frames in a row on
+                           the warm recurrence r0 = (b - b_prev) + r_prev, one frame forms the
+                           explicit r0 = b - M c0, which bounds the recurrence's drift in
+                           single precision; 0 = never */
 } fewha_params;
 
 typedef struct fewha_handle fewha_handle;
@@ -266,7 +284,9 @@ int fewha_run_loop_f64(fewha_handle* h, const double* h_slopes, int n_frames, do
                        void* stream);
 
 /* Non-finite flag of the slopes read by frames since the last call (1 if any NaN or
- * Inf was seen), then cleared.  Synchronises on `stream`. */
+ * Inf was seen), then cleared.  Returns FEWHA_ERR_TIMEOUT (the flag still written) if a
+ * persistent frame since the last call stopped because a grid-wide wait ran out.
+ * Synchronises on `stream`. */
 int fewha_check_input(fewha_handle* h, int* nonfinite, void* stream);
 
 /* ---- operator entry points (the handle's element type; asynchronous) ----------- */
@@ -320,6 +340,23 @@ int fewha_bench_stage(fewha_handle* h, int stage, int reps, void* stream);
 /* Kernel launches one frame enqueues (for the launch count of a timed region; for
  * FEWHA_FLAG_AUGMENTED, a frame that has the previous frame's directions). */
 int fewha_frame_launches(const fewha_handle* h, int* launches);
+
+/* Device memory held by the instance (its own allocations, made at creation and on first
+ * use of an option: the augmented PCG's directions, the reverse pass's record, the double
+ * copy of a single-precision instance's converged solves), in bytes. */
+int fewha_device_bytes(const fewha_handle* h, int64_t* bytes);
+
+/* Test hook of the allocation-failure paths: the device allocations of the calling thread
+ * succeed `after` more times, then one fails as if the device were out of memory (the
+ * call making it returns FEWHA_ERR_OOM and releases what it had allocated); after < 0
+ * turns the injection off.  Returns FEWHA_OK. */
+int fewha_test_fail_alloc(int after);
+
+/* Grid-wide waits of the persistent frame (FEWHA_FLAG_PERSISTENT): each gives up after
+ * `polls` polls of its arrival counter (each poll a load and a 64 ns sleep; default
+ * 1 << 20, well under a second).  `extra` is added to every wait's target; any value > 0 makes every wait run
+ * out (tests of the timeout path).  Applies to frames enqueued after the call. */
+int fewha_set_wait_limit(fewha_handle* h, unsigned polls, unsigned extra);
 
 /* ---- differentiable reconstruction (a build addition: the paper has no gradients) --
  * The differentiable map is the CONVERGED reconstruction: c* solves M c = b (Eq. 6) to a

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "fewha_batch.h"
+#include "fewha_persist.cuh"
 
 using namespace fewha;
 
@@ -48,6 +49,7 @@ struct fewha_handle {
     HostSetup setup;
     std::vector<double> weights;   // current layer Cn2 weights
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_sizes;   // bytes of each of allocs
     // device tables (precision independent)
     int *pi0y = nullptr, *pi0x = nullptr, *ry_lo = nullptr, *ry_hi = nullptr, *rx_lo = nullptr,
         *rx_hi = nullptr, *sidx = nullptr, *cidx = nullptr, *di0 = nullptr, *dr_lo = nullptr,
@@ -82,8 +84,9 @@ struct fewha_handle {
     int aug_set = 0, aug_m = 0;
     // frame-graph cache
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec[2] = {};    // plain frames: [explicit r0, warm r0]
     cudaGraphExec_t gaug[4] = {};     // augmented frames: [2 * set + (directions present)]
+    int warm_run = 0;                 // frames in a row on the warm-residual recurrence
     // reverse pass through the fixed-iteration frame: its recorded vectors (allocated on use)
     void* vjp = nullptr;
     size_t vjp_cap = 0;
@@ -97,6 +100,7 @@ struct fewha_handle {
     ClLayout lay_fwd{}, lay_inv{};
     SensorLayout lay_sen{};
     size_t smem_fwd = 0, smem_inv = 0, smem_sen = 0, smem_proj = 0, smem_projT = 0;
+    int kmax = KMAX;                  // most aperture rows / columns touching one layer row / column
     // (sensor, layer) pair terms of P and P^T
     int* box = nullptr;
     int* ytab = nullptr;              // band-run table of the forward kernel (PairBufs::ytab)
@@ -117,6 +121,13 @@ struct fewha_handle {
     std::vector<fewha_layer> layers_in;
     std::vector<fewha_dm> dms_in;
     fewha_handle* twin = nullptr;
+    // persistent frame (FEWHA_FLAG_PERSISTENT): grid-barrier words (arrivals, abort), the
+    // clusters of its launch (0 = not set up yet), its dynamic shared memory, wait limits
+    unsigned* gbar = nullptr;
+    int pers_ncl = 0;
+    size_t smem_frame = 0;
+    unsigned wait_limit = 1u << 20;
+    unsigned wait_extra = 0;
 };
 
 struct fewha_batch {
@@ -158,16 +169,38 @@ int cuda_fail(fewha_handle* H, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(H, e_, where); \
     } while (0)
 
+// Allocation-failure injection (fewha_test_fail_alloc): the number of device allocations
+// of this thread still to succeed before one fails; -1 = off.
+thread_local int g_fail_countdown = -1;
+
+// Every device allocation of the library goes through here.
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (g_fail_countdown >= 0) {
+        if (g_fail_countdown == 0) {
+            g_fail_countdown = -1;
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        --g_fail_countdown;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void track(fewha_handle* H, void* p, size_t bytes) {
+    H->allocs.push_back(p);
+    H->alloc_sizes.push_back(bytes);
+}
+
 template <class X>
 int dalloc(fewha_handle* H, X** ptr, size_t count) {
     void* p = nullptr;
     const size_t bytes = count * sizeof(X) > 0 ? count * sizeof(X) : 16;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dev_malloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(H, FEWHA_ERR_OOM, "device allocation failed");
     }
     cudaMemset(p, 0, bytes);
-    H->allocs.push_back(p);
+    track(H, p, bytes);
     *ptr = static_cast<X*>(p);
     return FEWHA_OK;
 }
@@ -176,12 +209,12 @@ int talloc(fewha_handle* H, void** ptr, size_t count) {
     void* p = nullptr;
     // 16 spare elements: the 16-byte staging copies may read up to one chunk past a vector
     const size_t bytes = (count + 16) * H->esz;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dev_malloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(H, FEWHA_ERR_OOM, "device allocation failed");
     }
     cudaMemset(p, 0, bytes);
-    H->allocs.push_back(p);
+    track(H, p, bytes);
     *ptr = p;
     return FEWHA_OK;
 }
@@ -388,9 +421,14 @@ int launch_projT(fewha_handle* H, const Desc<T>& d, const T* u, cudaStream_t st)
         record<T>(BK_PROJT).ptr = u;
         return FEWHA_OK;
     }
-    CK(launch_k(H, k_projT<T>, dim3(d.n_wfs, d.n_layers), dim3(cblk<T>()), H->smem_projT, st, d, u,
-                pair_bufs<T>(H)),
-       "k_projT launch");
+    if (H->kmax <= 4)
+        CK(launch_k(H, k_projT<T, 4>, dim3(d.n_wfs, d.n_layers), dim3(cblk<T>()), H->smem_projT, st, d, u,
+                    pair_bufs<T>(H)),
+           "k_projT launch");
+    else
+        CK(launch_k(H, k_projT<T, KMAX>, dim3(d.n_wfs, d.n_layers), dim3(cblk<T>()), H->smem_projT, st, d, u,
+                    pair_bufs<T>(H)),
+           "k_projT launch");
     return FEWHA_OK;
 }
 
@@ -647,11 +685,77 @@ int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain,
                          static_cast<T*>(H->a_old));
 }
 
+template <class K>
+int allow_smem(fewha_handle* H, K kernel, size_t need);
+
+// Set-up of the persistent frame: its shared memory (the largest of the stages' bodies) and
+// its clusters, at least one per layer and per sensor, up to one CTA per (sensor, layer)
+// pair, no more than can be co-resident (cooperative launch).
+template <class T>
+int persistent_setup(fewha_handle* H) {
+    if (H->pers_ncl) return FEWHA_OK;
+    const HostSetup& s = H->setup;
+    const int nl = static_cast<int>(s.L.size()), nw = static_cast<int>(s.G.size());
+    H->smem_frame = std::max({H->smem_fwd, H->smem_inv, H->smem_sen, H->smem_proj, H->smem_projT});
+    int rc;
+    if ((rc = allow_smem(H, k_frame<T>, H->smem_frame))) return rc;
+    const int need = std::max(nl, nw), want = std::max(need, (nl * nw + CL - 1) / CL);
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(CL, want);
+    q.blockDim = dim3(cblk<T>());
+    q.dynamicSmemBytes = H->smem_frame;
+    int fit = 0;
+    CK(cudaOccupancyMaxActiveClusters(&fit, k_frame<T>, &q), "persistent frame occupancy");
+    if (fit < need) return fail(H, FEWHA_ERR_LIMIT, "persistent frame: too few co-resident clusters");
+    H->pers_ncl = std::min(want, fit);
+    return FEWHA_OK;
+}
+
+// One frame of Algorithm 1 as the persistent kernel (see fewha_persist.cuh).
+template <class T>
+int enqueue_persistent(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStream_t st) {
+    const Desc<T> d = make_desc<T>(H);
+    const int ncl = H->pers_ncl, nctas = ncl * CL;
+    FrameArgs<T> f;
+    f.s = s;
+    f.c = c;
+    f.dm = dm;
+    f.a_prev = static_cast<T*>(H->a_prev);
+    f.b = static_cast<T*>(H->b);
+    f.phi = static_cast<T*>(H->phi);
+    f.u = static_cast<T*>(H->u);
+    f.q = static_cast<T*>(H->q);
+    f.v = vec_args<T>(H, c, 0);
+    f.v.pcg.npart = nctas;
+    f.status = H->status;
+    f.iters = H->params.iters;
+    f.warm = warm ? 1 : 0;
+    f.apply_gain = 1;
+    f.pq_scratch = PQ_SCRATCH_SLOT;
+    const GridSync g{H->gbar, H->gbar + 1, H->status, H->wait_limit, H->wait_extra, static_cast<unsigned>(nctas)};
+    CK(cudaMemsetAsync(H->gbar, 0, 2 * sizeof(unsigned), st), "persistent frame barrier");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, ncl);
+    cfg.blockDim = dim3(cblk<T>());
+    cfg.dynamicSmemBytes = H->smem_frame;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_frame<T>, d, H->lay_fwd, H->lay_inv, H->lay_sen, pair_bufs<T>(H), f, g),
+       "k_frame launch");
+    return FEWHA_OK;
+}
+
 // One frame of Algorithm 1 (open loop).
 // (With FEWHA_FLAG_AUGMENTED the PCG is the augmented one; its directions go to set
 // H->aug_set, augmented by the H->aug_m directions of the other set.)
 template <class T>
 int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStream_t st) {
+    if ((H->params.flags & FEWHA_FLAG_PERSISTENT) && !recorder<T>())
+        return enqueue_persistent<T>(H, s, c, dm, warm, st);
     const Desc<T> d = make_desc<T>(H);
     int rc;
     if (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) {
@@ -670,8 +774,10 @@ int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStrea
 }
 
 void drop_graph(fewha_handle* H) {
-    if (H->gexec) cudaGraphExecDestroy(H->gexec);
-    H->gexec = nullptr;
+    for (auto& g : H->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
     for (auto& g : H->gaug) {
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
@@ -683,14 +789,18 @@ void drop_graph(fewha_handle* H) {
 
 template <class T>
 int run_frame(fewha_handle* H, const T* s, T* c, T* dm, cudaStream_t st) {
-    const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) && H->have_prev;
+    // the warm recurrence, unless a periodic explicit refresh is due
+    const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) && H->have_prev &&
+                      !(H->params.warm_refresh > 0 && H->warm_run >= H->params.warm_refresh);
     const bool aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) != 0;
     int rc;
     if (aug && (rc = ensure_aug(H))) return rc;
+    if ((H->params.flags & FEWHA_FLAG_PERSISTENT) && (rc = persistent_setup<T>(H))) return rc;
     if (H->params.flags & FEWHA_FLAG_GRAPH) {
-        if (H->g_s != s || H->g_x != c || H->g_dm != dm || H->g_warm != warm) drop_graph(H);
-        // one graph per form: plain, or augmented per (direction set, directions present)
-        cudaGraphExec_t* gx = aug ? &H->gaug[2 * H->aug_set + (H->aug_m > 0 ? 1 : 0)] : &H->gexec;
+        if (H->g_s != s || H->g_x != c || H->g_dm != dm || (aug && H->g_warm != warm)) drop_graph(H);
+        // one graph per form: plain per initial residual (explicit, warm), or augmented per
+        // (direction set, directions present)
+        cudaGraphExec_t* gx = aug ? &H->gaug[2 * H->aug_set + (H->aug_m > 0 ? 1 : 0)] : &H->gexec[warm ? 1 : 0];
         if (!*gx) {
             CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             rc = enqueue_frame<T>(H, s, c, dm, warm, H->cap_stream);
@@ -717,6 +827,7 @@ int run_frame(fewha_handle* H, const T* s, T* c, T* dm, cudaStream_t st) {
         if ((rc = enqueue_frame<T>(H, s, c, dm, warm, st))) return rc;
     }
     H->have_prev = true;
+    H->warm_run = warm ? H->warm_run + 1 : 0;
     if (aug) {
         H->aug_m = H->params.iters;
         H->aug_set = 1 - H->aug_set;
@@ -824,7 +935,8 @@ int set_smem_limits(fewha_handle* H) {
         (rc = allow_smem(H, k_cl_inv<T, 2>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_sensor<T, SSRC_PHI>, H->smem_sen)) ||
         (rc = allow_smem(H, k_cl_sensor<T, SSRC_SLOPES>, H->smem_sen)) ||
-        (rc = allow_smem(H, k_proj<T>, H->smem_proj)) || (rc = allow_smem(H, k_projT<T>, H->smem_projT)))
+        (rc = allow_smem(H, k_proj<T>, H->smem_proj)) || (rc = allow_smem(H, k_projT<T, 4>, H->smem_projT)) ||
+        (rc = allow_smem(H, k_projT<T, KMAX>, H->smem_projT)))
         return rc;
     return FEWHA_OK;
 }
@@ -853,6 +965,7 @@ int cluster_layouts(fewha_handle* H) {
         }
     }
     if (kmax > KMAX) return fail(H, FEWHA_ERR_LIMIT, "more than 8 aperture rows touch one layer row");
+    H->kmax = kmax;
     ybuf = round4(ybuf);
     cbuf = round4(cbuf);
     lbuf = round4(lbuf);
@@ -1041,6 +1154,14 @@ int check_params(const fewha_params* p, std::string& err) {
         err = "iters out of range";
         return FEWHA_ERR_LIMIT;
     }
+    if (p->warm_refresh < 0) {
+        err = "warm_refresh must be >= 0";
+        return FEWHA_ERR_INVALID_ARG;
+    }
+    if ((p->flags & FEWHA_FLAG_PERSISTENT) && (p->flags & (FEWHA_FLAG_AUGMENTED | FEWHA_FLAG_CLOSED_LOOP))) {
+        err = "the persistent frame runs the plain open-loop PCG only";
+        return FEWHA_ERR_INVALID_ARG;
+    }
     if ((p->flags & FEWHA_FLAG_AUGMENTED) && p->iters > FEWHA_AUG_MAX_ITERS) {
         err = "augmented PCG keeps at most FEWHA_AUG_MAX_ITERS directions";
         return FEWHA_ERR_LIMIT;
@@ -1074,7 +1195,7 @@ int typed_create(fewha_handle* H) {
         (rc = dalloc(H, &H->pqpart, static_cast<size_t>(FEWHA_MAX_ITERS + 2) * PQ_SLOTS)) ||
         (rc = dalloc(H, &H->rztot, static_cast<size_t>(FEWHA_MAX_ITERS + 2))) ||
         (rc = dalloc(H, &H->pqtot, static_cast<size_t>(FEWHA_MAX_ITERS + 2))) ||
-        (rc = dalloc(H, &H->count, 2)) || (rc = dalloc(H, &H->status, 1)) ||
+        (rc = dalloc(H, &H->count, 2)) || (rc = dalloc(H, &H->status, 1)) || (rc = dalloc(H, &H->gbar, 4)) ||
         (rc = dalloc(H, &H->qi0y, s.qi0y.size())) || (rc = dalloc(H, &H->qi0x, s.qi0x.size())))
         return rc;
     if ((rc = talloc(H, &H->pfy, tab)) || (rc = talloc(H, &H->pfx, tab)) ||
@@ -1143,10 +1264,12 @@ int enqueue_host_frame(fewha_handle* H, const T* hs, T* hdm, unsigned* flag, cud
 }
 
 // After the stream has synchronised: clear a raised non-finite flag.
+// The frame's status word: bit 0 non-finite slopes, bit 1 a persistent frame's wait ran out.
 int clear_flag(fewha_handle* H, unsigned flag, cudaStream_t st) {
     if (!flag) return FEWHA_OK;
     cudaMemsetAsync(H->status, 0, sizeof(unsigned), st);
     cudaStreamSynchronize(st);
+    if (flag & 2u) return fail(H, FEWHA_ERR_TIMEOUT, "a grid-wide wait of the persistent frame ran out");
     return fail(H, FEWHA_ERR_NONFINITE, "non-finite value in the input slopes");
 }
 
@@ -1203,7 +1326,12 @@ int run_loop(fewha_handle* H, const T* hs, int n_frames, T* hdm, double period_u
             break;
         }
         const clock::time_point end = clock::now();
-        if (clear_flag(H, flag, st) && first_bad < 0) first_bad = k;
+        const int fr = clear_flag(H, flag, st);
+        if (fr == FEWHA_ERR_TIMEOUT) {
+            rc = fail(H, fr, "a grid-wide wait of the persistent frame ran out in frame " + std::to_string(k));
+            break;
+        }
+        if (fr && first_bad < 0) first_bad = k;
         if (wall_us) wall_us[k] = static_cast<float>(std::chrono::duration<double, std::micro>(end - start).count());
         if (device_us) {
             float ms = 0.f;
@@ -1570,7 +1698,9 @@ int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* 
     if (H->vjp_cap < need) {
         if (H->vjp) {
             cudaFree(H->vjp);
-            H->allocs.erase(std::remove(H->allocs.begin(), H->allocs.end(), H->vjp), H->allocs.end());
+            const size_t at = std::find(H->allocs.begin(), H->allocs.end(), H->vjp) - H->allocs.begin();
+            H->allocs.erase(H->allocs.begin() + at);
+            H->alloc_sizes.erase(H->alloc_sizes.begin() + at);
             H->vjp = nullptr;
         }
         int rc0;
@@ -1875,7 +2005,7 @@ int batch_build(fewha_batch* B, const std::vector<Recorder<T>>& recs, const std:
     }
     B->args_off = off;
     const size_t total = off + args.size();
-    cudaError_t e = cudaMalloc(&B->dev, total);
+    cudaError_t e = dev_malloc(&B->dev, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         B->dev = nullptr;
@@ -2023,7 +2153,7 @@ int batch_autotune(fewha_batch* B, const void* const* s, void* const* dm, int re
     size_t per = 0;
     for (const fewha_handle* H : B->h) per += (3 * static_cast<size_t>(H->setup.n_c) + H->setup.n_act) * sizeof(T);
     void* snap = nullptr;
-    if (cudaMalloc(&snap, per) != cudaSuccess) {
+    if (dev_malloc(&snap, per) != cudaSuccess) {
         cudaGetLastError();
         return bfail(B, FEWHA_ERR_OOM, "autotune snapshot allocation failed");
     }
@@ -2645,7 +2775,8 @@ int fewha_check_input(fewha_handle* H, int* nonfinite, void* stream) {
     CK(cudaMemcpyAsync(&flag, H->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "status");
     CK(cudaMemsetAsync(H->status, 0, sizeof(unsigned), st), "status");
     CK(cudaStreamSynchronize(st), "status");
-    *nonfinite = flag ? 1 : 0;
+    *nonfinite = (flag & 1u) ? 1 : 0;
+    if (flag & 2u) return fail(H, FEWHA_ERR_TIMEOUT, "a grid-wide wait of the persistent frame ran out");
     return FEWHA_OK;
 }
 
@@ -2685,7 +2816,29 @@ int fewha_frame_launches(const fewha_handle* H, int* launches) {
     // fused into the inverse kernel of each apply)
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
     const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
-    *launches = closed + 3 + (warm ? 1 : 6) + aug + 6 * H->params.iters + 2;
+    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + 3 + (warm ? 1 : 6) + aug + 6 * H->params.iters + 2;
+    return FEWHA_OK;
+}
+
+int fewha_device_bytes(const fewha_handle* H, int64_t* bytes) {
+    if (!H || !bytes) return FEWHA_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (const fewha_handle* X = H; X; X = X->twin)
+        for (size_t b : X->alloc_sizes) total += static_cast<int64_t>(b);
+    *bytes = total;
+    return FEWHA_OK;
+}
+
+int fewha_test_fail_alloc(int after) {
+    g_fail_countdown = after < 0 ? -1 : after;
+    return FEWHA_OK;
+}
+
+int fewha_set_wait_limit(fewha_handle* H, unsigned polls, unsigned extra) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    H->wait_limit = polls;
+    H->wait_extra = extra;
+    drop_graph(H);                    // the limits are kernel arguments of a captured frame
     return FEWHA_OK;
 }
 

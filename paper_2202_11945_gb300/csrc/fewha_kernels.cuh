@@ -838,7 +838,8 @@ constexpr int PVEC = 4;     // elements per thread and pass of the vector kernel
 // threads per CTA.
 template <class T, int PHASE, int NTV = PBLK>
 __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const int cta,
-                                         const int nparts) {
+                                         const int nparts, const int iter_override = -1) {
+    const int iter = iter_override >= 0 ? iter_override : v.iter;   // the CG iteration
     __shared__ bool last;
     __shared__ T salpha;
     T ta = T(0);
@@ -847,7 +848,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
         // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final).  Formed
         // once and broadcast (an FP64 division is ~10 instructions on GB300's slow FP64
         // pipe), while the first batch of vector loads is in flight
-        const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
+        const double rz = v.pcg.rztot[iter], pq = v.pcg.pqtot[iter];
         salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
     }
     DotAcc<T> dot;
@@ -905,7 +906,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     // CTA share of r.z (fixed order), then the last CTA forms the total in a fixed order
     __shared__ double part[NTV];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = (PHASE == V_UPDATE) ? v.iter + 1 : 0;
+    const int slot = (PHASE == V_UPDATE) ? iter + 1 : 0;
     cta_dot_store(dot, part, v.pcg.rzpart + slot * v.pcg.npart + cta);
     if (last_arrival(v.pcg.count, nparts, &last) && w == 0) {
         const double tot = warp_total(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart, &dot);

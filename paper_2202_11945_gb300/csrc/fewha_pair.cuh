@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(cblk<T>(), 1) k_proj(__grid_constant__ const D
     proj_body<T>(d, phi, pb, blockIdx.x, blockIdx.y);
 }
 
-// Y_gl(i, j) = sum_{a,b} wy(a, i) wx(b, j) u_g(a, b) on the pair's footprint box.
-template <class T>
+// Y_gl(i, j) = sum_{a,b} wy(a, i) wx(b, j) u_g(a, b) on the pair's footprint box.  KM >= the
+// largest number of aperture rows (columns) touching one layer row (column): the loops over
+// a row's taps are unrolled to KM (the weight tables keep the stride KMAX).
+template <class T, int KM = KMAX>
 __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict__ u,
                                            const PairBufs<T>& pb, const int g, const int l) {
     constexpr int NT = cblk<T>();
@@ -112,14 +114,14 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
         const int jj = threadIdx.x % cols, rg = threadIdx.x / cols;
         if (rg < groups) {
             const int2 ci = cinf[jj];
-            T w[KMAX];
+            T w[KM];
 #pragma unroll
-            for (int q = 0; q < KMAX; ++q) w[q] = cw[jj * KMAX + q];
+            for (int q = 0; q < KM; ++q) w[q] = cw[jj * KMAX + q];
             for (int a = rg; a < NP; a += groups) {
                 const T* urow = Us + a * NP + ci.x;
                 T acc = T(0);
 #pragma unroll
-                for (int q = 0; q < KMAX; ++q)
+                for (int q = 0; q < KM; ++q)
                     if (q < ci.y) acc += w[q] * urow[q];
                 Tx[a * cols + jj] = acc;
             }
@@ -132,26 +134,26 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
     (void)r0;
     for (int ii = warp; ii < rows; ii += nwarp) {
         const int2 ri = rinf[ii];
-        T wv[KMAX];
+        T wv[KM];
 #pragma unroll
-        for (int q = 0; q < KMAX; ++q) wv[q] = rw[ii * KMAX + q];
+        for (int q = 0; q < KM; ++q) wv[q] = rw[ii * KMAX + q];
         for (int jj = lane; jj < cols; jj += 32) {
             const T* tcol = Tx + ri.x * cols + jj;
             T acc = T(0);
 #pragma unroll
-            for (int q = 0; q < KMAX; ++q)
+            for (int q = 0; q < KM; ++q)
                 if (q < ri.y) acc += wv[q] * tcol[q * cols];
             out[ii * cols + jj] = acc;
         }
     }
 }
 
-template <class T>
+template <class T, int KM>
 __global__ void __launch_bounds__(cblk<T>(), 1) k_projT(__grid_constant__ const Desc<T> d,
                                                         const T* __restrict__ u,
                                                         __grid_constant__ const PairBufs<T> pb) {
     pdl_enter();
-    projT_body<T>(d, u, pb, blockIdx.x, blockIdx.y);
+    projT_body<T, KM>(d, u, pb, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace fewha

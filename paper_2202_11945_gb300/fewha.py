@@ -19,6 +19,7 @@ FLAG_WARM_RESIDUAL = 2
 FLAG_PDL = 4
 FLAG_AUGMENTED = 8
 FLAG_CLOSED_LOOP = 16
+FLAG_PERSISTENT = 32
 AUG_MAX_ITERS = 8
 
 ERRORS = {
@@ -28,6 +29,7 @@ ERRORS = {
     -4: "CUDA error",
     -5: "non-finite input",
     -6: "size limit",
+    -7: "a grid-wide wait ran out",
 }
 
 
@@ -62,7 +64,7 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tau", ctypes.c_double), ("gain", ctypes.c_double),
                 ("r0", ctypes.c_double), ("L0", ctypes.c_double), ("iters", ctypes.c_int),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_uint),
-                ("alpha_eta", ctypes.c_double)]
+                ("alpha_eta", ctypes.c_double), ("warm_refresh", ctypes.c_int)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -82,7 +84,8 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_batch_last_error", "fewha_batch_set_config", "fewha_batch_get_config",
            "fewha_batch_reconstruct", "fewha_batch_autotune", "fewha_reconstruct_batched",
            "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state", "fewha_solve",
-           "fewha_reconstruct_converged", "fewha_backward", "fewha_get_residual", "fewha_frame_vjp"] + _OPS
+           "fewha_reconstruct_converged", "fewha_backward", "fewha_get_residual", "fewha_frame_vjp",
+           "fewha_set_wait_limit", "fewha_device_bytes", "fewha_test_fail_alloc"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -121,6 +124,9 @@ def lib():
     L.fewha_get_diagonals.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_bench_stage.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
     L.fewha_frame_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    L.fewha_set_wait_limit.argtypes = [_VP, ctypes.c_uint, ctypes.c_uint]
+    L.fewha_device_bytes.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
+    L.fewha_test_fail_alloc.argtypes = [ctypes.c_int]
     ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
     for name in ["fewha_solve", "fewha_reconstruct_converged"]:
         getattr(L, name).argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ip, dp, _VP]
@@ -167,7 +173,7 @@ def structs_from_workload(wl, precision=32, flags=FLAG_GRAPH):
     dms = (Dm * len(wl["dms"]))(*[Dm(m["h"], m["spacing"], m["n_act"]) for m in wl["dms"]])
     p = wl["params"]
     params = Params(p["alpha"], p.get("tau", 0.0), p.get("gain", 1.0), p["r0"], p["L0"],
-                    p["iters"], precision, flags, p.get("alpha_eta", 0.0))
+                    p["iters"], precision, flags, p.get("alpha_eta", 0.0), p.get("warm_refresh", 0))
     return tel, wfs, layers, dms, params
 
 
@@ -181,7 +187,7 @@ class Reconstructor:
     """One FEWHA instance on the current CUDA device (a handle of the C library)."""
 
     def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False, augmented=False,
-                 closed_loop=False):
+                 closed_loop=False, persistent=False, warm_refresh=0):
         if not torch.cuda.is_available():
             raise RuntimeError("FEWHA needs a CUDA device; there is no CPU path")
         torch.cuda.init()
@@ -190,8 +196,9 @@ class Reconstructor:
         self.dtype = torch.float32 if precision == 32 else torch.float64
         flags = ((FLAG_GRAPH if graph else 0) | (FLAG_WARM_RESIDUAL if warm_residual else 0) |
                  (FLAG_PDL if pdl else 0) | (FLAG_AUGMENTED if augmented else 0) |
-                 (FLAG_CLOSED_LOOP if closed_loop else 0))
+                 (FLAG_CLOSED_LOOP if closed_loop else 0) | (FLAG_PERSISTENT if persistent else 0))
         self._structs = structs_from_workload(wl, precision, flags)
+        self._structs[4].warm_refresh = int(warm_refresh)
         tel, wfs, layers, dms, params = self._structs
         self.L = lib()
         h = _VP()
@@ -327,7 +334,7 @@ class Reconstructor:
 
     def update_params(self, alpha=None, tau=None, gain=None, r0=None, L0=None, iters=None, alpha_eta=None,
                       cn2_weights=None, sigmas=None, graph=None, warm_residual=None, augmented=None,
-                      closed_loop=None):
+                      closed_loop=None, warm_refresh=None):
         tel, wfs, layers, dms, p = self._structs
         if alpha is not None:
             p.alpha = alpha
@@ -343,6 +350,8 @@ class Reconstructor:
             p.iters = iters
         if alpha_eta is not None:
             p.alpha_eta = alpha_eta
+        if warm_refresh is not None:
+            p.warm_refresh = int(warm_refresh)
         if graph is not None:
             p.flags = (p.flags & ~FLAG_GRAPH) | (FLAG_GRAPH if graph else 0)
         if warm_residual is not None:
@@ -459,6 +468,17 @@ class Reconstructor:
     def bench_stage(self, stage, reps, stream=None):
         """Enqueue `reps` launches of one hot-path kernel (timing; clobbers the warm state)."""
         self._check(self.L.fewha_bench_stage(self.h, STAGES[stage], int(reps), _stream(stream)))
+
+    def set_wait_limit(self, polls, extra=0):
+        """Polls before a grid-wide wait of the persistent frame gives up; `extra` > 0 makes
+        every wait run out (tests of the timeout path)."""
+        self._check(self.L.fewha_set_wait_limit(self.h, int(polls), int(extra)))
+
+    def device_bytes(self):
+        """Device memory held by the instance, in bytes."""
+        n = ctypes.c_int64(0)
+        self._check(self.L.fewha_device_bytes(self.h, ctypes.byref(n)))
+        return n.value
 
     def frame_launches(self):
         n = ctypes.c_int(0)
