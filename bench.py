@@ -336,6 +336,21 @@ def time_batched(count, steps, warmup, flush):
     diff = max(float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
                for a, b in zip(dm_b, dm_solo))
     nbytes = sum(frame_bytes(R) for R in mem)
+    # every instance against the FP64 oracle: two fresh frames (cold, then warm-started)
+    import oracle as O
+    for R in mem:
+        R.reset()
+    torch.cuda.synchronize()
+    vs_oracle = 0.0
+    got = []
+    for t in range(2):
+        B.reconstruct([s[t] for s in S], dm_out=dm_b)
+        got.append([d.double().cpu().numpy() for d in dm_b])
+    for i, wl in enumerate(wls):
+        ref = O.Reconstructor(wl)
+        for t in range(2):
+            a_ref = ref.frame(S[i][t].double().cpu().numpy())
+            vs_oracle = max(vs_oracle, float(np.linalg.norm(got[t][i] - a_ref) / np.linalg.norm(a_ref)))
     out = {"workload": "batched_%d_uneven_instances" % count, "instances": count,
            "frames_per_s": count / (tb.mean() * 1e-3),
            "one_by_one_frames_per_s": count / (t1.mean() * 1e-3),
@@ -344,6 +359,8 @@ def time_batched(count, steps, warmup, flush):
            "ms_one_by_one": float(t1.mean()),
            "config": cfg, "autotune_us": tuned_us,
            "max_rel_l2_vs_one_by_one": diff,
+           "max_rel_l2_vs_oracle": vs_oracle,
+           "oracle_check": "every instance, 2 frames from a reset (cold, then warm-started)",
            "algorithmic_gb_s": nbytes / (tb.mean() * 1e-3) / 1e9,
            "l2": "512 MiB memset between timed batches", "steps": steps}
     B.close()

@@ -417,7 +417,13 @@ typedef struct {
     int order;       /* 0: work items in the given instance order; 1: costliest instance first */
     int groups;      /* 1..FEWHA_BATCH_MAX_GROUPS: instances split (by balanced cost) into this
                         many independent launch chains that run concurrently */
-    int vec_passes;  /* 1..8: 1024-element passes per CTA of the vector kernel */
+    int vec_passes;  /* 1..8: passes of 4 elements per thread of the vector kernel's CTAs */
+    int pair_threads;/* threads per CTA of the (sensor, layer) projection kernels: 0 = the
+                        single-instance size (512 in single, 256 in double precision), or
+                        half of it */
+    int proj_taps;   /* unrolled taps of the adjoint projection: 0 = as few as every member's
+                        geometry allows, 4 (only if every member allows it) or 8 */
+    int vec_threads; /* threads per CTA of the vector kernel: 0 = 256, 256 or 512 */
 } fewha_batch_config;
 
 #define FEWHA_BATCH_MAX_GROUPS 8
@@ -437,8 +443,11 @@ int fewha_batch_get_config(const fewha_batch* b, fewha_batch_config* cfg);
 int fewha_batch_reconstruct(fewha_batch* b, const void* const* d_slopes, void* const* d_dm_out,
                             void* stream);
 
-/* Autotuner: times every candidate configuration (order x groups x vec_passes) on
- * `reps` batched frames of the given slopes (CUDA events on `stream`), keeps the fastest
+/* Autotuner: times the candidate configurations on `reps` batched frames of the given
+ * slopes (CUDA events on `stream`): first every order x groups x vec_passes with the default
+ * kernel shapes, then, from the best of those, every pair_threads x proj_taps x vec_threads
+ * (the CTA sizes of the projection and vector kernels and the adjoint projection's tap
+ * unroll, as far as the members' geometry allows), and keeps the fastest
  * in the batch and in a process-wide table keyed by the instances' shapes (a later batch
  * of the same shapes starts from it), and restores every member's warm state afterwards.
  * *best_us (nullable) receives the chosen configuration's mean frame time.  Synchronous. */

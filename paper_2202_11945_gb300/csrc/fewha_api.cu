@@ -138,11 +138,11 @@ struct fewha_batch {
     bool dead = false;
     bool registry = false;          // owned by the fewha_reconstruct_batched cache
     std::string err;
-    fewha_batch_config cfg{0, 1, 1};
+    fewha_batch_config cfg{0, 1, 1, 0, 0, 0};
     // current plan: one device block [instances | work lists | argument table] and a graph
     bool have_plan = false;
     bool plan_warm = false;
-    fewha_batch_config plan_cfg{0, 0, 0};
+    fewha_batch_config plan_cfg{0, 0, 0, 0, 0, 0};
     void* dev = nullptr;
     size_t args_off = 0;
     std::vector<unsigned char> args_host;
@@ -531,6 +531,45 @@ int enqueue_apply_aug(fewha_handle* H, const Desc<T>& d, const T* pold, T* pnew,
     return launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, b, st);
 }
 
+// r = b - M c0 (as enqueue_apply, then V_INIT) with the initial residual's vector step fused
+// into the forward kernel's epilogue: r0, z0 = J^-1 r0, p0 = z0, b_prev = b, r.z into slot 0.
+template <class T>
+int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st) {
+    const T* x = c;
+    const int slot = PQ_SCRATCH_SLOT;
+    const bool pupdate = false;
+    T* phi = static_cast<T*>(H->phi);
+    T* u = static_cast<T*>(H->u);
+    int rc;
+    ClArgs<T> a = cl_args<T>(H, x, phi);
+    a.zero_piston = 1;
+    if (pupdate) {
+        a.pupd = static_cast<T*>(H->p);
+        a.zupd = static_cast<const T*>(H->z);
+        a.iter = slot;
+        rc = launch_inv<T, 1>(H, d, a, st);
+    } else {
+        rc = launch_inv<T, 0>(H, d, a, st);
+    }
+    if (rc) return rc;
+    if ((rc = launch_proj<T>(H, d, phi, st))) return rc;
+    if ((rc = launch_csensor<T, SSRC_PHI>(H, d, phi, u, st))) return rc;
+    if ((rc = launch_projT<T>(H, d, u, st))) return rc;
+    ClArgs<T> b = cl_args<T>(H, u, static_cast<T*>(H->q));
+    b.pin = x;
+    b.iter = slot;
+    b.zero_piston = 1;
+    b.vr = static_cast<T*>(H->r);
+    b.vz = static_cast<T*>(H->z);
+    b.vp = static_cast<T*>(H->p);
+    b.vb = static_cast<const T*>(H->b);
+    b.vbprev = static_cast<T*>(H->b_prev);
+    b.vj = static_cast<const T*>(H->Jinv);
+    b.rzslot = 0;
+    b.rzp = H->rzpart;
+    return launch_fwd<T, LSRC_NODES, LDST_APPLY_INIT>(H, d, b, st);
+}
+
 template <class T>
 int enqueue_rhs(fewha_handle* H, const Desc<T>& d, const T* s, T* bout, cudaStream_t st) {
     T* u = static_cast<T*>(H->u);
@@ -587,6 +626,23 @@ int launch_pol(fewha_handle* H, const Desc<T>& d, const T* s, T* out, cudaStream
 template <class T>
 int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, cudaStream_t st) {
     int rc;
+    // the initial residual's vector step fused into the forward kernel (single instances; the
+    // batched frame keeps the separate vector kernel).  The iterations' CG updates stay in
+    // their own kernel: fused behind a grid-wide wait for the p.q total (a cooperative
+    // launch) they measured slower on GB300 than the separate launch.
+    if (!recorder<T>()) {
+        if (warm) {
+            if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
+        } else {
+            if ((rc = enqueue_apply_init<T>(H, d, c, st))) return rc;
+        }
+        T* p = static_cast<T*>(H->p);
+        for (int k = 0; k < iters; ++k) {
+            if ((rc = enqueue_apply<T>(H, d, p, static_cast<T*>(H->q), k, k > 0, st))) return rc;
+            if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, vec_args<T>(H, c, k), st))) return rc;
+        }
+        return FEWHA_OK;
+    }
     if (warm) {
         if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
     } else {
@@ -930,6 +986,7 @@ int set_smem_limits(fewha_handle* H) {
     int rc = 0;
     if ((rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_APPLY>, H->smem_fwd)) ||
         (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_COEF>, H->smem_fwd)) ||
+        (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_APPLY_INIT>, H->smem_fwd)) ||
         (rc = allow_smem(H, k_cl_inv<T, 0>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_inv<T, 1>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_inv<T, 2>, H->smem_inv)) ||
@@ -1687,8 +1744,9 @@ int solve_entry(fewha_handle* H, const T* b, T* x, double tol, int max_iters, cu
 
 // Reverse mode through the fixed-iteration frame: the forward recurrence from c0 with
 // every vector kept, then each statement's adjoint in reverse order (M and J^-1 are
-// symmetric).  Scalars (rho, sigma, alpha, beta and their adjoints) live on the host in
-// double; each reverse iteration reads three inner products back.  Synchronous.
+// symmetric), three vector kernels and one M-apply per iteration (k_vjp).  The scalars
+// (rho, sigma, alpha, beta and their adjoints) stay on the device; the host synchronises
+// once, at the end.  Synchronous.
 template <class T>
 int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* g_s, cudaStream_t st) {
     const Desc<T> d = make_desc<T>(H);
@@ -1716,16 +1774,10 @@ int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* 
     T* scratch = c + ld;
     T* cbar = scratch + ld;
     T* rbar = cbar + ld;
-    T* zbar = rbar + ld;
-    T* pbar = zbar + ld;
+    T* pbar = rbar + ld;
     T* pbi = pbar + ld;
     T* qbar = pbi + ld;
     const T* Jinv = static_cast<const T*>(H->Jinv);
-    const int gl = std::min(4 * 152, static_cast<int>((n + PBLK - 1) / PBLK));
-    auto lin = [&](double a, const T* x, double b, const T* y, double cc, const T* u, const T* v, T* out) {
-        k_lin<T><<<gl, PBLK, 0, st>>>(n, a, x, b, y, cc, u, v, out);
-        return cudaGetLastError();
-    };
     int rc;
     // ---- forward: b, r0 = b - M c0, then the iterations, every vector kept -------------
     if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
@@ -1759,67 +1811,52 @@ int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* 
         CK(cudaStreamSynchronize(st), "vjp forward");
         return FEWHA_OK;
     }
+    // ---- reverse: every scalar on the device, no host round trip until the end ----------
+    if ((rc = launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, g_a, cbar), st))) return rc;
+    CK(cudaMemsetAsync(rbar, 0, n * sizeof(T), st), "vjp zero");
+    CK(cudaMemsetAsync(pbar, 0, n * sizeof(T), st), "vjp zero");
+    CK(cudaMemsetAsync(H->gdot, 0, 4 * sizeof(double), st), "vjp scalars");
+    VjpArgs<T> va;
+    va.rbar = rbar;
+    va.pbar = pbar;
+    va.pbi = pbi;
+    va.qbar = qbar;
+    va.cbar = cbar;
+    va.Mq = scratch;
+    va.Jinv = Jinv;
+    va.rho = H->rztot;
+    va.sigma = H->pqtot;
+    va.rs = H->gdot;
+    va.part = H->rzpart + static_cast<size_t>(FEWHA_MAX_ITERS + 1) * NPART_MAX;   // a free slot pair
+    va.count = H->count;
+    va.npart = NPART_MAX / 2;
+    const int gv = std::min(NPART_MAX / 2, (n + PBLK - 1) / PBLK);
+    for (int i = k - 1; i >= 0; --i) {
+        va.i = i;
+        va.first = i == k - 1;
+        va.p = P + i * ld;
+        va.q = Q + i * ld;
+        va.r1 = R + (i + 1) * ld;
+        va.z1 = Z + (i + 1) * ld;
+        k_vjp<T, VJ_A><<<gv, PBLK, 0, st>>>(n, va);
+        k_vjp<T, VJ_B><<<gv, PBLK, 0, st>>>(n, va);
+        k_vjp<T, VJ_C><<<gv, PBLK, 0, st>>>(n, va);
+        CK(cudaGetLastError(), "k_vjp launch");
+        // q_i = M p_i: p_bar_i += M q_bar (added by the next VJ_A, or VJ_E)
+        if ((rc = enqueue_apply<T>(H, d, qbar, scratch, PQ_SCRATCH_SLOT, false, st))) return rc;
+    }
+    // p_0 = z_0, rho_0 = r_0 . z_0, z_0 = J^-1 r_0, r_0 = b - M c0: b_bar = r_bar_0
+    if (k > 0) {
+        va.r1 = R;
+        va.z1 = Z;
+        k_vjp<T, VJ_E><<<gv, PBLK, 0, st>>>(n, va);
+        CK(cudaGetLastError(), "k_vjp launch");
+    }
+    // the recurrence must not have stopped (r.z or p.q vanished): checked once, at the end
     std::vector<double> rho(k + 1), sigma(k + 1);
     CK(cudaMemcpyAsync(rho.data(), H->rztot, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st), "vjp rho");
     if (k > 0)
         CK(cudaMemcpyAsync(sigma.data(), H->pqtot, k * sizeof(double), cudaMemcpyDeviceToHost, st), "vjp sigma");
-    CK(cudaStreamSynchronize(st), "vjp scalars");
-    for (int i = 0; i < k; ++i)
-        if (!(sigma[i] > 0.0) || rho[i] == 0.0)
-            return fail(H, FEWHA_ERR_NONFINITE, "the frame's recurrence stopped (r.z or p.q vanished)");
-    // ---- reverse ------------------------------------------------------------------------
-    double* dots = H->gdot;                        // MAXL + 1 doubles of device scratch
-    double hd[2];
-    if ((rc = launch_layer<T, LSRC_DM, LDST_COEF, false>(H, d, layer_args<T>(H, g_a, cbar), st))) return rc;
-    CK(cudaMemsetAsync(rbar, 0, n * sizeof(T), st), "vjp zero");
-    CK(cudaMemsetAsync(zbar, 0, n * sizeof(T), st), "vjp zero");
-    CK(cudaMemsetAsync(pbar, 0, n * sizeof(T), st), "vjp zero");
-    double rhobar = 0.0;
-    for (int i = k - 1; i >= 0; --i) {
-        const T* p = P + i * ld;
-        const T* q = Q + i * ld;
-        const T* r1 = R + (i + 1) * ld;
-        const T* z1 = Z + (i + 1) * ld;
-        const double alpha = rho[i] / sigma[i], beta = rho[i + 1] / rho[i];
-        // p_(i+1) = z_(i+1) + beta_i p_i
-        CK(lin(1.0, zbar, 1.0, pbar, 0.0, nullptr, nullptr, zbar), "vjp lin");
-        k_vdot<T><<<1, PBLK, 0, st>>>(n, pbar, p, dots);
-        CK(cudaGetLastError(), "vjp dot");
-        CK(cudaMemcpyAsync(hd, dots, sizeof(double), cudaMemcpyDeviceToHost, st), "vjp dot");
-        CK(cudaStreamSynchronize(st), "vjp dot");
-        const double betabar = hd[0];
-        CK(lin(beta, pbar, 0.0, nullptr, 0.0, nullptr, nullptr, pbi), "vjp lin");
-        // beta_i = rho_(i+1) / rho_i
-        rhobar += betabar / rho[i];
-        double rhobar_i = -betabar * rho[i + 1] / (rho[i] * rho[i]);
-        // rho_(i+1) = r_(i+1) . z_(i+1);  z_(i+1) = J^-1 r_(i+1)
-        CK(lin(1.0, rbar, rhobar, z1, 0.0, nullptr, nullptr, rbar), "vjp lin");
-        CK(lin(1.0, zbar, rhobar, r1, 0.0, nullptr, nullptr, zbar), "vjp lin");
-        CK(lin(1.0, rbar, 0.0, nullptr, 1.0, Jinv, zbar, rbar), "vjp lin");
-        // r_(i+1) = r_i - alpha_i q_i;  c_(i+1) = c_i + alpha_i p_i
-        k_vdot<T><<<1, PBLK, 0, st>>>(n, rbar, q, dots);
-        k_vdot<T><<<1, PBLK, 0, st>>>(n, cbar, p, dots + 1);
-        CK(cudaGetLastError(), "vjp dot");
-        CK(cudaMemcpyAsync(hd, dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "vjp dot");
-        CK(cudaStreamSynchronize(st), "vjp dot");
-        const double abar = -hd[0] + hd[1];
-        // alpha_i = rho_i / sigma_i;  sigma_i = p_i . q_i
-        rhobar_i += abar / sigma[i];
-        const double sigmabar = -abar * rho[i] / (sigma[i] * sigma[i]);
-        CK(lin(-alpha, rbar, sigmabar, p, 0.0, nullptr, nullptr, qbar), "vjp lin");
-        CK(lin(1.0, pbi, alpha, cbar, 0.0, nullptr, nullptr, pbi), "vjp lin");
-        CK(lin(1.0, pbi, sigmabar, q, 0.0, nullptr, nullptr, pbi), "vjp lin");
-        // q_i = M p_i
-        if ((rc = enqueue_apply<T>(H, d, qbar, scratch, PQ_SCRATCH_SLOT, false, st))) return rc;
-        CK(lin(1.0, pbi, 1.0, scratch, 0.0, nullptr, nullptr, pbar), "vjp lin");
-        rhobar = rhobar_i;
-        CK(cudaMemsetAsync(zbar, 0, n * sizeof(T), st), "vjp zero");
-    }
-    // p_0 = z_0, rho_0 = r_0 . z_0, z_0 = J^-1 r_0, r_0 = b - M c0: b_bar = r_bar_0
-    CK(lin(1.0, zbar, 1.0, pbar, 0.0, nullptr, nullptr, zbar), "vjp lin");
-    CK(lin(1.0, rbar, rhobar, Z, 0.0, nullptr, nullptr, rbar), "vjp lin");
-    CK(lin(1.0, zbar, rhobar, R, 0.0, nullptr, nullptr, zbar), "vjp lin");
-    CK(lin(1.0, rbar, 0.0, nullptr, 1.0, Jinv, zbar, rbar), "vjp lin");
     // dJ/ds = C_hat^-1 Gamma P W^T b_bar (b_bar's pistons, large and annihilated by Gamma,
     // left out first)
     T* phi = static_cast<T*>(H->phi);
@@ -1829,6 +1866,9 @@ int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* 
     if ((rc = launch_sensor<T, SSRC_PHI, false, SDST_SLOPES>(H, d, phi, st_s, st))) return rc;
     if ((rc = launch_sensor<T, SSRC_SLOPES, true, SDST_SLOPES>(H, d, st_s, g_s, st))) return rc;
     CK(cudaStreamSynchronize(st), "vjp");
+    for (int i = 0; i < k; ++i)
+        if (!(sigma[i] > 0.0) || rho[i] == 0.0)
+            return fail(H, FEWHA_ERR_NONFINITE, "the frame's recurrence stopped (r.z or p.q vanished)");
     return FEWHA_OK;
 }
 
@@ -1874,8 +1914,8 @@ double bcost(const fewha_handle* H) {
     return 2.0 * H->setup.n_c + static_cast<double>(H->setup.L.size()) * H->setup.n_nodes;
 }
 
-int bnparts(const fewha_handle* H, int vec_passes) {
-    const int per = PBLK * PVEC * vec_passes;
+int bnparts(const fewha_handle* H, int vec_passes, int vec_threads) {
+    const int per = (vec_threads ? vec_threads : PBLK) * PVEC * vec_passes;
     int n = (H->setup.n_c + per - 1) / per;
     return n < 1 ? 1 : (n > NPART_MAX ? NPART_MAX : n);
 }
@@ -2033,6 +2073,15 @@ int batch_build(fewha_batch* B, const std::vector<Recorder<T>>& recs, const std:
                 return bfail(B, FEWHA_ERR_LIMIT, "batched tile above the per-CTA shared-memory limit");
     }
     BCK(batch_set_taps(B->h[0]->setup.taps_h, B->h[0]->setup.taps_g), "batch taps");
+    // launch shapes: projection CTA size, adjoint-projection taps, vector CTA size
+    int kmax = 0;
+    for (int i = 0; i < n; ++i) kmax = std::max(kmax, B->h[i]->kmax);
+    const int pair_nt = cfg.pair_threads ? cfg.pair_threads : cblk<T>();
+    const int taps = cfg.proj_taps ? cfg.proj_taps : (kmax <= 4 ? 4 : KMAX);
+    const int vec_nt = cfg.vec_threads ? cfg.vec_threads : PBLK;
+    if ((pair_nt != cblk<T>() && pair_nt != cblk<T>() / 2) || (taps != 4 && taps != KMAX) || taps < kmax ||
+        (vec_nt != PBLK && vec_nt != 2 * PBLK))
+        return bfail(B, FEWHA_ERR_INVALID_ARG, "launch shape not available for these instances");
     // capture
     BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "batch capture");
     cudaError_t le = cudaSuccess;
@@ -2053,6 +2102,9 @@ int batch_build(fewha_batch* B, const std::vector<Recorder<T>>& recs, const std:
             L.n_items = static_cast<int>(lists[li].size());
             L.smem = smem[g * BK_COUNT + kind];
             L.pdl = (B->h[0]->params.flags & FEWHA_FLAG_PDL) != 0;
+            L.pair_nt = pair_nt;
+            L.taps = taps;
+            L.vec_nt = vec_nt;
             le = batch_launch<T>(L, st);
         }
     }
@@ -2081,7 +2133,8 @@ int batch_build(fewha_batch* B, const std::vector<Recorder<T>>& recs, const std:
 }
 
 bool same_cfg(const fewha_batch_config& a, const fewha_batch_config& b) {
-    return a.order == b.order && a.groups == b.groups && a.vec_passes == b.vec_passes;
+    return a.order == b.order && a.groups == b.groups && a.vec_passes == b.vec_passes &&
+           a.pair_threads == b.pair_threads && a.proj_taps == b.proj_taps && a.vec_threads == b.vec_threads;
 }
 
 template <class T>
@@ -2107,7 +2160,7 @@ int batch_run(fewha_batch* B, const void* const* s_in, void* const* dm_in, void*
     int rc;
     if ((rc = batch_record<T>(B, s, dm, warm, recs))) return rc;
     std::vector<int> nparts(n);
-    for (size_t i = 0; i < n; ++i) nparts[i] = bnparts(B->h[i], B->cfg.vec_passes);
+    for (size_t i = 0; i < n; ++i) nparts[i] = bnparts(B->h[i], B->cfg.vec_passes, B->cfg.vec_threads);
     std::vector<unsigned char> args;
     std::vector<size_t> offs;
     batch_pack<T>(recs, nparts, args, offs);
@@ -2181,29 +2234,47 @@ int batch_autotune(fewha_batch* B, const void* const* s, void* const* dm, int re
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = FEWHA_OK;
+    // time one candidate (two untimed frames first: the plan is rebuilt for a new shape)
+    auto trial = [&](const fewha_batch_config& c) {
+        B->cfg = c;
+        for (int w = 0; w < 2 && rc == FEWHA_OK; ++w) rc = batch_run<T>(B, s, dm, stream);
+        if (rc) return;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rc == FEWHA_OK; ++r) rc = batch_run<T>(B, s, dm, stream);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = bfail(B, FEWHA_ERR_CUDA, "autotune timing");
+        if (rc) return;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = 1e3f * ms / reps;
+        if (best_t < 0.f || us < best_t) {
+            best_t = us;
+            best = c;
+        }
+    };
+    // stage 1: work order, launch chains and vector passes with the default kernel shapes
     const int groups[] = {1, 2, 4, 8};
     const int vps[] = {1, 4};
     for (int order = 0; order < 2 && rc == FEWHA_OK; ++order)
         for (int gi = 0; gi < 4 && rc == FEWHA_OK; ++gi) {
             if (groups[gi] > static_cast<int>(n)) continue;
-            for (int vi = 0; vi < 2 && rc == FEWHA_OK; ++vi) {
-                B->cfg = fewha_batch_config{order, groups[gi], vps[vi]};
-                for (int w = 0; w < 2 && rc == FEWHA_OK; ++w) rc = batch_run<T>(B, s, dm, stream);
-                if (rc) break;
-                cudaEventRecord(e0, st);
-                for (int r = 0; r < reps && rc == FEWHA_OK; ++r) rc = batch_run<T>(B, s, dm, stream);
-                cudaEventRecord(e1, st);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = bfail(B, FEWHA_ERR_CUDA, "autotune timing");
-                if (rc) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const float us = 1e3f * ms / reps;
-                if (best_t < 0.f || us < best_t) {
-                    best_t = us;
-                    best = B->cfg;
-                }
-            }
+            for (int vi = 0; vi < 2 && rc == FEWHA_OK; ++vi) trial(fewha_batch_config{order, groups[gi], vps[vi], 0, 0, 0});
         }
+    // stage 2: from the best of stage 1, the kernels' launch shapes
+    int kmax = 0;
+    for (const fewha_handle* H : B->h) kmax = std::max(kmax, H->kmax);
+    const int nt = cblk<T>();
+    const fewha_batch_config base = best;
+    for (int pt : {nt, nt / 2})
+        for (int tp : {4, KMAX})
+            for (int vt : {PBLK, 2 * PBLK}) {
+                if (rc != FEWHA_OK || tp < kmax) continue;
+                fewha_batch_config c = base;
+                c.pair_threads = pt;
+                c.proj_taps = tp;
+                c.vec_threads = vt;
+                trial(c);
+            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     copy_state(false);
@@ -2653,9 +2724,18 @@ void fewha_batch_destroy(fewha_batch* b) {
 const char* fewha_batch_last_error(const fewha_batch* b) { return b ? b->err.c_str() : "null batch"; }
 int fewha_batch_set_config(fewha_batch* b, const fewha_batch_config* cfg) {
     if (!b || !cfg) return FEWHA_ERR_INVALID_ARG;
+    const int nt = b->precision == 32 ? cblk<float>() : cblk<double>();
     if (cfg->order < 0 || cfg->order > 1 || cfg->groups < 1 || cfg->groups > FEWHA_BATCH_MAX_GROUPS ||
-        cfg->vec_passes < 1 || cfg->vec_passes > 8)
+        cfg->vec_passes < 1 || cfg->vec_passes > 8 ||
+        (cfg->pair_threads != 0 && cfg->pair_threads != nt && cfg->pair_threads != nt / 2) ||
+        (cfg->proj_taps != 0 && cfg->proj_taps != 4 && cfg->proj_taps != KMAX) ||
+        (cfg->vec_threads != 0 && cfg->vec_threads != PBLK && cfg->vec_threads != 2 * PBLK))
         return bfail(b, FEWHA_ERR_INVALID_ARG, "configuration out of range");
+    int kmax = 0;
+    for (const fewha_handle* H : b->h)
+        if (H) kmax = std::max(kmax, H->kmax);
+    if (cfg->proj_taps != 0 && cfg->proj_taps < kmax)
+        return bfail(b, FEWHA_ERR_INVALID_ARG, "proj_taps below the members' tap count");
     b->cfg = *cfg;
     return FEWHA_OK;
 }
@@ -2811,12 +2891,15 @@ int fewha_bench_stage(fewha_handle* H, int stage, int reps, void* stream) {
 int fewha_frame_launches(const fewha_handle* H, int* launches) {
     if (!H || !launches) return FEWHA_ERR_INVALID_ARG;
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
-    // RHS 3, initial residual 6 (explicit) or 1 (warm), 6 per iteration, fit 2; the
-    // augmented frame (with directions) adds one start kernel (its direction update is
-    // fused into the inverse kernel of each apply)
+    // RHS 3, initial residual 5 (explicit, its vector step fused into the forward kernel) or
+    // 1 (warm), 6 per iteration, fit 2; the augmented frame runs 6 for r0 (a separate vector
+    // kernel) and one more start kernel (its direction update is fused into the inverse
+    // kernel of each apply)
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
     const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
-    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + 3 + (warm ? 1 : 6) + aug + 6 * H->params.iters + 2;
+    // the plain PCG's initial-residual vector step is fused into its forward kernel
+    const int per_iter = 6, r0 = warm ? 1 : (aug ? 6 : 5);
+    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + 3 + r0 + aug + per_iter * H->params.iters + 2;
     return FEWHA_OK;
 }
 

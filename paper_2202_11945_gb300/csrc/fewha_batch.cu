@@ -2,6 +2,7 @@
 // of many instances in one launch.  A CTA first copies its instance's descriptor into
 // shared memory (the bodies then read it from there, as the single-instance kernels read
 // theirs from the constant bank), then runs the body on its unit.
+#include <algorithm>
 #include <utility>
 
 #include "fewha_batch.h"
@@ -64,8 +65,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     cl_sensor_body<T, SRC>(sd, a, lay, pb, it.unit);
 }
 
-template <class T>
-__global__ void __launch_bounds__(cblk<T>(), 1)
+template <class T, int NTP>
+__global__ void __launch_bounds__(NTP, 1)
     kb_proj(const BInst<T>* __restrict__ inst, const T* const* __restrict__ args,
             const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
@@ -74,11 +75,11 @@ __global__ void __launch_bounds__(cblk<T>(), 1)
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
     const PairBufs<T> pb = I->pb;
-    proj_body<T>(sd, args[it.inst], pb, it.unit / MAXL, it.unit % MAXL);
+    proj_body<T, NTP>(sd, args[it.inst], pb, it.unit / MAXL, it.unit % MAXL);
 }
 
-template <class T>
-__global__ void __launch_bounds__(cblk<T>(), 1)
+template <class T, int KM, int NTP>
+__global__ void __launch_bounds__(NTP, 1)
     kb_projT(const BInst<T>* __restrict__ inst, const T* const* __restrict__ args,
              const BItem* __restrict__ items) {
     __shared__ __align__(16) Desc<T> sd;
@@ -87,18 +88,18 @@ __global__ void __launch_bounds__(cblk<T>(), 1)
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
     const PairBufs<T> pb = I->pb;
-    projT_body<T>(sd, args[it.inst], pb, it.unit / MAXL, it.unit % MAXL);
+    projT_body<T, KM, NTP>(sd, args[it.inst], pb, it.unit / MAXL, it.unit % MAXL);
 }
 
-template <class T, int PHASE>
-__global__ void __launch_bounds__(PBLK)
+template <class T, int PHASE, int NTV>
+__global__ void __launch_bounds__(NTV)
     kb_vec(const BInst<T>* __restrict__ inst, const VecArgs<T>* __restrict__ args,
            const BItem* __restrict__ items) {
     pdl_enter();
     const BItem it = items[blockIdx.x];
     const BInst<T>* I = inst + it.inst;
     const VecArgs<T> v = args[it.inst];
-    vec_body<T, PHASE>(I->d.n_c, v, it.unit, I->nparts);
+    vec_body<T, PHASE, NTV>(I->d.n_c, v, it.unit, I->nparts);
 }
 
 template <class T>
@@ -114,20 +115,36 @@ __global__ void __launch_bounds__(PBLK)
     fit_body<T>(sd, f.phi, f.a_prev, f.out, f.apply_gain, it.unit);
 }
 
+// The kernel of a step kind in one launch shape (variant v: bit 0 half-size projection
+// CTAs, bit 1 the 4-tap adjoint projection; for the vector kernels, bit 0 512 threads).
 template <class T>
-const void* kernel_of(int kind) {
+const void* kernel_of(int kind, int v) {
+    constexpr int NP = cblk<T>(), NH = cblk<T>() / 2;
+    const bool half = (v & 1) != 0, t4 = (v & 2) != 0;
     switch (kind) {
         case BK_INV: return reinterpret_cast<const void*>(kb_cl_inv<T, 0>);
         case BK_INV_UPD: return reinterpret_cast<const void*>(kb_cl_inv<T, 1>);
-        case BK_PROJ: return reinterpret_cast<const void*>(kb_proj<T>);
+        case BK_PROJ:
+            return half ? reinterpret_cast<const void*>(kb_proj<T, NH>) : reinterpret_cast<const void*>(kb_proj<T, NP>);
         case BK_SEN_PHI: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_PHI>);
         case BK_SEN_SLOPES: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_SLOPES>);
-        case BK_PROJT: return reinterpret_cast<const void*>(kb_projT<T>);
+        case BK_PROJT:
+            if (t4)
+                return half ? reinterpret_cast<const void*>(kb_projT<T, 4, NH>)
+                            : reinterpret_cast<const void*>(kb_projT<T, 4, NP>);
+            return half ? reinterpret_cast<const void*>(kb_projT<T, KMAX, NH>)
+                        : reinterpret_cast<const void*>(kb_projT<T, KMAX, NP>);
         case BK_FWD_APPLY: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_APPLY>);
         case BK_FWD_COEF: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_COEF>);
-        case BK_VEC_INIT: return reinterpret_cast<const void*>(kb_vec<T, V_INIT>);
-        case BK_VEC_WARM: return reinterpret_cast<const void*>(kb_vec<T, V_INIT_WARM>);
-        case BK_VEC_UPDATE: return reinterpret_cast<const void*>(kb_vec<T, V_UPDATE>);
+        case BK_VEC_INIT:
+            return half ? reinterpret_cast<const void*>(kb_vec<T, V_INIT, 2 * PBLK>)
+                        : reinterpret_cast<const void*>(kb_vec<T, V_INIT, PBLK>);
+        case BK_VEC_WARM:
+            return half ? reinterpret_cast<const void*>(kb_vec<T, V_INIT_WARM, 2 * PBLK>)
+                        : reinterpret_cast<const void*>(kb_vec<T, V_INIT_WARM, PBLK>);
+        case BK_VEC_UPDATE:
+            return half ? reinterpret_cast<const void*>(kb_vec<T, V_UPDATE, 2 * PBLK>)
+                        : reinterpret_cast<const void*>(kb_vec<T, V_UPDATE, PBLK>);
         case BK_FIT: return reinterpret_cast<const void*>(kb_fit<T>);
         default: return nullptr;
     }
@@ -150,19 +167,23 @@ cudaError_t batch_set_taps(const double* h, const double* g) {
 
 template <class T>
 cudaError_t batch_smem_limit(int kind, size_t* bytes) {
-    const void* k = kernel_of<T>(kind);
-    if (!k) return cudaErrorInvalidValue;
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k);
-    if (e != cudaSuccess) return e;
-    const int avail = 227 * 1024 - static_cast<int>(fa.sharedSizeBytes);
     if (bkind_list(kind) == BL_VEC) {
         *bytes = 0;
         return cudaSuccess;
     }
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
-    *bytes = static_cast<size_t>(avail);
-    return e;
+    int lim = 227 * 1024;
+    for (int v = 0; v < 4; ++v) {
+        const void* k = kernel_of<T>(kind, v);
+        if (!k) return cudaErrorInvalidValue;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return e;
+        const int avail = 227 * 1024 - static_cast<int>(fa.sharedSizeBytes);
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, avail)) != cudaSuccess) return e;
+        lim = std::min(lim, avail);
+    }
+    *bytes = static_cast<size_t>(lim);
+    return cudaSuccess;
 }
 
 template <typename... KArgs, typename... Args>
@@ -186,10 +207,12 @@ cudaError_t batch_launch(const BLaunch& L, cudaStream_t st) {
     if (L.n_items <= 0) return cudaSuccess;
     const BInst<T>* I = static_cast<const BInst<T>*>(L.inst);
     const int n = L.n_items;
-    const dim3 cg(CL, n), pg(n), nt(cblk<T>()), vt(PBLK);
+    const dim3 cg(CL, n), pg(n), nt(cblk<T>()), vt(L.vec_nt), pt(L.pair_nt);
+    const bool ph = L.pair_nt != cblk<T>(), t4 = L.taps == 4, v2 = L.vec_nt != PBLK;
+    const T* const* pa = static_cast<const T* const*>(L.args);
+    constexpr int NP = cblk<T>(), NH = cblk<T>() / 2;
     const ClArgs<T>* ca = static_cast<const ClArgs<T>*>(L.args);
     const SensorArgs<T>* sa = static_cast<const SensorArgs<T>*>(L.args);
-    const T* const* pa = static_cast<const T* const*>(L.args);
     const VecArgs<T>* va = static_cast<const VecArgs<T>*>(L.args);
     const FitArgs<T>* fa = static_cast<const FitArgs<T>*>(L.args);
     switch (L.kind) {
@@ -199,12 +222,25 @@ cudaError_t batch_launch(const BLaunch& L, cudaStream_t st) {
         case BK_FWD_COEF: return launch_b(L.pdl, kb_cl_fwd<T, LDST_COEF>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_SEN_PHI: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_PHI>, cg, nt, L.smem, st, I, sa, L.items);
         case BK_SEN_SLOPES: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_SLOPES>, cg, nt, L.smem, st, I, sa, L.items);
-        case BK_PROJ: return launch_b(L.pdl, kb_proj<T>, pg, nt, L.smem, st, I, pa, L.items);
-        case BK_PROJT: return launch_b(L.pdl, kb_projT<T>, pg, nt, L.smem, st, I, pa, L.items);
-        case BK_VEC_INIT: return launch_b(L.pdl, kb_vec<T, V_INIT>, pg, vt, 0, st, I, va, L.items);
-        case BK_VEC_WARM: return launch_b(L.pdl, kb_vec<T, V_INIT_WARM>, pg, vt, 0, st, I, va, L.items);
-        case BK_VEC_UPDATE: return launch_b(L.pdl, kb_vec<T, V_UPDATE>, pg, vt, 0, st, I, va, L.items);
-        case BK_FIT: return launch_b(L.pdl, kb_fit<T>, pg, vt, L.smem, st, I, fa, L.items);
+        case BK_PROJ:
+            return ph ? launch_b(L.pdl, kb_proj<T, NH>, pg, pt, L.smem, st, I, pa, L.items)
+                      : launch_b(L.pdl, kb_proj<T, NP>, pg, pt, L.smem, st, I, pa, L.items);
+        case BK_PROJT:
+            if (t4)
+                return ph ? launch_b(L.pdl, kb_projT<T, 4, NH>, pg, pt, L.smem, st, I, pa, L.items)
+                          : launch_b(L.pdl, kb_projT<T, 4, NP>, pg, pt, L.smem, st, I, pa, L.items);
+            return ph ? launch_b(L.pdl, kb_projT<T, KMAX, NH>, pg, pt, L.smem, st, I, pa, L.items)
+                      : launch_b(L.pdl, kb_projT<T, KMAX, NP>, pg, pt, L.smem, st, I, pa, L.items);
+        case BK_VEC_INIT:
+            return v2 ? launch_b(L.pdl, kb_vec<T, V_INIT, 2 * PBLK>, pg, vt, 0, st, I, va, L.items)
+                      : launch_b(L.pdl, kb_vec<T, V_INIT, PBLK>, pg, vt, 0, st, I, va, L.items);
+        case BK_VEC_WARM:
+            return v2 ? launch_b(L.pdl, kb_vec<T, V_INIT_WARM, 2 * PBLK>, pg, vt, 0, st, I, va, L.items)
+                      : launch_b(L.pdl, kb_vec<T, V_INIT_WARM, PBLK>, pg, vt, 0, st, I, va, L.items);
+        case BK_VEC_UPDATE:
+            return v2 ? launch_b(L.pdl, kb_vec<T, V_UPDATE, 2 * PBLK>, pg, vt, 0, st, I, va, L.items)
+                      : launch_b(L.pdl, kb_vec<T, V_UPDATE, PBLK>, pg, vt, 0, st, I, va, L.items);
+        case BK_FIT: return launch_b(L.pdl, kb_fit<T>, pg, dim3(PBLK), L.smem, st, I, fa, L.items);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -77,6 +77,9 @@ struct BLaunch {
     int n_items;
     size_t smem;           // dynamic shared memory (max over the instances present)
     bool pdl;              // programmatic stream serialization (see FEWHA_FLAG_PDL)
+    int pair_nt;           // threads of the projection kernels: cblk<T>() or half of it
+    int taps;              // unrolled taps of the adjoint projection: 4 or KMAX
+    int vec_nt;            // threads of the vector kernel: PBLK or 2 PBLK
 };
 
 // Launch one batched step (defined in fewha_batch.cu for float and double).
@@ -87,8 +90,8 @@ cudaError_t batch_launch(const BLaunch& L, cudaStream_t st);
 // this unit's copy is filled separately (per device, before the first batched launch).
 cudaError_t batch_set_taps(const double* h, const double* g);
 
-// Largest dynamic shared memory a batched kernel of this kind accepts; sets the
-// kernel's attribute to it on first use (per device).
+// Largest dynamic shared memory a batched kernel of this kind accepts (over its launch
+// shapes); sets the kernels' attribute to it on first use (per device).
 template <class T>
 cudaError_t batch_smem_limit(int kind, size_t* bytes);
 

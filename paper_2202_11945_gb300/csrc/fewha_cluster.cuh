@@ -292,6 +292,17 @@ struct ClArgs {
     const double* aug_pq;
     long long aug_ld;
     int aug_m;
+    // the initial residual's vector step fused into the forward kernel (DST_APPLY_INIT): the
+    // vectors r, z, p, b, b_prev, J^-1; r.z shares at rzp[l * CL + rank], total into rz slot
+    // rzslot
+    T* vr;
+    T* vz;
+    T* vp;
+    const T* vb;
+    T* vbprev;
+    const T* vj;
+    double* rzp;
+    int rzslot;
 };
 
 struct ClLayout {       // shared-memory offsets set by the host, in T units
@@ -344,13 +355,38 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     int4 ytv = make_int4(0, 0, 0, 0);
     if (SRC == LSRC_NODES && lay.ystg > 0 && has_band && threadIdx.x < 2 * d.n_wfs)
         ytv = pb.ytab[(l * CL + r) * 2 * d.n_wfs + threadIdx.x];
-    if (DST == LDST_APPLY) {
+    // this CTA's share of the LL quadrant's rows (coarse layers): [lr0, lr1), hb rows each
+    constexpr bool QAPPLY = DST == LDST_APPLY || DST == LDST_APPLY_INIT;
+    constexpr int PL = ((MAXN / 2) * (MAXN / 2) / CL + NT - 1) / NT;   // LL-share positions per thread
+    const int hb = max(h >> 3, 1);
+    const int lr0 = coarse ? min(r * hb, h) : 0, lr1 = coarse ? min(lr0 + hb, h) : 0;
+    const int lcnt = (lr1 - lr0) * h;
+    // operands of the epilogue at this CTA's positions (band, then LL share), loaded now so
+    // that their latency overlaps: p; with the fused initial residual also b and J^-1
+    T pl[PL], xb[PF], xl[PL], jb[PF], jl[PL];
+    if (QAPPLY) {
 #pragma unroll
         for (int s = 0; s < PF; ++s) {
             const int k = threadIdx.x + s * NT;
             if (k < ecnt) {
                 const int pos = off + (row_start + (k >> lrb)) * n + r0 + (k & (rb - 1));
                 pre_p[s] = a.pin[pos];
+                if (DST == LDST_APPLY_INIT) {
+                    xb[s] = a.vb[pos];
+                    jb[s] = a.vj[pos];
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < PL; ++s) {
+            const int k = threadIdx.x + s * NT;
+            if (k < lcnt) {
+                const int pos = off + (lr0 + (k >> lh)) * n + (k & (h - 1));
+                pl[s] = a.pin[pos];
+                if (DST == LDST_APPLY_INIT) {
+                    xl[s] = a.vb[pos];
+                    jl[s] = a.vj[pos];
+                }
             }
         }
     }
@@ -450,6 +486,30 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
     cluster.sync();                                                       // #1: column tiles complete
+    DotAcc<T> dot;                 // p.q share of this CTA (double accuracy)
+    DotAcc<T> drz;                 // r.z share (fused initial residual)
+    // The epilogue at one position: v = (W y)(i, j), p and the prefetched operands.
+    //   APPLY: q = v + alpha D p, written, p.q;  COEF: v written;
+    //   APPLY_INIT (initial residual, Algorithm 1): r = b - q, z = J^-1 r, p = z, b_prev = b, r.z.
+    auto epi = [&](int i, int j, int pos, T v, T p, T x, T jv) {
+        if (!QAPPLY) {
+            a.out[pos] = v;
+            return;
+        }
+        const T q = v + d.alpha * sD[level_of(i, j, L)] * p;
+        if (DST == LDST_APPLY) {
+            a.out[pos] = q;
+            dot.add(p, q);
+        } else {
+            const T rr = x - q;
+            const T z = jv * rr;
+            a.vr[pos] = rr;
+            a.vz[pos] = z;
+            a.vp[pos] = z;
+            a.vbprev[pos] = x;
+            drz.add(rr, z);
+        }
+    };
     if (has_band) {
         dwt_pass<T, false>(cbuf, rb, n, 1, cs);
         // ---- 4. the LL quadrant's part of this column band goes to the leader (pushed) ---
@@ -460,64 +520,43 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 lead[i * lsd + r0 + jj] = cbuf[i * cs + jj];
             }
         }
-    }
-    cluster.sync();                                                       // #2: the leader holds LL;
-                                                                          // no remote access after this
-    DotAcc<T> dot;                 // p.q share of this CTA (double accuracy)
-    if (coarse && r == 0) {
-        constexpr int PL = (MAXN / 2) * (MAXN / 2) / NT;     // LL positions per thread
-        T lp[PL];
-        if (DST == LDST_APPLY) {
-#pragma unroll
-            for (int s = 0; s < PL; ++s) {
-                const int k = threadIdx.x + s * NT;
-                if (k < h * h) {
-                    const int pos = off + ((k >> lh)) * n + (k & (h - 1));
-                    lp[s] = a.pin[pos];
-                }
-            }
-        }
-        __syncthreads();
-        coarse_forward<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
-        // The data term has no piston component: Gamma annihilates constants and bilinear
-        // weights sum to one, so its full-depth LL coefficient is exactly 0.  Write that
-        // zero rather than the rounding residue of a cancelling sum, which the solve would
-        // amplify by 1 / (alpha D_LL).
-        if (a.zero_piston && L.full && threadIdx.x == 0) lbuf[0] = T(0);
+        // ---- 5. epilogue of the column band (below the LL quadrant when coarse), while the
+        // leader's coarse levels wait for the barrier -----------------------------------------
+        if (!coarse && a.zero_piston && L.full && r == 0 && threadIdx.x == 0) cbuf[0] = T(0);
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < PL; ++s) {
-            const int k = threadIdx.x + s * NT;
-            if (k < h * h) {
-                const int i = (k >> lh), j = (k & (h - 1));
-                const int pos = off + i * n + j;
-                const T v = lbuf[i * lsd + j];
-                if (DST == LDST_APPLY) {
-                    const T q = v + d.alpha * sD[level_of(i, j, L)] * lp[s];
-                    a.out[pos] = q;
-                    dot.add(lp[s], q);
-                } else {
-                    a.out[pos] = v;
-                }
+        for (int s2 = 0; s2 < PF; ++s2) {
+            const int k = threadIdx.x + s2 * NT;
+            if (k < ecnt) {
+                const int i = row_start + (k >> lrb), jj = (k & (rb - 1));
+                epi(i, r0 + jj, off + i * n + r0 + jj, cbuf[i * cs + jj], pre_p[s2], xb[s2], jb[s2]);
             }
         }
     }
-    if (!coarse && a.zero_piston && L.full && r == 0 && threadIdx.x == 0) cbuf[0] = T(0);
-    __syncthreads();
-    // ---- 5. epilogue of the column band (the LL quadrant excluded when coarse) ----------
+    cluster.sync();                                                       // #2: the leader holds LL
+    if (coarse) {
+        // ---- 6. the leader's coarse levels; the LL quadrant's rows go back to their
+        // owners (pushed), whose epilogue takes its share of them ----------------------------
+        if (r == 0) {
+            coarse_forward<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+            // The data term has no piston component: Gamma annihilates constants and bilinear
+            // weights sum to one, so its full-depth LL coefficient is exactly 0.  Write that
+            // zero rather than the rounding residue of a cancelling sum, which the solve would
+            // amplify by 1 / (alpha D_LL).
+            if (a.zero_piston && L.full && threadIdx.x == 0) lbuf[0] = T(0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < h * h; k += NT) {
+                const int i = k >> lh, j = k & (h - 1), q = i / hb;
+                cluster.map_shared_rank(ybuf, static_cast<unsigned>(q))[(i - q * hb) * h + j] = lbuf[i * lsd + j];
+            }
+        }
+        cluster.sync();                                                   // #3: no remote access after this
 #pragma unroll
-    for (int s = 0; s < PF; ++s) {
-        const int k = threadIdx.x + s * NT;
-        if (k < ecnt) {
-            const int i = row_start + (k >> lrb), jj = (k & (rb - 1));
-            const int pos = off + i * n + r0 + jj;
-            const T v = cbuf[i * cs + jj];
-            if (DST == LDST_APPLY) {
-                const T q = v + d.alpha * sD[level_of(i, r0 + jj, L)] * pre_p[s];
-                a.out[pos] = q;
-                dot.add(pre_p[s], q);
-            } else {
-                a.out[pos] = v;
+        for (int s2 = 0; s2 < PL; ++s2) {
+            const int k = threadIdx.x + s2 * NT;
+            if (k < lcnt) {
+                const int i = lr0 + (k >> lh), j = k & (h - 1);
+                epi(i, j, off + i * n + j, ybuf[k], pl[s2], xl[s2], jl[s2]);
             }
         }
     }
@@ -530,6 +569,17 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             if (threadIdx.x == 0) {
                 a.pcg.pqtot[a.iter] = tot;
                 a.pcg.count[1] = 0;
+            }
+        }
+    }
+    if (DST == LDST_APPLY_INIT) {
+        // r.z of the new residual into rz slot `rzslot`, fixed order over the layer CTAs
+        cta_dot_store(drz, red, a.rzp + l * CL + r);
+        if (last_arrival(a.pcg.count, ctas, &last) && threadIdx.x < 32) {
+            const double tot = warp_total(a.rzp, d.n_layers * CL, &drz);
+            if (threadIdx.x == 0) {
+                a.pcg.rztot[a.rzslot] = tot;
+                a.pcg.count[0] = 0;
             }
         }
     }

@@ -451,7 +451,15 @@ __device__ __forceinline__ bool last_arrival(unsigned* count, unsigned ctas, boo
 // iteration k).
 // ---------------------------------------------------------------------------
 enum { LSRC_PHI = 0, LSRC_NODES = 1, LSRC_DM = 2, LSRC_COEF = 3 };
-enum { LDST_PHI = 0, LDST_COEF = 1, LDST_APPLY = 2 };
+// LDST_APPLY_INIT: the forward cluster kernel's apply with the initial residual's vector
+// step fused into its epilogue
+enum { LDST_PHI = 0, LDST_COEF = 1, LDST_APPLY = 2, LDST_APPLY_INIT = 3 };
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 template <class T>
 struct LayerArgs {
@@ -1360,9 +1368,8 @@ __global__ void __launch_bounds__(PBLK) k_layer_dots(__grid_constant__ const Des
     }
 }
 
-// Vector kernels of the reverse pass through the fixed-iteration frame (a build addition):
 // out = a x + b y + c (u o v) elementwise, a null pointer dropping its term (out may be x
-// or y); and x . y in double, one CTA, fixed order.
+// or y): the double residual b - M x of the mixed-precision converged solves.
 template <class T>
 __global__ void __launch_bounds__(PBLK) k_lin(const int n, const double a, const T* x, const double b, const T* y,
                                               const double c, const T* u, const T* v, T* out) {
@@ -1376,19 +1383,113 @@ __global__ void __launch_bounds__(PBLK) k_lin(const int n, const double a, const
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Reverse pass through the fixed-iteration frame with its scalars on the device (a build
+// addition).  Iteration i of the PCG recurrence (Sec. 3.3) is run backwards, statement by
+// statement, in three vector kernels around one M-apply (M and J^-1 are symmetric):
+//   VJ_A  p_bar = pi_bar + M q_bar (of iteration i + 1; not for the first), z_bar = p_bar,
+//         pi_bar = beta_i p_bar, beta_bar = p_bar . p_i, then rho_bar += beta_bar / rho_i and
+//         rho_bar_i = -beta_bar rho_(i+1) / rho_i^2;
+//   VJ_B  r_bar += rho_bar z_(i+1), z_bar += rho_bar r_(i+1), r_bar += J^-1 z_bar, then
+//         alpha_bar = -r_bar . q_i + c_bar . p_i, rho_bar_i += alpha_bar / sigma_i and
+//         sigma_bar = -alpha_bar rho_i / sigma_i^2;
+//   VJ_C  q_bar = -alpha_i r_bar + sigma_bar p_i, pi_bar += alpha_i c_bar + sigma_bar q_i
+//         (q_bar then goes through M);
+//   VJ_E  after iteration 0: p_bar = pi_bar + M q_bar, rho_bar = rho_bar_0, z_bar = p_bar,
+//         r_bar += rho_bar z_0, z_bar += rho_bar r_0, r_bar += J^-1 z_bar (r_bar = b_bar).
+// rho_i = r_i.z_i and sigma_i = p_i.q_i are the forward pass's own totals (rz and p.q slots).
+// The scalar adjoints live in rs[0] (rho_bar), rs[1] (rho_bar_i), rs[2] (sigma_bar); the
+// inner products are fixed-order CTA shares totalled by the last CTA to arrive.
+// ---------------------------------------------------------------------------
+enum { VJ_A = 0, VJ_B = 1, VJ_C = 2, VJ_E = 3 };
+
 template <class T>
-__global__ void __launch_bounds__(PBLK) k_vdot(const int n, const T* __restrict__ x, const T* __restrict__ y,
-                                               double* __restrict__ out) {
+struct VjpArgs {
+    T* rbar;
+    T* pbar;
+    T* pbi;
+    T* qbar;
+    const T* cbar;
+    const T* Mq;         // M q_bar of the previous reverse iteration (VJ_A not first, VJ_E)
+    const T* Jinv;
+    const T* p;          // p_i
+    const T* q;          // q_i
+    const T* r1;         // r_(i+1) (VJ_E: r_0)
+    const T* z1;         // z_(i+1) (VJ_E: z_0)
+    const double* rho;   // rho_0 .. rho_k
+    const double* sigma; // sigma_0 .. sigma_(k-1)
+    double* rs;          // scalar adjoints
+    double* part;        // CTA shares: [0 .. NPART) and [NPART .. 2 NPART)
+    unsigned* count;     // arrival counter, reset by the last CTA
+    int i;
+    int first;           // VJ_A: the first reverse iteration (p_bar = 0, nothing to add)
+    int npart;           // stride of the share slots
+};
+
+template <class T, int PHASE>
+__global__ void __launch_bounds__(PBLK) k_vjp(const int n, __grid_constant__ const VjpArgs<T> v) {
+    __shared__ bool last;
     __shared__ double part[PBLK];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += PBLK) acc += double(x[i]) * double(y[i]);
-    part[threadIdx.x] = acc;
+    __shared__ T sc[4];
+    const int i = v.i;
+    if (threadIdx.x == 0) {
+        // the CTA's scalar coefficients, formed once in double
+        const double rho = v.rho[PHASE == VJ_E ? 0 : i];
+        if (PHASE == VJ_A) sc[0] = T(v.rho[i + 1] / rho);                     // beta_i
+        if (PHASE == VJ_B) sc[0] = T(v.rs[0]);                                // rho_bar
+        if (PHASE == VJ_C) {
+            sc[0] = T(rho / v.sigma[i]);                                      // alpha_i
+            sc[1] = T(v.rs[2]);                                               // sigma_bar
+        }
+        if (PHASE == VJ_E) sc[0] = T(v.rs[1]);                                // rho_bar_0
+    }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double s = 0.0;
-        for (int k = threadIdx.x; k < PBLK; k += 32) s += part[k];
-        s = warp_sum(s);
-        if (threadIdx.x == 0) *out = s;
+    DotAcc<T> d1, d2;
+    for (int k = blockIdx.x * PBLK + threadIdx.x; k < n; k += gridDim.x * PBLK) {
+        if (PHASE == VJ_A) {
+            const T pb = v.first ? T(0) : v.pbi[k] + v.Mq[k];
+            if (!v.first) v.pbar[k] = pb;
+            v.pbi[k] = sc[0] * pb;
+            d1.add(pb, v.p[k]);
+        } else if (PHASE == VJ_B) {
+            const T rb = v.rbar[k] + sc[0] * v.z1[k];
+            const T zb = v.pbar[k] + sc[0] * v.r1[k];
+            const T r2 = rb + v.Jinv[k] * zb;
+            v.rbar[k] = r2;
+            d1.add(r2, v.q[k]);
+            d2.add(v.cbar[k], v.p[k]);
+        } else if (PHASE == VJ_C) {
+            const T qb = -sc[0] * v.rbar[k];
+            v.qbar[k] = qb + sc[1] * v.p[k];
+            const T pb = v.pbi[k] + sc[0] * v.cbar[k];
+            v.pbi[k] = pb + sc[1] * v.q[k];
+        } else {
+            const T pb = v.pbi[k] + v.Mq[k];
+            const T rb = v.rbar[k] + sc[0] * v.z1[k];
+            const T zb = pb + sc[0] * v.r1[k];
+            v.rbar[k] = rb + v.Jinv[k] * zb;
+        }
+    }
+    if (PHASE != VJ_A && PHASE != VJ_B) return;
+    cta_dot_store(d1, part, v.part + blockIdx.x);
+    if (PHASE == VJ_B) cta_dot_store(d2, part, v.part + v.npart + blockIdx.x);
+    if (last_arrival(v.count, gridDim.x, &last) && threadIdx.x < 32) {
+        const double t1 = warp_total(v.part, gridDim.x, &d1);
+        const double t2 = PHASE == VJ_B ? warp_total(v.part + v.npart, gridDim.x, &d2) : 0.0;
+        if (threadIdx.x == 0) {
+            const double rho = v.rho[i], rho1 = v.rho[i + 1];
+            if (PHASE == VJ_A) {
+                const double rb = v.first ? v.rs[0] : v.rs[1];                // rho_bar carried in
+                v.rs[0] = rb + t1 / rho;
+                v.rs[1] = -t1 * rho1 / (rho * rho);
+            } else {
+                const double sig = v.sigma[i], abar = -t1 + t2;
+                v.rs[1] += abar / sig;
+                v.rs[2] = -abar * rho / (sig * sig);
+            }
+            v.count[0] = 0;
+        }
     }
 }
 

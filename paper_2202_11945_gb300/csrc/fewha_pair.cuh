@@ -9,11 +9,11 @@
 
 namespace fewha {
 
-// V_gl(a, b) = sum_{i,j} wy(a, i) wx(b, j) phi_l(i, j) over the pair's footprint box.
-template <class T>
+// V_gl(a, b) = sum_{i,j} wy(a, i) wx(b, j) phi_l(i, j) over the pair's footprint box; NT
+// threads per CTA (at least the node row length N + 1).
+template <class T, int NT = cblk<T>()>
 __device__ __forceinline__ void proj_body(const Desc<T>& d, const T* __restrict__ phi,
                                           const PairBufs<T>& pb, const int g, const int l) {
-    constexpr int NT = cblk<T>();
     constexpr int V = vec16<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* F = reinterpret_cast<T*>(smem_raw);       // footprint of phi_l: rows x cols
@@ -77,11 +77,11 @@ __global__ void __launch_bounds__(cblk<T>(), 1) k_proj(__grid_constant__ const D
 
 // Y_gl(i, j) = sum_{a,b} wy(a, i) wx(b, j) u_g(a, b) on the pair's footprint box.  KM >= the
 // largest number of aperture rows (columns) touching one layer row (column): the loops over
-// a row's taps are unrolled to KM (the weight tables keep the stride KMAX).
-template <class T, int KM = KMAX>
+// a row's taps are unrolled to KM (the weight tables keep the stride KMAX).  NT threads per
+// CTA (at least the box width).
+template <class T, int KM = KMAX, int NT = cblk<T>()>
 __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict__ u,
                                            const PairBufs<T>& pb, const int g, const int l) {
-    constexpr int NT = cblk<T>();
     constexpr int V = vec16<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = reinterpret_cast<T*>(smem_raw);       // u_g, (N+1)^2 (+ alignment shift)

@@ -27,12 +27,6 @@ struct GridSync {
     unsigned nctas;      // CTAs of the grid
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // Barrier number k of the launch (k counted by the caller from 1).  Returns false, in every
 // CTA of the cluster alike, when the frame is to stop.
 __device__ __forceinline__ bool grid_barrier(const GridSync& gs, unsigned k) {
@@ -47,8 +41,8 @@ __device__ __forceinline__ bool grid_barrier(const GridSync& gs, unsigned k) {
         const unsigned target = k * gs.nctas + gs.extra;
         int ok = 1;
         for (unsigned spins = 0;; ++spins) {
-            if (ld_acquire(gs.count) >= target) break;
-            if (ld_acquire(gs.abort) != 0u || spins >= gs.limit) {
+            if (ld_acquire_u32(gs.count) >= target) break;
+            if (ld_acquire_u32(gs.abort) != 0u || spins >= gs.limit) {
                 ok = 0;
                 break;
             }

@@ -68,7 +68,8 @@ class Params(ctypes.Structure):
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("order", ctypes.c_int), ("groups", ctypes.c_int), ("vec_passes", ctypes.c_int)]
+    _fields_ = [("order", ctypes.c_int), ("groups", ctypes.c_int), ("vec_passes", ctypes.c_int),
+                ("pair_threads", ctypes.c_int), ("proj_taps", ctypes.c_int), ("vec_threads", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p
@@ -532,11 +533,15 @@ class Batch:
     def config(self):
         c = BatchConfig()
         self._check(self.L.fewha_batch_get_config(self.b, ctypes.byref(c)))
-        return {"order": c.order, "groups": c.groups, "vec_passes": c.vec_passes}
+        return {"order": c.order, "groups": c.groups, "vec_passes": c.vec_passes,
+                "pair_threads": c.pair_threads, "proj_taps": c.proj_taps, "vec_threads": c.vec_threads}
 
     @config.setter
     def config(self, cfg):
-        c = BatchConfig(cfg["order"], cfg["groups"], cfg["vec_passes"])
+        """Launch shape: order, groups, vec_passes and (optional, 0 = default) pair_threads,
+        proj_taps, vec_threads (see fewha_batch_config)."""
+        c = BatchConfig(cfg["order"], cfg["groups"], cfg["vec_passes"], cfg.get("pair_threads", 0),
+                        cfg.get("proj_taps", 0), cfg.get("vec_threads", 0))
         self._check(self.L.fewha_batch_set_config(self.b, ctypes.byref(c)))
 
     def reconstruct(self, slopes, dm_out=None, stream=None):

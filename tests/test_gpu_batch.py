@@ -50,10 +50,13 @@ def frames_batched(B, recons, seqs, precision):
     return out
 
 
+# the projection kernels' CTA size and tap unroll change which thread computes an element,
+# not its arithmetic: those shapes stay bit-identical to the single-instance frames
 @pytest.mark.parametrize("cfg", [dict(order=0, groups=1, vec_passes=1),
                                  dict(order=1, groups=1, vec_passes=1),
                                  dict(order=1, groups=3, vec_passes=1),
-                                 dict(order=0, groups=8, vec_passes=1)], ids=str)
+                                 dict(order=0, groups=8, vec_passes=1),
+                                 dict(order=0, groups=2, vec_passes=1, pair_threads=256, proj_taps=8)], ids=str)
 def test_batched_frames_equal_single_frames_bitwise(cfg):
     from paper_2202_11945_gb300 import Batch
     wls, seqs = instances()
@@ -68,6 +71,30 @@ def test_batched_frames_equal_single_frames_bitwise(cfg):
     B.close()
 
 
+def test_four_tap_adjoint_projection_and_small_ctas_are_bitwise():
+    """Where every member touches at most 4 aperture rows per layer row (the 8 m
+    single-conjugate geometry), the 4-tap adjoint projection is available and, like the
+    half-size projection CTAs, leaves the frames bit-identical; a 4-tap request on a batch
+    that needs more taps is refused."""
+    from paper_2202_11945_gb300 import Batch, FewhaError
+    wls, seqs = instances()
+    sub = [wls[0], synth.tiny_scao()]
+    sq = [seqs[0], seqs[0]]
+    ref = frames_single(make(sub), sq, 32)
+    recons = make(sub)
+    B = Batch(recons)
+    B.config = dict(order=0, groups=1, vec_passes=1, pair_threads=256, proj_taps=4)
+    got = frames_batched(B, recons, sq, 32)
+    for i in range(2):
+        for t in range(len(sq[0])):
+            assert np.array_equal(got[i][t], ref[i][t]), (i, t)
+    B.close()
+    B = Batch(make(wls))
+    with pytest.raises(FewhaError):
+        B.config = dict(order=0, groups=1, vec_passes=1, proj_taps=4)
+    B.close()
+
+
 def test_vector_partitions_stay_within_tolerance_of_the_oracle():
     from paper_2202_11945_gb300 import Batch
     wls, seqs = instances()
@@ -75,7 +102,8 @@ def test_vector_partitions_stay_within_tolerance_of_the_oracle():
     sub = [wls[i] for i in small]
     recons = make(sub)
     B = Batch(recons)
-    B.config = dict(order=1, groups=2, vec_passes=4)
+    B.config = dict(order=1, groups=2, vec_passes=4, vec_threads=512, pair_threads=256)
+    assert B.config["vec_threads"] == 512 and B.config["pair_threads"] == 256
     got = frames_batched(B, recons, [seqs[i] for i in small], 32)
     for k, i in enumerate(small):
         ref = O.Reconstructor(wls[i])

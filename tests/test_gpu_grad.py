@@ -37,8 +37,9 @@ def recon(wl, prec):
     return Reconstructor(wl, precision=prec, graph=False)
 
 
-def gpu_grads(R, s, target, prec):
-    dm, it, rel = R.reconstruct_converged(to_dev(s, prec), tol=SOLVE_TOL[prec], max_iters=MAX_IT)
+def gpu_grads(R, s, target, prec, tol=None):
+    dm, it, rel = R.reconstruct_converged(to_dev(s, prec), tol=SOLVE_TOL[prec] if tol is None else tol,
+                                          max_iters=MAX_IT)
     a = to_np(dm)
     J, g_a = G.dm_error_objective(a, target)
     gs, ga, gw = R.backward(to_dev(g_a, prec))
@@ -138,7 +139,9 @@ def test_forward_model_function_is_adjoint():
 
 def test_differentiable_workload_32_frames():
     """The 8 m geometry, 32 seeded frames of frozen flow: FP64 and FP32 gradients against
-    the FP64 oracle (each frame's solves warm-started from the previous frame's)."""
+    the FP64 oracle (each frame's solves warm-started from the previous frame's).  The solves
+    go to 1e-12: the alpha gradient -lambda^T D c cancels to ~1e-4 of its terms on some
+    frames, so a 1e-11 residual leaves it near the 1e-4 bound."""
     wl = synth.differentiable()
     geo = O.Geometry(wl)
     Bd = G.data_matrix(geo)
@@ -150,7 +153,7 @@ def test_differentiable_workload_32_frames():
         s = synth.simulate_slopes(wl, t, atm=atm)
         target = synth.true_phase_at(wl, x, y, t, atm=atm)
         for prec, R in ((64, R64), (32, R32)):
-            a, J, gs, ga, gw, g_a, it, rel = gpu_grads(R, s, target, prec)
+            a, J, gs, ga, gw, g_a, it, rel = gpu_grads(R, s, target, prec, tol=1e-12)
             gs_ref, ga_ref, gw_ref = G.map_gradients(geo, Bd, s, geo.alpha, w, g_a)
             check_grads(prec, gs, ga, gw, gs_ref, ga_ref, gw_ref, (t, prec))
     R32.close()
