@@ -355,10 +355,13 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     int4 ytv = make_int4(0, 0, 0, 0);
     if (SRC == LSRC_NODES && lay.ystg > 0 && has_band && threadIdx.x < 2 * d.n_wfs)
         ytv = pb.ytab[(l * CL + r) * 2 * d.n_wfs + threadIdx.x];
-    // this CTA's share of the LL quadrant's rows (coarse layers): [lr0, lr1), hb rows each
+    // this CTA's share of the LL quadrant's rows (coarse layers): [lr0, lr1), hb rows each.
+    // A quadrant narrower than 32 stays with the leader: sharing it out costs a cluster
+    // barrier, more than the leader's few positions take.
     constexpr bool QAPPLY = DST == LDST_APPLY || DST == LDST_APPLY_INIT;
     constexpr int PL = ((MAXN / 2) * (MAXN / 2) / CL + NT - 1) / NT;   // LL-share positions per thread
-    const int hb = max(h >> 3, 1);
+    const bool ldist = h >= 32;
+    const int hb = ldist ? h >> 3 : h;
     const int lr0 = coarse ? min(r * hb, h) : 0, lr1 = coarse ? min(lr0 + hb, h) : 0;
     const int lcnt = (lr1 - lr0) * h;
     // operands of the epilogue at this CTA's positions (band, then LL share), loaded now so
@@ -545,18 +548,20 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             // amplify by 1 / (alpha D_LL).
             if (a.zero_piston && L.full && threadIdx.x == 0) lbuf[0] = T(0);
             __syncthreads();
-            for (int k = threadIdx.x; k < h * h; k += NT) {
-                const int i = k >> lh, j = k & (h - 1), q = i / hb;
-                cluster.map_shared_rank(ybuf, static_cast<unsigned>(q))[(i - q * hb) * h + j] = lbuf[i * lsd + j];
-            }
+            if (ldist)
+                for (int k = threadIdx.x; k < h * h; k += NT) {
+                    const int i = k >> lh, j = k & (h - 1), q = i / hb;
+                    cluster.map_shared_rank(ybuf, static_cast<unsigned>(q))[(i - q * hb) * h + j] =
+                        lbuf[i * lsd + j];
+                }
         }
-        cluster.sync();                                                   // #3: no remote access after this
+        if (ldist) cluster.sync();                                        // #3: no remote access after this
 #pragma unroll
         for (int s2 = 0; s2 < PL; ++s2) {
             const int k = threadIdx.x + s2 * NT;
             if (k < lcnt) {
                 const int i = lr0 + (k >> lh), j = k & (h - 1);
-                epi(i, j, off + i * n + j, ybuf[k], pl[s2], xl[s2], jl[s2]);
+                epi(i, j, off + i * n + j, ldist ? ybuf[k] : lbuf[i * lsd + j], pl[s2], xl[s2], jl[s2]);
             }
         }
     }
@@ -626,8 +631,10 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     T* lbuf = sm + lay.lbuf;
     const int ys = n + 1, cs = rb + 1, lsd = h + 1;
     const bool coarse = L.levels >= 2;
-    // this CTA's rows of the LL quadrant (coarse layers): [lr0, lr1)
-    const int hb = max(h >> 3, 1);                     // h / CL
+    // this CTA's rows of the LL quadrant (coarse layers): [lr0, lr1); a quadrant narrower
+    // than 32 stays with the leader, as in the forward kernel
+    const bool ldist = h >= 32;
+    const int hb = ldist ? h >> 3 : h;                 // h / CL
     const int lr0 = coarse ? min(r * hb, h) : 0, lr1 = coarse ? min(lr0 + hb, h) : 0;
     const int lcnt = (lr1 - lr0) * h;
 
@@ -770,9 +777,12 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     // ---- 2. the LL rows go to the leader (pushed); the leader synthesises the coarse
     // levels and pushes the quadrant's columns into the column bands' tiles --------------
     if (coarse) {
-        T* lead = cluster.map_shared_rank(lbuf, 0);
+        T* lead = ldist ? cluster.map_shared_rank(lbuf, 0) : lbuf;
         for (int k = threadIdx.x; k < lcnt; k += NT) lead[(lr0 + (k >> lh)) * lsd + (k & (h - 1))] = lp[k];
-        cluster.sync();                                                   // #0: the leader holds LL
+        if (ldist)
+            cluster.sync();                                               // #0: the leader holds LL
+        else
+            __syncthreads();
         if (r == 0) {
             coarse_inverse<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
             for (int k = threadIdx.x; k < h * h; k += NT) {

@@ -78,12 +78,12 @@ def test_warm_residual_loop():
 
 
 def test_warm_residual_loop_with_periodic_refresh():
-    """The warm recurrence with an explicit r0 = b - M c0 every 50th frame (warm_refresh):
+    """The warm recurrence with an explicit r0 = b - M c0 every 20th frame (warm_refresh):
     each refresh removes the drift the recurrence has carried, so over the 2000 frames the
     FP32 commands stay within the frame tolerance of the explicit-residual oracle."""
     from paper_2202_11945_gb300 import Reconstructor
     S = sequence()
-    R = Reconstructor(synth.realtime_loop(), precision=32, graph=True, warm_residual=True, warm_refresh=50)
+    R = Reconstructor(synth.realtime_loop(), precision=32, graph=True, warm_residual=True, warm_refresh=20)
     dm, _, _, _ = R.run_loop(S, period_us=0.0)
     err = per_frame_error(dm.double().numpy(), oracle_dms(False))
     assert err.max() <= TOL_FRAME[32], (int(err.argmax()), err.max())
