@@ -365,6 +365,8 @@ VecArgs<T> vec_args(fewha_handle* H, T* c, int iter) {
     v.Jinv = static_cast<const T*>(H->Jinv);
     v.pcg = pcg_slots(H);
     v.iter = iter;
+    v.pq_cnt = 0;
+    v.defer_rz = 0;
     return v;
 }
 
@@ -471,16 +473,29 @@ int launch_csensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaS
     return FEWHA_OK;
 }
 
+// Deferred dot totals of one apply inside the frame's PCG (see ClArgs): the forward
+// kernel's p.q total is left to the CG update, and the inverse kernel forms the r.z total
+// of slot rz_slot from rz_cnt shares at rz_parts (rz_cnt = 0: none).
+struct Defer {
+    bool pq = false;
+    const double* rz_parts = nullptr;
+    int rz_cnt = 0;
+    int rz_slot = 0;
+};
+
 // q = M x (Eq. 6); the p.q partials go to slot `slot` (PQ_SLOTS doubles per slot).
 // With pupdate, x is the CG direction p, first advanced to z + beta p (iteration `slot`).
 template <class T>
 int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int slot, bool pupdate,
-                  cudaStream_t st) {
+                  cudaStream_t st, const Defer& df = Defer()) {
     T* phi = static_cast<T*>(H->phi);
     T* u = static_cast<T*>(H->u);
     int rc;
     ClArgs<T> a = cl_args<T>(H, x, phi);
     a.zero_piston = 1;                 // the data path's input leaves the piston out
+    a.rz_parts = df.rz_parts;
+    a.rz_cnt = df.rz_cnt;
+    a.rz_slot = df.rz_slot;
     if (pupdate) {
         a.pupd = static_cast<T*>(H->p);
         a.zupd = static_cast<const T*>(H->z);
@@ -497,6 +512,7 @@ int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int sl
     b.pin = x;
     b.iter = slot;
     b.zero_piston = 1;
+    b.defer_total = df.pq ? 1 : 0;
     return launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, b, st);
 }
 
@@ -532,9 +548,10 @@ int enqueue_apply_aug(fewha_handle* H, const Desc<T>& d, const T* pold, T* pnew,
 }
 
 // r = b - M c0 (as enqueue_apply, then V_INIT) with the initial residual's vector step fused
-// into the forward kernel's epilogue: r0, z0 = J^-1 r0, p0 = z0, b_prev = b, r.z into slot 0.
+// into the forward kernel's epilogue: r0, z0 = J^-1 r0, p0 = z0, b_prev = b, r.z into slot 0
+// (with `defer`, only its n_layers * CL shares, at the start of the r.z slots).
 template <class T>
-int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st) {
+int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st, bool defer = false) {
     const T* x = c;
     const int slot = PQ_SCRATCH_SLOT;
     const bool pupdate = false;
@@ -567,6 +584,7 @@ int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st)
     b.vj = static_cast<const T*>(H->Jinv);
     b.rzslot = 0;
     b.rzp = H->rzpart;
+    b.defer_total = defer ? 1 : 0;
     return launch_fwd<T, LSRC_NODES, LDST_APPLY_INIT>(H, d, b, st);
 }
 
@@ -630,16 +648,37 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
     // batched frame keeps the separate vector kernel).  The iterations' CG updates stay in
     // their own kernel: fused behind a grid-wide wait for the p.q total (a cooperative
     // launch) they measured slower on GB300 than the separate launch.
+    //
+    // Dot totals are deferred to their consumers: no kernel of an iteration waits for a
+    // grid-wide arrival count.  p.q of iteration k is totalled by the CG update of k; r.z of
+    // slot k (the initial residual's for k = 0, else the update of k - 1) by the inverse
+    // kernel that starts iteration k, which needs it for beta.  Every total still reaches
+    // its slot (rztot[iters] through the last update's own arrival count).
     if (!recorder<T>()) {
+        const bool defer = iters > 0;
         if (warm) {
             if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
         } else {
-            if ((rc = enqueue_apply_init<T>(H, d, c, st))) return rc;
+            if ((rc = enqueue_apply_init<T>(H, d, c, st, defer))) return rc;
         }
         T* p = static_cast<T*>(H->p);
         for (int k = 0; k < iters; ++k) {
-            if ((rc = enqueue_apply<T>(H, d, p, static_cast<T*>(H->q), k, k > 0, st))) return rc;
-            if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, vec_args<T>(H, c, k), st))) return rc;
+            Defer df;
+            df.pq = true;
+            if (k > 0) {
+                df.rz_parts = H->rzpart + static_cast<size_t>(k) * H->npart;
+                df.rz_cnt = H->npart;
+                df.rz_slot = k;
+            } else if (!warm) {
+                df.rz_parts = H->rzpart;
+                df.rz_cnt = d.n_layers * CL;
+                df.rz_slot = 0;
+            }
+            if ((rc = enqueue_apply<T>(H, d, p, static_cast<T*>(H->q), k, k > 0, st, df))) return rc;
+            VecArgs<T> v = vec_args<T>(H, c, k);
+            v.pq_cnt = d.n_layers * CL;
+            v.defer_rz = k + 1 < iters ? 1 : 0;
+            if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, v, st))) return rc;
         }
         return FEWHA_OK;
     }

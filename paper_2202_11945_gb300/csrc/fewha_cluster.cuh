@@ -62,7 +62,8 @@ __device__ __forceinline__ void stage16(T* dst, const T* src, int count, int t, 
 // keeps a sliding window of the inputs in registers.  R is a compile-time constant of
 // the code that runs (1, 2, 4 or 8): the small coarse levels have R = 1, and code
 // unrolled for the largest R under run-time predicates made them instruction-bound.
-template <class T, bool INV, int R>
+// WARP: the pass is run by one warp alone, which synchronises with __syncwarp.
+template <class T, bool INV, int R, bool WARP = false>
 __device__ __forceinline__ void dwt_run(T* Lp, int m, int h, int k0, int ps, bool act) {
     T o0[R], o1[R];
     if (act) {
@@ -98,7 +99,10 @@ __device__ __forceinline__ void dwt_run(T* Lp, int m, int h, int k0, int ps, boo
             }
         }
     }
-    __syncthreads();
+    if (WARP)
+        __syncwarp();
+    else
+        __syncthreads();
     if (act) {
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -111,7 +115,10 @@ __device__ __forceinline__ void dwt_run(T* Lp, int m, int h, int k0, int ps, boo
             }
         }
     }
-    __syncthreads();
+    if (WARP)
+        __syncwarp();
+    else
+        __syncthreads();
 }
 
 template <class T, bool INV>
@@ -132,6 +139,27 @@ __device__ __forceinline__ void dwt_pass(T* buf, int lines, int m, int ls, int p
         case 2: dwt_run<T, INV, 2>(Lp, m, h, k0, ps, act); break;
         case 4: dwt_run<T, INV, 4>(Lp, m, h, k0, ps, act); break;
         default: dwt_run<T, INV, RMAX>(Lp, m, h, k0, ps, act); break;
+    }
+}
+
+// The same pass on a small block (lines * m / 2 <= 32 * RMAX pairs) by the calling warp
+// alone: every lane of the warp calls it.  Each output is formed by the same expression as
+// in dwt_pass, so the result is identical; only the CTA-wide barriers are gone.
+template <class T, bool INV>
+__device__ __forceinline__ void dwt_pass_warp(T* buf, int lines, int m, int ls, int ps) {
+    const int h = m >> 1;
+    const int ll = __ffs(lines) - 1, lhh = __ffs(h) - 1;
+    const int lruns = min(max(5 - ll, 0), lhh);
+    const int R = h >> lruns;
+    const int t = threadIdx.x & 31;
+    const bool act = t < (lines << lruns);
+    const int line = t & (lines - 1), k0 = (t >> ll) * R;
+    T* Lp = buf + line * ls;
+    switch (R) {
+        case 1: dwt_run<T, INV, 1, true>(Lp, m, h, k0, ps, act); break;
+        case 2: dwt_run<T, INV, 2, true>(Lp, m, h, k0, ps, act); break;
+        case 4: dwt_run<T, INV, 4, true>(Lp, m, h, k0, ps, act); break;
+        default: dwt_run<T, INV, RMAX, true>(Lp, m, h, k0, ps, act); break;
     }
 }
 
@@ -215,15 +243,29 @@ __device__ __forceinline__ void cta_sum2_t(T& x, T& y, double* scratch) {
 constexpr int SMALL = 32;              // side of the spare scratch tile
 constexpr int SSTRIDE = SMALL + 1;
 
+// Levels whose block side is at most WARP_SIDE are run by warp 0 alone: a pass there is a
+// few hundred cycles of barrier latency on the whole CTA and little work.
+constexpr int WARP_SIDE = 16;
+
 // Forward (analysis) levels lev_begin..levels-1 of the LL block (stride lsd), whole CTA.
 template <class T>
 __device__ __forceinline__ void coarse_forward(T* lbuf, T* sbuf, int n, int lev_begin, int levels,
                                                int lsd) {
     (void)sbuf;
-    for (int lev = lev_begin; lev < levels; ++lev) {
+    int lev = lev_begin;
+    for (; lev < levels && (n >> lev) > WARP_SIDE; ++lev) {
         const int m = n >> lev;
         dwt_pass<T, false>(lbuf, m, m, lsd, 1);    // rows
         dwt_pass<T, false>(lbuf, m, m, 1, lsd);    // columns
+    }
+    if (lev < levels) {
+        if (threadIdx.x < 32)
+            for (; lev < levels; ++lev) {
+                const int m = n >> lev;
+                dwt_pass_warp<T, false>(lbuf, m, m, lsd, 1);
+                dwt_pass_warp<T, false>(lbuf, m, m, 1, lsd);
+            }
+        __syncthreads();
     }
 }
 
@@ -232,7 +274,18 @@ template <class T>
 __device__ __forceinline__ void coarse_inverse(T* lbuf, T* sbuf, int n, int lev_end, int levels,
                                                int lsd) {
     (void)sbuf;
-    for (int lev = levels - 1; lev >= lev_end; --lev) {
+    int lev = levels - 1;
+    if (lev >= lev_end && (n >> lev) <= WARP_SIDE) {
+        if (threadIdx.x < 32)
+            for (int k = lev; k >= lev_end && (n >> k) <= WARP_SIDE; --k) {
+                const int m = n >> k;
+                dwt_pass_warp<T, true>(lbuf, m, m, 1, lsd);
+                dwt_pass_warp<T, true>(lbuf, m, m, lsd, 1);
+            }
+        while (lev >= lev_end && (n >> lev) <= WARP_SIDE) --lev;
+        __syncthreads();
+    }
+    for (; lev >= lev_end; --lev) {
         const int m = n >> lev;
         dwt_pass<T, true>(lbuf, m, m, 1, lsd);     // columns
         dwt_pass<T, true>(lbuf, m, m, lsd, 1);     // rows
@@ -303,6 +356,15 @@ struct ClArgs {
     const T* vj;
     double* rzp;
     int rzslot;
+    // Deferred totals.  defer_total (forward kernel): the CTA shares of p.q (APPLY) or r.z
+    // (APPLY_INIT) are stored and the total is left to the next kernel that needs it, so no
+    // CTA waits for a grid-wide arrival count.  rz_cnt > 0 (inverse kernel): the r.z total
+    // of slot rz_slot is formed from the rz_cnt shares at rz_parts (fixed order, the same in
+    // every CTA), used for beta, and stored by the first CTA.
+    int defer_total;
+    const double* rz_parts;
+    int rz_cnt;
+    int rz_slot;
 };
 
 struct ClLayout {       // shared-memory offsets set by the host, in T units
@@ -568,7 +630,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     if (DST == LDST_APPLY) {
         double* slots = a.pcg.pqpart + a.iter * PQ_SLOTS;
         cta_dot_store(dot, red, slots + l * CL + r);
-        if (last_arrival(a.pcg.count + 1, ctas, &last) && threadIdx.x < 32) {
+        if (!a.defer_total && last_arrival(a.pcg.count + 1, ctas, &last) && threadIdx.x < 32) {
             // fixed order: layer-major, rank-minor over the slots of the layers present
             const double tot = warp_total(slots, d.n_layers * CL, &dot);
             if (threadIdx.x == 0) {
@@ -580,7 +642,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     if (DST == LDST_APPLY_INIT) {
         // r.z of the new residual into rz slot `rzslot`, fixed order over the layer CTAs
         cta_dot_store(drz, red, a.rzp + l * CL + r);
-        if (last_arrival(a.pcg.count, ctas, &last) && threadIdx.x < 32) {
+        if (!a.defer_total && last_arrival(a.pcg.count, ctas, &last) && threadIdx.x < 32) {
             const double tot = warp_total(a.rzp, d.n_layers * CL, &drz);
             if (threadIdx.x == 0) {
                 a.pcg.rztot[a.rzslot] = tot;
@@ -694,14 +756,23 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
             }
         }
     }
-    // beta and mu are formed while the copies are in flight
-    if (PUPD && threadIdx.x == 0) {
-        double b = 0.0;
-        if (has_old) {
-            const double rz_new = a.pcg.rztot[a.iter], rz_old = a.pcg.rztot[a.iter - 1];
-            b = rz_old != 0.0 ? rz_new / rz_old : 0.0;
+    // beta and mu are formed while the copies are in flight; a deferred r.z total first
+    // (warp 0, fixed order: the same value in every CTA)
+    if (threadIdx.x < 32 && (PUPD || a.rz_cnt > 0)) {
+        double rz_new = 0.0;
+        if (a.rz_cnt > 0) {
+            rz_new = warp_total(a.rz_parts, a.rz_cnt, static_cast<const DotAcc<T>*>(nullptr));
+            if (threadIdx.x == 0 && l == 0 && r == 0) a.pcg.rztot[a.rz_slot] = rz_new;
         }
-        sbeta = T(b);
+        if (PUPD && threadIdx.x == 0) {
+            double b = 0.0;
+            if (has_old) {
+                if (a.rz_cnt == 0) rz_new = a.pcg.rztot[a.iter];
+                const double rz_old = a.pcg.rztot[a.iter - 1];
+                b = rz_old != 0.0 ? rz_new / rz_old : 0.0;
+            }
+            sbeta = T(b);
+        }
     }
     if (PUPD == 2 && threadIdx.x >= 32 && threadIdx.x < 32 + a.aug_m) {
         const int j = threadIdx.x - 32;

@@ -836,6 +836,11 @@ struct VecArgs {
     const T* Jinv;
     PcgSlots pcg;
     int iter;
+    // V_UPDATE with deferred totals: pq_cnt > 0, the p.q total of the iteration is formed
+    // here from the forward kernel's pq_cnt shares (fixed order) and stored by CTA 0;
+    // defer_rz, the r.z shares are stored and their total is left to the next inverse kernel
+    int pq_cnt;
+    int defer_rz;
 };
 
 enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2 };
@@ -852,12 +857,22 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     __shared__ T salpha;
     T ta = T(0);
     bool have_alpha = PHASE != V_UPDATE;
-    if (!have_alpha && threadIdx.x == 0) {
+    if (!have_alpha && threadIdx.x < 32) {
         // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final).  Formed
         // once and broadcast (an FP64 division is ~10 instructions on GB300's slow FP64
-        // pipe), while the first batch of vector loads is in flight
-        const double rz = v.pcg.rztot[iter], pq = v.pcg.pqtot[iter];
-        salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
+        // pipe), while the first batch of vector loads is in flight; a deferred p.q total
+        // first (warp 0, fixed order: the same value in every CTA)
+        double pq = 0.0;
+        if (v.pq_cnt > 0) {
+            pq = warp_total(v.pcg.pqpart + static_cast<long long>(iter) * PQ_SLOTS, v.pq_cnt,
+                            static_cast<const DotAcc<T>*>(nullptr));
+            if (threadIdx.x == 0 && cta == 0) v.pcg.pqtot[iter] = pq;
+        }
+        if (threadIdx.x == 0) {
+            if (v.pq_cnt == 0) pq = v.pcg.pqtot[iter];
+            const double rz = v.pcg.rztot[iter];
+            salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
+        }
     }
     DotAcc<T> dot;
     for (int base = cta * NTV * PVEC; base < n; base += nparts * NTV * PVEC) {
@@ -916,6 +931,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = (PHASE == V_UPDATE) ? iter + 1 : 0;
     cta_dot_store(dot, part, v.pcg.rzpart + slot * v.pcg.npart + cta);
+    if (PHASE == V_UPDATE && v.defer_rz) return;        // the next inverse kernel totals r.z
     if (last_arrival(v.pcg.count, nparts, &last) && w == 0) {
         const double tot = warp_total(v.pcg.rzpart + slot * v.pcg.npart, v.pcg.npart, &dot);
         if (lane == 0) {
