@@ -83,9 +83,11 @@ extern "C" {
 #define FEWHA_FLAG_GRAPH 1u         /* replay each frame as a captured CUDA graph    */
 #define FEWHA_FLAG_WARM_RESIDUAL 2u /* r0 = (b - b_prev) + r_prev (Algorithm 1)     */
 #define FEWHA_FLAG_PDL 4u           /* programmatic dependent launch: each kernel lets
-                                       the next one launch its CTAs early, which wait on
-                                       the device for it to finish (off by default: on
-                                       GB300 it slows the graph-replayed frame)        */
+                                       the next one launch its CTAs early (the cluster
+                                       kernels from a barrier in their middle), which
+                                       wait on the device for it to finish; shortens
+                                       the gap between dependent kernels (the Python
+                                       binding sets it by default)                     */
 #define FEWHA_FLAG_AUGMENTED 8u     /* augmented PCG (Sec. 3.4, the augPCG step of
                                        Algorithm 1): the previous frame's search
                                        directions P and their images Q = M P are kept;

@@ -599,6 +599,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
     cluster.sync();                                                       // #2: the leader holds LL
+    pdl_trigger();
     if (coarse) {
         // ---- 6. the leader's coarse levels; the LL quadrant's rows go back to their
         // owners (pushed), whose epilogue takes its share of them ----------------------------
@@ -656,7 +657,7 @@ template <class T, int SRC, int DST>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_fwd(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay, __grid_constant__ const PairBufs<T> pb) {
-    pdl_enter();
+    pdl_wait();
     cl_fwd_body<T, SRC, DST>(d, a, lay, pb, blockIdx.y, gridDim.x * gridDim.y);
 }
 
@@ -864,6 +865,7 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
     cluster.sync();                                                       // #1
+    pdl_trigger();
     // ---- 3. column synthesis of level 0 on the column band; its rows go to every row
     // band's owner (pushed) -----------------------------------------------------------------
     if (has_band) {
@@ -888,7 +890,7 @@ template <class T, int PUPD>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_inv(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay) {
-    pdl_enter();
+    pdl_wait();
     cl_inv_body<T, PUPD>(d, a, lay, blockIdx.y);
 }
 
@@ -1156,6 +1158,7 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
         }
     }
     cluster.sync();                                                       // weighted slopes ready
+    pdl_trigger();
     // ---- Gamma_g^T on node rows [s0, s1) (and row N on the last band) --------------------
     if (rows > 0) {
         if (r > 0) {
@@ -1203,7 +1206,7 @@ template <class T, int SRC>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_sensor(__grid_constant__ const Desc<T> d, __grid_constant__ const SensorArgs<T> a,
                 __grid_constant__ const SensorLayout lay, __grid_constant__ const PairBufs<T> pb) {
-    pdl_enter();
+    pdl_wait();
     cl_sensor_body<T, SRC>(d, a, lay, pb, blockIdx.y);
 }
 

@@ -23,6 +23,12 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+// The two halves, for the cluster kernels: they wait at entry and let the next kernel
+// launch only from a barrier in their middle.  Launched at entry, the next kernel's CTAs
+// would take SMs and issue slots for most of the long cluster kernel (measured slower on
+// GB300); launched from the middle, they are resident and waiting when it ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 constexpr int NWARP = BLK / 32;
 
 __constant__ float c_h32[6];
@@ -1278,6 +1284,7 @@ __device__ __forceinline__ T dm_node(const Desc<T>& d, const PolArgs<T>& p, int 
 template <class T>
 __global__ void __launch_bounds__(PBLK) k_dmnodes(__grid_constant__ const Desc<T> d,
                                                   __grid_constant__ const PolArgs<T> p) {
+    pdl_enter();
     const int k = blockIdx.x * PBLK + threadIdx.x;
     if (k >= d.n_nodes) return;
     int g = 0;
@@ -1302,6 +1309,7 @@ constexpr int POLBLK = 1024;   // threads of the slope kernel: a coarse block in
 template <class T>
 __global__ void __launch_bounds__(POLBLK) k_pol(__grid_constant__ const Desc<T> d,
                                                 __grid_constant__ const PolArgs<T> p) {
+    pdl_enter();
     const int g = blockIdx.y;
     const WfsInfo& W = d.G[g];
     const int N = W.N, np = N + 1;

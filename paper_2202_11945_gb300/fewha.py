@@ -187,7 +187,7 @@ def _stream(stream):
 class Reconstructor:
     """One FEWHA instance on the current CUDA device (a handle of the C library)."""
 
-    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=False, augmented=False,
+    def __init__(self, wl, precision=32, graph=True, warm_residual=False, pdl=True, augmented=False,
                  closed_loop=False, persistent=False, warm_refresh=0):
         if not torch.cuda.is_available():
             raise RuntimeError("FEWHA needs a CUDA device; there is no CPU path")

@@ -149,7 +149,7 @@ def test_programmatic_dependent_launch_gives_identical_frames():
     from paper_2202_11945_gb300 import Reconstructor
     for name, prec, graph in (("tiny_mcao", 32, True), ("maory", 32, True), ("tiny_scao", 64, False)):
         wl = synth.workload_by_name(name)
-        A = Reconstructor(wl, precision=prec, graph=graph)
+        A = Reconstructor(wl, precision=prec, graph=graph, pdl=False)
         B = Reconstructor(wl, precision=prec, graph=graph, pdl=True)
         for t in range(3):
             s = to_dev(slopes(name, t), prec)
