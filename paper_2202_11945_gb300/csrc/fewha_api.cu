@@ -1177,7 +1177,7 @@ int cluster_layouts(fewha_handle* H) {
             int need = 0;
             for (size_t g = 0; g < s.G.size(); ++g) {
                 const int* bx = &box[(g * MAXL + l) * 4];
-                aligned = aligned && (bx[3] % V) == 0;
+                aligned = aligned && (bx[2] % V) == 0 && (bx[3] % V) == 0 && (n % V) == 0;
                 const int lo = std::max(r * rb, bx[0]), hi = std::min(r * rb + rb, bx[0] + bx[1]);
                 if (hi > lo) need += ((hi - lo) * bx[3] + V - 1) & ~(V - 1);
             }

@@ -46,6 +46,19 @@ template <class T>
 __host__ __device__ constexpr int vec16() {
     return 16 / static_cast<int>(sizeof(T));
 }
+// The 16-byte vector of T and its element access.
+template <class T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static __device__ __forceinline__ float at(const float4& v, int e) {
+        return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+    }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static __device__ __forceinline__ double at(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+};
+
 // Stage `count` elements from src to dst (both 16-byte aligned) in 16-byte chunks by the
 // threads [t0, t0 + nthr); reads up to one chunk past src + count (allocations are padded).
 template <class T>
@@ -456,6 +469,10 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         }
     }
 
+    // Everything above reads only data that the kernel two launches back (or earlier) had
+    // written: p and b are inputs of the apply, written before its first kernel.  The band
+    // below reads the adjoint projection's output, written by the previous kernel.
+    pdl_wait();
     // ---- 1. the row band of y ---------------------------------------------------
     if (has_band) {
         if (SRC == LSRC_PHI) {
@@ -469,9 +486,12 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             // y = sum_g R_y,gl^T u_g R_x,gl over this band.  The band's rows of sensor g's
             // term are one contiguous run of its pair slot (rows of box[g][l][3] columns);
             // the runs (host table) are staged with 16-byte copies, all in flight together,
-            // and added from shared memory in the fixed sensor order.  A thread owns one
-            // column j of the band (NT is a multiple of n) and the rows i0 + q * di.
-            constexpr int KB = (MAXN * (MAXN / CL) + NT - 1) / NT;   // band positions per thread
+            // and added from shared memory in the fixed sensor order.  The boxes' columns
+            // are 16-byte groups of the layer grid (host-checked), so a thread adds whole
+            // groups: one 16-byte shared-memory read per sensor and group.
+            constexpr int V = vec16<T>();
+            using VT = typename Vec16<T>::type;
+            constexpr int KG = (MAXN * (MAXN / CL) / V + NT - 1) / NT;   // groups per thread
             __shared__ int4 ygb[MAXG];        // per sensor: first and end band row, col0, cols
             __shared__ int4 ygx[MAXG];        // per sensor: offset in the stage, offset in Y
             T* ystg = sm + lay.ystg;
@@ -486,28 +506,29 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 const int4 bx = ygb[g];
                 if (bx.y > bx.x) stage16(ystg + ygx[g].x, pb.Y + ygx[g].y, (bx.y - bx.x) * bx.w, threadIdx.x, NT);
             }
-            const int j = threadIdx.x & (n - 1);
-            const int i0 = threadIdx.x >> L.log2n, di = NT >> L.log2n;
-            T acc[KB];
-#pragma unroll
-            for (int q = 0; q < KB; ++q) acc[q] = T(0);
+            const int lg = L.log2n - (V == 4 ? 2 : 1);        // log2 of the groups per row
+            const int ngrp = rb << lg;
             cp_async_wait();
             __syncthreads();
-            for (int g = 0; g < d.n_wfs; ++g) {
-                const int4 bx = ygb[g];
-                if (bx.y > bx.x && j >= bx.z && j < bx.z + bx.w) {
-                    const T* col = ystg + ygx[g].x + (j - bx.z);
 #pragma unroll
-                    for (int q = 0; q < KB; ++q) {
-                        const int ii = i0 + q * di, i = r0 + ii;
-                        if (ii < rb && i >= bx.x && i < bx.y) acc[q] += col[(i - bx.x) * bx.w];
+            for (int s2 = 0; s2 < KG; ++s2) {
+                const int grp = threadIdx.x + s2 * NT;
+                if (grp < ngrp) {
+                    const int ii = grp >> lg, j0 = (grp & ((1 << lg) - 1)) * V, i = r0 + ii;
+                    T acc[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) acc[e] = T(0);
+                    for (int g = 0; g < d.n_wfs; ++g) {
+                        const int4 bx = ygb[g];
+                        if (i >= bx.x && i < bx.y && j0 >= bx.z && j0 < bx.z + bx.w) {
+                            const VT v = *reinterpret_cast<const VT*>(ystg + ygx[g].x + (i - bx.x) * bx.w + (j0 - bx.z));
+#pragma unroll
+                            for (int e = 0; e < V; ++e) acc[e] += Vec16<T>::at(v, e);
+                        }
                     }
-                }
-            }
 #pragma unroll
-            for (int q = 0; q < KB; ++q) {
-                const int ii = i0 + q * di;
-                if (ii < rb) ybuf[ii * ys + j] = acc[q];
+                    for (int e = 0; e < V; ++e) ybuf[ii * ys + j0 + e] = acc[e];
+                }
             }
             __syncthreads();
         } else {
@@ -657,7 +678,6 @@ template <class T, int SRC, int DST>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_fwd(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay, __grid_constant__ const PairBufs<T> pb) {
-    pdl_wait();
     cl_fwd_body<T, SRC, DST>(d, a, lay, pb, blockIdx.y, gridDim.x * gridDim.y);
 }
 

@@ -15,20 +15,25 @@ constexpr int BLK = 1024;   // threads of the per-layer and per-sensor kernels
 constexpr int PQ_SLOTS = MAXL * 8;   // p.q partial slots per CG iteration (layer x cluster rank)
 constexpr int PBLK = 256;   // threads of the vector (PCG) kernels
 
-// Programmatic dependent launch: let the stream's next kernel start launching its CTAs,
-// then wait until the previous kernel has completed and its writes are visible.  Nothing
-// of this kernel's own work happens before the wait.  Both instructions are no-ops when the
-// kernel was launched without programmatic stream serialization.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-// The two halves, for the cluster kernels: they wait at entry and let the next kernel
-// launch only from a barrier in their middle.  Launched at entry, the next kernel's CTAs
-// would take SMs and issue slots for most of the long cluster kernel (measured slower on
-// GB300); launched from the middle, they are resident and waiting when it ends.
+// Programmatic dependent launch: wait until the previous kernel has completed and its
+// writes are visible, then let the stream's next kernel start launching its CTAs.  Both
+// instructions are no-ops when the kernel was launched without programmatic stream
+// serialization.
+//
+// Every kernel lets the next one launch only after its own wait.  So while any CTA of a
+// kernel runs, the kernel two places before it in the stream has completed, and a kernel
+// may read, before its wait, data that no kernel closer than that wrote (the forward layer
+// kernel prefetches its epilogue operands this way).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+// The cluster kernels trigger later, from a barrier in their middle: launched at their
+// entry, the next kernel's CTAs would take SMs and issue slots for most of the long
+// cluster kernel (measured slower on GB300); launched from the middle, they are resident
+// and waiting when it ends.
 constexpr int NWARP = BLK / 32;
 
 __constant__ float c_h32[6];
