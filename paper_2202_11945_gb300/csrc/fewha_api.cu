@@ -105,6 +105,7 @@ struct fewha_handle {
     int* box = nullptr;
     int* ytab = nullptr;              // band-run table of the forward kernel (PairBufs::ytab)
     void* ptw = nullptr;              // adjoint-projection weights (PairBufs::tw), T
+    void* tailop = nullptr;           // the 8 x 8 tail levels as one matrix (Desc::tailop), T
     int* pti = nullptr;               // their first index and count (PairBufs::ti)
     std::vector<int> box_host;
     void* pairV = nullptr;
@@ -266,6 +267,7 @@ Desc<T> make_desc(const fewha_handle* H) {
     d.Jinv = static_cast<const T*>(H->Jinv);
     for (int l = 0; l < d.n_layers && !s.dlev.empty(); ++l)
         for (int k = 0; k <= MAXLEV; ++k) d.Dlev[l][k] = T(s.dlev[l * (MAXLEV + 1) + k]);
+    d.tailop = static_cast<const T*>(H->tailop);
     for (int g = 0; g < d.n_wfs; ++g)
         for (int l = 0; l < d.n_layers; ++l)
             for (int k = 0; k < 4; ++k) d.box[g][l][k] = H->box_host[(g * MAXL + l) * 4 + k];
@@ -1037,6 +1039,69 @@ int set_smem_limits(fewha_handle* H) {
     return FEWHA_OK;
 }
 
+// One periodic db3 step of the host (the same rule as the kernels' dwt_run): analysis of
+// the m values x[0], x[st], ... into [a | d], or synthesis of [a | d] back.
+void db3_step_host(double* x, int m, int st, const double* h, const double* g, bool inv) {
+    double y[8];
+    const int hm = m / 2;
+    for (int k = 0; k < hm; ++k) {
+        if (!inv) {
+            double a = 0.0, d = 0.0;
+            for (int t = 0; t < 6; ++t) {
+                a += h[t] * x[((2 * k + t) % m) * st];
+                d += g[t] * x[((2 * k + t) % m) * st];
+            }
+            y[k] = a;
+            y[hm + k] = d;
+        } else {
+            double e = 0.0, o = 0.0;
+            for (int s2 = 0; s2 < 3; ++s2) {
+                const int i = ((k - s2) % hm + hm) % hm;
+                e += h[2 * s2] * x[i * st] + g[2 * s2] * x[(hm + i) * st];
+                o += h[2 * s2 + 1] * x[i * st] + g[2 * s2 + 1] * x[(hm + i) * st];
+            }
+            y[2 * k] = e;
+            y[2 * k + 1] = o;
+        }
+    }
+    for (int k = 0; k < m; ++k) x[k * st] = y[k];
+}
+
+// The last three levels of a full decomposition (an 8 x 8 LL block down to 1 x 1) as one
+// matrix A, entry (k, o) at k * TAIL_LD + o (input k = 8 i + j to output o), from unit
+// inputs through the level steps (rows, then columns, for sides 8, 4, 2).  The synthesis
+// of the same steps is checked to be A^T, which the inverse kernel applies; empty if not.
+std::vector<double> tail_operator(const double* h, const double* g) {
+    std::vector<double> A(TAIL_N, 0.0);
+    for (int k = 0; k < 64; ++k) {
+        double X[64] = {};
+        X[k] = 1.0;
+        for (int m = 8; m >= 2; m /= 2) {
+            for (int i = 0; i < m; ++i) db3_step_host(X + 8 * i, m, 1, h, g, false);   // rows
+            for (int j = 0; j < m; ++j) db3_step_host(X + j, m, 8, h, g, false);       // columns
+        }
+        for (int o = 0; o < 64; ++o) A[k * TAIL_LD + o] = X[o];
+    }
+    for (int o = 0; o < 64; ++o) {
+        double Y[64] = {};
+        Y[o] = 1.0;
+        for (int m = 2; m <= 8; m *= 2) {
+            for (int j = 0; j < m; ++j) db3_step_host(Y + j, m, 8, h, g, true);        // columns
+            for (int i = 0; i < m; ++i) db3_step_host(Y + 8 * i, m, 1, h, g, true);    // rows
+        }
+        for (int k = 0; k < 64; ++k)
+            if (std::fabs(Y[k] - A[k * TAIL_LD + o]) > 1e-12) return {};
+    }
+    return A;
+}
+
+// Whether some layer's coarse levels end with the three tail levels (Desc::tailop).
+bool tail_used(const HostSetup& s) {
+    for (const auto& L : s.L)
+        if (L.levels >= 4 && (L.n >> (L.levels - 1)) == 2) return true;
+    return false;
+}
+
 // Shared-memory layouts of the cluster kernels: the largest band over all layers and
 // sensors, element counts in T units after a fixed header; every region starts on a
 // 16-byte boundary (cp.async targets).
@@ -1070,8 +1135,7 @@ int cluster_layouts(fewha_handle* H) {
     f.ybuf = 0;
     f.cbuf = ybuf;
     f.lbuf = ybuf + cbuf;
-    f.sbuf = f.lbuf + lbuf;
-    f.total = f.sbuf + round4(SMALL * SSTRIDE);
+    f.total = f.lbuf + lbuf;
     H->lay_fwd = f;
     H->smem_fwd = hdr_cl + static_cast<size_t>(f.total) * sizeof(T);
     ClLayout v{};
@@ -1080,8 +1144,18 @@ int cluster_layouts(fewha_handle* H) {
     v.lbuf = ybuf + cbuf;
     v.stage = v.lbuf + lbuf;                               // p and z of the column band
     v.stage2 = v.stage + 2 * MAXN * (MAXN / CL);           // p and z of the LL quadrant
-    v.sbuf = v.stage2 + 2 * (MAXN / 2) * (MAXN / 2);
-    v.total = v.sbuf + round4(SMALL * SSTRIDE);
+    v.total = v.stage2 + 2 * (MAXN / 2) * (MAXN / 2);
+    // the tail operator of the coarse levels (the forward kernel's region is placed after
+    // its staged band sums, space permitting)
+    std::vector<double> tail = tail_used(s) ? tail_operator(s.taps_h, s.taps_g) : std::vector<double>();
+    if (!tail.empty()) {
+        v.tail = v.total;
+        v.total += round4(TAIL_N);
+        int rc0;
+        if ((rc0 = talloc(H, &H->tailop, TAIL_N))) return rc0;
+        const std::vector<T> tt(tail.begin(), tail.end());
+        CK(cudaMemcpy(H->tailop, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice), "tail operator");
+    }
     H->lay_inv = v;
     H->smem_inv = hdr_cl + static_cast<size_t>(v.total) * sizeof(T);
     int Vn = 0, SXn = 0, halo = 0;
@@ -1213,6 +1287,15 @@ int cluster_layouts(fewha_handle* H) {
                     so += ((hi - lo) * bx[3] + V - 1) & ~(V - 1);
                 }
             }
+        }
+    }
+    if (H->tailop) {
+        const long long room = 227LL * 1024 - static_cast<long long>(H->smem_fwd) -
+                               static_cast<long long>(sizeof(Desc<T>)) - 2048;
+        if (static_cast<long long>(round4(TAIL_N)) * static_cast<long long>(sizeof(T)) <= room) {
+            H->lay_fwd.tail = H->lay_fwd.total;
+            H->lay_fwd.total += round4(TAIL_N);
+            H->smem_fwd += static_cast<size_t>(round4(TAIL_N)) * sizeof(T);
         }
     }
     H->smem_proj = proj * sizeof(T);

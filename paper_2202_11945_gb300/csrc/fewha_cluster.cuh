@@ -253,41 +253,81 @@ __device__ __forceinline__ void cta_sum2_t(T& x, T& y, double* scratch) {
     __syncthreads();
 }
 
-constexpr int SMALL = 32;              // side of the spare scratch tile
-constexpr int SSTRIDE = SMALL + 1;
-
 // Levels whose block side is at most WARP_SIDE are run by warp 0 alone: a pass there is a
 // few hundred cycles of barrier latency on the whole CTA and little work.
 constexpr int WARP_SIDE = 16;
 
+// The last three levels of a full decomposition (block sides 8, 4 and 2, down to the 1 x 1
+// LL) as one linear map of the 8 x 8 block: the analysis is the 64 x 64 matrix A, stored
+// with row stride TAIL_LD so that entry (k, o) maps input k = 8 i + j to output o; the
+// synthesis is its transpose (the periodic db3 transform is orthogonal; the host checks
+// that its own synthesis matches A^T).  One pass of 64 threads instead of six dependent
+// level passes: each costs ~0.4 us of latency on one CTA, whatever its size.
+constexpr int TAIL_LD = 65;
+constexpr int TAIL_N = 64 * TAIL_LD;
+
+// Whether the levels [lev0, levels) of a layer of side n end with the three tail levels.
+__device__ __forceinline__ bool tail_applies(int n, int lev0, int levels) {
+    return (n >> (levels - 1)) == 2 && levels - 3 >= lev0;
+}
+
+// y = A x (forward) or y = A^T x (inverse) on the 8 x 8 block at lbuf (stride lsd), whole
+// CTA; `op` in shared memory.  Reads of x are broadcasts; reads of op are conflict-free
+// (stride TAIL_LD is odd).
+template <class T, bool INV>
+__device__ __forceinline__ void tail_map(T* lbuf, int lsd, const T* op) {
+    const int t = threadIdx.x;
+    T y = T(0);
+    if (t < 64) {
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int k = 0; k < 64; k += 4) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int kk = k + e;
+                const T x = lbuf[(kk >> 3) * lsd + (kk & 7)];
+                acc[e] += (INV ? op[t * TAIL_LD + kk] : op[kk * TAIL_LD + t]) * x;
+            }
+        }
+        y = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+    __syncthreads();
+    if (t < 64) lbuf[(t >> 3) * lsd + (t & 7)] = y;
+    __syncthreads();
+}
+
 // Forward (analysis) levels lev_begin..levels-1 of the LL block (stride lsd), whole CTA.
+// `tail`: the tail operator in shared memory, or null.
 template <class T>
-__device__ __forceinline__ void coarse_forward(T* lbuf, T* sbuf, int n, int lev_begin, int levels,
+__device__ __forceinline__ void coarse_forward(T* lbuf, const T* tail, int n, int lev_begin, int levels,
                                                int lsd) {
-    (void)sbuf;
+    const int lev_end = (tail && tail_applies(n, lev_begin, levels)) ? levels - 3 : levels;
     int lev = lev_begin;
-    for (; lev < levels && (n >> lev) > WARP_SIDE; ++lev) {
+    for (; lev < lev_end && (n >> lev) > WARP_SIDE; ++lev) {
         const int m = n >> lev;
         dwt_pass<T, false>(lbuf, m, m, lsd, 1);    // rows
         dwt_pass<T, false>(lbuf, m, m, 1, lsd);    // columns
     }
-    if (lev < levels) {
+    if (lev < lev_end) {
         if (threadIdx.x < 32)
-            for (; lev < levels; ++lev) {
+            for (; lev < lev_end; ++lev) {
                 const int m = n >> lev;
                 dwt_pass_warp<T, false>(lbuf, m, m, lsd, 1);
                 dwt_pass_warp<T, false>(lbuf, m, m, 1, lsd);
             }
         __syncthreads();
     }
+    if (lev_end < levels) tail_map<T, false>(lbuf, lsd, tail);
 }
 
 // Inverse (synthesis) levels levels-1..lev_end of the LL block.
 template <class T>
-__device__ __forceinline__ void coarse_inverse(T* lbuf, T* sbuf, int n, int lev_end, int levels,
+__device__ __forceinline__ void coarse_inverse(T* lbuf, const T* tail, int n, int lev_end, int levels,
                                                int lsd) {
-    (void)sbuf;
     int lev = levels - 1;
+    if (tail && tail_applies(n, lev_end, levels)) {
+        tail_map<T, true>(lbuf, lsd, tail);
+        lev = levels - 4;
+    }
     if (lev >= lev_end && (n >> lev) <= WARP_SIDE) {
         if (threadIdx.x < 32)
             for (int k = lev; k >= lev_end && (n >> k) <= WARP_SIDE; --k) {
@@ -381,7 +421,8 @@ struct ClArgs {
 };
 
 struct ClLayout {       // shared-memory offsets set by the host, in T units
-    int ybuf, cbuf, lbuf, stage, stage2, tbuf, sbuf;
+    int ybuf, cbuf, lbuf, stage, stage2, tbuf;
+    int tail;           // the tail operator (TAIL_N), staged by the leader; 0 = none
     int total;
     int umax;           // one staging buffer of the P^T pipeline
     int ystg;           // staged pair terms of the band (forward kernel), 0 = not staged
@@ -417,6 +458,10 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     // the exchanges below push into peers' shared memory before the first full cluster
     // barrier: arrive now, wait before the first push, so that every CTA has started
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+    // the tail operator of the leader's coarse levels (constant data: staged at once; every
+    // band path below waits for its copies before the first cluster barrier)
+    const bool tail_on = coarse && r == 0 && lay.tail > 0 && d.tailop != nullptr;
+    if (tail_on) stage16(sm + lay.tail, d.tailop, TAIL_N, threadIdx.x, NT);
     // ---- 0. prefetch the epilogue operands of the column band (independent of u) ----
     constexpr int PF = MAXN * (MAXN / CL) / NT;     // column-band positions per thread
     const int row_start = (coarse && r0 < h) ? h : 0;
@@ -557,6 +602,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                     if (in[g]) acc += v[g];
                 ybuf[ii * ys + j] = acc;
             }
+            cp_async_wait();
             __syncthreads();
         }
         // ---- 2. level-0 analysis along the rows of the band --------------------
@@ -625,7 +671,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         // ---- 6. the leader's coarse levels; the LL quadrant's rows go back to their
         // owners (pushed), whose epilogue takes its share of them ----------------------------
         if (r == 0) {
-            coarse_forward<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+            coarse_forward<T>(lbuf, tail_on ? sm + lay.tail : nullptr, n, 1, L.levels, lsd);
             // The data term has no piston component: Gamma annihilates constants and bilinear
             // weights sum to one, so its full-depth LL coefficient is exactly 0.  Write that
             // zero rather than the rounding residue of a cancelling sum, which the solve would
@@ -741,6 +787,9 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     T* sz = sp + MAXN * (MAXN / CL);            // column band: z (PUPD)
     T* lp = sm + lay.stage2;                    // LL rows, stride h: p (or c)
     T* lz = lp + (MAXN / 2) * (MAXN / 2);       // LL rows: z (PUPD)
+    // the tail operator of the leader's coarse levels, with the staging copies below
+    const bool tail_on = coarse && r == 0 && lay.tail > 0 && d.tailop != nullptr;
+    if (tail_on) stage16(sm + lay.tail, d.tailop, TAIL_N, threadIdx.x, NT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
     if (has_band) {
         if ((rb & (V - 1)) == 0) {
@@ -876,7 +925,7 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
         else
             __syncthreads();
         if (r == 0) {
-            coarse_inverse<T>(lbuf, sm + lay.sbuf, n, 1, L.levels, lsd);
+            coarse_inverse<T>(lbuf, tail_on ? sm + lay.tail : nullptr, n, 1, L.levels, lsd);
             for (int k = threadIdx.x; k < h * h; k += NT) {
                 const int i = k >> lh, j = k & (h - 1);
                 cluster.map_shared_rank(cbuf, static_cast<unsigned>(j >> lrb))[i * cs + (j & (rb - 1))] =

@@ -91,6 +91,7 @@ struct alignas(16) Desc {   // 16-byte multiple: batched kernels copy it in 16-b
     const T* Jinv;
     // D per (layer, level): detail level k = 1 .. levels (1 the finest), levels + 1 the LL band
     T Dlev[MAXL][9];
+    const T* tailop;   // analysis of the 8 x 8 tail levels (64 x TAIL_LD), or null
     // footprint box of each (sensor, layer) pair: row0, rows, col0, cols (16-byte aligned
     // column superset); kept in the descriptor so that warps read it from the constant bank
     int box[MAXG][MAXL][4];
