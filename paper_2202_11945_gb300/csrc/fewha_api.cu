@@ -1262,10 +1262,19 @@ int cluster_layouts(fewha_handle* H) {
     const long long spare = 227LL * 1024 - static_cast<long long>(H->smem_fwd) -
                             static_cast<long long>(sizeof(Desc<T>)) - 2048;
     std::vector<int> ytab;
-    if (aligned && ystg > 0 && static_cast<long long>(round4(ystg)) * static_cast<long long>(sizeof(T)) <= spare) {
-        H->lay_fwd.ystg = H->lay_fwd.total;
-        H->lay_fwd.total += round4(ystg);
-        H->smem_fwd += static_cast<size_t>(round4(ystg)) * sizeof(T);
+    // single precision reads the band's terms straight from L2 (one 16-byte group per thread
+    // and sensor, every read in flight at once); double precision stages them in shared
+    // memory (its threads own several groups each)
+    const bool direct = aligned && ystg > 0 && sizeof(T) == 4;
+    if (direct ||
+        (aligned && ystg > 0 && static_cast<long long>(round4(ystg)) * static_cast<long long>(sizeof(T)) <= spare)) {
+        if (direct) {
+            H->lay_fwd.ydirect = 1;
+        } else {
+            H->lay_fwd.ystg = H->lay_fwd.total;
+            H->lay_fwd.total += round4(ystg);
+            H->smem_fwd += static_cast<size_t>(round4(ystg)) * sizeof(T);
+        }
         // the run table (see PairBufs::ytab)
         const int nw = static_cast<int>(s.G.size());
         ytab.assign(s.L.size() * CL * nw * 8, 0);

@@ -426,6 +426,7 @@ struct ClLayout {       // shared-memory offsets set by the host, in T units
     int total;
     int umax;           // one staging buffer of the P^T pipeline
     int ystg;           // staged pair terms of the band (forward kernel), 0 = not staged
+    int ydirect;        // the band's pair terms read straight from L2 in 16-byte groups
 };
 
 constexpr int KMAX = 8;      // aperture rows / columns touching one layer row / column
@@ -473,7 +474,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     if (threadIdx.x <= MAXLEV) sD[threadIdx.x] = d.Dlev[l][threadIdx.x];
     // the band-run table of the staged sum, loaded now so that its latency overlaps
     int4 ytv = make_int4(0, 0, 0, 0);
-    if (SRC == LSRC_NODES && lay.ystg > 0 && has_band && threadIdx.x < 2 * d.n_wfs)
+    if (SRC == LSRC_NODES && (lay.ystg > 0 || lay.ydirect) && has_band && threadIdx.x < 2 * d.n_wfs)
         ytv = pb.ytab[(l * CL + r) * 2 * d.n_wfs + threadIdx.x];
     // this CTA's share of the LL quadrant's rows (coarse layers): [lr0, lr1), hb rows each.
     // A quadrant narrower than 32 stays with the leader: sharing it out costs a cluster
@@ -524,6 +525,53 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             for (int k = threadIdx.x; k < rb * n; k += NT) {
                 const int i = (k >> L.log2n), j = k - i * n;
                 cp_async(ybuf + i * ys + j, a.in + off + (r0 + i) * n + j);
+            }
+            cp_async_wait();
+            __syncthreads();
+        } else if (lay.ydirect) {
+            // y = sum_g R_y,gl^T u_g R_x,gl over this band, read straight from the pair slots:
+            // the boxes' columns are 16-byte groups of the layer grid (host-checked), so a
+            // thread owns one group and issues one 16-byte L2 read per sensor, all in flight
+            // together (single precision: one group per thread), then adds them in the fixed
+            // sensor order.  The runs of the band (host table) give each sensor's rows.
+            constexpr int V = vec16<T>();
+            using VT = typename Vec16<T>::type;
+            __shared__ int4 ygb[MAXG];        // per sensor: first and end band row, col0, cols
+            __shared__ int4 ygx[MAXG];        // per sensor: offset in the stage, offset in Y
+            if (threadIdx.x < 2 * d.n_wfs) {
+                if (threadIdx.x & 1)
+                    ygx[threadIdx.x >> 1] = ytv;
+                else
+                    ygb[threadIdx.x >> 1] = ytv;
+            }
+            __syncthreads();
+            const int lg = L.log2n - (V == 4 ? 2 : 1);        // log2 of the groups per row
+            for (int grp = threadIdx.x; grp < (rb << lg); grp += NT) {
+                const int ii = grp >> lg, j0 = (grp & ((1 << lg) - 1)) * V, i = r0 + ii;
+                VT v[MAXG];
+                bool in[MAXG];
+#pragma unroll
+                for (int g = 0; g < MAXG; ++g) {
+                    in[g] = false;
+                    if (g < d.n_wfs) {
+                        const int4 bx = ygb[g];
+                        in[g] = i >= bx.x && i < bx.y && j0 >= bx.z && j0 < bx.z + bx.w;
+                        if (in[g])
+                            v[g] = __ldcg(reinterpret_cast<const VT*>(pb.Y + ygx[g].y + (i - bx.x) * bx.w +
+                                                                      (j0 - bx.z)));
+                    }
+                }
+                T acc[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = T(0);
+#pragma unroll
+                for (int g = 0; g < MAXG; ++g)
+                    if (in[g]) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) acc[e] += Vec16<T>::at(v[g], e);
+                    }
+#pragma unroll
+                for (int e = 0; e < V; ++e) ybuf[ii * ys + j0 + e] = acc[e];
             }
             cp_async_wait();
             __syncthreads();
