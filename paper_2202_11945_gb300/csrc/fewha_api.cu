@@ -1307,6 +1307,22 @@ int cluster_layouts(fewha_handle* H) {
             H->smem_fwd += static_cast<size_t>(round4(TAIL_N)) * sizeof(T);
         }
     }
+    // single precision: the leader of a layer's cluster stages the LL quadrant's epilogue
+    // operands (p, b, J^-1) and forms the LL epilogue itself (ClLayout::lstage); it needs
+    // 16-byte aligned quadrant rows in every coarse layer
+    if (sizeof(T) == 4) {
+        bool ok = true;
+        for (const auto& L : s.L)
+            if (L.levels >= 2) ok = ok && (L.n / 2) % V == 0 && L.n % V == 0 && L.off % V == 0;
+        const int need = round4(3 * (MAXN / 2) * (MAXN / 2));
+        const long long room = 227LL * 1024 - static_cast<long long>(H->smem_fwd) -
+                               static_cast<long long>(sizeof(Desc<T>)) - 2048;
+        if (ok && static_cast<long long>(need) * static_cast<long long>(sizeof(T)) <= room) {
+            H->lay_fwd.lstage = H->lay_fwd.total;
+            H->lay_fwd.total += need;
+            H->smem_fwd += static_cast<size_t>(need) * sizeof(T);
+        }
+    }
     H->smem_proj = proj * sizeof(T);
     H->smem_projT = projT * sizeof(T);
     H->pvs = round4(s.max_N + 1);

@@ -427,6 +427,8 @@ struct ClLayout {       // shared-memory offsets set by the host, in T units
     int umax;           // one staging buffer of the P^T pipeline
     int ystg;           // staged pair terms of the band (forward kernel), 0 = not staged
     int ydirect;        // the band's pair terms read straight from L2 in 16-byte groups
+    int lstage;         // the LL quadrant's epilogue operands, staged by the leader (3 x
+                        // (MAXN / 2)^2); 0 = the LL epilogue is shared out over the cluster
 };
 
 constexpr int KMAX = 8;      // aperture rows / columns touching one layer row / column
@@ -481,10 +483,29 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     // barrier, more than the leader's few positions take.
     constexpr bool QAPPLY = DST == LDST_APPLY || DST == LDST_APPLY_INIT;
     constexpr int PL = ((MAXN / 2) * (MAXN / 2) / CL + NT - 1) / NT;   // LL-share positions per thread
-    const bool ldist = h >= 32;
+    // With lay.lstage (single precision), the leader stages the LL quadrant's operands in
+    // shared memory now and forms the whole LL epilogue itself after its coarse levels: no
+    // rows go back to the other ranks and no third cluster barrier is needed.
+    const bool lstaged = lay.lstage > 0 && coarse;
+    const bool ldist = !lstaged && h >= 32;
     const int hb = ldist ? h >> 3 : h;
     const int lr0 = coarse ? min(r * hb, h) : 0, lr1 = coarse ? min(lr0 + hb, h) : 0;
-    const int lcnt = (lr1 - lr0) * h;
+    const int lcnt = lstaged ? 0 : (lr1 - lr0) * h;     // LL positions prefetched to registers
+    T* lsp = sm + lay.lstage;                           // staged p, b, J^-1 of LL (stride h)
+    T* lsb = lsp + (MAXN / 2) * (MAXN / 2);
+    T* lsj = lsb + (MAXN / 2) * (MAXN / 2);
+    if (lstaged && r == 0 && QAPPLY) {
+        constexpr int V = vec16<T>();
+        const int lc = lh - (V == 4 ? 2 : 1);           // log2 of the 16-byte chunks per row
+        for (int k = threadIdx.x; k < (h << lc); k += NT) {
+            const int i = k >> lc, c = (k & ((1 << lc) - 1)) * V, pos = off + i * n + c;
+            cp_async16(lsp + i * h + c, a.pin + pos);
+            if (DST == LDST_APPLY_INIT) {
+                cp_async16(lsb + i * h + c, a.vb + pos);
+                cp_async16(lsj + i * h + c, a.vj + pos);
+            }
+        }
+    }
     // operands of the epilogue at this CTA's positions (band, then LL share), loaded now so
     // that their latency overlaps: p; with the fused initial residual also b and J^-1
     T pl[PL], xb[PF], xl[PL], jb[PF], jl[PL];
@@ -734,12 +755,21 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 }
         }
         if (ldist) cluster.sync();                                        // #3: no remote access after this
+        if (lstaged) {
+            if (r == 0)
+                for (int k = threadIdx.x; k < h * h; k += NT) {
+                    const int i = k >> lh, j = k & (h - 1);
+                    epi(i, j, off + i * n + j, lbuf[i * lsd + j], QAPPLY ? lsp[k] : T(0),
+                        DST == LDST_APPLY_INIT ? lsb[k] : T(0), DST == LDST_APPLY_INIT ? lsj[k] : T(0));
+                }
+        } else {
 #pragma unroll
-        for (int s2 = 0; s2 < PL; ++s2) {
-            const int k = threadIdx.x + s2 * NT;
-            if (k < lcnt) {
-                const int i = lr0 + (k >> lh), j = k & (h - 1);
-                epi(i, j, off + i * n + j, ldist ? ybuf[k] : lbuf[i * lsd + j], pl[s2], xl[s2], jl[s2]);
+            for (int s2 = 0; s2 < PL; ++s2) {
+                const int k = threadIdx.x + s2 * NT;
+                if (k < lcnt) {
+                    const int i = lr0 + (k >> lh), j = k & (h - 1);
+                    epi(i, j, off + i * n + j, ldist ? ybuf[k] : lbuf[i * lsd + j], pl[s2], xl[s2], jl[s2]);
+                }
             }
         }
     }
