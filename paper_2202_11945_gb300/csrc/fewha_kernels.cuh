@@ -868,11 +868,16 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     __shared__ T salpha;
     T ta = T(0);
     bool have_alpha = PHASE != V_UPDATE;
-    if (!have_alpha && threadIdx.x < 32) {
+    // The CG update waits for its predecessor (the apply's forward kernel) only after it has
+    // issued the loads of c, p, r and J^-1, which that kernel does not write (k_vec launches
+    // it without a wait of its own); the other phases were waited for by their caller.
+    bool waited = PHASE != V_UPDATE;
+    auto form_alpha = [&]() {
+        if (threadIdx.x >= 32) return;
         // alpha = rz_k / (p . q)_k; zero if rz vanished (the iterate is final).  Formed
         // once and broadcast (an FP64 division is ~10 instructions on GB300's slow FP64
-        // pipe), while the first batch of vector loads is in flight; a deferred p.q total
-        // first (warp 0, fixed order: the same value in every CTA)
+        // pipe), while the batch's vector loads are in flight; a deferred p.q total first
+        // (warp 0, fixed order: the same value in every CTA)
         double pq = 0.0;
         if (v.pq_cnt > 0) {
             pq = warp_total(v.pcg.pqpart + static_cast<long long>(iter) * PQ_SLOTS, v.pq_cnt,
@@ -884,7 +889,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
             const double rz = v.pcg.rztot[iter];
             salpha = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
         }
-    }
+    };
     DotAcc<T> dot;
     for (int base = cta * NTV * PVEC; base < n; base += nparts * NTV * PVEC) {
         // issue every load of the batch before the arithmetic
@@ -905,8 +910,20 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
                     c[k] = v.c[i];
                     p[k] = v.p[i];
                     r[k] = v.r[i];
-                    q[k] = v.q[i];
                 }
+            }
+        }
+        if (!waited) {                   // uniform over the CTA
+            pdl_wait();
+            pdl_trigger();
+            waited = true;
+            form_alpha();
+        }
+        if (PHASE == V_UPDATE) {
+#pragma unroll
+            for (int k = 0; k < PVEC; ++k) {
+                const int i = base + k * NTV + threadIdx.x;
+                if (i < n) q[k] = v.q[i];
             }
         }
         if (!have_alpha) {               // uniform over the CTA (base does not depend on the thread)
@@ -937,6 +954,10 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
             }
         }
     }
+    if (!waited) {                       // a CTA without a batch
+        pdl_wait();
+        pdl_trigger();
+    }
     // CTA share of r.z (fixed order), then the last CTA forms the total in a fixed order
     __shared__ double part[NTV];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -954,7 +975,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
 
 template <class T, int PHASE>
 __global__ void __launch_bounds__(PBLK) k_vec(const int n, __grid_constant__ const VecArgs<T> v) {
-    pdl_enter();
+    if (PHASE != V_UPDATE) pdl_enter();          // V_UPDATE waits inside, after its first loads
     vec_body<T, PHASE>(n, v, blockIdx.x, gridDim.x);
 }
 
