@@ -869,41 +869,40 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
     const bool tail_on = coarse && r == 0 && lay.tail > 0 && d.tailop != nullptr;
     if (tail_on) stage16(sm + lay.tail, d.tailop, TAIL_N, threadIdx.x, NT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = NT >> 5;
-    if (has_band) {
-        if ((rb & (V - 1)) == 0) {
-            const int cpr = rb / V;             // chunks per row (a power of two)
-            const int lcpr = __ffs(cpr) - 1;
-            for (int k = threadIdx.x; k < nrow * cpr; k += NT) {
-                const int i = k >> lcpr, c = k & (cpr - 1);
-                const int pos = off + (row_start + i) * n + r0 + c * V;
-                if (stage_src) cp_async16(sp + i * rb + c * V, src + pos);
-                if (PUPD) cp_async16(sz + i * rb + c * V, a.zupd + pos);
-            }
-        } else {
-            for (int k = threadIdx.x; k < nrow * rb; k += NT) {
-                const int i = k >> lrb, jj = k & (rb - 1);
-                const int pos = off + (row_start + i) * n + r0 + jj;
-                if (stage_src) cp_async(sp + k, src + pos);
-                if (PUPD) cp_async(sz + k, a.zupd + pos);
-            }
-        }
-    }
-    for (int i = lr0 + warp; i < lr1; i += nwarp) {
-        const int pos = off + i * n;
-        T* dp = lp + (i - lr0) * h;
-        T* dz = lz + (i - lr0) * h;
-        if ((h & (V - 1)) == 0) {
-            for (int c = lane; c < h / V; c += 32) {
-                if (stage_src) cp_async16(dp + c * V, src + pos + c * V);
-                if (PUPD) cp_async16(dz + c * V, a.zupd + pos + c * V);
-            }
-        } else {
-            for (int j = lane; j < h; j += 32) {
-                if (stage_src) cp_async(dp + j, src + pos + j);
-                if (PUPD) cp_async(dz + j, a.zupd + pos + j);
+    // The copies of one vector (x = p or c, or z): the column band, then the LL rows.
+    auto stage_vec = [&](const T* x, T* dst_band, T* dst_ll) {
+        if (has_band) {
+            if ((rb & (V - 1)) == 0) {
+                const int cpr = rb / V;             // chunks per row (a power of two)
+                const int lcpr = __ffs(cpr) - 1;
+                for (int k = threadIdx.x; k < nrow * cpr; k += NT) {
+                    const int i = k >> lcpr, c = k & (cpr - 1);
+                    cp_async16(dst_band + i * rb + c * V, x + off + (row_start + i) * n + r0 + c * V);
+                }
+            } else {
+                for (int k = threadIdx.x; k < nrow * rb; k += NT) {
+                    const int i = k >> lrb, jj = k & (rb - 1);
+                    cp_async(dst_band + k, x + off + (row_start + i) * n + r0 + jj);
+                }
             }
         }
-    }
+        for (int i = lr0 + warp; i < lr1; i += nwarp) {
+            const T* xs = x + off + i * n;
+            T* dl = dst_ll + (i - lr0) * h;
+            if ((h & (V - 1)) == 0) {
+                for (int c = lane; c < h / V; c += 32) cp_async16(dl + c * V, xs + c * V);
+            } else {
+                for (int j = lane; j < h; j += 32) cp_async(dl + j, xs + j);
+            }
+        }
+    };
+    // The direction being advanced (PUPD > 0: p_old, last written by the inverse kernel of
+    // the previous iteration) is staged before the dependency wait; z, the plain input (its
+    // writer may be the previous kernel) and the scalars after it.
+    if (PUPD && stage_src) stage_vec(src, sp, lp);
+    pdl_wait();
+    if (!PUPD && stage_src) stage_vec(src, sp, lp);
+    if (PUPD) stage_vec(a.zupd, sz, lz);
     // beta and mu are formed while the copies are in flight; a deferred r.z total first
     // (warp 0, fixed order: the same value in every CTA)
     if (threadIdx.x < 32 && (PUPD || a.rz_cnt > 0)) {
@@ -1037,7 +1036,6 @@ template <class T, int PUPD>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_inv(__grid_constant__ const Desc<T> d, __grid_constant__ const ClArgs<T> a,
              __grid_constant__ const ClLayout lay) {
-    pdl_wait();
     cl_inv_body<T, PUPD>(d, a, lay, blockIdx.y);
 }
 
@@ -1088,6 +1086,9 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     // the band's rows of the active-subaperture table, copied while the terms are summed
     int* msk = reinterpret_cast<int*>(sm + lay.msk);
     for (int k = threadIdx.x; k < rows * N; k += NT) cp_async(msk + k, sidx + s0 * N + k);
+    // the mask and the descriptor are set-up data, read before the dependency wait; the
+    // projected layers or the slopes after it
+    pdl_wait();
     if (SRC == SSRC_PHI && rows > 0) {
         // ---- V = P_g phi = sum_l (pair term of layer l) on node rows [s0, s1] ---------
         // a warp per node row; every lane's columns accumulate in the fixed layer order,
@@ -1353,7 +1354,6 @@ template <class T, int SRC>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(cblk<T>(), 1)
     k_cl_sensor(__grid_constant__ const Desc<T> d, __grid_constant__ const SensorArgs<T> a,
                 __grid_constant__ const SensorLayout lay, __grid_constant__ const PairBufs<T> pb) {
-    pdl_wait();
     cl_sensor_body<T, SRC>(d, a, lay, pb, blockIdx.y);
 }
 

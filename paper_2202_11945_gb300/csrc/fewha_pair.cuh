@@ -35,6 +35,9 @@ __device__ __forceinline__ void proj_body(const Desc<T>& d, const T* __restrict_
         cp_async(tj0 + k, d.pi0x + tp + k);
         cp_async(ti0 + k, d.pi0y + tp + k);
     }
+    // the tables are set-up data, copied before the dependency wait; phi after it
+    pdl_wait();
+    pdl_trigger();
     const T* src = phi + d.L[l].off + r0 * n + c0;
     if ((n & (V - 1)) == 0) {
         const int cpr = cols / V;
@@ -71,7 +74,6 @@ template <class T>
 __global__ void __launch_bounds__(cblk<T>(), 1) k_proj(__grid_constant__ const Desc<T> d,
                                                        const T* __restrict__ phi,
                                                        __grid_constant__ const PairBufs<T> pb) {
-    pdl_enter();
     proj_body<T>(d, phi, pb, blockIdx.x, blockIdx.y);
 }
 
@@ -97,14 +99,17 @@ __device__ __forceinline__ void projT_body(const Desc<T>& d, const T* __restrict
     int2* cinf = reinterpret_cast<int2*>(rw + rows * KMAX);   // first aperture column, count
     int2* rinf = cinf + ((cols + 1) & ~1);        // 16-byte aligned
     constexpr int I2 = sizeof(int2) / sizeof(T);  // T elements per int2
-    // u_g and the pair's weight tables, 16-byte copies all in flight together
-    stage16(U, u + s0a, ushift + NP * NP, threadIdx.x, NT);
+    // the pair's weight tables and u_g, 16-byte copies all in flight together; the tables
+    // (set-up data) before the dependency wait, u_g after it
     stage16(cw, pb.tw + static_cast<size_t>(pr * 2) * MAXN * KMAX, cols * KMAX, threadIdx.x, NT);
     stage16(rw, pb.tw + static_cast<size_t>(pr * 2 + 1) * MAXN * KMAX, rows * KMAX, threadIdx.x, NT);
     stage16(reinterpret_cast<T*>(cinf), reinterpret_cast<const T*>(pb.ti + static_cast<size_t>(pr * 2) * MAXN),
             cols * I2, threadIdx.x, NT);
     stage16(reinterpret_cast<T*>(rinf), reinterpret_cast<const T*>(pb.ti + static_cast<size_t>(pr * 2 + 1) * MAXN),
             rows * I2, threadIdx.x, NT);
+    pdl_wait();
+    pdl_trigger();
+    stage16(U, u + s0a, ushift + NP * NP, threadIdx.x, NT);
     cp_async_wait();
     __syncthreads();
     const T* Us = U + ushift;
@@ -152,7 +157,6 @@ template <class T, int KM>
 __global__ void __launch_bounds__(cblk<T>(), 1) k_projT(__grid_constant__ const Desc<T> d,
                                                         const T* __restrict__ u,
                                                         __grid_constant__ const PairBufs<T> pb) {
-    pdl_enter();
     projT_body<T, KM>(d, u, pb, blockIdx.x, blockIdx.y);
 }
 
