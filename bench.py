@@ -482,7 +482,8 @@ def time_augmented(wl, S32, S_np, flush, steps, parity=True):
             rel = []
             for k in range(S32.shape[0]):
                 R.reconstruct(S32[k])
-                r, b = R.residual()
+                r, _ = R.residual(with_b=False)
+                b = R.rhs(S32[k])            # the plain frame does not form b
                 rel.append(float(torch.linalg.norm(r.double()) / torch.linalg.norm(b.double())))
             dm = torch.empty(R.n_act, dtype=torch.float32, device="cuda")
             t = time_frames(R, S32, steps, 20, flush, dm)

@@ -219,9 +219,10 @@ int fewha_update_params(fewha_handle* h, const fewha_params* params, const doubl
 /* Zero the warm-start state (c, a_prev, residual history). Stream-ordered. */
 int fewha_reset(fewha_handle* h, void* stream);
 
-/* One frame of Algorithm 1 (open loop): b from d_slopes, r0 = b - M c0 (or the warm
- * residual form with FEWHA_FLAG_WARM_RESIDUAL), `iters` PCG iterations, DM fit and
- * gain.  d_x_warm (n_coeffs) is the warm start, read and overwritten with the new c;
+/* One frame of Algorithm 1 (open loop): r0 = b - M c0 from d_slopes (formed as
+ * W P^T Gamma^T C^-1 (s - Gamma P W^-1 c0) - alpha D c0, without b; the warm residual
+ * form with FEWHA_FLAG_WARM_RESIDUAL and the augmented start form b first), `iters` PCG
+ * iterations, DM fit and gain.  d_x_warm (n_coeffs) is the warm start, read and overwritten with the new c;
  * NULL uses the handle's internal state.  d_dm_out (n_act) receives the commands
  * a = (1 - gain) a_prev + gain a~.  Asynchronous on `stream`. */
 int fewha_reconstruct(fewha_handle* h, const float* d_slopes, float* d_x_warm, float* d_dm_out,
@@ -247,7 +248,11 @@ int fewha_set_state(fewha_handle* h, const void* d_c, const void* d_a_prev, void
 /* The residual r and right-hand side b of the last frame's PCG (the recurrence residual;
  * Sec. 3.3), n_coeffs each, copied into device buffers of the handle's element type
  * (either pointer may be NULL).  Inspection only: ||r|| / ||b|| measures how far the
- * fixed iteration count left the frame from M c = b.  Stream-ordered. */
+ * fixed iteration count left the frame from M c = b.  b exists only for the frame forms
+ * that keep it (FEWHA_FLAG_WARM_RESIDUAL, _AUGMENTED, _PERSISTENT): the plain explicit
+ * frame forms r0 = b - M c0 from the slopes' residual in one chain and never forms b, and
+ * a request for it returns FEWHA_ERR_INVALID_ARG (fewha_rhs computes b from the slopes).
+ * Stream-ordered. */
 int fewha_get_residual(fewha_handle* h, void* d_r, void* d_b, void* stream);
 
 /* Reverse mode through the fixed-iteration frame (a build addition; the paper has no

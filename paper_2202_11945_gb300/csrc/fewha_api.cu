@@ -439,9 +439,9 @@ int launch_projT(fewha_handle* H, const Desc<T>& d, const T* u, cudaStream_t st)
 template <class T, int SRC, int DST>
 int launch_fwd(fewha_handle* H, const Desc<T>& d, const ClArgs<T>& a, cudaStream_t st) {
     if (recorder<T>()) {
-        if (SRC != LSRC_NODES || (DST != LDST_APPLY && DST != LDST_COEF))
+        if (SRC != LSRC_NODES || (DST != LDST_APPLY && DST != LDST_COEF && DST != LDST_RESID_INIT))
             return fail(H, FEWHA_ERR_INVALID_ARG, "step without a batched form");
-        record<T>(DST == LDST_APPLY ? BK_FWD_APPLY : BK_FWD_COEF).cl = a;
+        record<T>(DST == LDST_APPLY ? BK_FWD_APPLY : DST == LDST_RESID_INIT ? BK_FWD_RINIT : BK_FWD_COEF).cl = a;
         return FEWHA_OK;
     }
     CK(launch_k(H, k_cl_fwd<T, SRC, DST>, dim3(CL, d.n_layers), dim3(cblk<T>()), H->smem_fwd, st, d, a,
@@ -466,7 +466,7 @@ template <class T, int SRC>
 int launch_csensor(fewha_handle* H, const Desc<T>& d, const T* in, T* out, cudaStream_t st) {
     SensorArgs<T> a{in, out, H->status};
     if (recorder<T>()) {
-        record<T>(SRC == SSRC_PHI ? BK_SEN_PHI : BK_SEN_SLOPES).sa = a;
+        record<T>(SRC == SSRC_PHI ? BK_SEN_PHI : SRC == SSRC_RESID ? BK_SEN_RESID : BK_SEN_SLOPES).sa = a;
         return FEWHA_OK;
     }
     CK(launch_k(H, k_cl_sensor<T, SRC>, dim3(CL, d.n_wfs), dim3(cblk<T>()), H->smem_sen, st, d, a,
@@ -590,6 +590,37 @@ int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st,
     return launch_fwd<T, LSRC_NODES, LDST_APPLY_INIT>(H, d, b, st);
 }
 
+// r0 = b - M c0 formed in one chain, from the slopes' residual: the sensor kernel takes
+// C^-1 (s - Gamma P phi0) (phi0 = W^-1 c0, its piston left out), the adjoint projection and
+// the forward kernel give r0 = W P^T Gamma^T C^-1 (s - Gamma P phi0) - alpha D c0 and the
+// initial residual's vector step (z0, p0, r.z in slot 0, only shares with `defer`).  By
+// linearity this is b - M c0 of Algorithm 1 without forming b: 5 kernels instead of the
+// right-hand side's 3 plus the apply's 5.  b and b_prev are not written.
+template <class T>
+int enqueue_resid_init(fewha_handle* H, const Desc<T>& d, const T* s, T* c, cudaStream_t st, bool defer) {
+    T* phi = static_cast<T*>(H->phi);
+    T* u = static_cast<T*>(H->u);
+    int rc;
+    ClArgs<T> a = cl_args<T>(H, c, phi);
+    a.zero_piston = 1;
+    if ((rc = launch_inv<T, 0>(H, d, a, st))) return rc;
+    if ((rc = launch_proj<T>(H, d, phi, st))) return rc;
+    if ((rc = launch_csensor<T, SSRC_RESID>(H, d, s, u, st))) return rc;
+    if ((rc = launch_projT<T>(H, d, u, st))) return rc;
+    ClArgs<T> b = cl_args<T>(H, u, static_cast<T*>(H->q));
+    b.pin = c;
+    b.iter = PQ_SCRATCH_SLOT;
+    b.zero_piston = 1;
+    b.vr = static_cast<T*>(H->r);
+    b.vz = static_cast<T*>(H->z);
+    b.vp = static_cast<T*>(H->p);
+    b.vj = static_cast<const T*>(H->Jinv);
+    b.rzslot = 0;
+    b.rzp = H->rzpart;
+    b.defer_total = defer ? 1 : 0;
+    return launch_fwd<T, LSRC_NODES, LDST_RESID_INIT>(H, d, b, st);
+}
+
 template <class T>
 int enqueue_rhs(fewha_handle* H, const Desc<T>& d, const T* s, T* bout, cudaStream_t st) {
     T* u = static_cast<T*>(H->u);
@@ -643,8 +674,11 @@ int launch_pol(fewha_handle* H, const Desc<T>& d, const T* s, T* out, cudaStream
 }
 
 // `iters` PCG iterations on M c = b (b in H->b), r0 explicit or warm.
+// With s_resid (the explicit residual, single instances), r0 comes from the slopes'
+// residual chain (enqueue_resid_init) and b is not formed.
 template <class T>
-int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, cudaStream_t st) {
+int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, cudaStream_t st,
+                const T* s_resid = nullptr) {
     int rc;
     // the initial residual's vector step fused into the forward kernel (single instances; the
     // batched frame keeps the separate vector kernel).  The iterations' CG updates stay in
@@ -660,6 +694,8 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
         const bool defer = iters > 0;
         if (warm) {
             if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
+        } else if (s_resid) {
+            if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, defer))) return rc;
         } else {
             if ((rc = enqueue_apply_init<T>(H, d, c, st, defer))) return rc;
         }
@@ -686,6 +722,8 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
     }
     if (warm) {
         if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
+    } else if (s_resid) {
+        if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, false))) return rc;
     } else {
         if ((rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
         if ((rc = launch_vec<T, V_INIT>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
@@ -861,11 +899,15 @@ int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStrea
         if ((rc = launch_pol<T>(H, d, s, sp, st))) return rc;
         s = sp;
     }
-    if ((rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
+    // the plain explicit-residual frame (single or batched) forms r0 from the slopes'
+    // residual (no b); frames that keep b (the warm recurrence's b_prev, the augmented
+    // start) form b first
+    const bool resid = !warm && !(H->params.flags & (FEWHA_FLAG_WARM_RESIDUAL | FEWHA_FLAG_AUGMENTED));
+    if (!resid && (rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
     if (H->params.flags & FEWHA_FLAG_AUGMENTED)
         rc = enqueue_pcg_aug<T>(H, d, c, H->params.iters, warm, H->aug_set, H->aug_m, st);
     else
-        rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st);
+        rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st, resid ? s : nullptr);
     if (rc) return rc;
     return enqueue_fit<T>(H, d, c, dm, true, st);
 }
@@ -1028,11 +1070,13 @@ int set_smem_limits(fewha_handle* H) {
     if ((rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_APPLY>, H->smem_fwd)) ||
         (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_COEF>, H->smem_fwd)) ||
         (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_APPLY_INIT>, H->smem_fwd)) ||
+        (rc = allow_smem(H, k_cl_fwd<T, LSRC_NODES, LDST_RESID_INIT>, H->smem_fwd)) ||
         (rc = allow_smem(H, k_cl_inv<T, 0>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_inv<T, 1>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_inv<T, 2>, H->smem_inv)) ||
         (rc = allow_smem(H, k_cl_sensor<T, SSRC_PHI>, H->smem_sen)) ||
         (rc = allow_smem(H, k_cl_sensor<T, SSRC_SLOPES>, H->smem_sen)) ||
+        (rc = allow_smem(H, k_cl_sensor<T, SSRC_RESID>, H->smem_sen)) ||
         (rc = allow_smem(H, k_proj<T>, H->smem_proj)) || (rc = allow_smem(H, k_projT<T, 4>, H->smem_projT)) ||
         (rc = allow_smem(H, k_projT<T, KMAX>, H->smem_projT)))
         return rc;
@@ -2036,8 +2080,9 @@ size_t round16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 template <class T>
 size_t barg_size(int kind) {
     switch (kind) {
-        case BK_INV: case BK_INV_UPD: case BK_FWD_APPLY: case BK_FWD_COEF: return sizeof(ClArgs<T>);
-        case BK_SEN_PHI: case BK_SEN_SLOPES: return sizeof(SensorArgs<T>);
+        case BK_INV: case BK_INV_UPD: case BK_FWD_APPLY: case BK_FWD_COEF: case BK_FWD_RINIT:
+            return sizeof(ClArgs<T>);
+        case BK_SEN_PHI: case BK_SEN_SLOPES: case BK_SEN_RESID: return sizeof(SensorArgs<T>);
         case BK_PROJ: case BK_PROJT: return sizeof(const T*);
         case BK_FIT: return sizeof(FitArgs<T>);
         default: return sizeof(VecArgs<T>);
@@ -2047,8 +2092,8 @@ size_t barg_size(int kind) {
 size_t bsmem(const fewha_handle* H, int kind) {
     switch (kind) {
         case BK_INV: case BK_INV_UPD: return H->smem_inv;
-        case BK_FWD_APPLY: case BK_FWD_COEF: return H->smem_fwd;
-        case BK_SEN_PHI: case BK_SEN_SLOPES: return H->smem_sen;
+        case BK_FWD_APPLY: case BK_FWD_COEF: case BK_FWD_RINIT: return H->smem_fwd;
+        case BK_SEN_PHI: case BK_SEN_SLOPES: case BK_SEN_RESID: return H->smem_sen;
         case BK_PROJ: return H->smem_proj;
         case BK_PROJT: return H->smem_projT;
         default: return 0;
@@ -2939,7 +2984,12 @@ int fewha_get_residual(fewha_handle* H, void* r, void* b, void* stream) {
     DeviceGuard g(H->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (r) CK(cudaMemcpyAsync(r, H->r, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
-    if (b) CK(cudaMemcpyAsync(b, H->b, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
+    if (b) {
+        // the plain explicit frame forms r0 from the slopes' residual and never forms b
+        if (!(H->params.flags & (FEWHA_FLAG_WARM_RESIDUAL | FEWHA_FLAG_AUGMENTED | FEWHA_FLAG_PERSISTENT)))
+            return fail(H, FEWHA_ERR_INVALID_ARG, "this frame form does not form b (use fewha_rhs)");
+        CK(cudaMemcpyAsync(b, H->b, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
+    }
     return FEWHA_OK;
 }
 
@@ -3038,15 +3088,15 @@ int fewha_bench_stage(fewha_handle* H, int stage, int reps, void* stream) {
 int fewha_frame_launches(const fewha_handle* H, int* launches) {
     if (!H || !launches) return FEWHA_ERR_INVALID_ARG;
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
-    // RHS 3, initial residual 5 (explicit, its vector step fused into the forward kernel) or
-    // 1 (warm), 6 per iteration, fit 2; the augmented frame runs 6 for r0 (a separate vector
-    // kernel) and one more start kernel (its direction update is fused into the inverse
-    // kernel of each apply)
+    // the plain explicit frame: r0 from the slopes' residual, 5 (the right-hand side is not
+    // formed); with the warm recurrence, RHS 3 and r0 1 (its explicit refresh frames: 3 + 5);
+    // augmented: RHS 3, r0 6 (a separate vector kernel) and one more start kernel (its
+    // direction update is fused into the inverse kernel of each apply); 6 per iteration,
+    // fit 2
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
     const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
-    // the plain PCG's initial-residual vector step is fused into its forward kernel
-    const int per_iter = 6, r0 = warm ? 1 : (aug ? 6 : 5);
-    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + 3 + r0 + aug + per_iter * H->params.iters + 2;
+    const int per_iter = 6, start = warm ? 3 + 1 : (aug ? 3 + 6 : 5);
+    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + start + aug + per_iter * H->params.iters + 2;
     return FEWHA_OK;
 }
 

@@ -128,6 +128,7 @@ const void* kernel_of(int kind, int v) {
             return half ? reinterpret_cast<const void*>(kb_proj<T, NH>) : reinterpret_cast<const void*>(kb_proj<T, NP>);
         case BK_SEN_PHI: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_PHI>);
         case BK_SEN_SLOPES: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_SLOPES>);
+        case BK_SEN_RESID: return reinterpret_cast<const void*>(kb_cl_sensor<T, SSRC_RESID>);
         case BK_PROJT:
             if (t4)
                 return half ? reinterpret_cast<const void*>(kb_projT<T, 4, NH>)
@@ -136,6 +137,7 @@ const void* kernel_of(int kind, int v) {
                         : reinterpret_cast<const void*>(kb_projT<T, KMAX, NP>);
         case BK_FWD_APPLY: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_APPLY>);
         case BK_FWD_COEF: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_COEF>);
+        case BK_FWD_RINIT: return reinterpret_cast<const void*>(kb_cl_fwd<T, LDST_RESID_INIT>);
         case BK_VEC_INIT:
             return half ? reinterpret_cast<const void*>(kb_vec<T, V_INIT, 2 * PBLK>)
                         : reinterpret_cast<const void*>(kb_vec<T, V_INIT, PBLK>);
@@ -220,8 +222,10 @@ cudaError_t batch_launch(const BLaunch& L, cudaStream_t st) {
         case BK_INV_UPD: return launch_b(L.pdl, kb_cl_inv<T, 1>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_FWD_APPLY: return launch_b(L.pdl, kb_cl_fwd<T, LDST_APPLY>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_FWD_COEF: return launch_b(L.pdl, kb_cl_fwd<T, LDST_COEF>, cg, nt, L.smem, st, I, ca, L.items);
+        case BK_FWD_RINIT: return launch_b(L.pdl, kb_cl_fwd<T, LDST_RESID_INIT>, cg, nt, L.smem, st, I, ca, L.items);
         case BK_SEN_PHI: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_PHI>, cg, nt, L.smem, st, I, sa, L.items);
         case BK_SEN_SLOPES: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_SLOPES>, cg, nt, L.smem, st, I, sa, L.items);
+        case BK_SEN_RESID: return launch_b(L.pdl, kb_cl_sensor<T, SSRC_RESID>, cg, nt, L.smem, st, I, sa, L.items);
         case BK_PROJ:
             return ph ? launch_b(L.pdl, kb_proj<T, NH>, pg, pt, L.smem, st, I, pa, L.items)
                       : launch_b(L.pdl, kb_proj<T, NP>, pg, pt, L.smem, st, I, pa, L.items);

@@ -52,6 +52,8 @@ enum BKind {
     BK_VEC_WARM,       // r0 = (b - b_prev) + r_prev        (VecArgs)
     BK_VEC_UPDATE,     // CG update                         (VecArgs)
     BK_FIT,            // DM fit and gain                   (FitArgs)
+    BK_SEN_RESID,      // C^-1, Gamma^T of s - Gamma P phi  (SensorArgs)
+    BK_FWD_RINIT,      // r0 = W sum P^T u - alpha D c0, z0, p0, r.z (ClArgs)
     BK_COUNT
 };
 
@@ -60,8 +62,8 @@ enum BList { BL_LAYER = 0, BL_SENSOR, BL_PAIR, BL_VEC, BL_FIT, BL_COUNT };
 
 inline int bkind_list(int kind) {
     switch (kind) {
-        case BK_INV: case BK_INV_UPD: case BK_FWD_APPLY: case BK_FWD_COEF: return BL_LAYER;
-        case BK_SEN_PHI: case BK_SEN_SLOPES: return BL_SENSOR;
+        case BK_INV: case BK_INV_UPD: case BK_FWD_APPLY: case BK_FWD_COEF: case BK_FWD_RINIT: return BL_LAYER;
+        case BK_SEN_PHI: case BK_SEN_SLOPES: case BK_SEN_RESID: return BL_SENSOR;
         case BK_PROJ: case BK_PROJT: return BL_PAIR;
         case BK_FIT: return BL_FIT;
         default: return BL_VEC;

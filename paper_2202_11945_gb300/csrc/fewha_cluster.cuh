@@ -481,7 +481,9 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
     // this CTA's share of the LL quadrant's rows (coarse layers): [lr0, lr1), hb rows each.
     // A quadrant narrower than 32 stays with the leader: sharing it out costs a cluster
     // barrier, more than the leader's few positions take.
-    constexpr bool QAPPLY = DST == LDST_APPLY || DST == LDST_APPLY_INIT;
+    constexpr bool INIT = DST == LDST_APPLY_INIT || DST == LDST_RESID_INIT;   // fused r0 step
+    constexpr bool NEEDB = DST == LDST_APPLY_INIT;                              // b read
+    constexpr bool QAPPLY = DST == LDST_APPLY || INIT;                         // p read
     constexpr int PL = ((MAXN / 2) * (MAXN / 2) / CL + NT - 1) / NT;   // LL-share positions per thread
     // With lay.lstage (single precision), the leader stages the LL quadrant's operands in
     // shared memory now and forms the whole LL epilogue itself after its coarse levels: no
@@ -500,10 +502,8 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
         for (int k = threadIdx.x; k < (h << lc); k += NT) {
             const int i = k >> lc, c = (k & ((1 << lc) - 1)) * V, pos = off + i * n + c;
             cp_async16(lsp + i * h + c, a.pin + pos);
-            if (DST == LDST_APPLY_INIT) {
-                cp_async16(lsb + i * h + c, a.vb + pos);
-                cp_async16(lsj + i * h + c, a.vj + pos);
-            }
+            if (NEEDB) cp_async16(lsb + i * h + c, a.vb + pos);
+            if (INIT) cp_async16(lsj + i * h + c, a.vj + pos);
         }
     }
     // operands of the epilogue at this CTA's positions (band, then LL share), loaded now so
@@ -516,10 +516,8 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             if (k < ecnt) {
                 const int pos = off + (row_start + (k >> lrb)) * n + r0 + (k & (rb - 1));
                 pre_p[s] = a.pin[pos];
-                if (DST == LDST_APPLY_INIT) {
-                    xb[s] = a.vb[pos];
-                    jb[s] = a.vj[pos];
-                }
+                if (NEEDB) xb[s] = a.vb[pos];
+                if (INIT) jb[s] = a.vj[pos];
             }
         }
 #pragma unroll
@@ -528,10 +526,8 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             if (k < lcnt) {
                 const int pos = off + (lr0 + (k >> lh)) * n + (k & (h - 1));
                 pl[s] = a.pin[pos];
-                if (DST == LDST_APPLY_INIT) {
-                    xl[s] = a.vb[pos];
-                    jl[s] = a.vj[pos];
-                }
+                if (NEEDB) xl[s] = a.vb[pos];
+                if (INIT) jl[s] = a.vj[pos];
             }
         }
     }
@@ -697,6 +693,16 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             a.out[pos] = v;
             return;
         }
+        if (DST == LDST_RESID_INIT) {
+            // v is the residual's data term: r0 = v - alpha D c0
+            const T rr = v - d.alpha * sD[level_of(i, j, L)] * p;
+            const T z = jv * rr;
+            a.vr[pos] = rr;
+            a.vz[pos] = z;
+            a.vp[pos] = z;
+            drz.add(rr, z);
+            return;
+        }
         const T q = v + d.alpha * sD[level_of(i, j, L)] * p;
         if (DST == LDST_APPLY) {
             a.out[pos] = q;
@@ -760,7 +766,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
                 for (int k = threadIdx.x; k < h * h; k += NT) {
                     const int i = k >> lh, j = k & (h - 1);
                     epi(i, j, off + i * n + j, lbuf[i * lsd + j], QAPPLY ? lsp[k] : T(0),
-                        DST == LDST_APPLY_INIT ? lsb[k] : T(0), DST == LDST_APPLY_INIT ? lsj[k] : T(0));
+                        NEEDB ? lsb[k] : T(0), INIT ? lsj[k] : T(0));
                 }
         } else {
 #pragma unroll
@@ -785,7 +791,7 @@ __device__ __forceinline__ void cl_fwd_body(const Desc<T>& d, const ClArgs<T>& a
             }
         }
     }
-    if (DST == LDST_APPLY_INIT) {
+    if (INIT) {
         // r.z of the new residual into rz slot `rzslot`, fixed order over the layer CTAs
         cta_dot_store(drz, red, a.rzp + l * CL + r);
         if (!a.defer_total && last_arrival(a.pcg.count, ctas, &last) && threadIdx.x < 32) {
@@ -1089,7 +1095,9 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
     // the mask and the descriptor are set-up data, read before the dependency wait; the
     // projected layers or the slopes after it
     pdl_wait();
-    if (SRC == SSRC_PHI && rows > 0) {
+    constexpr bool FROM_PHI = SRC == SSRC_PHI || SRC == SSRC_RESID;
+    bool bad = false;                          // a non-finite measured slope (SLOPES, RESID)
+    if (FROM_PHI && rows > 0) {
         // ---- V = P_g phi = sum_l (pair term of layer l) on node rows [s0, s1] ---------
         // a warp per node row; every lane's columns accumulate in the fixed layer order,
         // with the loads of several layers in flight
@@ -1123,18 +1131,26 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
         for (int j = lane; j < N; j += 32) {
             const int k = ii * N + j;
             T sx = T(0), sy = T(0);
-            if (msk[ii * N + j] >= 0) {
+            const int id = msk[ii * N + j];
+            if (id >= 0) {
                 const T v00 = V[ii * NP + j], v01 = V[ii * NP + j + 1];
                 const T v10 = V[(ii + 1) * NP + j], v11 = V[(ii + 1) * NP + j + 1];
                 sx = T(0.5) * ((v01 - v00) + (v11 - v10));
                 sy = T(0.5) * ((v10 - v00) + (v11 - v01));
+                if (SRC == SSRC_RESID && W.nb == 1) {
+                    // residual of an ordinary sensor: measured minus modelled slope (a coarse
+                    // sensor's measurement enters after its block sums, below)
+                    const T mx = a.in[W.soff + id], my = a.in[W.soff + W.n_active + id];
+                    bad |= !(isfinite(mx) && isfinite(my));
+                    sx = mx - sx;
+                    sy = my - sy;
+                }
             }
             SX[k] = sx;
             SY[k] = sy;
         }
     } else if (SRC == SSRC_SLOPES && rows > 0) {
         const T* s = a.in + W.soff;
-        bool bad = false;
         cp_async_wait();
         __syncthreads();
         for (int k = threadIdx.x; k < rows * N; k += NT) {
@@ -1152,14 +1168,14 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
             SX[k] = sx;
             SY[k] = sy;
         }
-        if (bad && a.status) atomicOr(a.status, 1u);
     }
+    if (bad && a.status) atomicOr(a.status, 1u);
     cp_async_wait();
     __syncthreads();
 
     // ---- cluster reductions (fixed order): LGS tip/tilt sums, coarse block sums -------
     const bool need_tt = W.lgs;
-    const bool need_coarse = (SRC == SSRC_PHI) && W.nb > 1;
+    const bool need_coarse = FROM_PHI && W.nb > 1;
     asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
     if (need_tt) {
         T tx = T(0), ty = T(0), ex = T(0), ey = T(0);
@@ -1279,9 +1295,22 @@ __device__ __forceinline__ void cl_sensor_body(const Desc<T>& d, const SensorArg
                     sx += cps[q * 2 * MAXCOARSE + 2 * blk];
                     sy += cps[q * 2 * MAXCOARSE + 2 * blk + 1];
                 }
-                // coarse slope = sum / nb; Gamma_coarse^T spreads sigma^-2 slope / nb
-                cw[2 * blk] = sx * nbinv * inv * nbinv;
-                cw[2 * blk + 1] = sy * nbinv * inv * nbinv;
+                // coarse slope = sum / nb; Gamma_coarse^T spreads sigma^-2 slope / nb.  The
+                // residual form subtracts it from the block's measured slope.
+                if (SRC == SSRC_RESID) {
+                    const int K = d.cidx[W.cmask_off + blk];
+                    T mx = T(0), my = T(0);
+                    if (K >= 0) {
+                        mx = a.in[W.soff + K];
+                        my = a.in[W.soff + W.n_active + K];
+                        if (!(isfinite(mx) && isfinite(my)) && a.status) atomicOr(a.status, 1u);
+                    }
+                    cw[2 * blk] = (mx - sx * nbinv) * inv * nbinv;
+                    cw[2 * blk + 1] = (my - sy * nbinv) * inv * nbinv;
+                } else {
+                    cw[2 * blk] = sx * nbinv * inv * nbinv;
+                    cw[2 * blk + 1] = sy * nbinv * inv * nbinv;
+                }
             }
             __syncthreads();
             for (int ii = warp; ii < rows; ii += nwarp)

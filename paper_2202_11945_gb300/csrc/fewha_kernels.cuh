@@ -464,7 +464,9 @@ __device__ __forceinline__ bool last_arrival(unsigned* count, unsigned ctas, boo
 enum { LSRC_PHI = 0, LSRC_NODES = 1, LSRC_DM = 2, LSRC_COEF = 3 };
 // LDST_APPLY_INIT: the forward cluster kernel's apply with the initial residual's vector
 // step fused into its epilogue
-enum { LDST_PHI = 0, LDST_COEF = 1, LDST_APPLY = 2, LDST_APPLY_INIT = 3 };
+// LDST_RESID_INIT: the same vector step with the data term already the residual's (the
+// sensor kernel's SSRC_RESID): r0 = W y - alpha D c0, with no b
+enum { LDST_PHI = 0, LDST_COEF = 1, LDST_APPLY = 2, LDST_APPLY_INIT = 3, LDST_RESID_INIT = 4 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -596,7 +598,9 @@ __global__ void __launch_bounds__(BLK) k_layer(const Desc<T> d, const LayerArgs<
 // SRC / WEIGHT / DST.  Shared tiles: V (aperture nodes), SX, SY (per subaperture,
 // zero outside the active set).
 // ---------------------------------------------------------------------------
-enum { SSRC_PHI = 0, SSRC_NODES = 1, SSRC_SLOPES = 2 };
+// SSRC_RESID (cluster sensor kernel only): the measured slopes (in) minus the projected
+// layers' slopes, the initial residual's data term before the noise weighting
+enum { SSRC_PHI = 0, SSRC_NODES = 1, SSRC_SLOPES = 2, SSRC_RESID = 3 };
 enum { SDST_NODES = 0, SDST_SLOPES = 1, SDST_ADJ = 2 };
 
 template <class T>

@@ -304,11 +304,15 @@ class Reconstructor:
         ap = self._dev(a_prev, self.n_act, "a_prev") if a_prev is not None else None
         self._check(self.L.fewha_set_state(self.h, cp, ap, _stream(stream)))
 
-    def residual(self, stream=None):
-        """(r, b): the last frame's PCG residual and right-hand side (copies)."""
-        r, b = self._new(self.n_coeffs), self._new(self.n_coeffs)
+    def residual(self, with_b=True, stream=None):
+        """(r, b): the last frame's PCG residual and right-hand side (copies).  b exists only
+        for the warm-residual, augmented and persistent frames (the plain explicit frame
+        never forms it: use rhs(slopes)); with_b=False returns (r, None)."""
+        r = self._new(self.n_coeffs)
+        b = self._new(self.n_coeffs) if with_b else None
         self._check(self.L.fewha_get_residual(self.h, self._dev(r, self.n_coeffs, "r"),
-                                              self._dev(b, self.n_coeffs, "b"), _stream(stream)))
+                                              self._dev(b, self.n_coeffs, "b") if with_b else None,
+                                              _stream(stream)))
         return r, b
 
     def frame_vjp(self, slopes, c0, grad_dm=None, stream=None):

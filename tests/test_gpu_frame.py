@@ -156,3 +156,27 @@ def test_programmatic_dependent_launch_gives_identical_frames():
             assert np.array_equal(to_np(A.reconstruct(s)), to_np(B.reconstruct(s))), (name, t)
         A.close()
         B.close()
+
+
+def test_plain_frame_residual_without_b():
+    """The plain explicit frame forms r0 = b - M c0 from the slopes' residual and never
+    forms b: its recurrence residual matches the oracle's true residual b - M c, b comes
+    from the rhs operator, and asking the frame for b is refused."""
+    from paper_2202_11945_gb300 import FewhaError
+    name = "tiny_mcao"
+    ref = O.Reconstructor(synth.workload_by_name(name))
+    R = recon(name, 64)
+    for t in range(3):
+        s = slopes(name, t)
+        ref.frame(s)
+        R.reconstruct(to_dev(s, 64))
+    r, _ = R.residual(with_b=False)
+    s = slopes(name, 2)
+    b_ref = O.rhs(ref.geo, s)
+    r_ref = b_ref - O.apply_M(ref.geo, ref.c, ref.D)
+    assert rel_l2(to_np(r), r_ref) <= 1e-6          # recurrence vs true residual of the oracle
+    assert rel_l2(to_np(R.rhs(to_dev(s, 64))), b_ref) <= 1e-12
+    with pytest.raises(FewhaError) as e:
+        R.residual()
+    assert e.value.code == -1
+    R.close()
