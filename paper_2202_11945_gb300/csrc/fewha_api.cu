@@ -597,7 +597,8 @@ int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st,
 // linearity this is b - M c0 of Algorithm 1 without forming b: 5 kernels instead of the
 // right-hand side's 3 plus the apply's 5.  b and b_prev are not written.
 template <class T>
-int enqueue_resid_init(fewha_handle* H, const Desc<T>& d, const T* s, T* c, cudaStream_t st, bool defer) {
+int enqueue_resid_init(fewha_handle* H, const Desc<T>& d, const T* s, T* c, cudaStream_t st, bool defer,
+                       T* p0 = nullptr) {
     T* phi = static_cast<T*>(H->phi);
     T* u = static_cast<T*>(H->u);
     int rc;
@@ -613,7 +614,7 @@ int enqueue_resid_init(fewha_handle* H, const Desc<T>& d, const T* s, T* c, cuda
     b.zero_piston = 1;
     b.vr = static_cast<T*>(H->r);
     b.vz = static_cast<T*>(H->z);
-    b.vp = static_cast<T*>(H->p);
+    b.vp = p0 ? p0 : static_cast<T*>(H->p);
     b.vj = static_cast<const T*>(H->Jinv);
     b.rzslot = 0;
     b.rzp = H->rzpart;
@@ -765,7 +766,7 @@ int ensure_aug(fewha_handle* H) {
 // kernel and the apply runs on it without the fused update.
 template <class T>
 int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, int set, int m,
-                    cudaStream_t st) {
+                    cudaStream_t st, const T* s_resid = nullptr) {
     const size_t ld = H->aug_ld;
     T* Pn = static_cast<T*>(H->Pd[set]);
     T* Qn = static_cast<T*>(H->Qd[set]);
@@ -780,15 +781,26 @@ int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool war
     a.m = m;
     a.mu_next = 0;
     int rc;
-    if (!warm && (rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
     VecArgs<T> v = vec_args<T>(H, c, 0);
-    if (m > 0) {
-        rc = warm ? launch_aug<T, V_AUG_R0_WARM>(H, d.n_c, v, a, st) : launch_aug<T, V_AUG_R0>(H, d.n_c, v, a, st);
-        if (rc || (rc = launch_aug<T, V_AUG_INIT>(H, d.n_c, v, a, st))) return rc;
+    if (!warm && s_resid) {
+        // r0 from the slopes' residual chain (its vector step writes z0 and p0 = z0, the
+        // first direction of this set when there are no previous directions); with
+        // previous directions, their p_j.r0, then the corrected start
+        if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, false, m > 0 ? nullptr : Pn))) return rc;
+        if (m > 0 && ((rc = launch_aug<T, V_AUG_R0_RESID>(H, d.n_c, v, a, st)) ||
+                      (rc = launch_aug<T, V_AUG_INIT>(H, d.n_c, v, a, st))))
+            return rc;
     } else {
-        v.p = Pn;                                // p_0 = z_0
-        rc = warm ? launch_vec<T, V_INIT_WARM>(H, d.n_c, v, st) : launch_vec<T, V_INIT>(H, d.n_c, v, st);
-        if (rc) return rc;
+        if (!warm && (rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st)))
+            return rc;
+        if (m > 0) {
+            rc = warm ? launch_aug<T, V_AUG_R0_WARM>(H, d.n_c, v, a, st) : launch_aug<T, V_AUG_R0>(H, d.n_c, v, a, st);
+            if (rc || (rc = launch_aug<T, V_AUG_INIT>(H, d.n_c, v, a, st))) return rc;
+        } else {
+            v.p = Pn;                            // p_0 = z_0
+            rc = warm ? launch_vec<T, V_INIT_WARM>(H, d.n_c, v, st) : launch_vec<T, V_INIT>(H, d.n_c, v, st);
+            if (rc) return rc;
+        }
     }
     for (int k = 0; k < iters; ++k) {
         T* pk = Pn + k * ld;
@@ -899,13 +911,12 @@ int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStrea
         if ((rc = launch_pol<T>(H, d, s, sp, st))) return rc;
         s = sp;
     }
-    // the plain explicit-residual frame (single or batched) forms r0 from the slopes'
-    // residual (no b); frames that keep b (the warm recurrence's b_prev, the augmented
-    // start) form b first
-    const bool resid = !warm && !(H->params.flags & (FEWHA_FLAG_WARM_RESIDUAL | FEWHA_FLAG_AUGMENTED));
+    // the explicit-residual frame (plain or augmented, single or batched) forms r0 from the
+    // slopes' residual (no b); the warm recurrence keeps b (its b_prev) and forms it first
+    const bool resid = !warm && !(H->params.flags & FEWHA_FLAG_WARM_RESIDUAL);
     if (!resid && (rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
     if (H->params.flags & FEWHA_FLAG_AUGMENTED)
-        rc = enqueue_pcg_aug<T>(H, d, c, H->params.iters, warm, H->aug_set, H->aug_m, st);
+        rc = enqueue_pcg_aug<T>(H, d, c, H->params.iters, warm, H->aug_set, H->aug_m, st, resid ? s : nullptr);
     else
         rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st, resid ? s : nullptr);
     if (rc) return rc;
@@ -2986,7 +2997,7 @@ int fewha_get_residual(fewha_handle* H, void* r, void* b, void* stream) {
     if (r) CK(cudaMemcpyAsync(r, H->r, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
     if (b) {
         // the plain explicit frame forms r0 from the slopes' residual and never forms b
-        if (!(H->params.flags & (FEWHA_FLAG_WARM_RESIDUAL | FEWHA_FLAG_AUGMENTED | FEWHA_FLAG_PERSISTENT)))
+        if (!(H->params.flags & (FEWHA_FLAG_WARM_RESIDUAL | FEWHA_FLAG_PERSISTENT)))
             return fail(H, FEWHA_ERR_INVALID_ARG, "this frame form does not form b (use fewha_rhs)");
         CK(cudaMemcpyAsync(b, H->b, H->setup.n_c * H->esz, cudaMemcpyDeviceToDevice, st), "get residual");
     }
@@ -3095,7 +3106,7 @@ int fewha_frame_launches(const fewha_handle* H, int* launches) {
     // fit 2
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
     const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
-    const int per_iter = 6, start = warm ? 3 + 1 : (aug ? 3 + 6 : 5);
+    const int per_iter = 6, start = warm ? 3 + (aug ? 6 : 1) : (aug ? 5 + 1 : 5);
     *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + start + aug + per_iter * H->params.iters + 2;
     return FEWHA_OK;
 }

@@ -999,6 +999,7 @@ enum {
     V_AUG_R0 = 3,        // r0 = b - q (q = M c0), b_prev = b, and p_j.r0
     V_AUG_R0_WARM = 4,   // r0 = (b - b_prev) + r_prev, b_prev = b, and p_j.r0
     V_AUG_INIT = 5,      // c0 += P y, r0 -= Q y, z0 = J^-1 r0, r.z, and q_j.z0
+    V_AUG_R0_RESID = 8,  // p_j.r0 of an r0 already formed (the slopes' residual chain)
     V_UPDATE_AUG = 7     // the CG update of V_UPDATE; keeps p.q; q_j.z for the next direction
                          // (the direction update p = z + beta p_old - P mu runs fused into the
                          // inverse wavelet kernel, k_cl_inv with PUPD = 2)
@@ -1047,7 +1048,7 @@ __device__ __forceinline__ void shares_store(const double* src, int nw, double* 
 template <class T, int PHASE>
 __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const AugArgs<T>& a,
                                          const int cta, const int nparts) {
-    constexpr bool R0 = PHASE == V_AUG_R0 || PHASE == V_AUG_R0_WARM;
+    constexpr bool R0 = PHASE == V_AUG_R0 || PHASE == V_AUG_R0_WARM || PHASE == V_AUG_R0_RESID;
     __shared__ bool last;
     __shared__ T scoef[AUG_MAX + 1];                 // y_j or mu_j; [AUG_MAX]: alpha or beta
     __shared__ double shares[AUG_MAX + 1][32];       // per-warp shares: [0] r.z, [1 + j] dot j
@@ -1087,6 +1088,8 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
                     x0[k] = v.b[i];
                     x1[k] = v.b_prev[i];
                     x2[k] = v.r[i];
+                } else if (PHASE == V_AUG_R0_RESID) {
+                    x0[k] = v.r[i];
                 } else if (PHASE == V_AUG_INIT) {
                     x0[k] = v.c[i];
                     x1[k] = v.r[i];
@@ -1112,9 +1115,12 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
             const int i = base + k * PBLK + threadIdx.x;
             if (i < n) {
                 if (R0) {
-                    const T rr = PHASE == V_AUG_R0 ? x0[k] - x1[k] : (x0[k] - x1[k]) + x2[k];
-                    v.r[i] = rr;
-                    v.b_prev[i] = x0[k];
+                    const T rr = PHASE == V_AUG_R0 ? x0[k] - x1[k]
+                                 : PHASE == V_AUG_R0_WARM ? (x0[k] - x1[k]) + x2[k] : x0[k];
+                    if (PHASE != V_AUG_R0_RESID) {
+                        v.r[i] = rr;
+                        v.b_prev[i] = x0[k];
+                    }
 #pragma unroll
                     for (int j = 0; j < AUG_MAX; ++j)
                         if (j < m) dj[j].add(pj[j][k], rr);
