@@ -154,6 +154,11 @@ def time_frames(R, S, steps, warmup, flush, dm):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
+    # a lead of device work (L2 flushes, ~0.6 ms) so that the host's submissions run ahead
+    # of the timed frames: a host stall between a frame's start event and its launch would
+    # otherwise be timed as part of that frame
+    for _ in range(8):
+        flush.zero_()
     for k in range(steps):
         flush.zero_()
         ev[k][0].record()
