@@ -473,13 +473,13 @@ def time_backward(frames=8):
 
 
 def time_augmented(wl, S32, S_np, flush, steps, parity=True):
-    """Augmented PCG (Sec. 3.4) on the MAORY workload against the plain warm start, at 4
-    and 2 iterations: frames/s of the graph-replayed frame, and the mean relative
+    """Augmented PCG (Sec. 3.4) on the MAORY workload against the plain warm start, at 4,
+    3 and 2 iterations: frames/s of the graph-replayed frame, and the mean relative
     residual ||r|| / ||b|| that the fixed iteration count leaves (frames 2..7 of the
     frozen-flow sequence, each configuration from a cold start)."""
     from paper_2202_11945_gb300 import Reconstructor
     out = {"workload": wl["name"], "form": "FP32 operators, FP64 dots, CUDA graph"}
-    for it in (4, 2):
+    for it in (4, 3, 2):
         for aug in (False, True):
             R = Reconstructor(wl, precision=32, graph=True, augmented=aug)
             if it != wl["params"]["iters"]:

@@ -523,7 +523,8 @@ int enqueue_apply(fewha_handle* H, const Desc<T>& d, const T* x, T* qout, int sl
 // `slot - 1`; no p_old, and beta = 0, when pold is null; the m directions of `aug`).
 template <class T>
 int enqueue_apply_aug(fewha_handle* H, const Desc<T>& d, const T* pold, T* pnew, const T* z, T* qout, int slot,
-                      const AugArgs<T>& aug, cudaStream_t st) {
+                      const AugArgs<T>& aug, cudaStream_t st, const Defer& df = Defer(),
+                      int aug_pcnt = 0) {
     T* phi = static_cast<T*>(H->phi);
     T* u = static_cast<T*>(H->u);
     int rc;
@@ -538,6 +539,11 @@ int enqueue_apply_aug(fewha_handle* H, const Desc<T>& d, const T* pold, T* pnew,
     a.aug_pq = aug.pq;
     a.aug_ld = aug.ld;
     a.aug_m = aug.m;
+    a.aug_parts = aug.part;
+    a.aug_pcnt = aug_pcnt;
+    a.rz_parts = df.rz_parts;
+    a.rz_cnt = df.rz_cnt;
+    a.rz_slot = df.rz_slot;
     if ((rc = launch_inv<T, 2>(H, d, a, st))) return rc;
     if ((rc = launch_proj<T>(H, d, phi, st))) return rc;
     if ((rc = launch_csensor<T, SSRC_PHI>(H, d, phi, u, st))) return rc;
@@ -546,6 +552,7 @@ int enqueue_apply_aug(fewha_handle* H, const Desc<T>& d, const T* pold, T* pnew,
     b.pin = pnew;
     b.iter = slot;
     b.zero_piston = 1;
+    b.defer_total = df.pq ? 1 : 0;
     return launch_fwd<T, LSRC_NODES, LDST_APPLY>(H, d, b, st);
 }
 
@@ -802,20 +809,34 @@ int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool war
             if (rc) return rc;
         }
     }
+    // Deferred totals (as in the plain PCG, single instances): the forward kernels leave p.q
+    // to the CG update; the update of iteration k leaves r.z and its q_j.z dots to the
+    // inverse kernel of iteration k + 1 (all but the last iteration's, whose r.z is totalled
+    // by its own arrival count)
+    const bool defer = !recorder<T>();
     for (int k = 0; k < iters; ++k) {
         T* pk = Pn + k * ld;
         T* qk = Qn + k * ld;
         v = vec_args<T>(H, c, k);
+        Defer df;
+        df.pq = defer;
+        if (defer && k > 0) {
+            df.rz_parts = H->rzpart + static_cast<size_t>(k) * H->npart;
+            df.rz_cnt = H->npart;
+            df.rz_slot = k;
+        }
         if (k > 0 || m > 0) {
             // p_k = z_k + beta p_(k-1) - P mu, fused into the apply's inverse kernel
             rc = enqueue_apply_aug<T>(H, d, k > 0 ? Pn + (k - 1) * ld : nullptr, pk, static_cast<const T*>(H->z), qk,
-                                      k, a, st);
+                                      k, a, st, df, (defer && k > 0) ? H->npart : 0);
         } else {
-            rc = enqueue_apply<T>(H, d, pk, qk, k, false, st);       // p_0 = z_0 (no directions)
+            rc = enqueue_apply<T>(H, d, pk, qk, k, false, st, df);   // p_0 = z_0 (no directions)
         }
         if (rc) return rc;
         v.p = pk;
         v.q = qk;
+        v.pq_cnt = defer ? d.n_layers * CL : 0;
+        v.defer_rz = (defer && k + 1 < iters) ? 1 : 0;
         a.mu_next = (m > 0 && k + 1 < iters) ? 1 : 0;
         if ((rc = launch_aug<T, V_UPDATE_AUG>(H, d.n_c, v, a, st))) return rc;
     }

@@ -398,6 +398,10 @@ struct ClArgs {
     const double* aug_pq;
     long long aug_ld;
     int aug_m;
+    // deferred q_j.z totals (aug_pcnt > 0): dot j's shares at aug_parts + j * aug_pcnt, totalled
+    // here in the fixed order instead of read from aug_tot
+    const double* aug_parts;
+    int aug_pcnt;
     // the initial residual's vector step fused into the forward kernel (DST_APPLY_INIT): the
     // vectors r, z, p, b, b_prev, J^-1; r.z shares at rzp[l * CL + rank], total into rz slot
     // rzslot
@@ -927,10 +931,23 @@ __device__ __forceinline__ void cl_inv_body(const Desc<T>& d, const ClArgs<T>& a
             sbeta = T(b);
         }
     }
-    if (PUPD == 2 && threadIdx.x >= 32 && threadIdx.x < 32 + a.aug_m) {
-        const int j = threadIdx.x - 32;
-        const double num = a.aug_tot[AUG_MAX + j], den = a.aug_pq[j];
-        smu[j] = T(den > 0.0 ? num / den : 0.0);
+    if (PUPD == 2) {
+        if (a.aug_pcnt > 0) {
+            // deferred totals: warps 1, 2, ... each total dot j in the fixed order
+            const int warp1 = threadIdx.x >> 5, nw1 = NT >> 5;
+            for (int j = warp1 - 1; warp1 > 0 && j < a.aug_m; j += nw1 - 1) {
+                const double num = warp_total(a.aug_parts + static_cast<long long>(j) * a.aug_pcnt, a.aug_pcnt,
+                                              static_cast<const DotAcc<T>*>(nullptr));
+                if ((threadIdx.x & 31) == 0) {
+                    const double den = a.aug_pq[j];
+                    smu[j] = T(den > 0.0 ? num / den : 0.0);
+                }
+            }
+        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + a.aug_m) {
+            const int j = threadIdx.x - 32;
+            const double num = a.aug_tot[AUG_MAX + j], den = a.aug_pq[j];
+            smu[j] = T(den > 0.0 ? num / den : 0.0);
+        }
     }
     // the augmented update's sum_j mu_j P_j at this thread's positions, its loads in flight
     // beside the staging copies

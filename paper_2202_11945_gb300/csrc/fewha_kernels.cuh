@@ -1060,11 +1060,21 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
         const double den = a.pq[threadIdx.x];
         scoef[threadIdx.x] = T(den > 0.0 ? num / den : 0.0);
     }
-    if (threadIdx.x == 32) {
-        if (PHASE == V_UPDATE_AUG) {
-            const double rz = v.pcg.rztot[v.iter], pq = v.pcg.pqtot[v.iter];
+    if (PHASE == V_UPDATE_AUG && w == 1) {
+        // alpha; a deferred p.q total first (v.pq_cnt > 0: warp 1, fixed order)
+        double pq = 0.0;
+        if (v.pq_cnt > 0) {
+            pq = warp_total(v.pcg.pqpart + static_cast<long long>(v.iter) * PQ_SLOTS, v.pq_cnt,
+                            static_cast<const DotAcc<T>*>(nullptr));
+        }
+        if (lane == 0) {
+            if (v.pq_cnt == 0) pq = v.pcg.pqtot[v.iter];
+            const double rz = v.pcg.rztot[v.iter];
             scoef[AUG_MAX] = T((rz != 0.0 && pq > 0.0) ? rz / pq : 0.0);
-            if (cta == 0) a.pqnew[v.iter] = pq;
+            if (cta == 0) {
+                a.pqnew[v.iter] = pq;
+                if (v.pq_cnt > 0) v.pcg.pqtot[v.iter] = pq;
+            }
         }
     }
     __syncthreads();
@@ -1173,6 +1183,8 @@ __device__ __forceinline__ void aug_body(const int n, const VecArgs<T>& v, const
         double* dst = t == 0 ? v.pcg.rzpart + slot * v.pcg.npart + cta : a.part + (t - 1) * v.pcg.npart + cta;
         shares_store(shares[t], nw, dst, &dot);
     }
+    // deferred: the next inverse kernel totals r.z and the q_j.z dots
+    if (PHASE == V_UPDATE_AUG && v.defer_rz) return;
     if (last_arrival(v.pcg.count, nparts, &last)) {
         // the totals, one warp each, in a fixed order over the CTAs
         for (int t = w; t <= nd; t += nw) {
