@@ -62,7 +62,7 @@ struct fewha_handle {
     // typed device arrays (float or double per precision)
     void *pfy = nullptr, *pfx = nullptr, *dfw = nullptr, *D = nullptr, *Jinv = nullptr;
     void *c = nullptr, *b = nullptr, *b_prev = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
-         *q = nullptr, *phi = nullptr, *u = nullptr, *a_prev = nullptr, *dm_tmp = nullptr,
+         *q = nullptr, *phi = nullptr, *phic = nullptr, *u = nullptr, *a_prev = nullptr, *dm_tmp = nullptr,
          *s_tmp = nullptr, *c_tmp = nullptr, *cgrad = nullptr, *lam = nullptr;
     double* gdot = nullptr;           // per-layer sums of the backward pass
     // closed loop (FEWHA_FLAG_CLOSED_LOOP): DM projection tables, pseudo-open-loop slopes
@@ -369,6 +369,8 @@ VecArgs<T> vec_args(fewha_handle* H, T* c, int iter) {
     v.iter = iter;
     v.pq_cnt = 0;
     v.defer_rz = 0;
+    v.phic = nullptr;
+    v.phip = nullptr;
     return v;
 }
 
@@ -605,8 +607,8 @@ int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st,
 // right-hand side's 3 plus the apply's 5.  b and b_prev are not written.
 template <class T>
 int enqueue_resid_init(fewha_handle* H, const Desc<T>& d, const T* s, T* c, cudaStream_t st, bool defer,
-                       T* p0 = nullptr) {
-    T* phi = static_cast<T*>(H->phi);
+                       T* p0 = nullptr, T* phi_out = nullptr) {
+    T* phi = phi_out ? phi_out : static_cast<T*>(H->phi);
     T* u = static_cast<T*>(H->u);
     int rc;
     ClArgs<T> a = cl_args<T>(H, c, phi);
@@ -654,14 +656,14 @@ int launch_vec(fewha_handle* H, int n, const VecArgs<T>& v, cudaStream_t st) {
 
 template <class T>
 int launch_fit(fewha_handle* H, const Desc<T>& d, const T* phi, T* a_prev, T* dm, int gain, cudaStream_t st,
-               T* a_old = nullptr) {
+               T* a_old = nullptr, const T* cpist = nullptr) {
     if (recorder<T>()) {
         if (gain == 2) return fail(H, FEWHA_ERR_INVALID_ARG, "closed-loop frames are not batched");
-        record<T>(BK_FIT).fa = FitArgs<T>{phi, a_prev, dm, gain};
+        record<T>(BK_FIT).fa = FitArgs<T>{phi, a_prev, dm, gain, cpist};
         return FEWHA_OK;
     }
     CK(launch_k(H, k_fit<T>, dim3((d.n_act + PBLK - 1) / PBLK), dim3(PBLK), 0, st, d, phi, a_prev, dm, gain,
-                a_old),
+                a_old, cpist),
        "k_fit launch");
     return FEWHA_OK;
 }
@@ -686,7 +688,11 @@ int launch_pol(fewha_handle* H, const Desc<T>& d, const T* s, T* out, cudaStream
 // residual chain (enqueue_resid_init) and b is not formed.
 template <class T>
 int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, cudaStream_t st,
-                const T* s_resid = nullptr) {
+                const T* s_resid = nullptr, bool carry = false) {
+    // carry (with s_resid): the layers of c are carried through the iterations in H->phic
+    // (W^T c without the full layers' pistons; the fit adds them), so the fit needs no
+    // inverse transform
+    T* phic = (carry && s_resid) ? static_cast<T*>(H->phic) : nullptr;
     int rc;
     // the initial residual's vector step fused into the forward kernel (single instances; the
     // batched frame keeps the separate vector kernel).  The iterations' CG updates stay in
@@ -703,7 +709,7 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
         if (warm) {
             if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
         } else if (s_resid) {
-            if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, defer))) return rc;
+            if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, defer, nullptr, phic))) return rc;
         } else {
             if ((rc = enqueue_apply_init<T>(H, d, c, st, defer))) return rc;
         }
@@ -724,6 +730,8 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
             VecArgs<T> v = vec_args<T>(H, c, k);
             v.pq_cnt = d.n_layers * CL;
             v.defer_rz = k + 1 < iters ? 1 : 0;
+            v.phic = phic;
+            v.phip = static_cast<const T*>(H->phi);
             if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, v, st))) return rc;
         }
         return FEWHA_OK;
@@ -731,7 +739,7 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
     if (warm) {
         if ((rc = launch_vec<T, V_INIT_WARM>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
     } else if (s_resid) {
-        if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, false))) return rc;
+        if ((rc = enqueue_resid_init<T>(H, d, s_resid, c, st, false, nullptr, phic))) return rc;
     } else {
         if ((rc = enqueue_apply<T>(H, d, c, static_cast<T*>(H->q), PQ_SCRATCH_SLOT, false, st))) return rc;
         if ((rc = launch_vec<T, V_INIT>(H, d.n_c, vec_args<T>(H, c, 0), st))) return rc;
@@ -739,7 +747,10 @@ int enqueue_pcg(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool warm, c
     T* p = static_cast<T*>(H->p);
     for (int k = 0; k < iters; ++k) {
         if ((rc = enqueue_apply<T>(H, d, p, static_cast<T*>(H->q), k, k > 0, st))) return rc;
-        if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, vec_args<T>(H, c, k), st))) return rc;
+        VecArgs<T> v = vec_args<T>(H, c, k);
+        v.phic = phic;
+        v.phip = static_cast<const T*>(H->phi);
+        if ((rc = launch_vec<T, V_UPDATE>(H, d.n_c, v, st))) return rc;
     }
     return FEWHA_OK;
 }
@@ -843,14 +854,17 @@ int enqueue_pcg_aug(fewha_handle* H, const Desc<T>& d, T* c, int iters, bool war
     return FEWHA_OK;
 }
 
+// carried: the layers of c are in H->phic already (enqueue_pcg's carry), without the full
+// layers' pistons, which the fit adds from c
 template <class T>
-int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain, cudaStream_t st) {
-    T* phi = static_cast<T*>(H->phi);
+int enqueue_fit(fewha_handle* H, const Desc<T>& d, const T* c, T* dm, bool gain, cudaStream_t st,
+                bool carried = false) {
+    T* phi = static_cast<T*>(carried ? H->phic : H->phi);
     int rc;
-    if ((rc = launch_inv<T, 0>(H, d, cl_args<T>(H, c, phi), st))) return rc;
+    if (!carried && (rc = launch_inv<T, 0>(H, d, cl_args<T>(H, c, phi), st))) return rc;
     const bool closed = gain && (H->params.flags & FEWHA_FLAG_CLOSED_LOOP);
     return launch_fit<T>(H, d, phi, static_cast<T*>(H->a_prev), dm, closed ? 2 : (gain ? 1 : 0), st,
-                         static_cast<T*>(H->a_old));
+                         static_cast<T*>(H->a_old), carried ? c : nullptr);
 }
 
 template <class K>
@@ -936,12 +950,15 @@ int enqueue_frame(fewha_handle* H, const T* s, T* c, T* dm, bool warm, cudaStrea
     // slopes' residual (no b); the warm recurrence keeps b (its b_prev) and forms it first
     const bool resid = !warm && !(H->params.flags & FEWHA_FLAG_WARM_RESIDUAL);
     if (!resid && (rc = enqueue_rhs<T>(H, d, s, static_cast<T*>(H->b), st))) return rc;
+    // the plain frame with the residual chain also carries the layers of c through its
+    // iterations, so that its fit needs no inverse transform
+    const bool carry = resid && !(H->params.flags & FEWHA_FLAG_AUGMENTED);
     if (H->params.flags & FEWHA_FLAG_AUGMENTED)
         rc = enqueue_pcg_aug<T>(H, d, c, H->params.iters, warm, H->aug_set, H->aug_m, st, resid ? s : nullptr);
     else
-        rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st, resid ? s : nullptr);
+        rc = enqueue_pcg<T>(H, d, c, H->params.iters, warm, st, resid ? s : nullptr, carry);
     if (rc) return rc;
-    return enqueue_fit<T>(H, d, c, dm, true, st);
+    return enqueue_fit<T>(H, d, c, dm, true, st, carry);
 }
 
 void drop_graph(fewha_handle* H) {
@@ -1484,7 +1501,7 @@ int typed_create(fewha_handle* H) {
         (rc = talloc(H, &H->b, s.n_c)) || (rc = talloc(H, &H->b_prev, s.n_c)) ||
         (rc = talloc(H, &H->r, s.n_c)) || (rc = talloc(H, &H->z, s.n_c)) ||
         (rc = talloc(H, &H->p, s.n_c)) || (rc = talloc(H, &H->q, s.n_c)) ||
-        (rc = talloc(H, &H->phi, s.n_c)) || (rc = talloc(H, &H->c_tmp, s.n_c)) ||
+        (rc = talloc(H, &H->phi, s.n_c)) || (rc = talloc(H, &H->phic, s.n_c)) || (rc = talloc(H, &H->c_tmp, s.n_c)) ||
         (rc = talloc(H, &H->u, s.n_nodes)) || (rc = talloc(H, &H->a_prev, s.n_act)) ||
         (rc = talloc(H, &H->dm_tmp, s.n_act)) || (rc = talloc(H, &H->s_tmp, s.n_s)) ||
         (rc = talloc(H, &H->cgrad, s.n_c)) || (rc = talloc(H, &H->lam, s.n_c)) ||
@@ -3122,13 +3139,15 @@ int fewha_frame_launches(const fewha_handle* H, int* launches) {
     const bool warm = (H->params.flags & FEWHA_FLAG_WARM_RESIDUAL) != 0;
     // the plain explicit frame: r0 from the slopes' residual, 5 (the right-hand side is not
     // formed); with the warm recurrence, RHS 3 and r0 1 (its explicit refresh frames: 3 + 5);
-    // augmented: RHS 3, r0 6 (a separate vector kernel) and one more start kernel (its
-    // direction update is fused into the inverse kernel of each apply); 6 per iteration,
-    // fit 2
+    // augmented: r0 5 and one more start kernel (its direction update is fused into the
+    // inverse kernel of each apply); 6 per iteration
     const int aug = (H->params.flags & FEWHA_FLAG_AUGMENTED) ? 1 : 0;
     const int closed = (H->params.flags & FEWHA_FLAG_CLOSED_LOOP) ? 2 : 0;
-    const int per_iter = 6, start = warm ? 3 + (aug ? 6 : 1) : (aug ? 5 + 1 : 5);
-    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + start + aug + per_iter * H->params.iters + 2;
+    // fit: 2 (inverse transform, fit), or 1 where the plain explicit frame carries the
+    // layers of c through its iterations
+    const int per_iter = 6, start = warm ? 3 + 1 : (aug ? 5 + 1 : 5);
+    const int fit = (warm || aug) ? 2 : 1;
+    *launches = (H->params.flags & FEWHA_FLAG_PERSISTENT) ? 1 : closed + start + aug + per_iter * H->params.iters + fit;
     return FEWHA_OK;
 }
 

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(PBLK)
     const BInst<T>* I = inst + it.inst;
     load_desc<T>(sd, I);
     const FitArgs<T> f = args[it.inst];
-    fit_body<T>(sd, f.phi, f.a_prev, f.out, f.apply_gain, it.unit);
+    fit_body<T>(sd, f.phi, f.a_prev, f.out, f.apply_gain, it.unit, nullptr, f.cpist);
 }
 
 // The kernel of a step kind in one launch shape (variant v: bit 0 half-size projection

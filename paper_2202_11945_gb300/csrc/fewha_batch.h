@@ -36,6 +36,7 @@ struct FitArgs {
     T* a_prev;
     T* out;
     int apply_gain;
+    const T* cpist;     // c, when phi lacks the full layers' pistons (carried layers)
 };
 
 // Step kinds of the frame (each names one kernel template instance).

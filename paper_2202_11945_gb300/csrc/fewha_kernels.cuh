@@ -856,6 +856,11 @@ struct VecArgs {
     // defer_rz, the r.z shares are stored and their total is left to the next inverse kernel
     int pq_cnt;
     int defer_rz;
+    // V_UPDATE with phic: phi_c += alpha phi_p, the layers of c carried through the
+    // iterations (phi_p = W^T p of the iteration's apply, piston left out like the data
+    // path), so that the fit needs no inverse transform of the final c
+    T* phic;
+    const T* phip;
 };
 
 enum { V_INIT = 0, V_INIT_WARM = 1, V_UPDATE = 2 };
@@ -897,7 +902,8 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
     DotAcc<T> dot;
     for (int base = cta * NTV * PVEC; base < n; base += nparts * NTV * PVEC) {
         // issue every load of the batch before the arithmetic
-        T b[PVEC], q[PVEC], r[PVEC], p[PVEC], c[PVEC], bp[PVEC], jv[PVEC];
+        T b[PVEC], q[PVEC], r[PVEC], p[PVEC], c[PVEC], bp[PVEC], jv[PVEC], fc[PVEC], fp[PVEC];
+        const bool track = PHASE == V_UPDATE && v.phic != nullptr;
 #pragma unroll
         for (int k = 0; k < PVEC; ++k) {
             const int i = base + k * NTV + threadIdx.x;
@@ -914,6 +920,10 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
                     c[k] = v.c[i];
                     p[k] = v.p[i];
                     r[k] = v.r[i];
+                    if (track) {
+                        fc[k] = v.phic[i];
+                        fp[k] = v.phip[i];
+                    }
                 }
             }
         }
@@ -948,6 +958,7 @@ __device__ __forceinline__ void vec_body(const int n, const VecArgs<T>& v, const
                     v.b_prev[i] = b[k];
                 } else {
                     v.c[i] = c[k] + ta * p[k];
+                    if (track) v.phic[i] = fc[k] + ta * fp[k];
                     rr = r[k] - ta * q[k];
                 }
                 v.r[i] = rr;
@@ -1219,7 +1230,8 @@ __global__ void __launch_bounds__(PBLK) k_aug(const int n, __grid_constant__ con
 template <class T, int NTF = PBLK>
 __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__ phi,
                                          T* __restrict__ a_prev, T* __restrict__ out, int apply_gain,
-                                         const int blk, T* __restrict__ a_old = nullptr) {
+                                         const int blk, T* __restrict__ a_old = nullptr,
+                                         const T* __restrict__ cpist = nullptr) {
     const int idx = blk * NTF + threadIdx.x;
     if (idx >= d.n_act) return;
     int m = 0;
@@ -1261,6 +1273,15 @@ __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__
                 acc += w[u] * ((T(1) - fy[u]) * ((T(1) - fx[u]) * v[u][0] + fx[u] * v[u][1]) +
                                fy[u] * ((T(1) - fx[u]) * v[u][2] + fx[u] * v[u][3]));
     }
+    if (cpist) {
+        // phi without the full layers' pistons (the carried layers): a unit piston coefficient
+        // synthesises to 1/n on every node of an n x n layer, and the bilinear weights sum
+        // to one, so each adds w_lm c_piston / n
+        for (int l = 0; l < d.n_layers; ++l) {
+            const T wl = d.fitw[m][l];
+            if (d.L[l].full && wl != T(0)) acc += wl * (cpist[d.L[l].off] / T(d.L[l].n));
+        }
+    }
     if (apply_gain == 2) {
         const T cur = a_prev[idx];
         const T a = cur + d.gain * (acc - a_old[idx]);
@@ -1279,9 +1300,10 @@ __device__ __forceinline__ void fit_body(const Desc<T>& d, const T* __restrict__
 template <class T>
 __global__ void __launch_bounds__(PBLK) k_fit(__grid_constant__ const Desc<T> d, const T* __restrict__ phi,
                                               T* __restrict__ a_prev, T* __restrict__ out,
-                                              int apply_gain, T* __restrict__ a_old) {
+                                              int apply_gain, T* __restrict__ a_old,
+                                              const T* __restrict__ cpist) {
     pdl_enter();
-    fit_body<T>(d, phi, a_prev, out, apply_gain, blockIdx.x, a_old);
+    fit_body<T>(d, phi, a_prev, out, apply_gain, blockIdx.x, a_old, cpist);
 }
 
 // ---------------------------------------------------------------------------
