@@ -61,6 +61,16 @@ def test_constant_has_only_coarse_coefficient():
     np.testing.assert_allclose(c, expect, atol=1e-11)
 
 
+@pytest.mark.parametrize("n", [16, 64, 128])
+def test_piston_coefficient_synthesises_to_constant(n):
+    """A unit full-depth LL coefficient is the constant 1/n on an n x n layer: the identity
+    by which the fit adds a full layer's piston, w c_piston / n, to layers carried without it."""
+    levels = int(np.log2(n))
+    c = np.zeros((n, n))
+    c[0, 0] = 1.0
+    np.testing.assert_allclose(O.idwt2(c, levels), np.full((n, n), 1.0 / n), rtol=0, atol=1e-15)
+
+
 def test_quadratics_have_no_interior_details():
     """Three vanishing moments: level-1 details of x^2 (away from the seam) are 0."""
     n = 32
