@@ -177,15 +177,19 @@ def stage_bytes(R, b):
         "sensor": 2 * nn * b,             # read P phi; write the aperture-node adjoint u
         "projT": (nn + nc) * b,           # read u; write P^T u on the layers
         "layer": 3 * nc * b,              # read P^T u and p; write q (D: one value per level)
-        "vector": 8 * nc * b,             # read c, p, r, q, J^-1; write c, r, z
+        "vector": 11 * nc * b,            # read c, p, r, q, J^-1, phi_c, phi_p; write c, r, z, phi_c
         "rhs": (ns + nn) * b,             # read slopes; write u
         "fit": (nc + 3 * na) * b,         # read phi, a_prev; write a_prev, dm
     }
 
 
 def stage_launches(iters):
-    return {"idwt": iters + 2, "proj": iters + 1, "sensor": iters + 1, "projT": iters + 2,
-            "layer": iters + 2, "vector": iters + 1, "rhs": 1, "fit": 1}
+    """Launches of each stage's kernel in one explicit-residual frame: the initial residual's
+    chain (inverse transform, P, the sensor kernel on the slopes' residual, P^T, the forward
+    kernel with the vector step) and one apply plus one CG update per iteration; the fit
+    reads the carried layers (no inverse transform) and no right-hand side is formed."""
+    return {"idwt": iters + 1, "proj": iters + 1, "sensor": iters + 1, "projT": iters + 1,
+            "layer": iters + 1, "vector": iters, "rhs": 0, "fit": 1}
 
 
 def time_stages(R, flush, reps=100):
