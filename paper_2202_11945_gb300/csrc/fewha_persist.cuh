@@ -30,7 +30,7 @@ struct GridSync {
 // Barrier number k of the launch (k counted by the caller from 1).  Returns false, in every
 // CTA of the cluster alike, when the frame is to stop.
 __device__ __forceinline__ bool grid_barrier(const GridSync& gs, unsigned k) {
-    __shared__ int verdict;
+    __shared__ int gate;
     cg::cluster_group cluster = cg::this_cluster();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -53,11 +53,11 @@ __device__ __forceinline__ bool grid_barrier(const GridSync& gs, unsigned k) {
             atomicOr(gs.status, 2u);
         }
         // every CTA of the cluster is running (they start together and all reach the
-        // cluster barrier below), so the verdict can be pushed into their shared memory
-        for (unsigned q = 0; q < cluster.num_blocks(); ++q) *cluster.map_shared_rank(&verdict, q) = ok;
+        // cluster barrier below), so the outcome can be pushed into their shared memory
+        for (unsigned q = 0; q < cluster.num_blocks(); ++q) *cluster.map_shared_rank(&gate, q) = ok;
     }
     cluster.sync();
-    const int ok = verdict;
+    const int ok = gate;
     if (threadIdx.x == 0) __threadfence();     // later loads see the other CTAs' writes
     __syncthreads();
     return ok != 0;
