@@ -220,7 +220,7 @@ int fewha_update_params(fewha_handle* h, const fewha_params* params, const doubl
 int fewha_reset(fewha_handle* h, void* stream);
 
 /* One frame of Algorithm 1 (open loop): r0 = b - M c0 from d_slopes (formed as
- * W P^T Gamma^T C^-1 (s - Gamma P W^-1 c0) - alpha D c0, without b; the warm residual
+ * W P^T Gamma^T C^-1 (s - Gamma P W^T c0) - alpha D c0, without b; the warm residual
  * form with FEWHA_FLAG_WARM_RESIDUAL and the augmented start form b first), `iters` PCG
  * iterations, DM fit and gain.  d_x_warm (n_coeffs) is the warm start, read and overwritten with the new c;
  * NULL uses the handle's internal state.  d_dm_out (n_act) receives the commands

@@ -600,7 +600,7 @@ int enqueue_apply_init(fewha_handle* H, const Desc<T>& d, T* c, cudaStream_t st,
 }
 
 // r0 = b - M c0 formed in one chain, from the slopes' residual: the sensor kernel takes
-// C^-1 (s - Gamma P phi0) (phi0 = W^-1 c0, its piston left out), the adjoint projection and
+// C^-1 (s - Gamma P phi0) (phi0 = W^T c0, its piston left out), the adjoint projection and
 // the forward kernel give r0 = W P^T Gamma^T C^-1 (s - Gamma P phi0) - alpha D c0 and the
 // initial residual's vector step (z0, p0, r.z in slot 0, only shares with `defer`).  By
 // linearity this is b - M c0 of Algorithm 1 without forming b: 5 kernels instead of the
