@@ -326,6 +326,45 @@ int fewha_pcg(fewha_handle* h, const void* d_b, void* d_c, int iters, void* stre
  * D of Sec. 3.1 and J of Eq. (7). */
 int fewha_get_diagonals(fewha_handle* h, void* d_D, void* d_J, void* stream);
 
+/* ---- least-squares DM fitting over fitting directions ---------------------------
+ * Sec. 4.1 notes that reconstructing more layers than there are DMs turns the fitting
+ * step into a least-squares problem of its own, in place of the projection F.  Here the
+ * commands minimise
+ *
+ *     sum_k w_k || Pi (A_k a - L_k phi) ||^2 + eps ||a||^2,    phi = W^T c,
+ *
+ * over the fitting directions theta_k: the pupil nodes x (n_fit + 1 per side, spacing
+ * D / n_fit from -D/2, those with obs*D/2 <= |x| <= D/2) see layer l bilinearly at
+ * x + theta_k h_l (L_k; the sample must stay inside the layer grid, else
+ * FEWHA_ERR_GEOMETRY) and DM m as the sum of its actuators' bilinear hats at
+ * x + theta_k h_m (A_k; zero beyond the outer actuators), and Pi removes the mean over
+ * the pupil nodes (piston is not fitted).  The normal equations
+ * (sum_k w_k A_k^T Pi A_k + eps I) a = sum_k w_k A_k^T Pi L_k phi are solved by
+ * (unpreconditioned) CG from a = 0 until the recurrence residual falls to tol times the
+ * right-hand side's norm or max_iters iterations have run; the CG inner products and
+ * scalars are double, the operators the handle's element type. */
+#define FEWHA_MAX_FIT_DIRS 32
+#define FEWHA_MAX_FIT_NODES 256  /* largest n_fit                                      */
+typedef struct fewha_lsfit {
+    int n_dirs;              /* 1 .. FEWHA_MAX_FIT_DIRS                                */
+    const double* theta_x;   /* direction of each [rad], host arrays of n_dirs          */
+    const double* theta_y;
+    const double* weight;    /* w_k >= 0, not all zero                                  */
+    int n_fit;               /* pupil intervals per side, 1 .. FEWHA_MAX_FIT_NODES       */
+    double eps;              /* Tikhonov weight >= 0                                    */
+} fewha_lsfit;
+
+/* d_c: coefficient vector (n_coeffs), d_dm_out: commands (n_act), both device pointers of
+ * the handle's element type.  The fitting tables and CG vectors are built and kept in the
+ * handle on the first call and rebuilt when the configuration changes (FEWHA_ERR_OOM if
+ * their allocation fails).  Synchronises on `stream` (convergence is checked from the host
+ * every FEWHA_MAX_ITERS iterations).  *iters_done and *rel_residual (both nullable) give
+ * the iterations run and the final relative recurrence residual.  FEWHA_ERR_INVALID_ARG
+ * for a null pointer, a count or n_fit out of range, a negative weight or eps, or no
+ * positive weight; FEWHA_ERR_NONFINITE if the residual is not finite. */
+int fewha_fit_ls(fewha_handle* h, const fewha_lsfit* cfg, const void* d_c, void* d_dm_out, double tol,
+                 int max_iters, int* iters_done, double* rel_residual, void* stream);
+
 /* ---- measurement --------------------------------------------------------------- */
 
 /* Hot-path stages of one PCG iteration and of the frame, for timing one kernel alone. */

@@ -8,12 +8,14 @@
 #include <cstring>
 #include <algorithm>
 #include <chrono>
+#include <initializer_list>
 #include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
 
 #include "fewha_batch.h"
+#include "fewha_lsfit.cuh"
 #include "fewha_persist.cuh"
 
 using namespace fewha;
@@ -40,6 +42,23 @@ constexpr int PQ_SCRATCH_SLOT = FEWHA_MAX_ITERS;   // p.q slot of the explicit r
 static_assert(AUG_MAX == FEWHA_AUG_MAX_ITERS, "augmented PCG direction count");
 
 }  // namespace
+
+// Least-squares fit over fitting directions (fewha_fit_ls): the configuration whose tables
+// are on the device, those tables (see LsfitHost) and the CG vectors.  Buffers grow with the
+// configuration and are owned by the handle's allocation list.
+struct LsfitDev {
+    std::vector<double> key;
+    LsfitHost host;
+    unsigned char* mask = nullptr;
+    int *ly0 = nullptr, *lx0 = nullptr, *my0 = nullptr, *mx0 = nullptr;
+    int *ylo = nullptr, *yhi = nullptr, *xlo = nullptr, *xhi = nullptr;
+    void *lfy = nullptr, *lfx = nullptr, *mfy = nullptr, *mfx = nullptr;
+    void *v = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    double* part = nullptr;
+    double* sc = nullptr;
+    int* state = nullptr;
+    size_t cap_pix = 0, cap_l = 0, cap_lf = 0, cap_m = 0, cap_mf = 0, cap_rng = 0, cap_v = 0;
+};
 
 struct fewha_handle {
     int device = 0;
@@ -129,6 +148,7 @@ struct fewha_handle {
     size_t smem_frame = 0;
     unsigned wait_limit = 1u << 20;
     unsigned wait_extra = 0;
+    LsfitDev* lsf = nullptr;
 };
 
 struct fewha_batch {
@@ -1435,6 +1455,7 @@ void free_handle(fewha_handle* H) {
     drop_graph(H);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
     for (void* p : H->allocs) cudaFree(p);
+    delete H->lsf;
     delete H;
 }
 
@@ -1987,6 +2008,194 @@ int solve_entry(fewha_handle* H, const T* b, T* x, double tol, int max_iters, cu
 // symmetric), three vector kernels and one M-apply per iteration (k_vjp).  The scalars
 // (rho, sigma, alpha, beta and their adjoints) stay on the device; the host synchronises
 // once, at the end.  Synchronous.
+// ---- least-squares fit over fitting directions (Sec. 4.1) --------------------------
+
+int check_lsfit(fewha_handle* H, const fewha_lsfit* cfg) {
+    if (!cfg || !cfg->theta_x || !cfg->theta_y || !cfg->weight)
+        return fail(H, FEWHA_ERR_INVALID_ARG, "fit_ls: null configuration or direction array");
+    if (cfg->n_dirs < 1 || cfg->n_dirs > FEWHA_MAX_FIT_DIRS)
+        return fail(H, FEWHA_ERR_INVALID_ARG, "fit_ls: n_dirs out of 1 .. FEWHA_MAX_FIT_DIRS");
+    if (cfg->n_fit < 1 || cfg->n_fit > FEWHA_MAX_FIT_NODES)
+        return fail(H, FEWHA_ERR_INVALID_ARG, "fit_ls: n_fit out of 1 .. FEWHA_MAX_FIT_NODES");
+    if (!(cfg->eps >= 0.0) || !std::isfinite(cfg->eps))
+        return fail(H, FEWHA_ERR_INVALID_ARG, "fit_ls: eps must be finite and >= 0");
+    bool any = false;
+    for (int k = 0; k < cfg->n_dirs; ++k) {
+        if (!std::isfinite(cfg->theta_x[k]) || !std::isfinite(cfg->theta_y[k]) || !(cfg->weight[k] >= 0.0) ||
+            !std::isfinite(cfg->weight[k]))
+            return fail(H, FEWHA_ERR_INVALID_ARG, "fit_ls: directions must be finite and weights finite and >= 0");
+        any = any || cfg->weight[k] > 0.0;
+    }
+    if (!any) return fail(H, FEWHA_ERR_INVALID_ARG, "fit_ls: no positive weight");
+    return FEWHA_OK;
+}
+
+// Grow a group of device buffers to `need` elements each (new buffers when the group's
+// capacity *cap is smaller; the old ones stay on the handle's list until it is destroyed).
+template <class X>
+int lsf_grow(fewha_handle* H, std::initializer_list<X**> ptrs, size_t* cap, size_t need) {
+    if (*cap >= need) return FEWHA_OK;
+    for (X** p : ptrs) {
+        int rc = dalloc(H, p, need);
+        if (rc) return rc;
+    }
+    *cap = need;
+    return FEWHA_OK;
+}
+
+int lsf_grow_t(fewha_handle* H, std::initializer_list<void**> ptrs, size_t* cap, size_t need) {
+    if (*cap >= need) return FEWHA_OK;
+    for (void** p : ptrs) {
+        int rc = talloc(H, p, need);
+        if (rc) return rc;
+    }
+    *cap = need;
+    return FEWHA_OK;
+}
+
+template <class T>
+int lsf_upload(fewha_handle* H, void* dst, const std::vector<double>& src) {
+    std::vector<T> t(src.begin(), src.end());
+    return upload(H, static_cast<T*>(dst), t);
+}
+
+// Tables of configuration `cfg` on the device (built unless they already are).
+template <class T>
+int ensure_lsfit(fewha_handle* H, const fewha_lsfit& cfg) {
+    std::vector<double> key{double(cfg.n_dirs), double(cfg.n_fit), cfg.eps};
+    for (int k = 0; k < cfg.n_dirs; ++k) {
+        key.push_back(cfg.theta_x[k]);
+        key.push_back(cfg.theta_y[k]);
+        key.push_back(cfg.weight[k]);
+    }
+    if (!H->lsf) H->lsf = new LsfitDev();
+    LsfitDev& F = *H->lsf;
+    if (F.key == key) return FEWHA_OK;
+    F.key.clear();
+    std::string err;
+    int rc = build_lsfit(H->setup, H->tel_in.obs, H->dms_in.data(), cfg, F.host, err);
+    if (rc) return fail(H, rc, "fit_ls: " + err);
+    const LsfitHost& L = F.host;
+    const size_t n_a = static_cast<size_t>(H->setup.n_act);
+    const size_t nb = (n_a + LSF_ABLK - 1) / LSF_ABLK;
+    if (!F.state) {   // allocated last: all of them are there
+        if ((rc = talloc(H, &F.r, n_a)) || (rc = talloc(H, &F.p, n_a)) || (rc = talloc(H, &F.q, n_a)) ||
+            (rc = dalloc(H, &F.part, nb)) || (rc = dalloc(H, &F.sc, 2)) || (rc = dalloc(H, &F.state, 2)))
+            return rc;
+    }
+    if ((rc = lsf_grow<unsigned char>(H, {&F.mask}, &F.cap_pix, L.mask.size())) ||
+        (rc = lsf_grow<int>(H, {&F.ly0, &F.lx0}, &F.cap_l, L.ly0.size())) ||
+        (rc = lsf_grow_t(H, {&F.lfy, &F.lfx}, &F.cap_lf, L.lfy.size())) ||
+        (rc = lsf_grow<int>(H, {&F.my0, &F.mx0}, &F.cap_m, L.my0.size())) ||
+        (rc = lsf_grow_t(H, {&F.mfy, &F.mfx}, &F.cap_mf, L.mfy.size())) ||
+        (rc = lsf_grow<int>(H, {&F.ylo, &F.yhi, &F.xlo, &F.xhi}, &F.cap_rng, L.ylo.size())) ||
+        (rc = lsf_grow_t(H, {&F.v}, &F.cap_v, static_cast<size_t>(L.n_dirs) * L.mask.size())))
+        return rc;
+    if ((rc = upload(H, F.mask, L.mask)) || (rc = upload(H, F.ly0, L.ly0)) || (rc = upload(H, F.lx0, L.lx0)) ||
+        (rc = lsf_upload<T>(H, F.lfy, L.lfy)) || (rc = lsf_upload<T>(H, F.lfx, L.lfx)) ||
+        (rc = upload(H, F.my0, L.my0)) || (rc = upload(H, F.mx0, L.mx0)) ||
+        (rc = lsf_upload<T>(H, F.mfy, L.mfy)) || (rc = lsf_upload<T>(H, F.mfx, L.mfx)) ||
+        (rc = upload(H, F.ylo, L.ylo)) || (rc = upload(H, F.yhi, L.yhi)) || (rc = upload(H, F.xlo, L.xlo)) ||
+        (rc = upload(H, F.xhi, L.xhi)))
+        return rc;
+    F.key = key;
+    return FEWHA_OK;
+}
+
+template <class T>
+LsDesc<T> lsf_desc(const fewha_handle* H, const fewha_lsfit& cfg) {
+    const LsfitDev& F = *H->lsf;
+    const HostSetup& S = H->setup;
+    LsDesc<T> d{};
+    d.n_dirs = F.host.n_dirs;
+    d.nf1 = F.host.nf1;
+    d.n_pup = F.host.n_pup;
+    d.n_layers = static_cast<int>(S.L.size());
+    d.n_dms = static_cast<int>(S.Mi.size());
+    d.n_a = S.n_act;
+    for (int l = 0; l < d.n_layers; ++l) {
+        d.lay_n[l] = S.L[l].n;
+        d.lay_off[l] = S.L[l].off;
+    }
+    for (int m = 0; m < d.n_dms; ++m) {
+        d.dm_n[m] = S.Mi[m].n_act;
+        d.dm_off[m] = S.Mi[m].off;
+    }
+    for (int k = 0; k < d.n_dirs; ++k) d.w[k] = static_cast<T>(cfg.weight[k]);
+    d.eps = static_cast<T>(cfg.eps);
+    d.mask = F.mask;
+    d.ly0 = F.ly0;
+    d.lx0 = F.lx0;
+    d.my0 = F.my0;
+    d.mx0 = F.mx0;
+    d.lfy = static_cast<const T*>(F.lfy);
+    d.lfx = static_cast<const T*>(F.lfx);
+    d.mfy = static_cast<const T*>(F.mfy);
+    d.mfx = static_cast<const T*>(F.mfx);
+    d.ylo = F.ylo;
+    d.yhi = F.yhi;
+    d.xlo = F.xlo;
+    d.xhi = F.xhi;
+    return d;
+}
+
+// phi = W^T c, the right-hand side, then CG chunks of FEWHA_MAX_ITERS steps until the
+// device reports that the CG has stopped.
+template <class T>
+int fit_ls(fewha_handle* H, const fewha_lsfit& cfg, const T* c, T* a, double tol, int max_iters, int* iters_out,
+           double* rel_out, cudaStream_t st) {
+    int rc = ensure_lsfit<T>(H, cfg);
+    if (rc) return rc;
+    LsfitDev& F = *H->lsf;
+    const Desc<T> d = make_desc<T>(H);
+    T* phi = static_cast<T*>(H->phi);
+    if ((rc = launch_layer<T, LSRC_COEF, LDST_PHI, false>(H, d, layer_args<T>(H, c, phi), st))) return rc;
+    const LsDesc<T> ld = lsf_desc<T>(H, cfg);
+    T* v = static_cast<T*>(F.v);
+    T* p = static_cast<T*>(F.p);
+    T* q = static_cast<T*>(F.q);
+    const int nb = (ld.n_a + LSF_ABLK - 1) / LSF_ABLK;
+    k_lsf_sample<T, true><<<ld.n_dirs, LSF_SBLK, 0, st>>>(ld, phi, v, nullptr);
+    k_lsf_adj<T><<<nb, LSF_ABLK, 0, st>>>(ld, v, nullptr, q, nullptr, nullptr);
+    LsCg<T> g{};
+    g.n = ld.n_a;
+    g.nparts = nb;
+    g.max_iters = max_iters;
+    g.tol2 = tol * tol;
+    g.a = a;
+    g.r = static_cast<T*>(F.r);
+    g.p = p;
+    g.q = q;
+    g.part = F.part;
+    g.sc = F.sc;
+    g.state = F.state;
+    k_lsf_cg<T, true><<<1, LSF_CBLK, 0, st>>>(g);
+    CK(cudaGetLastError(), "fit_ls launch");
+    int hst[2] = {0, 0};
+    double hsc[2] = {0.0, 0.0};
+    int run = 0;
+    for (;;) {
+        const int k = std::min(FEWHA_MAX_ITERS, max_iters - run);
+        for (int j = 0; j < k; ++j) {
+            k_lsf_sample<T, false><<<ld.n_dirs, LSF_SBLK, 0, st>>>(ld, p, v, F.state);
+            k_lsf_adj<T><<<nb, LSF_ABLK, 0, st>>>(ld, v, p, q, F.part, F.state);
+            k_lsf_cg<T, false><<<1, LSF_CBLK, 0, st>>>(g);
+        }
+        CK(cudaGetLastError(), "fit_ls launch");
+        run += k;
+        CK(cudaMemcpyAsync(hst, F.state, sizeof hst, cudaMemcpyDeviceToHost, st), "fit_ls state");
+        CK(cudaMemcpyAsync(hsc, F.sc, sizeof hsc, cudaMemcpyDeviceToHost, st), "fit_ls state");
+        CK(cudaStreamSynchronize(st), "fit_ls");
+        if (hst[0] || run >= max_iters) break;
+    }
+    if (iters_out) *iters_out = hst[1];
+    if (rel_out) *rel_out = hsc[1] > 0.0 ? std::sqrt(std::max(hsc[0], 0.0) / hsc[1]) : 0.0;
+    if (!std::isfinite(hsc[0]) || !std::isfinite(hsc[1]))
+        return fail(H, FEWHA_ERR_NONFINITE, "fit_ls: non-finite residual");
+    if (hst[0] == 2) return fail(H, FEWHA_ERR_NONFINITE, "fit_ls: CG breakdown (p.q <= 0)");
+    return FEWHA_OK;
+}
+
 template <class T>
 int frame_vjp(fewha_handle* H, const T* s, const T* c0, const T* g_a, T* dm, T* g_s, cudaStream_t st) {
     const Desc<T> d = make_desc<T>(H);
@@ -3122,6 +3331,21 @@ int fewha_fit_adj(fewha_handle* h, const void* dm, void* c, void* st) { return o
 int fewha_pcg(fewha_handle* h, const void* b, void* c, int iters, void* st) {
     if (h && (iters < 0 || iters > FEWHA_MAX_ITERS)) return fail(h, FEWHA_ERR_LIMIT, "iters out of range");
     return op_entry(h, 13, b, c, iters, st);
+}
+
+int fewha_fit_ls(fewha_handle* H, const fewha_lsfit* cfg, const void* c, void* dm, double tol, int max_iters,
+                 int* iters, double* rel, void* stream) {
+    if (!H) return FEWHA_ERR_INVALID_ARG;
+    if (!c || !dm || !(tol >= 0.0) || max_iters < 0) return fail(H, FEWHA_ERR_INVALID_ARG, "bad fit_ls arguments");
+    int rc = check_lsfit(H, cfg);
+    if (rc) return rc;
+    DeviceGuard g(H->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return H->precision == 32
+               ? fit_ls<float>(H, *cfg, static_cast<const float*>(c), static_cast<float*>(dm), tol, max_iters,
+                               iters, rel, st)
+               : fit_ls<double>(H, *cfg, static_cast<const double*>(c), static_cast<double*>(dm), tol, max_iters,
+                                iters, rel, st);
 }
 
 int fewha_bench_stage(fewha_handle* H, int stage, int reps, void* stream) {

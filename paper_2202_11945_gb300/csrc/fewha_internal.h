@@ -135,6 +135,27 @@ __host__ __device__
 #endif
 inline int basis_index(int l, int j, int kind) { return (l * (MAXLEV + 1) + j) * 2 + kind; }
 
+// Least-squares DM fitting over fitting directions (fewha_fit_ls), host tables in double.
+// Pupil node (i, j), i, j = 0 .. n_fit, sits at (x_j, x_i), x_i = -D/2 + i D / n_fit.
+struct LsfitHost {
+    int n_dirs = 0;
+    int nf1 = 0;                        // pupil nodes per side, n_fit + 1
+    int n_pup = 0;                      // pupil nodes inside the annulus
+    std::vector<unsigned char> mask;    // nf1 * nf1, row-major
+    // layer l along direction k, entry (k * MAXL + l) * nf1 + i: grid row (y) / column (x)
+    // i0 of the first node of the linear stencil of pupil row / column i and the weight f of
+    // node i0 + 1 (node i0 has 1 - f)
+    std::vector<int> ly0, lx0;
+    std::vector<double> lfy, lfx;
+    // DM m along direction k, entry (k * MAXM + m) * nf1 + i: the same for the actuator
+    // lattice; i0 and i0 + 1 may leave it (a hat beyond the outer actuators is zero)
+    std::vector<int> my0, mx0;
+    std::vector<double> mfy, mfx;
+    // pupil rows / columns whose stencil touches actuator row / column p of DM m along
+    // direction k, entry (k * MAXM + m) * MAXNACT + p: the range [lo, hi)
+    std::vector<int> ylo, yhi, xlo, xhi;
+};
+
 // Host set-up (fewha_setup.cpp).  Return FEWHA_OK or an error code with a message.
 int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
                 const fewha_layer* layers, int n_layers, const fewha_dm* dms, int n_dms,
@@ -142,6 +163,11 @@ int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
 void db3_taps(double h[6], double g[6]);
 // Spot-elongation constants of every LGS for alpha_eta (Eq. 3); 0 turns them off.
 void set_elongation(HostSetup& s, double alpha_eta);
+// Tables of the least-squares fit over fitting directions (Sec. 4.1) for an instance set
+// up as `s` with central obstruction ratio `obs` and DMs `dms`.  FEWHA_ERR_GEOMETRY if a
+// pupil node along a direction samples a layer outside its grid.
+int build_lsfit(const HostSetup& s, double obs, const fewha_dm* dms, const fewha_lsfit& cfg,
+                LsfitHost& out, std::string& err);
 // Prior D (Sec. 3.1), one value per coefficient.
 void prior_diag(const HostSetup& s, const std::vector<double>& weights, double r0, double L0,
                 std::vector<double>& D);

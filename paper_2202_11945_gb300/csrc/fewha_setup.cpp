@@ -343,6 +343,98 @@ int build_setup(const fewha_telescope& tel, const fewha_wfs* wfs, int n_wfs,
     return FEWHA_OK;
 }
 
+// Least-squares fit over fitting directions (Sec. 4.1): pupil node x along direction
+// theta sees layer l at x + theta h_l (linear stencils on its grid, which they must not
+// leave) and DM m at x + theta h_m (the bilinear hats of its actuators, which are zero
+// beyond the outer ones).
+int build_lsfit(const HostSetup& s, double obs, const fewha_dm* dms, const fewha_lsfit& cfg,
+                LsfitHost& o, std::string& err) {
+    const int K = cfg.n_dirs, nf1 = cfg.n_fit + 1;
+    const int n_layers = static_cast<int>(s.L.size()), n_dms = static_cast<int>(s.Mi.size());
+    const double D = s.D;
+    std::vector<double> xs(nf1);
+    for (int i = 0; i < nf1; ++i) xs[i] = -D / 2 + i * (D / cfg.n_fit);
+    o.n_dirs = K;
+    o.nf1 = nf1;
+    o.mask.assign(static_cast<size_t>(nf1) * nf1, 0);
+    o.n_pup = 0;
+    for (int i = 0; i < nf1; ++i)
+        for (int j = 0; j < nf1; ++j) {
+            const double r = std::hypot(xs[j], xs[i]);
+            if (r >= obs * D / 2 && r <= D / 2) {
+                o.mask[static_cast<size_t>(i) * nf1 + j] = 1;
+                ++o.n_pup;
+            }
+        }
+    if (o.n_pup == 0) { err = "no pupil node of the fitting grid lies in the aperture"; return FEWHA_ERR_GEOMETRY; }
+    o.ly0.assign(static_cast<size_t>(K) * MAXL * nf1, 0);
+    o.lx0 = o.ly0;
+    o.lfy.assign(o.ly0.size(), 0.0);
+    o.lfx = o.lfy;
+    o.my0.assign(static_cast<size_t>(K) * MAXM * nf1, 0);
+    o.mx0 = o.my0;
+    o.mfy.assign(o.my0.size(), 0.0);
+    o.mfx = o.mfy;
+    o.ylo.assign(static_cast<size_t>(K) * MAXM * MAXNACT, 0);
+    o.yhi = o.ylo;
+    o.xlo = o.ylo;
+    o.xhi = o.ylo;
+    for (int k = 0; k < K; ++k) {
+        const double tx = cfg.theta_x[k], ty = cfg.theta_y[k];
+        for (int l = 0; l < n_layers; ++l) {
+            const double h = s.layer_h[l], delta = s.layer_delta[l];
+            const int n = s.L[l].n;
+            const size_t base = (static_cast<size_t>(k) * MAXL + l) * nf1;
+            for (int i = 0; i < nf1; ++i) {
+                int iy, ix;
+                double fy, fx;
+                if (!interp((xs[i] + ty * h) / delta + n / 2, n, iy, fy) ||
+                    !interp((xs[i] + tx * h) / delta + n / 2, n, ix, fx)) {
+                    err = "fitting direction " + std::to_string(k) + " leaves the grid of layer " +
+                          std::to_string(l);
+                    return FEWHA_ERR_GEOMETRY;
+                }
+                o.ly0[base + i] = iy;
+                o.lfy[base + i] = fy;
+                o.lx0[base + i] = ix;
+                o.lfx[base + i] = fx;
+            }
+        }
+        for (int m = 0; m < n_dms; ++m) {
+            const double h = dms[m].h, sp = dms[m].spacing;
+            const int na = dms[m].n_act;
+            const size_t base = (static_cast<size_t>(k) * MAXM + m) * nf1;
+            for (int i = 0; i < nf1; ++i) {
+                const double uy = (xs[i] + ty * h) / sp + (na - 1) / 2.0;
+                const double ux = (xs[i] + tx * h) / sp + (na - 1) / 2.0;
+                const double fly = std::floor(uy), flx = std::floor(ux);
+                // far outside the lattice only the clamp matters: both hats are zero there
+                o.my0[base + i] = static_cast<int>(std::max(-2.0, std::min(fly, double(na) + 1.0)));
+                o.mfy[base + i] = uy - fly;
+                o.mx0[base + i] = static_cast<int>(std::max(-2.0, std::min(flx, double(na) + 1.0)));
+                o.mfx[base + i] = ux - flx;
+            }
+            // pupil rows (columns) i touch actuator row p iff i0[i] is p - 1 or p; i0 is
+            // non-decreasing in i, so they form one range
+            const size_t rb = (static_cast<size_t>(k) * MAXM + m) * MAXNACT;
+            for (int pass = 0; pass < 2; ++pass) {
+                const int* i0 = (pass == 0 ? o.my0.data() : o.mx0.data()) + base;
+                int* lo = (pass == 0 ? o.ylo.data() : o.xlo.data()) + rb;
+                int* hi = (pass == 0 ? o.yhi.data() : o.xhi.data()) + rb;
+                for (int p = 0; p < na; ++p) {
+                    int a = 0;
+                    while (a < nf1 && i0[a] < p - 1) ++a;
+                    int b = a;
+                    while (b < nf1 && i0[b] <= p) ++b;
+                    lo[p] = a;
+                    hi[p] = b > a ? b : a;
+                }
+            }
+        }
+    }
+    return FEWHA_OK;
+}
+
 // D (Sec. 3.1): diagonal approximation of C_phi^-1 in the wavelet domain.  For a
 // level band (detail level j: FFT index box [-n/2^j, n/2^j)^2 minus [-n/2^(j+1),
 // n/2^(j+1))^2; the coarsest approximation: [-n/2^(L+1), n/2^(L+1))^2) the

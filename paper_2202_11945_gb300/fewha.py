@@ -67,6 +67,12 @@ class Params(ctypes.Structure):
                 ("alpha_eta", ctypes.c_double), ("warm_refresh", ctypes.c_int)]
 
 
+class LsFit(ctypes.Structure):
+    _fields_ = [("n_dirs", ctypes.c_int), ("theta_x", ctypes.POINTER(ctypes.c_double)),
+                ("theta_y", ctypes.POINTER(ctypes.c_double)), ("weight", ctypes.POINTER(ctypes.c_double)),
+                ("n_fit", ctypes.c_int), ("eps", ctypes.c_double)]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("groups", ctypes.c_int), ("vec_passes", ctypes.c_int),
                 ("pair_threads", ctypes.c_int), ("proj_taps", ctypes.c_int), ("vec_threads", ctypes.c_int)]
@@ -86,7 +92,7 @@ EXPORTS = ["fewha_create", "fewha_destroy", "fewha_last_error", "fewha_create_er
            "fewha_batch_reconstruct", "fewha_batch_autotune", "fewha_reconstruct_batched",
            "fewha_reconstruct_batched_f64", "fewha_get_state", "fewha_set_state", "fewha_solve",
            "fewha_reconstruct_converged", "fewha_backward", "fewha_get_residual", "fewha_frame_vjp",
-           "fewha_set_wait_limit", "fewha_device_bytes", "fewha_test_fail_alloc"] + _OPS
+           "fewha_set_wait_limit", "fewha_device_bytes", "fewha_test_fail_alloc", "fewha_fit_ls"] + _OPS
 
 STAGES = {"idwt": 0, "sensor": 1, "layer": 2, "vector": 3, "rhs": 4, "fit": 5, "proj": 6,
           "projT": 7}
@@ -132,6 +138,7 @@ def lib():
     for name in ["fewha_solve", "fewha_reconstruct_converged"]:
         getattr(L, name).argtypes = [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ip, dp, _VP]
     L.fewha_backward.argtypes = [_VP, _VP, _VP, dp, dp, _VP]
+    L.fewha_fit_ls.argtypes = [_VP, ctypes.POINTER(LsFit), _VP, _VP, ctypes.c_double, ctypes.c_int, ip, dp, _VP]
     L.fewha_get_state.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_set_state.argtypes = [_VP, _VP, _VP, _VP]
     L.fewha_get_residual.argtypes = [_VP, _VP, _VP, _VP]
@@ -456,6 +463,28 @@ class Reconstructor:
             self.h, self._dev(slopes, self.n_slopes, "slopes"), self._dev(dm_out, self.n_act, "dm_out"),
             self.default_tol() if tol is None else float(tol), int(max_iters), ctypes.byref(it),
             ctypes.byref(rel), _stream(stream)))
+        return dm_out, it.value, rel.value
+
+    def fit_ls(self, c, directions, weights, n_fit, eps, tol=None, max_iters=5000, dm_out=None, stream=None):
+        """Least-squares DM fit of the layers W^T c over fitting directions ((theta_x,
+        theta_y) pairs in rad, with weights), on n_fit + 1 pupil nodes per side with
+        Tikhonov weight eps.  Returns (commands, CG iterations, relative residual); the
+        default tol is 1e-7 in single and 1e-12 in double precision."""
+        if dm_out is None:
+            dm_out = self._new(self.n_act)
+        if tol is None:
+            tol = 1e-7 if self.dtype == torch.float32 else 1e-12
+        k = len(directions)
+        if len(weights) != k:
+            raise ValueError("need one weight per fitting direction")
+        tx = (ctypes.c_double * k)(*[float(d[0]) for d in directions])
+        ty = (ctypes.c_double * k)(*[float(d[1]) for d in directions])
+        w = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
+        cfg = LsFit(k, tx, ty, w, int(n_fit), float(eps))
+        it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.L.fewha_fit_ls(self.h, ctypes.byref(cfg), self._dev(c, self.n_coeffs, "c"),
+                                        self._dev(dm_out, self.n_act, "dm_out"), float(tol), int(max_iters),
+                                        ctypes.byref(it), ctypes.byref(rel), _stream(stream)))
         return dm_out, it.value, rel.value
 
     def backward(self, grad_dm, stream=None):

@@ -99,7 +99,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no host C compiler")
     structs = {"fewha_telescope": fewha.Telescope, "fewha_wfs": fewha.Wfs, "fewha_layer": fewha.Layer,
-               "fewha_dm": fewha.Dm, "fewha_params": fewha.Params, "fewha_batch_config": fewha.BatchConfig}
+               "fewha_dm": fewha.Dm, "fewha_params": fewha.Params, "fewha_batch_config": fewha.BatchConfig,
+               "fewha_lsfit": fewha.LsFit}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fewha.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
