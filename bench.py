@@ -639,6 +639,41 @@ def time_paper_geometry(flush, steps, parity=True):
     return out
 
 
+def time_ls_fit(wl, reps=3):
+    """Least-squares DM fitting over fitting directions (fewha_fit_ls, Sec. 4.1) on the
+    MAORY geometry: a 3 x 3 grid of directions 20 arcsec apart, 81 x 81 pupil nodes,
+    eps = 1e-2, seeded random coefficients.  Wall time per call (the CG is host-paced: a
+    convergence check every 64 steps), CG steps to 1e-7 (FP32) / 1e-12 (FP64), and the
+    FP32 commands against the FP64 ones (oracle parity is in the GPU tests)."""
+    from paper_2202_11945_gb300 import Reconstructor
+    dirs = [(synth.arcsec(x), synth.arcsec(y)) for y in (-20, 0, 20) for x in (-20, 0, 20)]
+    w, n_fit, eps = [1.0] * 9, 80, 1e-2
+    out = {"directions": "3 x 3 grid, 20 arcsec apart", "n_fit": n_fit, "eps": eps,
+           "input": "seeded random wavelet coefficients"}
+    try:
+        res = {}
+        for prec in (32, 64):
+            R = Reconstructor(wl, precision=prec, graph=False)
+            dt = torch.float32 if prec == 32 else torch.float64
+            c_np = np.random.default_rng(11).standard_normal(R.n_coeffs)
+            c = torch.as_tensor(c_np, dtype=dt, device="cuda")
+            R.fit_ls(c, dirs, w, n_fit, eps)
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                a, it, rel = R.fit_ls(c, dirs, w, n_fit, eps)
+                ts.append(time.perf_counter() - t0)
+            res[prec] = a.double().cpu().numpy()
+            out["fp%d" % prec] = {"ms_per_call": 1e3 * float(np.median(ts)), "cg_steps": it,
+                                  "us_per_step": 1e6 * float(np.median(ts)) / max(it, 1),
+                                  "rel_residual": rel}
+            R.close()
+        out["fp32_vs_fp64_rel_l2"] = float(np.linalg.norm(res[32] - res[64]) / np.linalg.norm(res[64]))
+    except Exception as e:  # a failing leg is reported, not fatal to the line
+        out["error"] = "%s: %s" % (type(e).__name__, e)
+    return out
+
+
 def time_unrolled(wl, S_np, reps=10, parity=True):
     """Reverse mode through the fixed-iteration MAORY frame (fewha_frame_vjp): wall time of
     forward + reverse per call (synchronous), FP32 and FP64, and the FP32 gradient against
@@ -819,6 +854,7 @@ def main():
     paper = (time_paper_geometry(flush, args.aug_steps, parity=(rank == 0 and world == 1))
              if args.aug_steps > 0 else None)
     unrolled = time_unrolled(wl, S_np, parity=(rank == 0 and world == 1)) if args.backward_frames > 0 else None
+    lsfit = time_ls_fit(wl) if args.aug_steps > 0 else None
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")
@@ -869,6 +905,7 @@ def main():
             "footprint": foot,
             "paper_geometry": paper,
             "unrolled_backward": unrolled,
+            "ls_fit": lsfit,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):

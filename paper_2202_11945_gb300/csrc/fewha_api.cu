@@ -55,6 +55,7 @@ struct LsfitDev {
     void *lfy = nullptr, *lfx = nullptr, *mfy = nullptr, *mfx = nullptr;
     void *v = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     double* part = nullptr;
+    double* msum = nullptr;
     double* sc = nullptr;
     int* state = nullptr;
     size_t cap_pix = 0, cap_l = 0, cap_lf = 0, cap_m = 0, cap_mf = 0, cap_rng = 0, cap_v = 0;
@@ -2080,7 +2081,8 @@ int ensure_lsfit(fewha_handle* H, const fewha_lsfit& cfg) {
     const size_t nb = (n_a + LSF_ABLK - 1) / LSF_ABLK;
     if (!F.state) {   // allocated last: all of them are there
         if ((rc = talloc(H, &F.r, n_a)) || (rc = talloc(H, &F.p, n_a)) || (rc = talloc(H, &F.q, n_a)) ||
-            (rc = dalloc(H, &F.part, nb)) || (rc = dalloc(H, &F.sc, 2)) || (rc = dalloc(H, &F.state, 2)))
+            (rc = dalloc(H, &F.part, nb)) || (rc = dalloc(H, &F.msum, LSF_MAXSL)) || (rc = dalloc(H, &F.sc, 2)) ||
+            (rc = dalloc(H, &F.state, 2)))
             return rc;
     }
     if ((rc = lsf_grow<unsigned char>(H, {&F.mask}, &F.cap_pix, L.mask.size())) ||
@@ -2110,6 +2112,9 @@ LsDesc<T> lsf_desc(const fewha_handle* H, const fewha_lsfit& cfg) {
     d.n_dirs = F.host.n_dirs;
     d.nf1 = F.host.nf1;
     d.n_pup = F.host.n_pup;
+    // slices of each direction's pupil grid: about one node per thread, at most LSF_MAXSL
+    // (direction, slice) CTAs in all
+    d.n_slices = std::max(1, std::min((d.nf1 * d.nf1 + LSF_SBLK - 1) / LSF_SBLK, LSF_MAXSL / d.n_dirs));
     d.n_layers = static_cast<int>(S.L.size());
     d.n_dms = static_cast<int>(S.Mi.size());
     d.n_a = S.n_act;
@@ -2155,8 +2160,9 @@ int fit_ls(fewha_handle* H, const fewha_lsfit& cfg, const T* c, T* a, double tol
     T* p = static_cast<T*>(F.p);
     T* q = static_cast<T*>(F.q);
     const int nb = (ld.n_a + LSF_ABLK - 1) / LSF_ABLK;
-    k_lsf_sample<T, true><<<ld.n_dirs, LSF_SBLK, 0, st>>>(ld, phi, v, nullptr);
-    k_lsf_adj<T><<<nb, LSF_ABLK, 0, st>>>(ld, v, nullptr, q, nullptr, nullptr);
+    const dim3 sgrid(ld.n_slices, ld.n_dirs);
+    k_lsf_sample<T, true><<<sgrid, LSF_SBLK, 0, st>>>(ld, phi, v, F.msum, nullptr);
+    k_lsf_adj<T><<<nb, LSF_ABLK, 0, st>>>(ld, v, F.msum, nullptr, q, nullptr, nullptr);
     LsCg<T> g{};
     g.n = ld.n_a;
     g.nparts = nb;
@@ -2177,8 +2183,8 @@ int fit_ls(fewha_handle* H, const fewha_lsfit& cfg, const T* c, T* a, double tol
     for (;;) {
         const int k = std::min(FEWHA_MAX_ITERS, max_iters - run);
         for (int j = 0; j < k; ++j) {
-            k_lsf_sample<T, false><<<ld.n_dirs, LSF_SBLK, 0, st>>>(ld, p, v, F.state);
-            k_lsf_adj<T><<<nb, LSF_ABLK, 0, st>>>(ld, v, p, q, F.part, F.state);
+            k_lsf_sample<T, false><<<sgrid, LSF_SBLK, 0, st>>>(ld, p, v, F.msum, F.state);
+            k_lsf_adj<T><<<nb, LSF_ABLK, 0, st>>>(ld, v, F.msum, p, q, F.part, F.state);
             k_lsf_cg<T, false><<<1, LSF_CBLK, 0, st>>>(g);
         }
         CK(cudaGetLastError(), "fit_ls launch");

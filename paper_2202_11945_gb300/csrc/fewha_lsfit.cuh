@@ -6,11 +6,13 @@
 // layer grids) and the DMs (A_k, bilinear actuator hats), and Pi removes the mean over
 // the pupil nodes.  The normal equations N a = sum_k w_k A_k^T Pi L_k phi,
 // N = sum_k w_k A_k^T Pi A_k + eps I, are solved by CG.  One CG step is three kernels:
-//   k_lsf_sample<DM>  one CTA per direction: v_k = Pi A_k p on the pupil grid (the mean
-//                     over the pupil nodes is a fixed-order block sum in double);
-//   k_lsf_adj         one thread per actuator: q = sum_k w_k A_k^T v_k + eps p, gathered
-//                     over the pupil rows and columns whose stencils touch the actuator
-//                     (host-built ranges, no atomics), and per-CTA shares of p.q;
+//   k_lsf_sample<DM>  a grid of (slices, directions): u_k = A_k p on the pupil nodes of a
+//                     slice (zero off the pupil) and the slice's sum of u_k in double;
+//   k_lsf_adj         one thread per actuator: the means of the u_k from the slice sums in
+//                     a fixed order, then q = sum_k w_k A_k^T Pi u_k + eps p, gathered over
+//                     the pupil rows and columns whose stencils touch the actuator
+//                     (host-built ranges, no atomics; Pi applied on the fly), and per-CTA
+//                     shares of p.q;
 //   k_lsf_cg          one CTA: the p.q total in a fixed order, the CG step, r.r.
 // The right-hand side is k_lsf_sample<LAYER> on phi followed by k_lsf_adj without p.
 // Once the CG has stopped (state[0] != 0) the kernels of the remaining steps of a chunk
@@ -21,7 +23,8 @@
 
 namespace fewha {
 
-constexpr int LSF_SBLK = 512;    // k_lsf_sample: threads per direction
+constexpr int LSF_SBLK = 256;    // k_lsf_sample: threads per slice of a direction's pupil grid
+constexpr int LSF_MAXSL = 304;   // most (direction, slice) CTAs of k_lsf_sample (2 per SM)
 constexpr int LSF_ABLK = 256;    // k_lsf_adj: actuators per CTA
 constexpr int LSF_CBLK = 1024;   // k_lsf_cg: the single CTA
 constexpr int LSF_MAXK = FEWHA_MAX_FIT_DIRS;
@@ -29,6 +32,7 @@ constexpr int LSF_MAXK = FEWHA_MAX_FIT_DIRS;
 template <class T>
 struct LsDesc {
     int n_dirs, nf1, n_pup, n_layers, n_dms, n_a;
+    int n_slices;                        // k_lsf_sample CTAs per direction
     int lay_n[MAXL], lay_off[MAXL];
     int dm_n[MAXM], dm_off[MAXM];
     T w[LSF_MAXK];
@@ -71,11 +75,12 @@ __host__ __device__ inline T lsf_sample(const LsDesc<T>& d, const T* src, int k,
     return val;
 }
 
-// (sum_k w_k A_k^T v_k) at actuator (p, q) of DM m: the pupil rows [ylo, yhi) and columns
-// [xlo, xhi) are those whose stencils include the actuator; its hat weight in each is the
-// stencil weight on that actuator.
+// (sum_k w_k A_k^T Pi u_k) at actuator (p, q) of DM m, u_k zero off the pupil and mean[k]
+// its mean over the pupil nodes: the pupil rows [ylo, yhi) and columns [xlo, xhi) are those
+// whose stencils include the actuator; its hat weight in each is the stencil weight on that
+// actuator.
 template <class T>
-__host__ __device__ inline T lsf_adjoint(const LsDesc<T>& d, const T* v, int m, int p, int q) {
+__host__ __device__ inline T lsf_adjoint(const LsDesc<T>& d, const T* v, const T* mean, int m, int p, int q) {
     T acc = T(0);
     const int nf1 = d.nf1;
     for (int k = 0; k < d.n_dirs; ++k) {
@@ -83,6 +88,7 @@ __host__ __device__ inline T lsf_adjoint(const LsDesc<T>& d, const T* v, int m, 
         const int ylo = d.ylo[e * MAXNACT + p], yhi = d.yhi[e * MAXNACT + p];
         const int xlo = d.xlo[e * MAXNACT + q], xhi = d.xhi[e * MAXNACT + q];
         const T* vk = v + static_cast<size_t>(k) * nf1 * nf1;
+        const T mk = mean[k];
         T sk = T(0);
         for (int i = ylo; i < yhi; ++i) {
             const int y0 = d.my0[e * nf1 + i];
@@ -92,7 +98,8 @@ __host__ __device__ inline T lsf_adjoint(const LsDesc<T>& d, const T* v, int m, 
             for (int j = xlo; j < xhi; ++j) {
                 const int x0 = d.mx0[e * nf1 + j];
                 const T fx = d.mfx[e * nf1 + j];
-                row += (x0 == q ? T(1) - fx : fx) * vk[i * nf1 + j];
+                const int g = i * nf1 + j;
+                row += (x0 == q ? T(1) - fx : fx) * (vk[g] - mk * static_cast<T>(d.mask[g]));
             }
             sk += wy * row;
         }
@@ -116,16 +123,19 @@ __device__ __forceinline__ double lsf_block_sum(double v) {
     return t;
 }
 
-// v_k = Pi (A_k src) (DMs) or Pi (L_k src) (layers) on the full nf1 x nf1 pupil grid of
-// direction k = blockIdx.x, zero outside the pupil.
+// u_k = A_k src (DMs) or L_k src (layers) on slice blockIdx.x of the nf1 x nf1 pupil grid
+// of direction k = blockIdx.y, zero off the pupil, and the slice's sum of u_k (msum).
 template <class T, bool LAYER>
-__global__ void __launch_bounds__(LSF_SBLK) k_lsf_sample(LsDesc<T> d, const T* src, T* v, const int* state) {
+__global__ void __launch_bounds__(LSF_SBLK) k_lsf_sample(LsDesc<T> d, const T* src, T* v, double* msum,
+                                                         const int* state) {
     if (state && state[0]) return;
-    const int k = blockIdx.x;
+    const int k = blockIdx.y;
     const int nf1 = d.nf1, npix = nf1 * nf1;
+    const int chunk = (npix + d.n_slices - 1) / d.n_slices;
+    const int g0 = blockIdx.x * chunk, g1 = min(npix, g0 + chunk);
     T* vk = v + static_cast<size_t>(k) * npix;
     double acc = 0.0;
-    for (int g = threadIdx.x; g < npix; g += LSF_SBLK) {
+    for (int g = g0 + threadIdx.x; g < g1; g += LSF_SBLK) {
         T val = T(0);
         if (d.mask[g]) {
             const int i = g / nf1;
@@ -134,17 +144,23 @@ __global__ void __launch_bounds__(LSF_SBLK) k_lsf_sample(LsDesc<T> d, const T* s
         }
         vk[g] = val;
     }
-    const T mean = static_cast<T>(lsf_block_sum<LSF_SBLK>(acc) / d.n_pup);
-    for (int g = threadIdx.x; g < npix; g += LSF_SBLK)   // each thread re-reads its own nodes
-        if (d.mask[g]) vk[g] -= mean;
+    const double t = lsf_block_sum<LSF_SBLK>(acc);
+    if (threadIdx.x == 0) msum[k * d.n_slices + blockIdx.x] = t;
 }
 
-// out = sum_k w_k A_k^T v_k (+ eps x, and the CTA's share of x.out into part, when x is
-// given).
+// out = sum_k w_k A_k^T Pi u_k (+ eps x, and the CTA's share of x.out into part, when x is
+// given); the mean of u_k is its slice sums (msum) added in slice order over n_pup.
 template <class T>
-__global__ void __launch_bounds__(LSF_ABLK) k_lsf_adj(LsDesc<T> d, const T* v, const T* x, T* out, double* part,
-                                                      const int* state) {
+__global__ void __launch_bounds__(LSF_ABLK) k_lsf_adj(LsDesc<T> d, const T* v, const double* msum, const T* x,
+                                                      T* out, double* part, const int* state) {
     if (state && state[0]) return;
+    __shared__ T s_mean[LSF_MAXK];
+    if (threadIdx.x < d.n_dirs) {
+        double t = 0.0;
+        for (int sl = 0; sl < d.n_slices; ++sl) t += msum[threadIdx.x * d.n_slices + sl];
+        s_mean[threadIdx.x] = static_cast<T>(t / d.n_pup);
+    }
+    __syncthreads();
     const int a = blockIdx.x * LSF_ABLK + threadIdx.x;
     double pq = 0.0;
     if (a < d.n_a) {
@@ -152,7 +168,7 @@ __global__ void __launch_bounds__(LSF_ABLK) k_lsf_adj(LsDesc<T> d, const T* v, c
         while (m + 1 < d.n_dms && a >= d.dm_off[m + 1]) ++m;
         const int n = d.dm_n[m], loc = a - d.dm_off[m];
         const int p = loc / n;
-        T val = lsf_adjoint<T>(d, v, m, p, loc - p * n);
+        T val = lsf_adjoint<T>(d, v, s_mean, m, p, loc - p * n);
         if (x) {
             const T xa = x[a];
             val += d.eps * xa;
