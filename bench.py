@@ -516,6 +516,35 @@ def time_augmented(wl, S32, S_np, flush, steps, parity=True):
     return out
 
 
+def time_iteration_sweep(wl, S32, flush, steps, iters=(1, 2, 3, 4, 6, 8)):
+    """Frame time against the PCG iteration count (the paper finds its run-time linear in
+    the iterations, Sec. 4.3): the FP32 graph form of the MAORY frame at each count, and the
+    least-squares line through the mean frame times (its slope is one iteration, its
+    intercept the initial residual and the fit)."""
+    from paper_2202_11945_gb300 import Reconstructor
+    out = {"workload": wl["name"], "form": "FP32 operators, FP64 dots, CUDA graph", "steps": steps}
+    try:
+        ms = []
+        for it in iters:
+            R = Reconstructor(wl, precision=32, graph=True)
+            if it != wl["params"]["iters"]:
+                R.update_params(iters=it)
+            dm = torch.empty(R.n_act, dtype=torch.float32, device="cuda")
+            t = time_frames(R, S32, steps, 20, flush, dm)
+            ms.append(float(t.mean()))
+            out["iters%d" % it] = {"frames_per_s": 1e3 / ms[-1], "mean_ms": ms[-1],
+                                   "p99_ms": float(np.percentile(t, 99)), "launches_per_frame": R.frame_launches()}
+            R.close()
+        slope, icpt = np.polyfit(np.array(iters, float), np.array(ms), 1)
+        line = icpt + slope * np.array(iters, float)
+        out["us_per_iteration"] = 1e3 * float(slope)
+        out["us_fixed"] = 1e3 * float(icpt)
+        out["max_rel_deviation_from_line"] = float(np.max(np.abs(line - np.array(ms)) / np.array(ms)))
+    except Exception as e:  # a failing leg is reported, not fatal to the line
+        out["error"] = "%s: %s" % (type(e).__name__, e)
+    return out
+
+
 def time_persistent(wl, S32, S_np, flush, steps, parity=True):
     """The persistent frame (one cooperative launch per frame, grid-wide waits between the
     stages) on the MAORY workload, FP32 and graph-captured, against the graph of separate
@@ -855,6 +884,7 @@ def main():
              if args.aug_steps > 0 else None)
     unrolled = time_unrolled(wl, S_np, parity=(rank == 0 and world == 1)) if args.backward_frames > 0 else None
     lsfit = time_ls_fit(wl) if args.aug_steps > 0 else None
+    sweep = time_iteration_sweep(wl, S32, flush, args.aug_steps) if args.aug_steps > 0 else None
 
     total32, total64, tot_e2e = max_over_ranks([float(t32.sum()), float(t64.sum()), float(te.sum())],
                                                world, "cuda")
@@ -906,6 +936,7 @@ def main():
             "paper_geometry": paper,
             "unrolled_backward": unrolled,
             "ls_fit": lsfit,
+            "iteration_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     for R in (R32, R64, Re):
