@@ -64,7 +64,7 @@ Readings where the paper is silent or garbled:
       is sigma^-2 (I - gamma beta beta^T), gamma = c / (1 + c |beta|^2), c = alpha_eta^2
       / f^2, and C_hat^-1 = (I - T) C^-1 (I - T) no longer collapses to sigma^-2 (I - T).
       Elongation is on for an LGS when alpha_eta, FWHM and f are all > 0.
-  R30 least-squares DM fitting (the "additional minimization problem" of Sec. 4.1): the
+  R30 least-squares DM fitting (Sec. 4.1: more layers than DMs need a fit of their own): the
       commands minimise sum_k w_k ||Pi (A_k a - L_k phi)||^2 + eps ||a||^2, where along
       fitting direction theta_k the pupil nodes x (spacing D / n_fit, inside the annulus)
       see the layers at x + theta_k h_l (bilinear, R5) and the DMs at x + theta_k h_m
