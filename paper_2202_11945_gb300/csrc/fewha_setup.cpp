@@ -435,7 +435,7 @@ int build_lsfit(const HostSetup& s, double obs, const fewha_dm* dms, const fewha
     return FEWHA_OK;
 }
 
-// D (Sec. 3.1): diagonal approximation of C_phi^-1 in the wavelet domain.  For a
+// D (Sec. 3.1): a diagonal stand-in for C_phi^-1 on the wavelet coefficients.  For a
 // level band (detail level j: FFT index box [-n/2^j, n/2^j)^2 minus [-n/2^(j+1),
 // n/2^(j+1))^2; the coarsest approximation: [-n/2^(L+1), n/2^(L+1))^2) the
 // coefficient variance is the band mean of (n dk)^2 w Phi(|k| dk), dk = 1/(n delta),
