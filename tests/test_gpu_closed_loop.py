@@ -41,8 +41,14 @@ def recon(wl, prec, **kw):
 
 
 def check(a, a_ref, geo, tol, what):
-    """Each DM's commands without their mean within tol (the layers' piston is unseen by
-    the slopes and set by the prior alone), the full commands within 10 tol."""
+    """Each DM's commands without their mean within tol, the full commands within 10 tol.
+
+    The layers' piston is unseen by the slopes and set by the prior alone, so the oracle's
+    own rounding in it is amplified (by 1 / (alpha D_LL) ~ 1e5) and the integrator of the
+    closed-loop law accumulates it over the frames; it reaches the commands only as a
+    constant per DM.  The two checks together show that everything beyond the frame
+    tolerance lies in the per-DM means: the error orthogonal to them, the part the slopes
+    determine, is held to the frame tolerance itself."""
     assert rel_l2(a, a_ref) <= 10 * tol, (what, rel_l2(a, a_ref))
     for m in geo.dms:
         sl = slice(m["off"], m["off"] + m["n_act"] ** 2)
