@@ -42,16 +42,17 @@ def _compile(src, extra):
     return out, r.stderr
 
 
-def build(verbose=False, extra=()):
+def build(verbose=False, extra=(), nvtx=False):
+    """Compile and link the library; nvtx=True adds NVTX ranges around the entry points."""
     os.makedirs(OBJ, exist_ok=True)
-    extra = list(extra)
+    extra = list(extra) + (["-DFEWHA_NVTX"] if nvtx else [])
     if verbose:
         extra = extra + ["-Xptxas", "-v"]
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"] + (["-ldl"] if nvtx else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
@@ -63,4 +64,4 @@ def build(verbose=False, extra=()):
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, nvtx="--nvtx" in sys.argv))

@@ -15,10 +15,25 @@
 #include <vector>
 
 #include "fewha_batch.h"
+#ifdef FEWHA_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
 #include "fewha_lsfit.cuh"
 #include "fewha_persist.cuh"
 
 using namespace fewha;
+
+// Optional NVTX ranges around the entry points (build with -DFEWHA_NVTX), so that a
+// timeline tool shows each call's span over its kernels; compiled out otherwise.
+#ifdef FEWHA_NVTX
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define FEWHA_RANGE(name) NvtxRange fewha_nvtx_range_(name)
+#else
+#define FEWHA_RANGE(name) ((void)0)
+#endif
 
 namespace {
 
@@ -3028,6 +3043,7 @@ const char* fewha_last_error(const fewha_handle* h) { return h ? h->err.c_str() 
 int fewha_create(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, const fewha_layer* layers,
                  int n_layers, const fewha_dm* dms, int n_dms, const fewha_params* params,
                  fewha_handle** out) {
+    FEWHA_RANGE("fewha_create");
     g_create_error.clear();
     if (!out) {
         g_create_error = "out is NULL";
@@ -3099,6 +3115,7 @@ int fewha_sizes(const fewha_handle* h, int64_t* n_slopes, int64_t* n_coeffs, int
 
 int fewha_update_params(fewha_handle* H, const fewha_params* params, const double* cn2_weights,
                         const double* sigmas) {
+    FEWHA_RANGE("fewha_update_params");
     if (!H) return FEWHA_ERR_INVALID_ARG;
     std::string e;
     int rc = check_params(params, e);
@@ -3148,24 +3165,30 @@ int fewha_reset(fewha_handle* H, void* stream) {
 }
 
 int fewha_reconstruct(fewha_handle* h, const float* s, float* x, float* dm, void* stream) {
+    FEWHA_RANGE("fewha_reconstruct");
     return reconstruct_dev<float>(h, s, x, dm, stream);
 }
 int fewha_reconstruct_f64(fewha_handle* h, const double* s, double* x, double* dm, void* stream) {
+    FEWHA_RANGE("fewha_reconstruct_f64");
     return reconstruct_dev<double>(h, s, x, dm, stream);
 }
 int fewha_reconstruct_host(fewha_handle* h, const float* s, float* dm, void* stream) {
+    FEWHA_RANGE("fewha_reconstruct_host");
     return reconstruct_host<float>(h, s, dm, stream);
 }
 int fewha_reconstruct_host_f64(fewha_handle* h, const double* s, double* dm, void* stream) {
+    FEWHA_RANGE("fewha_reconstruct_host_f64");
     return reconstruct_host<double>(h, s, dm, stream);
 }
 
 int fewha_run_loop(fewha_handle* h, const float* s, int n_frames, float* dm, double period_us,
                    float* wall_us, float* device_us, int* n_late, void* stream) {
+    FEWHA_RANGE("fewha_run_loop");
     return run_loop<float>(h, s, n_frames, dm, period_us, wall_us, device_us, n_late, stream);
 }
 int fewha_run_loop_f64(fewha_handle* h, const double* s, int n_frames, double* dm, double period_us,
                        float* wall_us, float* device_us, int* n_late, void* stream) {
+    FEWHA_RANGE("fewha_run_loop_f64");
     return run_loop<double>(h, s, n_frames, dm, period_us, wall_us, device_us, n_late, stream);
 }
 
@@ -3201,6 +3224,7 @@ int fewha_batch_get_config(const fewha_batch* b, fewha_batch_config* cfg) {
     return FEWHA_OK;
 }
 int fewha_batch_reconstruct(fewha_batch* b, const void* const* s, void* const* dm, void* stream) {
+    FEWHA_RANGE("fewha_batch_reconstruct");
     if (!b) return FEWHA_ERR_INVALID_ARG;
     return b->precision == 32 ? batch_run<float>(b, s, dm, stream) : batch_run<double>(b, s, dm, stream);
 }
@@ -3212,11 +3236,13 @@ int fewha_batch_autotune(fewha_batch* b, const void* const* s, void* const* dm, 
 }
 int fewha_reconstruct_batched(fewha_handle* const* hs, int count, const float* const* s, float* const* dm,
                               void* stream) {
+    FEWHA_RANGE("fewha_reconstruct_batched");
     if (hs && count > 0 && hs[0] && hs[0]->precision != 32) return fail(hs[0], FEWHA_ERR_INVALID_ARG, "precision mismatch");
     return reconstruct_batched<float>(hs, count, s, dm, stream);
 }
 int fewha_reconstruct_batched_f64(fewha_handle* const* hs, int count, const double* const* s, double* const* dm,
                                   void* stream) {
+    FEWHA_RANGE("fewha_reconstruct_batched_f64");
     if (hs && count > 0 && hs[0] && hs[0]->precision != 64) return fail(hs[0], FEWHA_ERR_INVALID_ARG, "precision mismatch");
     return reconstruct_batched<double>(hs, count, s, dm, stream);
 }
@@ -3259,6 +3285,7 @@ int fewha_get_residual(fewha_handle* H, void* r, void* b, void* stream) {
 
 int fewha_solve(fewha_handle* H, const void* b, void* x, double tol, int max_iters, int* iters,
                 double* rel, void* stream) {
+    FEWHA_RANGE("fewha_solve");
     if (!H) return FEWHA_ERR_INVALID_ARG;
     if (!b || !x || !(tol >= 0.0) || max_iters < 0) return fail(H, FEWHA_ERR_INVALID_ARG, "bad solve arguments");
     DeviceGuard g(H->device);
@@ -3272,6 +3299,7 @@ int fewha_solve(fewha_handle* H, const void* b, void* x, double tol, int max_ite
 
 int fewha_reconstruct_converged(fewha_handle* H, const void* s, void* dm, double tol, int max_iters,
                                 int* iters, double* rel, void* stream) {
+    FEWHA_RANGE("fewha_reconstruct_converged");
     if (!H) return FEWHA_ERR_INVALID_ARG;
     if (!s || !dm || !(tol >= 0.0) || max_iters < 0) return fail(H, FEWHA_ERR_INVALID_ARG, "bad arguments");
     DeviceGuard g(H->device);
@@ -3284,6 +3312,7 @@ int fewha_reconstruct_converged(fewha_handle* H, const void* s, void* dm, double
 }
 
 int fewha_backward(fewha_handle* H, const void* g_dm, void* g_s, double* g_alpha, double* g_cn2, void* stream) {
+    FEWHA_RANGE("fewha_backward");
     if (!H) return FEWHA_ERR_INVALID_ARG;
     if (!g_dm) return fail(H, FEWHA_ERR_INVALID_ARG, "null gradient of the commands");
     DeviceGuard g(H->device);
@@ -3296,6 +3325,7 @@ int fewha_backward(fewha_handle* H, const void* g_dm, void* g_s, double* g_alpha
 
 int fewha_frame_vjp(fewha_handle* H, const void* s, const void* c0, const void* g_dm, void* dm, void* g_s,
                     void* stream) {
+    FEWHA_RANGE("fewha_frame_vjp");
     if (!H) return FEWHA_ERR_INVALID_ARG;
     if (!s || !c0 || (g_dm && !g_s)) return fail(H, FEWHA_ERR_INVALID_ARG, "null slopes, warm start or gradient output");
     DeviceGuard g(H->device);
@@ -3341,6 +3371,7 @@ int fewha_pcg(fewha_handle* h, const void* b, void* c, int iters, void* st) {
 
 int fewha_fit_ls(fewha_handle* H, const fewha_lsfit* cfg, const void* c, void* dm, double tol, int max_iters,
                  int* iters, double* rel, void* stream) {
+    FEWHA_RANGE("fewha_fit_ls");
     if (!H) return FEWHA_ERR_INVALID_ARG;
     if (!c || !dm || !(tol >= 0.0) || max_iters < 0) return fail(H, FEWHA_ERR_INVALID_ARG, "bad fit_ls arguments");
     int rc = check_lsfit(H, cfg);
