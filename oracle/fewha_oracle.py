@@ -540,7 +540,7 @@ def von_karman_psd(kappa, r0, L0):
 
 
 def prior_diag(geo, r0=None, L0=None, weights=None):
-    """D: diagonal approximation of C_phi^-1 in the wavelet domain (Sec. 3.1, R8).
+    """D: a diagonal stand-in for C_phi^-1 on the wavelet coefficients (Sec. 3.1, R8).
 
     For layer l (grid n, spacing delta, Cn2 weight w_l) and level band B (detail
     level j: FFT index box [-n/2^j, n/2^j)^2 minus [-n/2^(j+1), n/2^(j+1))^2; the LL
