@@ -78,3 +78,27 @@ extern "C" int setup_tables(const fewha_telescope* tel, const fewha_wfs* wfs, in
     }
     return 0;
 }
+
+// The closed loop's DM stencils of each (sensor, DM) pair, entry (g * MAXM + m) * TAB + a,
+// and, after set_elongation(alpha_eta), per sensor the ten elongation constants (on flag,
+// k, c, launch x and y, first midpoint, pitch, K11, K12, K22) at g * 10.
+extern "C" int setup_extra(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, const fewha_layer* layers,
+                           int n_layers, const fewha_dm* dms, int n_dms, double alpha_eta, int* qi0y, int* qi0x,
+                           double* qfy, double* qfx, double* el) {
+    HostSetup s;
+    std::string err;
+    const int rc = build_setup(*tel, wfs, n_wfs, layers, n_layers, dms, n_dms, s, err);
+    if (rc) return rc;
+    put(qi0y, s.qi0y);
+    put(qi0x, s.qi0x);
+    put(qfy, s.qfy);
+    put(qfx, s.qfx);
+    set_elongation(s, alpha_eta);
+    for (size_t g = 0; g < s.G.size(); ++g) {
+        const WfsInfo& W = s.G[g];
+        const double v[10] = {double(W.el), W.el_k, W.el_c, W.el_lx, W.el_ly, W.el_x0, W.el_d,
+                              W.el_K11, W.el_K12, W.el_K22};
+        for (int q = 0; q < 10; ++q) el[g * 10 + q] = v[q];
+    }
+    return 0;
+}

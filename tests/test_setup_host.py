@@ -156,3 +156,62 @@ def test_db3_taps_match_the_oracle(H):
     h, g = O.db3_filters()
     assert np.abs(t["taps"][:6] - h).max() <= 1e-15
     assert np.abs(t["taps"][6:] - g).max() <= 1e-15
+
+
+def extra(H, name):
+    from paper_2202_11945_gb300 import fewha
+    wl, geo, t = tables(H, name)
+    tel, wfs, layers, dms, _ = fewha.structs_from_workload(wl, 64)
+    n = len(t["pi0y"]) // t["MAXL"] * t["MAXM"]                # MAXG * MAXM * TAB
+    q = {k: np.zeros(n, np.int32 if k.startswith("qi") else float) for k in ("qi0y", "qi0x", "qfy", "qfx")}
+    el = np.zeros(10 * len(wl["wfs"]))
+    rc = H.setup_extra(ctypes.byref(tel), wfs, len(wfs), layers, len(layers), dms, len(dms),
+                       ctypes.c_double(wl["params"].get("alpha_eta", 0.0)),
+                       *[q[k].ctypes.data_as(IP if k.startswith("qi") else DP) for k in ("qi0y", "qi0x", "qfy", "qfx")],
+                       el.ctypes.data_as(DP))
+    assert rc == 0
+    return wl, geo, t, q, el.reshape(-1, 10)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_closed_loop_dm_stencils(H, name):
+    """The DM shapes each sensor sees (reading R27): bilinear hats, zero off the lattice."""
+    wl, geo, t, q, _ = extra(H, name)
+    for g, W in enumerate(geo.wfs):
+        for m, dm in enumerate(geo.dms):
+            base = (g * t["MAXM"] + m) * t["TAB"]
+            for ax, Qm in (("y", W["Qy"][m]), ("x", W["Qx"][m])):
+                i0 = q["qi0" + ax][base:base + W["N"] + 1]
+                f = q["qf" + ax][base:base + W["N"] + 1]
+                Q = np.zeros_like(Qm)
+                for a in range(W["N"] + 1):
+                    for col, wgt in ((i0[a], 1.0 - f[a]), (i0[a] + 1, f[a])):
+                        if 0 <= col < dm["n_act"]:
+                            Q[a, col] += wgt
+                assert np.abs(Q - Qm).max() <= 1e-13, (g, m, ax)
+
+
+@pytest.mark.parametrize("name", ["tiny_mcao_elongated", "paper_mcao", "tiny_mcao"])
+def test_spot_elongation_constants(H, name):
+    """Eq. 3 (reading R28): beta and gamma of every subaperture rebuilt from the per-sensor
+    constants the kernels use, and the sums K of gamma beta beta^T over the active ones."""
+    wl, geo, t, q, el = extra(H, name)
+    for g, W in enumerate(geo.wfs):
+        if W["el"] is None:
+            assert el[g, 0] == 0
+            continue
+        on, k, c, lx, ly, x0, d = el[g, :7]
+        assert on == 1
+        N = W["N"]
+        mid = x0 + np.arange(N) * d
+        b1 = k * (mid[None, :] - lx) * np.ones((N, 1))
+        b2 = k * (mid[:, None] - ly) * np.ones((1, N))
+        gam = c / (1.0 + c * (b1 ** 2 + b2 ** 2))
+        ref = W["el"]
+        for got, want in ((b1, ref["b1"]), (b2, ref["b2"]), (gam, ref["gamma"])):
+            assert np.abs(got - want).max() <= 1e-13 * max(np.abs(want).max(), 1e-300)
+        m = W["mask"]
+        K = [np.sum((ref["gamma"] * a * b)[m]) for a, b in ((ref["b1"], ref["b1"]), (ref["b1"], ref["b2"]),
+                                                            (ref["b2"], ref["b2"]))]
+        # K12 cancels to rounding on a symmetric geometry: compare against the largest K
+        assert np.abs(el[g, 7:] - K).max() <= 1e-12 * np.abs(K).max()
