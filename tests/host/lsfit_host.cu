@@ -127,3 +127,133 @@ extern "C" int lsfit_host_apply(const fewha_telescope* tel, const fewha_wfs* wfs
     adjoint(c, u_dms, a, out);
     return 0;
 }
+
+namespace {
+
+// The CG of fewha_fit_ls step by step (k_lsf_cg's arithmetic: vectors and operators in T,
+// inner products and scalars in double), with the operators evaluated as above.
+template <class T>
+int solve(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, const fewha_layer* layers, int n_layers,
+          const fewha_dm* dms, int n_dms, const fewha_lsfit* cfg, const double* phi64, double* a64, double tol,
+          int max_iters, int* iters, double* rel) {
+    Ctx c;
+    int rc = setup(c, tel, wfs, n_wfs, layers, n_layers, dms, n_dms, cfg);
+    if (rc) return rc;
+    const LsDesc<double>& d64 = c.d;
+    LsDesc<T> d{};
+    d.n_dirs = d64.n_dirs;
+    d.nf1 = d64.nf1;
+    d.n_pup = d64.n_pup;
+    d.n_layers = d64.n_layers;
+    d.n_dms = d64.n_dms;
+    d.n_a = d64.n_a;
+    d.n_slices = d64.n_slices;
+    for (int l = 0; l < MAXL; ++l) {
+        d.lay_n[l] = d64.lay_n[l];
+        d.lay_off[l] = d64.lay_off[l];
+    }
+    for (int m = 0; m < MAXM; ++m) {
+        d.dm_n[m] = d64.dm_n[m];
+        d.dm_off[m] = d64.dm_off[m];
+    }
+    for (int k = 0; k < LSF_MAXK; ++k) d.w[k] = static_cast<T>(d64.w[k]);
+    d.eps = static_cast<T>(d64.eps);
+    d.mask = d64.mask;
+    d.ly0 = d64.ly0;
+    d.lx0 = d64.lx0;
+    d.my0 = d64.my0;
+    d.mx0 = d64.mx0;
+    d.ylo = d64.ylo;
+    d.yhi = d64.yhi;
+    d.xlo = d64.xlo;
+    d.xhi = d64.xhi;
+    const std::vector<T> lfy(c.L.lfy.begin(), c.L.lfy.end()), lfx(c.L.lfx.begin(), c.L.lfx.end()),
+        mfy(c.L.mfy.begin(), c.L.mfy.end()), mfx(c.L.mfx.begin(), c.L.mfx.end());
+    d.lfy = lfy.data();
+    d.lfx = lfx.data();
+    d.mfy = mfy.data();
+    d.mfx = mfx.data();
+    const int n = d.n_a, npix = d.nf1 * d.nf1, S = d.n_slices, chunk = (npix + S - 1) / S;
+    std::vector<T> phi(phi64, phi64 + c.S.n_c), a(n), v(static_cast<size_t>(d.n_dirs) * npix), r(n), p(n), q(n);
+    std::vector<double> msum(static_cast<size_t>(d.n_dirs) * S);
+    auto sample = [&](const T* src, bool layer) {
+        for (int k = 0; k < d.n_dirs; ++k)
+            for (int sl = 0; sl < S; ++sl) {
+                double acc = 0.0;
+                for (int g = sl * chunk; g < std::min(npix, (sl + 1) * chunk); ++g) {
+                    T val = T(0);
+                    if (d.mask[g]) {
+                        const int i = g / d.nf1;
+                        val = layer ? lsf_sample<T, true>(d, src, k, i, g - i * d.nf1)
+                                    : lsf_sample<T, false>(d, src, k, i, g - i * d.nf1);
+                        acc += static_cast<double>(val);
+                    }
+                    v[static_cast<size_t>(k) * npix + g] = val;
+                }
+                msum[k * S + sl] = acc;
+            }
+    };
+    auto adjoint = [&](const T* x, T* out) {
+        T mean[LSF_MAXK];
+        for (int k = 0; k < d.n_dirs; ++k) {
+            double t = 0.0;
+            for (int sl = 0; sl < S; ++sl) t += msum[k * S + sl];
+            mean[k] = static_cast<T>(t / d.n_pup);
+        }
+        for (int i = 0; i < n; ++i) {
+            int m = 0;
+            while (m + 1 < d.n_dms && i >= d.dm_off[m + 1]) ++m;
+            const int na = d.dm_n[m], loc = i - d.dm_off[m], pp = loc / na;
+            T val = lsf_adjoint<T>(d, v.data(), mean, m, pp, loc - pp * na);
+            if (x) val += d.eps * x[i];
+            out[i] = val;
+        }
+    };
+    sample(phi.data(), true);
+    adjoint(nullptr, q.data());
+    double rr = 0.0;
+    for (int i = 0; i < n; ++i) {
+        a[i] = T(0);
+        r[i] = p[i] = q[i];
+        rr += static_cast<double>(q[i]) * static_cast<double>(q[i]);
+    }
+    const double rr0 = rr;
+    int it = 0;
+    bool stop = rr == 0.0 || max_iters <= 0;
+    while (!stop) {
+        sample(p.data(), false);
+        adjoint(p.data(), q.data());
+        double pq = 0.0;
+        for (int i = 0; i < n; ++i) pq += static_cast<double>(p[i]) * static_cast<double>(q[i]);
+        if (!(pq > 0.0)) break;
+        const T al = static_cast<T>(rr / pq);
+        double rn = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const T ri = r[i] - al * q[i];
+            a[i] += al * p[i];
+            r[i] = ri;
+            rn += static_cast<double>(ri) * static_cast<double>(ri);
+        }
+        const T beta = static_cast<T>(rn / rr);
+        for (int i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rr = rn;
+        ++it;
+        if (!(rn > tol * tol * rr0) || it >= max_iters) stop = true;
+    }
+    for (int i = 0; i < n; ++i) a64[i] = static_cast<double>(a[i]);
+    *iters = it;
+    *rel = rr0 > 0.0 ? std::sqrt(rr / rr0) : 0.0;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int lsfit_host_solve(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs,
+                                const fewha_layer* layers, int n_layers, const fewha_dm* dms, int n_dms,
+                                const fewha_lsfit* cfg, int precision, const double* phi, double* a, double tol,
+                                int max_iters, int* iters, double* rel) {
+    return precision == 32 ? solve<float>(tel, wfs, n_wfs, layers, n_layers, dms, n_dms, cfg, phi, a, tol,
+                                          max_iters, iters, rel)
+                           : solve<double>(tel, wfs, n_wfs, layers, n_layers, dms, n_dms, cfg, phi, a, tol,
+                                           max_iters, iters, rel);
+}

@@ -88,3 +88,33 @@ def test_a_direction_leaving_a_layer_grid_is_a_geometry_error(H):
     assert rc == -2
     with pytest.raises(O.GeometryError):
         O.fitting_geometry(geo, [(300 * ARC, 0.0)], 8)
+
+
+@pytest.mark.parametrize("name,dirs,w,n_fit,eps", [
+    ("tiny_mcao", DIRS5, [1.0, 0.5, 0.5, 0.5, 0.5], 8, 1e-2),
+    ("paper_mcao", [(x * ARC, y * ARC) for y in (-25, 0, 25) for x in (-25, 0, 25)], [1.0] * 9, 74, 1e-2),
+])
+@pytest.mark.parametrize("prec,tol,bound", [(64, 1e-12, 1e-9), (32, 1e-7, 1e-4)])
+def test_cg_arithmetic_reaches_the_oracle(H, name, dirs, w, n_fit, eps, prec, tol, bound):
+    """The CG of the fit with the kernels' arithmetic (operators and vectors in the handle's
+    type, inner products and scalars in double), run on the host: in double it meets the
+    oracle's CG to 1e-9, in float to the FP32 frame bound 1e-4 (the accuracy the GPU tests
+    hold the device to)."""
+    from paper_2202_11945_gb300 import fewha
+    wl = synth.workload_by_name(name)
+    geo = O.Geometry(wl)
+    c = np.random.default_rng(11).standard_normal(geo.n_c)
+    phis = O.W_inv(geo, c)
+    ref = O.ls_fit(geo, phis, O.fitting_geometry(geo, dirs, n_fit), w, eps)
+    tel, wfs, layers, dms, _ = fewha.structs_from_workload(wl, prec)
+    D = ctypes.POINTER(ctypes.c_double)
+    keep = [np.ascontiguousarray(x, float) for x in ([d[0] for d in dirs], [d[1] for d in dirs], w)]
+    cfg = fewha.LsFit(len(dirs), *[x.ctypes.data_as(D) for x in keep], n_fit, eps)
+    phi = np.ascontiguousarray(np.concatenate([p.ravel() for p in phis]))
+    a = np.zeros(geo.n_a)
+    it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+    rc = H.lsfit_host_solve(ctypes.byref(tel), wfs, len(wfs), layers, len(layers), dms, len(dms), ctypes.byref(cfg),
+                            prec, phi.ctypes.data_as(D), a.ctypes.data_as(D), ctypes.c_double(tol), 5000,
+                            ctypes.byref(it), ctypes.byref(rel))
+    assert rc == 0 and 0 < it.value < 5000 and rel.value <= tol
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= bound
