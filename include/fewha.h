@@ -14,7 +14,8 @@
  * Options: the augmented PCG of Sec. 3.4 (FEWHA_FLAG_AUGMENTED), the LGS spot-elongation
  * noise model of Eq. 3 (fewha_params.alpha_eta); batches of uneven instances; gradients
  * of the converged map (fewha_backward) and of the fixed-iteration frame
- * (fewha_frame_vjp).
+ * (fewha_frame_vjp); least-squares DM fitting over fitting directions in place of the
+ * projection F (fewha_fit_ls, Sec. 4.1).
  *
  * Conventions shared by every entry point
  *   - All functions return FEWHA_OK (0) or a negative FEWHA_ERR_* code; the text of
