@@ -1170,60 +1170,6 @@ int set_smem_limits(fewha_handle* H) {
 
 // One periodic db3 step of the host (the same rule as the kernels' dwt_run): analysis of
 // the m values x[0], x[st], ... into [a | d], or synthesis of [a | d] back.
-void db3_step_host(double* x, int m, int st, const double* h, const double* g, bool inv) {
-    double y[8];
-    const int hm = m / 2;
-    for (int k = 0; k < hm; ++k) {
-        if (!inv) {
-            double a = 0.0, d = 0.0;
-            for (int t = 0; t < 6; ++t) {
-                a += h[t] * x[((2 * k + t) % m) * st];
-                d += g[t] * x[((2 * k + t) % m) * st];
-            }
-            y[k] = a;
-            y[hm + k] = d;
-        } else {
-            double e = 0.0, o = 0.0;
-            for (int s2 = 0; s2 < 3; ++s2) {
-                const int i = ((k - s2) % hm + hm) % hm;
-                e += h[2 * s2] * x[i * st] + g[2 * s2] * x[(hm + i) * st];
-                o += h[2 * s2 + 1] * x[i * st] + g[2 * s2 + 1] * x[(hm + i) * st];
-            }
-            y[2 * k] = e;
-            y[2 * k + 1] = o;
-        }
-    }
-    for (int k = 0; k < m; ++k) x[k * st] = y[k];
-}
-
-// The last three levels of a full decomposition (an 8 x 8 LL block down to 1 x 1) as one
-// matrix A, entry (k, o) at k * TAIL_LD + o (input k = 8 i + j to output o), from unit
-// inputs through the level steps (rows, then columns, for sides 8, 4, 2).  The synthesis
-// of the same steps is checked to be A^T, which the inverse kernel applies; empty if not.
-std::vector<double> tail_operator(const double* h, const double* g) {
-    std::vector<double> A(TAIL_N, 0.0);
-    for (int k = 0; k < 64; ++k) {
-        double X[64] = {};
-        X[k] = 1.0;
-        for (int m = 8; m >= 2; m /= 2) {
-            for (int i = 0; i < m; ++i) db3_step_host(X + 8 * i, m, 1, h, g, false);   // rows
-            for (int j = 0; j < m; ++j) db3_step_host(X + j, m, 8, h, g, false);       // columns
-        }
-        for (int o = 0; o < 64; ++o) A[k * TAIL_LD + o] = X[o];
-    }
-    for (int o = 0; o < 64; ++o) {
-        double Y[64] = {};
-        Y[o] = 1.0;
-        for (int m = 2; m <= 8; m *= 2) {
-            for (int j = 0; j < m; ++j) db3_step_host(Y + j, m, 8, h, g, true);        // columns
-            for (int i = 0; i < m; ++i) db3_step_host(Y + 8 * i, m, 1, h, g, true);    // rows
-        }
-        for (int k = 0; k < 64; ++k)
-            if (std::fabs(Y[k] - A[k * TAIL_LD + o]) > 1e-12) return {};
-    }
-    return A;
-}
-
 // Whether some layer's coarse levels end with the three tail levels (Desc::tailop).
 bool tail_used(const HostSetup& s) {
     for (const auto& L : s.L)
@@ -1276,7 +1222,7 @@ int cluster_layouts(fewha_handle* H) {
     v.total = v.stage2 + 2 * (MAXN / 2) * (MAXN / 2);
     // the tail operator of the coarse levels (the forward kernel's region is placed after
     // its staged band sums, space permitting)
-    std::vector<double> tail = tail_used(s) ? tail_operator(s.taps_h, s.taps_g) : std::vector<double>();
+    std::vector<double> tail = tail_used(s) ? tail_operator(s.taps_h, s.taps_g, TAIL_LD) : std::vector<double>();
     if (!tail.empty()) {
         v.tail = v.total;
         v.total += round4(TAIL_N);

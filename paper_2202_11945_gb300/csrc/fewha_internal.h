@@ -168,6 +168,13 @@ void set_elongation(HostSetup& s, double alpha_eta);
 // pupil node along a direction samples a layer outside its grid.
 int build_lsfit(const HostSetup& s, double obs, const fewha_dm* dms, const fewha_lsfit& cfg,
                 LsfitHost& out, std::string& err);
+// One periodic db3 level step on m values of stride st, analysis or synthesis (inv).
+void db3_step_host(double* x, int m, int st, const double* h, const double* g, bool inv);
+// The last three levels of a full decomposition (an 8 x 8 LL block down to 1 x 1) as one
+// 64 x 64 analysis matrix A, entry (k, o) at k * ld + o (input k = 8 i + j to output o),
+// from unit inputs through the level steps; empty unless the synthesis of the same steps is
+// A^T (which the inverse kernels apply).
+std::vector<double> tail_operator(const double* h, const double* g, int ld);
 // Prior D (Sec. 3.1), one value per coefficient.
 void prior_diag(const HostSetup& s, const std::vector<double>& weights, double r0, double L0,
                 std::vector<double>& D);

@@ -435,6 +435,59 @@ int build_lsfit(const HostSetup& s, double obs, const fewha_dm* dms, const fewha
     return FEWHA_OK;
 }
 
+void db3_step_host(double* x, int m, int st, const double* h, const double* g, bool inv) {
+    double y[8];
+    const int hm = m / 2;
+    for (int k = 0; k < hm; ++k) {
+        if (!inv) {
+            double a = 0.0, d = 0.0;
+            for (int t = 0; t < 6; ++t) {
+                a += h[t] * x[((2 * k + t) % m) * st];
+                d += g[t] * x[((2 * k + t) % m) * st];
+            }
+            y[k] = a;
+            y[hm + k] = d;
+        } else {
+            double e = 0.0, o = 0.0;
+            for (int s2 = 0; s2 < 3; ++s2) {
+                const int i = ((k - s2) % hm + hm) % hm;
+                e += h[2 * s2] * x[i * st] + g[2 * s2] * x[(hm + i) * st];
+                o += h[2 * s2 + 1] * x[i * st] + g[2 * s2 + 1] * x[(hm + i) * st];
+            }
+            y[2 * k] = e;
+            y[2 * k + 1] = o;
+        }
+    }
+    for (int k = 0; k < m; ++k) x[k * st] = y[k];
+}
+
+// The tail matrix (rows, then columns, for block sides 8, 4, 2), entry (k, o) at k * ld + o.
+// The synthesis of the same steps is checked to be A^T, which the inverse kernel applies;
+// empty if not.
+std::vector<double> tail_operator(const double* h, const double* g, int ld) {
+    std::vector<double> A(static_cast<size_t>(64) * ld, 0.0);
+    for (int k = 0; k < 64; ++k) {
+        double X[64] = {};
+        X[k] = 1.0;
+        for (int m = 8; m >= 2; m /= 2) {
+            for (int i = 0; i < m; ++i) db3_step_host(X + 8 * i, m, 1, h, g, false);   // rows
+            for (int j = 0; j < m; ++j) db3_step_host(X + j, m, 8, h, g, false);       // columns
+        }
+        for (int o = 0; o < 64; ++o) A[k * ld + o] = X[o];
+    }
+    for (int o = 0; o < 64; ++o) {
+        double Y[64] = {};
+        Y[o] = 1.0;
+        for (int m = 2; m <= 8; m *= 2) {
+            for (int j = 0; j < m; ++j) db3_step_host(Y + j, m, 8, h, g, true);        // columns
+            for (int i = 0; i < m; ++i) db3_step_host(Y + 8 * i, m, 1, h, g, true);    // rows
+        }
+        for (int k = 0; k < 64; ++k)
+            if (std::fabs(Y[k] - A[k * ld + o]) > 1e-12) return {};
+    }
+    return A;
+}
+
 // D (Sec. 3.1): a diagonal stand-in for C_phi^-1 on the wavelet coefficients.  For a
 // level band (detail level j: FFT index box [-n/2^j, n/2^j)^2 minus [-n/2^(j+1),
 // n/2^(j+1))^2; the coarsest approximation: [-n/2^(L+1), n/2^(L+1))^2) the

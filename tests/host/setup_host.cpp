@@ -102,3 +102,14 @@ extern "C" int setup_extra(const fewha_telescope* tel, const fewha_wfs* wfs, int
     }
     return 0;
 }
+
+// The 8 x 8 tail matrix of the wavelet kernels (row stride 64 here); 0 if its synthesis
+// check failed.
+extern "C" int setup_tail(double* A) {
+    double h[6], g[6];
+    db3_taps(h, g);
+    const std::vector<double> t = tail_operator(h, g, 64);
+    if (t.empty()) return -1;
+    put(A, t);
+    return 0;
+}

@@ -215,3 +215,18 @@ def test_spot_elongation_constants(H, name):
                                                             (ref["b2"], ref["b2"]))]
         # K12 cancels to rounding on a symmetric geometry: compare against the largest K
         assert np.abs(el[g, 7:] - K).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_tail_matrix_is_the_oracles_three_level_transform(H):
+    """The wavelet kernels apply the last three levels of a full decomposition (an 8 x 8 LL
+    block down to 1 x 1) as one host-built 64 x 64 matrix: row k must be the oracle's
+    three-level 2-D transform of the unit input k (Mallat layout), and its transpose the
+    synthesis."""
+    A = np.zeros(64 * 64)
+    assert H.setup_tail(A.ctypes.data_as(DP)) == 0
+    A = A.reshape(64, 64)
+    for k in range(64):
+        e = np.zeros(64)
+        e[k] = 1.0
+        assert np.abs(A[k] - O.dwt2(e.reshape(8, 8), 3).ravel()).max() <= 1e-14, k
+        assert np.abs(A[:, k] - O.idwt2(e.reshape(8, 8), 3).ravel()).max() <= 1e-14, k
