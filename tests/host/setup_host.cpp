@@ -113,3 +113,19 @@ extern "C" int setup_tail(double* A) {
     put(A, t);
     return 0;
 }
+
+// The 1-D wavelet basis tables of the exact Jacobi diagonal: basis (all functions
+// concatenated) and basis_off (MAXL * (MAXLEV + 1) * 2 offsets, basis_index(l, j, kind)).
+extern "C" int setup_basis(const fewha_telescope* tel, const fewha_wfs* wfs, int n_wfs, const fewha_layer* layers,
+                           int n_layers, const fewha_dm* dms, int n_dms, double* basis, long n_basis,
+                           int* basis_off, int* maxlev) {
+    HostSetup s;
+    std::string err;
+    const int rc = build_setup(*tel, wfs, n_wfs, layers, n_layers, dms, n_dms, s, err);
+    if (rc) return rc;
+    *maxlev = MAXLEV;
+    if (static_cast<long>(s.basis.size()) != n_basis) return -100;
+    put(basis, s.basis);
+    put(basis_off, s.basis_off);
+    return 0;
+}

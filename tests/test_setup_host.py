@@ -230,3 +230,31 @@ def test_tail_matrix_is_the_oracles_three_level_transform(H):
         e[k] = 1.0
         assert np.abs(A[k] - O.dwt2(e.reshape(8, 8), 3).ravel()).max() <= 1e-14, k
         assert np.abs(A[:, k] - O.idwt2(e.reshape(8, 8), 3).ravel()).max() <= 1e-14, k
+
+
+@pytest.mark.parametrize("name", ["tiny_mcao", "maory"])
+def test_basis_tables_of_the_jacobi_diagonal(H, name):
+    """The exact diagonal of W B W^T (Eq. 7) is built on the GPU from 1-D basis functions of
+    each layer and level: the table holds the synthesis of the unit coefficient at shift 0
+    of the level-j scaling (kind 0) and wavelet (kind 1) bands, i.e. column 0 of the oracle's
+    basis matrices."""
+    from paper_2202_11945_gb300 import fewha
+    wl = synth.workload_by_name(name)
+    geo = O.Geometry(wl)
+    tel, wfs, layers, dms, _ = fewha.structs_from_workload(wl, 64)
+    n_basis = sum(2 * L["levels"] * L["n"] for L in geo.layers)
+    basis = np.zeros(n_basis)
+    MAXL = tables(H, name)[2]["MAXL"]
+    off = np.zeros(MAXL * 9 * 2, np.int32)
+    maxlev = ctypes.c_int(0)
+    assert H.setup_basis(ctypes.byref(tel), wfs, len(wfs), layers, len(layers), dms, len(dms),
+                         basis.ctypes.data_as(DP), ctypes.c_long(n_basis), off.ctypes.data_as(IP),
+                         ctypes.byref(maxlev)) == 0
+    assert maxlev.value + 1 == 9
+    for l, L in enumerate(geo.layers):
+        n = L["n"]
+        for j in range(1, L["levels"] + 1):
+            for kind, name_k in ((0, "a"), (1, "d")):
+                o = off[(l * 9 + j) * 2 + kind]
+                ref = O.basis_1d(n, j, name_k)[:, 0]
+                assert np.abs(basis[o:o + n] - ref).max() <= 1e-14, (l, j, kind)
